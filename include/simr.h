@@ -1,0 +1,187 @@
+/*
+ * simr.h -- C ABI of the GB300 Heston Monte Carlo pricing library (libsimr.so).
+ *
+ * The library implements the data-parallel hot path of the SIMR (STAC-A2
+ * inspired market risk) workload studied in "Evaluating Versal AI Engines for
+ * option price discovery in market risk analysis" (Klaisoongnoen et al.,
+ * FPGA'24): per path and per time step the VariancePathQE stage (Sec. 4), the
+ * LogPricePathQE and AssetPathExponential stages (Sec. 5, Fig. 1), and the
+ * reduction over paths (Sec. 6), over the assets x timesteps x paths loop nest
+ * of Sec. 5.1 (Listing 2) with the per-path state carried between timesteps.
+ * The paper names the stages but prints no formula; the scheme is the
+ * Quadratic-Exponential (QE) discretisation of L. Andersen (J. Comput. Finance
+ * 11(3), 2008) of the Heston (1993) model under the risk-neutral measure with a
+ * constant rate r and no dividends: psi_c = 1.5, gamma1 = gamma2 = 1/2.
+ * The paper's random inputs V and Z (Sec. 3, Table 1: two FP32 data points per
+ * element) are generated in-kernel by Philox4x32-10 (Salmon et al., SC'11):
+ *   key     = (seed mod 2^32, seed >> 32)
+ *   counter = (step / 2, path mod 2^32, path >> 32, option_index)
+ *   words 0,1 drive even steps and words 2,3 odd steps: (U_V, U_X)
+ *   u       = ((word >> 9) + 1/2) * 2^-23, Z = Phi^-1(u).
+ * A result therefore depends only on (seed, option, path, step), never on the
+ * launch configuration, and shards of a path range agree with the whole.
+ * Path arithmetic is FP32 (the paper's SIMR precision, Sec. 3); sums over paths
+ * and the final normalisation are FP64.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (SIMR_OK) or a negative simr_status; simr_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.
+ *  - Arguments are validated on the host before anything is launched; an
+ *    invalid argument returns SIMR_EINVAL and writes nothing.  The one
+ *    exception is a strike array in device memory, which the kernel checks:
+ *    a strike that is not finite and > 0 yields NaN results for that strike
+ *    and sets a device status that simr_sync returns as SIMR_EINVAL.
+ *  - Array arguments are plain pointers to caller-owned memory, either device
+ *    memory of the context's device or host memory (detected per pointer).
+ *    With device pointers the call is asynchronous on `stream` (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream) and the
+ *    caller synchronises.  If any output pointer is host memory the call
+ *    copies results back and synchronises `stream` before returning.
+ *  - The library never frees caller memory.  Its own device scratch belongs to
+ *    the context; calls on one context must not run concurrently on different
+ *    streams (they share that scratch).
+ *  - Model validity: S0, K, T > 0; v0, theta >= 0; kappa > 0; sigma > 0 (the
+ *    log-spot coefficients divide by sigma); rho in [-1, 1]; all finite;
+ *    steps >= 1; paths >= 1.
+ */
+#ifndef SIMR_H
+#define SIMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SIMR_API __attribute__((visibility("default")))
+#else
+#define SIMR_API
+#endif
+
+typedef enum {
+  SIMR_OK = 0,
+  SIMR_EINVAL = -1,      /* invalid argument (nothing launched)                 */
+  SIMR_ENOMEM = -2,      /* device or host allocation failed                    */
+  SIMR_ECUDA = -3,       /* a CUDA runtime call failed (message has the reason) */
+  SIMR_ETIMEOUT = -4,    /* a device-side bounded wait gave up                  */
+  SIMR_EUNSUPPORTED = -5 /* size or feature beyond what this build supports     */
+} simr_status;
+
+/* Opaque context bound to one CUDA device; owns scratch memory. */
+typedef struct simr_ctx simr_ctx;
+
+/* Model and market inputs (the paper's problem statement per asset). */
+typedef struct {
+  double S0;    /* spot                          */
+  double r;     /* continuously compounded rate  */
+  double T;     /* maturity in years             */
+  double v0;    /* initial variance              */
+  double kappa; /* mean-reversion speed          */
+  double theta; /* long-run variance             */
+  double sigma; /* volatility of variance        */
+  double rho;   /* spot/variance correlation     */
+} simr_heston;
+
+/* Greek selection bits for simr_greeks_fd; output columns follow bit order. */
+#define SIMR_G_DELTA (1u << 0)  /* d/dS0, analytic S-bump on the same path   */
+#define SIMR_G_GAMMA (1u << 1)  /* d2/dS0^2, same path                       */
+#define SIMR_G_VEGA (1u << 2)   /* d/dv0, re-simulated                       */
+#define SIMR_G_THETA (1u << 3)  /* -d/dT (calendar theta), re-simulated      */
+#define SIMR_G_RHO (1u << 4)    /* d/dr, exact r-shift of the same path      */
+#define SIMR_G_KAPPA (1u << 5)  /* d/dkappa, re-simulated                    */
+#define SIMR_G_LRVAR (1u << 6)  /* d/dtheta (long-run variance), re-simulated */
+#define SIMR_G_VOLVOL (1u << 7) /* d/dsigma, re-simulated                    */
+#define SIMR_G_CORR (1u << 8)   /* d/drho, re-simulated                      */
+#define SIMR_G_ALL 0x1FFu
+
+/* Create a context on CUDA device `device`.  *out is set on success. */
+SIMR_API int simr_create(simr_ctx** out, int device);
+
+/* Destroy a context (NULL allowed).  Synchronises the device first. */
+SIMR_API void simr_destroy(simr_ctx* ctx);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+SIMR_API const char* simr_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+SIMR_API int simr_version(void);
+
+/*
+ * European price of one asset on a strike grid by Monte Carlo over paths
+ * [0, paths): the stages VariancePathQE, LogPricePathQE, AssetPathExponential
+ * (paper Sec. 4-5) and the reduction over paths (Sec. 6).
+ *   strikes[n_strikes] (FP64)   in   strike grid, each K > 0
+ *   is_put                      in   0 call, 1 put (payoff zero at S_T = K)
+ *   price[n_strikes]            out  e^{-rT} mean_p f_k(S_T)
+ *   stderr_out[n_strikes]       out  e^{-rT} sqrt((mean f^2 - mean(f)^2)/(paths-1)); may be NULL
+ * n_strikes in [1, 1024].  option_index is the fourth Philox counter word (use 0
+ * for a single asset; distinct assets of one book use distinct indices).
+ */
+SIMR_API int simr_price(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes,
+               int is_put, uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index,
+               double* price, double* stderr_out, void* stream);
+
+/*
+ * Bump-and-revalue Greeks with common random numbers: every scenario reuses the
+ * Philox counters of the base paths.  Central differences with bump
+ * h = rel_bump * |value| (rel_bump itself when the value is 0; rho is bumped by
+ * rel_bump in absolute terms); where the down-bump leaves the domain (v0 or theta
+ * below 0, rho outside [-1, 1]) the one-sided difference is used.
+ * Delta and gamma re-value the same path at S0(1 +- h) (x_T does not depend on
+ * S0); rho shifts x_T by the exact r-dependence of the log-spot step (+- h T)
+ * and the discount; vega, theta, kappa, long-run variance, vol-of-vol and
+ * correlation re-simulate every step with the bumped constants.
+ *   greek_mask   in   SIMR_G_* bits, at least one
+ *   price[n_strikes]                out  base price
+ *   greeks[n_strikes * n_greeks]    out  row-major [strike][greek], greeks in bit order
+ * n_strikes in [1, 256].
+ */
+SIMR_API int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes,
+                   int is_put, uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index,
+                   double rel_bump, uint32_t greek_mask, double* price, double* greeks,
+                   void* stream);
+
+/*
+ * Terminal state of paths [path_begin, path_begin + n_paths): x_T = ln(S_T/S0)
+ * and v_T per path, FP32, the state the paper's writeLongstaffSchwartzPath stage
+ * writes out (Sec. 5).  x_T[n_paths], v_T[n_paths] out; v_T may be NULL.
+ */
+SIMR_API int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
+                        uint64_t path_begin, uint64_t n_paths, uint64_t seed,
+                        uint32_t option_index, float* x_T, float* v_T, void* stream);
+
+/*
+ * Raw (undiscounted) per-strike path sums over paths [path_begin, path_begin +
+ * path_count) for a sharded run: sums[k * n_acc + a] with n_acc = 2 + number of
+ * Greeks, a = 0: sum f, 1: sum f^2, then one sum per Greek of the per-path
+ * difference the FD estimator averages.  Combine shards by adding sums, then
+ * call simr_finalize_sums.  FP64 throughout the accumulation.
+ */
+SIMR_API int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes,
+                   int is_put, uint32_t steps, uint64_t path_begin, uint64_t path_count,
+                   uint64_t seed, uint32_t option_index, double rel_bump, uint32_t greek_mask,
+                   double* sums, void* stream);
+
+/*
+ * Normalise combined sums (from simr_path_sums over a total of `paths` paths)
+ * into price[n_strikes], stderr_out[n_strikes] (nullable) and
+ * greeks[n_strikes * n_greeks] (nullable when greek_mask is 0).
+ */
+SIMR_API int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes,
+                       int n_strikes, int is_put, uint32_t steps, uint64_t paths, double rel_bump,
+                       uint32_t greek_mask, const double* sums, double* price, double* stderr_out,
+                       double* greeks, void* stream);
+
+/*
+ * Wait for `stream` and report any asynchronous device error as a status; also
+ * reports (and clears) a device-side argument error such as a device-resident
+ * strike that is not finite and > 0 (SIMR_EINVAL).
+ */
+SIMR_API int simr_sync(simr_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMR_H */

@@ -1,0 +1,21 @@
+"""GB300-native Heston QE Monte Carlo pricing: the SIMR hot path of arXiv:2402.12111.
+
+Public API (torch tensors for device memory and streams; all arithmetic runs in
+libsimr.so's sm_103a kernels behind the C ABI of include/simr.h):
+
+  price(model, strikes, ...)            -> (price, stderr)      simr_price
+  greeks_fd(model, strikes, ...)        -> (price, greeks)      simr_greeks_fd
+  paths_terminal(model, steps, ...)     -> (x_T, v_T)           simr_paths_terminal
+  path_sums / finalize_sums                                     sharded runs
+  sharded.price_greeks(...)             multi-rank path sharding (torch.distributed)
+
+``model`` is a dict (or Heston struct) with S0, r, T, v0, kappa, theta, sigma, rho.
+Tensors on a CUDA device give an asynchronous call on the current stream; CPU
+tensors or sequences give a synchronous call with host buffers.
+"""
+from .api import finalize_sums, greeks_fd, path_sums, paths_terminal, price, sync  # noqa: F401
+from ._simr import (G_ALL, G_CORR, G_DELTA, G_GAMMA, G_KAPPA, G_LRVAR, G_RHO, G_THETA, G_VEGA,  # noqa: F401
+                    G_VOLVOL, GREEK_BITS, Heston, SimrError, greek_mask, load)
+
+__all__ = ["price", "greeks_fd", "paths_terminal", "path_sums", "finalize_sums", "sync", "Heston", "SimrError",
+           "greek_mask", "load", "GREEK_BITS"]

@@ -1,0 +1,124 @@
+"""Tensor-level entry points: one C-ABI call each, no arithmetic of the method here."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _simr as S
+
+
+def _as_f64(x, device=None) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        t = x.to(dtype=torch.float64)
+        if device is not None:
+            t = t.to(device)
+        return t.contiguous()
+    t = torch.as_tensor(np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64))))
+    return t if device is None else t.to(device)
+
+
+def _device_index(t: torch.Tensor, device) -> int:
+    if t.is_cuda:
+        return t.device.index if t.device.index is not None else torch.cuda.current_device()
+    if device is not None:
+        d = torch.device(device)
+        if d.type == "cuda":
+            return d.index if d.index is not None else torch.cuda.current_device()
+    return 0
+
+
+def _stream(t: torch.Tensor, stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    if t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(None)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
+
+
+def price(model, strikes, is_put: bool = False, steps: int = 64, paths: int = 65536, seed: int = 1,
+          option_index: int = 0, stderr: bool = True, device=None, stream=None):
+    """simr_price: (price[n_K], stderr[n_K] or None), FP64, on the strikes' device."""
+    K = _as_f64(strikes)
+    p = torch.empty(K.numel(), dtype=torch.float64, device=K.device)
+    se = torch.empty_like(p) if stderr else None
+    L = S.load()
+    ctx = S.context(_device_index(K, device))
+    S.check(L.simr_price(ctx, ctypes.byref(S.as_heston(model)), _ptr(K), K.numel(), int(bool(is_put)), int(steps),
+                         int(paths), int(seed), int(option_index), _ptr(p), _ptr(se), _stream(K, stream)))
+    return p, se
+
+
+def greeks_fd(model, strikes, is_put: bool = False, steps: int = 64, paths: int = 65536, seed: int = 1,
+              greeks=("delta", "gamma", "vega"), rel_bump: float = 1e-4, option_index: int = 0, device=None,
+              stream=None):
+    """simr_greeks_fd: (price[n_K], greeks[n_K, n_greeks]) with columns in bit order of the mask."""
+    K = _as_f64(strikes)
+    mask = S.greek_mask(greeks)
+    ng = bin(mask & S.G_ALL).count("1")
+    p = torch.empty(K.numel(), dtype=torch.float64, device=K.device)
+    g = torch.empty(K.numel(), max(ng, 1), dtype=torch.float64, device=K.device)
+    L = S.load()
+    ctx = S.context(_device_index(K, device))
+    S.check(L.simr_greeks_fd(ctx, ctypes.byref(S.as_heston(model)), _ptr(K), K.numel(), int(bool(is_put)),
+                             int(steps), int(paths), int(seed), int(option_index), float(rel_bump), int(mask), _ptr(p),
+                             _ptr(g), _stream(K, stream)))
+    return p, g
+
+
+def paths_terminal(model, steps: int, path_begin: int, n_paths: int, seed: int = 1, option_index: int = 0,
+                   device="cuda", with_variance: bool = True, stream=None):
+    """simr_paths_terminal: (x_T, v_T) FP32 per path, x_T = ln(S_T/S0)."""
+    dev = torch.device(device)
+    x = torch.empty(int(n_paths), dtype=torch.float32, device=dev)
+    v = torch.empty_like(x) if with_variance else None
+    L = S.load()
+    ctx = S.context(_device_index(x, device))
+    S.check(L.simr_paths_terminal(ctx, ctypes.byref(S.as_heston(model)), int(steps), int(path_begin), int(n_paths),
+                                  int(seed), int(option_index), _ptr(x), _ptr(v), _stream(x, stream)))
+    return x, v
+
+
+def path_sums(model, strikes, is_put: bool, steps: int, path_begin: int, path_count: int, seed: int = 1,
+              greeks=(), rel_bump: float = 1e-4, option_index: int = 0, device=None, stream=None):
+    """simr_path_sums: raw FP64 sums [n_K, 2 + n_greeks] over a path range (for sharded runs)."""
+    K = _as_f64(strikes)
+    mask = S.greek_mask(greeks)
+    n_acc = 2 + bin(mask & S.G_ALL).count("1")
+    out = torch.empty(K.numel(), n_acc, dtype=torch.float64, device=K.device)
+    L = S.load()
+    ctx = S.context(_device_index(K, device))
+    S.check(L.simr_path_sums(ctx, ctypes.byref(S.as_heston(model)), _ptr(K), K.numel(), int(bool(is_put)),
+                             int(steps), int(path_begin), int(path_count), int(seed), int(option_index),
+                             float(rel_bump), int(mask), _ptr(out), _stream(K, stream)))
+    return out
+
+
+def finalize_sums(model, strikes, is_put: bool, steps: int, paths: int, sums: torch.Tensor, greeks=(),
+                  rel_bump: float = 1e-4, device=None, stream=None):
+    """simr_finalize_sums: (price, stderr, greeks) from combined sums over `paths` paths."""
+    K = _as_f64(strikes, device=sums.device)
+    mask = S.greek_mask(greeks)
+    ng = bin(mask & S.G_ALL).count("1")
+    sums = sums.to(torch.float64).contiguous()
+    p = torch.empty(K.numel(), dtype=torch.float64, device=sums.device)
+    se = torch.empty_like(p)
+    g = torch.empty(K.numel(), max(ng, 1), dtype=torch.float64, device=sums.device) if ng else None
+    L = S.load()
+    ctx = S.context(_device_index(sums, device))
+    S.check(L.simr_finalize_sums(ctx, ctypes.byref(S.as_heston(model)), _ptr(K), K.numel(), int(bool(is_put)),
+                                 int(steps), int(paths), float(rel_bump), int(mask), _ptr(sums), _ptr(p), _ptr(se),
+                                 _ptr(g), _stream(sums, stream)))
+    return p, se, g
+
+
+def sync(device: int = 0, stream=None):
+    """simr_sync on a device's current (or given) stream."""
+    L = S.load()
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    S.check(L.simr_sync(S.context(device), ctypes.c_void_p(st.cuda_stream)))

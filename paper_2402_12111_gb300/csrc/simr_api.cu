@@ -1,0 +1,546 @@
+// simr_api.cu -- the C ABI of include/simr.h: context, validation, per-scenario
+// constants (FP64 on the host, rounded once to FP32), launches and host staging.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "simr.h"
+#include "simr_internal.h"
+
+using namespace simr;
+
+struct simr_ctx {
+  int device = 0;
+  int num_sms = 0;
+  // path-kernel scratch: partial rows + ticket
+  double* partials = nullptr;
+  size_t partial_doubles = 0;
+  unsigned int* ticket = nullptr;  // 256-byte block: ticket word at 0, status word at 64
+  int* status = nullptr;
+  // staging for host-pointer arguments
+  double* dev_strikes = nullptr;
+  size_t strikes_cap = 0;
+  double* dev_out = nullptr;
+  size_t out_cap = 0;
+  float* dev_f32 = nullptr;
+  size_t f32_cap = 0;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SIMR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+int check_model(const simr_heston* m) {
+  if (!m) return fail(SIMR_EINVAL, "model is NULL");
+  const double v[8] = {m->S0, m->r, m->T, m->v0, m->kappa, m->theta, m->sigma, m->rho};
+  for (double x : v)
+    if (!finite(x)) return fail(SIMR_EINVAL, "model has a non-finite value");
+  if (!(m->S0 > 0)) return fail(SIMR_EINVAL, "S0 must be > 0");
+  if (!(m->T > 0)) return fail(SIMR_EINVAL, "T must be > 0");
+  if (!(m->v0 >= 0)) return fail(SIMR_EINVAL, "v0 must be >= 0");
+  if (!(m->theta >= 0)) return fail(SIMR_EINVAL, "theta must be >= 0");
+  if (!(m->kappa > 0)) return fail(SIMR_EINVAL, "kappa must be > 0");
+  if (!(m->sigma > 0)) return fail(SIMR_EINVAL, "sigma must be > 0");
+  if (!(m->rho >= -1.0 && m->rho <= 1.0)) return fail(SIMR_EINVAL, "rho must lie in [-1, 1]");
+  return SIMR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int ensure(T** buf, size_t* cap, size_t n, const char* what) {
+  if (*cap >= n) return SIMR_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc((void**)buf, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SIMR_ENOMEM, "cudaMalloc of %s (%zu bytes) failed: %s", what, n * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  *cap = n;
+  return SIMR_OK;
+}
+
+// FP64 -> FP32 constants of one scenario (formulas in simr_device.cuh).
+ScenConst scen_const(const simr_heston& m, uint32_t steps, double T_base) {
+  const double dt = m.T / (double)steps;
+  const double kdt = m.kappa * dt;
+  const double E = std::exp(-kdt);
+  const double omE = -std::expm1(-kdt);
+  const double s2 = m.sigma * m.sigma;
+  const double rs = m.rho / m.sigma;
+  ScenConst c;
+  c.E = (float)E;
+  c.thE = (float)(m.theta * omE);
+  c.c1 = (float)(s2 * E * omE / m.kappa);
+  c.c2 = (float)(m.theta * s2 * omE * omE / (2.0 * m.kappa));
+  c.C0 = (float)(m.r * dt);
+  c.Cv = (float)(-0.25 * dt);
+  c.Cd = (float)(rs * (omE - 0.5 * kdt * (1.0 + E)));
+  c.Cdl = (float)(rs * (1.0 + 0.5 * kdt));
+  c.sK3 = (float)std::sqrt(0.5 * dt * (1.0 - m.rho * m.rho));
+  c.theta = (float)m.theta;
+  c.ratio = (float)std::exp(-m.r * (m.T - T_base));
+  c.v0 = (float)m.v0;
+  return c;
+}
+
+void philox_round_keys(uint64_t seed, uint32_t rk[10][2]) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int i = 0; i < 10; ++i) {
+    rk[i][0] = k0;
+    rk[i][1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+int popcount9(uint32_t m) {
+  int n = 0;
+  for (int b = 0; b < kMaxGreeks; ++b) n += (m >> b) & 1u;
+  return n;
+}
+
+// Build the launch descriptor: base scenario, re-simulated scenarios per Greek,
+// analytic bumps and the FP64 normalisation constants.
+int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps, uint64_t path_begin,
+                 uint64_t path_count, uint64_t paths_total, uint64_t seed, uint32_t option_index,
+                 double rel_bump, uint32_t mask, PathLaunch* L) {
+  std::memset(L, 0, sizeof(*L));
+  philox_round_keys(seed, L->rk);
+  L->path_begin = path_begin;
+  L->path_count = path_count;
+  L->steps = steps;
+  L->option_index = option_index;
+  L->n_strikes = n_strikes;
+  L->nk_pad = n_strikes == 1 ? 1 : ((n_strikes + 31) / 32) * 32;
+  L->n_acc = 2 + popcount9(mask);
+  L->is_put = is_put ? 1 : 0;
+  L->greek_mask = mask;
+  L->S0 = (float)m->S0;
+  L->h_s = (float)rel_bump;
+  L->disc = std::exp(-m->r * m->T);
+  L->paths_total = (double)paths_total;
+  L->sc[0] = scen_const(*m, steps, m->T);
+  int ns = 1, r = 0, g = 0;
+  for (int bit = 0; bit < kMaxGreeks; ++bit) {
+    if (!((mask >> bit) & 1u)) continue;
+    const uint32_t b = 1u << bit;
+    double denom = 1.0;
+    if (b == SIMR_G_DELTA) {
+      denom = 2.0 * rel_bump * m->S0;
+    } else if (b == SIMR_G_GAMMA) {
+      denom = (rel_bump * m->S0) * (rel_bump * m->S0);
+    } else if (b == SIMR_G_RHO) {
+      double h = rel_bump * std::fabs(m->r);
+      if (h == 0.0) h = rel_bump;
+      L->rho_em = (float)std::exp(-h * m->T);
+      L->rho_ep = (float)std::exp(h * m->T);
+      denom = 2.0 * h;
+    } else {
+      // re-simulated: field selection
+      simr_heston up = *m, dn = *m;
+      double* fu;
+      double* fd;
+      double val;
+      bool absolute = false, nonneg = false, unit = false;
+      double sign = 1.0;
+      if (b == SIMR_G_VEGA) {
+        fu = &up.v0; fd = &dn.v0; val = m->v0; nonneg = true;
+      } else if (b == SIMR_G_THETA) {
+        fu = &up.T; fd = &dn.T; val = m->T; sign = -1.0;
+      } else if (b == SIMR_G_KAPPA) {
+        fu = &up.kappa; fd = &dn.kappa; val = m->kappa;
+      } else if (b == SIMR_G_LRVAR) {
+        fu = &up.theta; fd = &dn.theta; val = m->theta; nonneg = true;
+      } else if (b == SIMR_G_VOLVOL) {
+        fu = &up.sigma; fd = &dn.sigma; val = m->sigma;
+      } else {
+        fu = &up.rho; fd = &dn.rho; val = m->rho; absolute = true; unit = true;
+      }
+      double h = absolute ? rel_bump : rel_bump * std::fabs(val);
+      if (h == 0.0) h = rel_bump;
+      *fu = val + h;
+      *fd = val - h;
+      bool up_ok = true, dn_ok = true;
+      if (nonneg && *fd < 0.0) dn_ok = false;
+      if (unit && *fd < -1.0) dn_ok = false;
+      if (unit && *fu > 1.0) up_ok = false;
+      int iu = 0, id = 0;
+      double hu = 0.0, hd = 0.0;
+      if (up_ok) {
+        iu = ns;
+        L->sc[ns++] = scen_const(up, steps, m->T);
+        hu = h;
+      }
+      if (dn_ok) {
+        id = ns;
+        L->sc[ns++] = scen_const(dn, steps, m->T);
+        hd = h;
+      }
+      L->resim_up[r] = iu;
+      L->resim_dn[r] = id;
+      ++r;
+      denom = sign * (hu + hd);
+      if (!(denom != 0.0)) return fail(SIMR_EINVAL, "degenerate bump for Greek bit %d", bit);
+    }
+    L->denom[g++] = denom;
+  }
+  L->n_scen = ns;
+  return SIMR_OK;
+}
+
+int check_common(simr_ctx* ctx, const simr_heston* m, const double* strikes, int n_strikes, int max_strikes,
+                 uint32_t steps, uint64_t paths) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  int rc = check_model(m);
+  if (rc) return rc;
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (paths < 1) return fail(SIMR_EINVAL, "paths must be >= 1");
+  if (!strikes) return fail(SIMR_EINVAL, "strikes is NULL");
+  if (n_strikes < 1 || n_strikes > max_strikes)
+    return fail(SIMR_EINVAL, "n_strikes must lie in [1, %d]", max_strikes);
+  return SIMR_OK;
+}
+
+int check_strikes_host(const double* strikes, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!(strikes[i] > 0) || !finite(strikes[i])) return fail(SIMR_EINVAL, "strike %d must be finite and > 0", i);
+  return SIMR_OK;
+}
+
+// Return a device pointer to the strikes.  Host strikes are validated here and
+// copied to staging; device strikes are validated by the kernel, which sets bit 0
+// of the context's status word (reported by simr_sync) and yields NaN results.
+int stage_strikes(simr_ctx* ctx, const double* strikes, int n, cudaStream_t st, const double** dev) {
+  if (is_device_ptr(strikes)) {
+    *dev = strikes;
+    return SIMR_OK;
+  }
+  int rc = check_strikes_host(strikes, n);
+  if (rc) return rc;
+  rc = ensure(&ctx->dev_strikes, &ctx->strikes_cap, (size_t)n, "strike staging");
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(ctx->dev_strikes, strikes, n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copying strikes");
+  *dev = ctx->dev_strikes;
+  return SIMR_OK;
+}
+
+// Read and clear the device status word (the stream must be idle).
+int take_status(simr_ctx* ctx, cudaStream_t st) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+  if (h & 1) return fail(SIMR_EINVAL, "a device-resident strike was not finite and > 0 (results are NaN)");
+  return SIMR_OK;
+}
+
+struct OutStage {
+  double* user[3] = {nullptr, nullptr, nullptr};
+  double* dev[3] = {nullptr, nullptr, nullptr};
+  size_t n[3] = {0, 0, 0};
+  bool any_host = false;
+};
+
+// Map each output (price, stderr, greeks/sums) to a device pointer; host outputs
+// are placed in the context's staging buffer and copied back after the launch.
+int stage_outputs(simr_ctx* ctx, OutStage* o) {
+  size_t total = 0;
+  for (int i = 0; i < 3; ++i)
+    if (o->user[i] && !is_device_ptr(o->user[i])) total += o->n[i], o->any_host = true;
+  if (o->any_host) {
+    int rc = ensure(&ctx->dev_out, &ctx->out_cap, total, "output staging");
+    if (rc) return rc;
+  }
+  size_t off = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (!o->user[i]) continue;
+    if (is_device_ptr(o->user[i])) {
+      o->dev[i] = o->user[i];
+    } else {
+      o->dev[i] = ctx->dev_out + off;
+      off += o->n[i];
+    }
+  }
+  return SIMR_OK;
+}
+
+int finish_outputs(simr_ctx* ctx, const OutStage& o, cudaStream_t st) {
+  if (!o.any_host) return SIMR_OK;
+  for (int i = 0; i < 3; ++i) {
+    if (o.user[i] && o.dev[i] != o.user[i]) {
+      cudaError_t e = cudaMemcpyAsync(o.user[i], o.dev[i], o.n[i] * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copying results to the host");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
+  return take_status(ctx, st);
+}
+
+int with_device(simr_ctx* ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return SIMR_OK;
+}
+
+int ensure_scratch(simr_ctx* ctx, const PathLaunch& L) {
+  return ensure(&ctx->partials, &ctx->partial_doubles, paths_scratch_doubles(L, ctx->num_sms), "reduction scratch");
+}
+
+int run_paths(simr_ctx* ctx, const PathLaunch& L, const double* dev_strikes, OutStage& o, cudaStream_t st) {
+  int rc = ensure_scratch(ctx, L);
+  if (rc) return rc;
+  PathOutputs out{};
+  out.status = ctx->status;
+  if (L.raw_sums) {
+    out.sums = o.dev[0];
+  } else {
+    out.price = o.dev[0];
+    out.stderr_ = o.dev[1];
+    out.greeks = o.dev[2];
+  }
+  Scratch s{ctx->partials, ctx->ticket, ctx->partial_doubles};
+  int grid = 0;
+  cudaError_t e = launch_paths(L, dev_strikes, out, s, ctx->num_sms, st, &grid);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the path kernel");
+  return finish_outputs(ctx, o, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int simr_version(void) { return 100; }
+
+const char* simr_last_error(void) { return g_err; }
+
+int simr_create(simr_ctx** out, int device) {
+  if (!out) return fail(SIMR_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(SIMR_EINVAL, "device %d out of range (%d devices)", device, n);
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  simr_ctx* c = new (std::nothrow) simr_ctx();
+  if (!c) return fail(SIMR_ENOMEM, "host allocation failed");
+  c->device = device;
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "querying the SM count");
+  }
+  e = cudaMalloc((void**)&c->ticket, 256);
+  if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, 256);
+  c->status = reinterpret_cast<int*>(reinterpret_cast<char*>(c->ticket) + 64);
+  if (e != cudaSuccess) {
+    cudaFree(c->ticket);
+    delete c;
+    return cuda_fail(e, "allocating the ticket word");
+  }
+  *out = c;
+  return SIMR_OK;
+}
+
+void simr_destroy(simr_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->partials);
+  cudaFree(ctx->ticket);
+  cudaFree(ctx->dev_strikes);
+  cudaFree(ctx->dev_out);
+  cudaFree(ctx->dev_f32);
+  delete ctx;
+}
+
+int simr_sync(simr_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "asynchronous error");
+  return take_status(ctx, (cudaStream_t)stream);
+}
+
+int simr_price(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+               uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, double* price,
+               double* stderr_out, void* stream) {
+  int rc = check_common(ctx, model, strikes, n_strikes, 1024, steps, paths);
+  if (rc) return rc;
+  if (!price) return fail(SIMR_EINVAL, "price is NULL");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, 1e-4, 0u, &L)))
+    return rc;
+  const double* ks = nullptr;
+  if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_strikes;
+  o.user[1] = stderr_out;
+  o.n[1] = n_strikes;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  return run_paths(ctx, L, ks, o, st);
+}
+
+int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+                   uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, double rel_bump,
+                   uint32_t greek_mask, double* price, double* greeks, void* stream) {
+  int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
+  if (rc) return rc;
+  if (!(rel_bump > 0.0 && rel_bump < 0.5)) return fail(SIMR_EINVAL, "rel_bump must lie in (0, 0.5)");
+  if (greek_mask == 0 || (greek_mask & ~SIMR_G_ALL)) return fail(SIMR_EINVAL, "greek_mask must select Greeks");
+  if (!price || !greeks) return fail(SIMR_EINVAL, "price and greeks must be non-NULL");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, rel_bump,
+                         greek_mask, &L)))
+    return rc;
+  const double* ks = nullptr;
+  if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_strikes;
+  o.user[2] = greeks;
+  o.n[2] = (size_t)n_strikes * popcount9(greek_mask);
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  return run_paths(ctx, L, ks, o, st);
+}
+
+int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+                   uint32_t steps, uint64_t path_begin, uint64_t path_count, uint64_t seed, uint32_t option_index,
+                   double rel_bump, uint32_t greek_mask, double* sums, void* stream) {
+  int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, path_count);
+  if (rc) return rc;
+  if (greek_mask & ~SIMR_G_ALL) return fail(SIMR_EINVAL, "unknown Greek bits");
+  if (greek_mask && !(rel_bump > 0.0 && rel_bump < 0.5)) return fail(SIMR_EINVAL, "rel_bump must lie in (0, 0.5)");
+  if (!sums) return fail(SIMR_EINVAL, "sums is NULL");
+  if (path_begin + path_count < path_begin) return fail(SIMR_EINVAL, "path range overflows");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, n_strikes, is_put, steps, path_begin, path_count, path_count, seed, option_index,
+                         greek_mask ? rel_bump : 1e-4, greek_mask, &L)))
+    return rc;
+  L.raw_sums = 1;
+  const double* ks = nullptr;
+  if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
+  OutStage o;
+  o.user[0] = sums;
+  o.n[0] = (size_t)n_strikes * L.n_acc;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  return run_paths(ctx, L, ks, o, st);
+}
+
+int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+                       uint32_t steps, uint64_t paths, double rel_bump, uint32_t greek_mask, const double* sums,
+                       double* price, double* stderr_out, double* greeks, void* stream) {
+  int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
+  if (rc) return rc;
+  if (!sums || !price) return fail(SIMR_EINVAL, "sums and price must be non-NULL");
+  if (greek_mask & ~SIMR_G_ALL) return fail(SIMR_EINVAL, "unknown Greek bits");
+  if (greek_mask && !greeks) return fail(SIMR_EINVAL, "greeks is NULL");
+  if (greek_mask && !(rel_bump > 0.0 && rel_bump < 0.5)) return fail(SIMR_EINVAL, "rel_bump must lie in (0, 0.5)");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, 0, 0, greek_mask ? rel_bump : 1e-4,
+                         greek_mask, &L)))
+    return rc;
+  const size_t ns = (size_t)n_strikes * L.n_acc;
+  const double* dsums = sums;
+  if (!is_device_ptr(sums)) {
+    // sums are staged behind the strike staging area
+    if ((rc = ensure(&ctx->dev_strikes, &ctx->strikes_cap, ns, "sum staging"))) return rc;
+    cudaError_t e = cudaMemcpyAsync(ctx->dev_strikes, sums, ns * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying sums");
+    dsums = ctx->dev_strikes;
+  }
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_strikes;
+  o.user[1] = stderr_out;
+  o.n[1] = n_strikes;
+  o.user[2] = greek_mask ? greeks : nullptr;
+  o.n[2] = (size_t)n_strikes * (L.n_acc - 2);
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  PathOutputs out{};
+  out.price = o.dev[0];
+  out.stderr_ = o.dev[1];
+  out.greeks = o.dev[2];
+  out.status = ctx->status;
+  cudaError_t e = launch_finalize(L, dsums, out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the finalize kernel");
+  return finish_outputs(ctx, o, st);
+}
+
+int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin,
+                        uint64_t n_paths, uint64_t seed, uint32_t option_index, float* x_T, float* v_T,
+                        void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  int rc = check_model(model);
+  if (rc) return rc;
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (n_paths < 1 || n_paths > (1ull << 31)) return fail(SIMR_EINVAL, "n_paths must lie in [1, 2^31]");
+  if (!x_T) return fail(SIMR_EINVAL, "x_T is NULL");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, 1, 0, steps, path_begin, n_paths, n_paths, seed, option_index, 1e-4, 0u, &L)))
+    return rc;
+  const bool hx = !is_device_ptr(x_T), hv = v_T && !is_device_ptr(v_T);
+  float* dx = x_T;
+  float* dv = v_T;
+  if (hx || hv) {
+    if ((rc = ensure(&ctx->dev_f32, &ctx->f32_cap, 2 * (size_t)n_paths, "terminal staging"))) return rc;
+    if (hx) dx = ctx->dev_f32;
+    if (hv) dv = ctx->dev_f32 + n_paths;
+  }
+  cudaError_t e = launch_terminal(L, dx, dv, st);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the terminal kernel");
+  if (hx) e = cudaMemcpyAsync(x_T, dx, n_paths * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hv) e = cudaMemcpyAsync(v_T, dv, n_paths * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && (hx || hv)) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "copying terminal states");
+  return SIMR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// simr_device.cuh -- device primitives of the fused Heston QE path kernels (sm_103a).
+//
+// One thread carries one path's state (v, x = ln S/S0) in registers through all
+// time steps: the paper's per-path cached state of the asset/timestep/path loop
+// nest (Sec. 5.1, Listing 2) becomes register state, with the timestep loop
+// inside the thread.  Random inputs are drawn in-kernel (no V/Z arrays in
+// HBM, unlike the host-streamed inputs of the paper's Table 1).
+#pragma once
+
+#include <cstdint>
+
+namespace simr {
+
+constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
+
+// Per-scenario FP32 constants of the QE variance step and the log-spot step
+// (Andersen 2008 with gamma1 = gamma2 = 1/2, risk-neutral drift r), computed on
+// the host in FP64 and rounded once:
+//   m   = theta + (v - theta) E          = fma(v, E, thE)
+//   s^2 = v c1 + c2
+//   x' = x + K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X, rewritten without
+//   the large cancelling rho/sigma terms as
+//   x' = x + C0 + Cv (v + v') + Cd (theta - v) + Cdl (v' - m) + sK3 sqrt(v + v') Z_X
+// with C0 = r dt, Cv = -dt/4, Cd = (rho/sigma)((1-E) - kappa dt (1+E)/2),
+// Cdl = (rho/sigma)(1 + kappa dt/2), sK3 = sqrt(dt (1 - rho^2)/2): the same
+// polynomial in (v, v'), since v' - v = (theta - v)(1 - E) + (v' - m).
+struct ScenConst {
+  float E, thE, c1, c2;
+  float C0, Cv, Cd, Cdl;
+  float sK3, theta, ratio;  // ratio = discount of this scenario / base discount
+  float v0;                 // initial variance of this scenario
+};
+
+// ---------------------------------------------------------------- PTX ----
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ------------------------------------------------------------- Philox ----
+// Philox4x32-10 (Salmon et al., SC'11).  rk[i] = key + i * (0x9E3779B9, 0xBB67AE85)
+// is precomputed on the host (the key is uniform over the launch), so each round
+// is two 32x32->64 multiplies and two three-input XORs with a constant operand.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const uint32_t (&rk)[10][2]) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ rk[i][0];
+    const uint32_t n2 = hi0 ^ c3 ^ rk[i][1];
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// x = 2u - 1 for u = ((w >> 9) + 1/2) 2^-23, exact in FP32:
+// f = 1 + (w >> 9) 2^-23 from the bits, f - 1.5 is exact, and
+// 2 (f - 1.5) + 2^-23 = (2k + 1 - 2^23) 2^-23 needs at most 23 significant bits.
+__device__ __forceinline__ float centered_uniform(uint32_t w) {
+  const float f = __uint_as_float(0x3f800000u | (w >> 9));
+  return fmaf(2.0f, f - 1.5f, 0x1p-23f);
+}
+
+// Z = Phi^-1(u) = sqrt(2) erfinv(x), x = 2u - 1, by M. Giles' single-precision
+// erfinv approximation ("Approximating the erfinv function", GPU Computing Gems
+// Jade Edition, 2011): w = -ln(1 - x^2); a degree-8 polynomial in w - 2.5 for
+// w < 5, else in sqrt(w) - 3, times x.  The coefficients below are Giles'
+// multiplied by sqrt(2) (in double, rounded once), so no final scaling is needed.
+// 1 - x^2 is formed by one FMA (exact product, one rounding).
+#define SIMR_S2(c) ((float)((c) * 1.4142135623730951))
+__device__ __forceinline__ float norminv_centered(float x) {
+  float w = -0.69314718055994531f * lg2_approx(fmaf(-x, x, 1.0f));
+  float p;
+  if (w < 5.0f) {
+    w = w - 2.5f;
+    p = SIMR_S2(2.81022636e-08);
+    p = fmaf(p, w, SIMR_S2(3.43273939e-07));
+    p = fmaf(p, w, SIMR_S2(-3.5233877e-06));
+    p = fmaf(p, w, SIMR_S2(-4.39150654e-06));
+    p = fmaf(p, w, SIMR_S2(0.00021858087));
+    p = fmaf(p, w, SIMR_S2(-0.00125372503));
+    p = fmaf(p, w, SIMR_S2(-0.00417768164));
+    p = fmaf(p, w, SIMR_S2(0.246640727));
+    p = fmaf(p, w, SIMR_S2(1.50140941));
+  } else {
+    w = sqrt_approx(w) - 3.0f;
+    p = SIMR_S2(-0.000200214257);
+    p = fmaf(p, w, SIMR_S2(0.000100950558));
+    p = fmaf(p, w, SIMR_S2(0.00134934322));
+    p = fmaf(p, w, SIMR_S2(-0.00367342844));
+    p = fmaf(p, w, SIMR_S2(0.00573950773));
+    p = fmaf(p, w, SIMR_S2(-0.0076224613));
+    p = fmaf(p, w, SIMR_S2(0.00943887047));
+    p = fmaf(p, w, SIMR_S2(1.00167406));
+    p = fmaf(p, w, SIMR_S2(2.83297682));
+  }
+  return p * x;
+}
+#undef SIMR_S2
+
+// ------------------------------------------------------------ QE step ----
+// VariancePathQE (paper Sec. 4) with Andersen's QE rule, psi_c = 1.5:
+//   psi = s^2/m^2 <= 1.5 : v' = a (b + Z_V)^2, b^2 = t - 1 + sqrt(t (t - 1)),
+//                          t = 2/psi, a = m / (1 + b^2)
+//   psi > 1.5            : p = (psi-1)/(psi+1); v' = 0 if U_V <= p,
+//                          else ((1-p)/m)^-1 ln((1-p)/(1-U_V))
+// The branch test s^2 <= 1.5 m^2 needs no division; U_V <= p is tested as
+// (1 - U_V)(m^2 + s^2) >= 2 m^2.  Besides v' it returns dl = v' - m (the
+// innovation the log-spot step needs) without cancellation in the quadratic
+// branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1) since m = a (1 + b^2).
+// omu = 1 - U_V (exact), zv = Phi^-1(U_V).
+__device__ __forceinline__ void qe_variance_step(const ScenConst& c, float v, float omu, float zv,
+                                                 float& v_next, float& dl) {
+  const float m = fmaf(v, c.E, c.thE);
+  const float s2 = fmaf(v, c.c1, c.c2);
+  const float m2 = m * m;
+  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
+    const float t = 2.0f * m2 * rcp_approx(s2);
+    const float root = sqrt_approx(fmaf(t, t, -t));
+    const float b2 = (t - 1.0f) + root;
+    const float b = sqrt_approx(b2);
+    const float a = m * rcp_approx(t + root);
+    const float bz = b + zv;
+    v_next = a * bz * bz;
+    dl = a * fmaf(zv, zv + 2.0f * b, -1.0f);
+  } else if (m > 0.0f) {
+    const float ms = m2 + s2;
+    const float W = omu * ms;
+    if (W >= 2.0f * m2) {
+      v_next = 0.0f;
+    } else {
+      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
+      v_next = 0.5f * ms * rcp_approx(m) * L;
+    }
+    dl = v_next - m;
+  } else {
+    v_next = 0.0f;
+    dl = 0.0f;
+  }
+}
+
+// LogPricePathQE (paper Sec. 5) for one scenario, Kahan-compensated in x.
+__device__ __forceinline__ void log_spot_step(const ScenConst& c, float v, float v_next, float dl,
+                                              float zx, float& x, float& comp) {
+  const float s = v + v_next;
+  float inc = fmaf(c.Cv, s, c.C0);
+  inc = fmaf(c.Cd, c.theta - v, inc);
+  inc = fmaf(c.Cdl, dl, inc);
+  inc = fmaf(c.sK3 * sqrt_approx(s), zx, inc);
+  const float y = inc - comp;
+  const float t = x + y;
+  comp = (t - x) - y;
+  x = t;
+}
+
+// AssetPathExponential (paper Sec. 5): S_T = S0 e^{x} with the Kahan remainder
+// (true sum = x - comp) applied as S (1 - comp).  expf is the accurate one.
+__device__ __forceinline__ float terminal_spot(float S0, float x, float comp) {
+  const float e = S0 * expf(x);
+  return fmaf(-comp, e, e);
+}
+
+}  // namespace simr

@@ -1,0 +1,69 @@
+// simr_internal.h -- host-side launch descriptors shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "simr_device.cuh"
+
+namespace simr {
+
+// Accumulator slot of each Greek bit, in bit order (slot 0 = sum f, 1 = sum f^2).
+constexpr int kMaxGreeks = 9;
+constexpr int kMaxResim = 6;  // vega, theta, kappa, long-run var, vol-of-vol, correlation
+
+// Everything one launch of the fused path kernel needs, passed by value
+// (kernel parameter space; all of it is uniform over the grid).
+struct PathLaunch {
+  uint32_t rk[10][2];     // Philox round keys
+  uint64_t path_begin;    // first path index
+  uint64_t path_count;    // paths in this launch
+  uint32_t steps;
+  uint32_t option_index;  // fourth counter word
+  int32_t n_scen;         // simulated scenarios (base first)
+  int32_t n_strikes;
+  int32_t nk_pad;         // strikes rounded up to the tile width (1 or multiple of 32)
+  int32_t n_acc;          // accumulators per strike = 2 + number of Greeks
+  int32_t is_put;
+  uint32_t greek_mask;
+  float S0;
+  float h_s;              // relative S0 bump (delta, gamma)
+  float rho_em, rho_ep;   // e^{-h_r T}, e^{+h_r T}: strikes of the r-shifted revaluation
+  int32_t resim_up[kMaxResim], resim_dn[kMaxResim];  // scenario of each re-simulated Greek
+  ScenConst sc[kMaxScen];
+  // finalisation (FP64)
+  double disc;            // e^{-rT}
+  double paths_total;     // denominator of the mean
+  double denom[kMaxGreeks];  // per Greek: bump denominator (sign folded in)
+  int32_t raw_sums;       // 1: write raw sums instead of normalised results
+};
+
+struct PathOutputs {
+  double* price;   // [n_strikes]
+  double* stderr_; // [n_strikes] or null
+  double* greeks;  // [n_strikes][n_greeks] or null
+  double* sums;    // raw mode: [n_strikes][n_acc]
+  int* status;     // device status word: bit 0 = invalid strike seen
+};
+
+struct Scratch {
+  double* partials;      // [grid][n_acc * nk_pad]
+  unsigned int* ticket;  // zero between launches
+  size_t partial_doubles;
+};
+
+// Launch the fused price / Greeks kernel; returns a cudaError_t.
+cudaError_t launch_paths(const PathLaunch& L, const double* strikes_dev, const PathOutputs& out,
+                         const Scratch& s, int num_sms, cudaStream_t stream, int* grid_used);
+
+// Upper bound of the partial-sum doubles launch_paths needs for this shape.
+size_t paths_scratch_doubles(const PathLaunch& L, int num_sms);
+
+// Normalise combined raw sums [n_strikes][n_acc] into the outputs.
+cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathOutputs& out, cudaStream_t stream);
+
+// Terminal (x_T, v_T) per path of scenario 0.
+cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);
+
+}  // namespace simr

@@ -1,0 +1,348 @@
+// simr_paths.cu -- fused Heston QE path kernels for sm_103a: pricing, bump-and-revalue
+// Greeks with common random numbers, terminal states.
+//
+// Per path (one lane) and per time step, entirely in registers:
+//   Philox4x32-10 (one call per two steps) -> two 23-bit uniforms per step ->
+//   inverse normals -> QE variance step (paper Sec. 4, VariancePathQE) ->
+//   log-spot step (Sec. 5, LogPricePathQE), for every simulated scenario, all
+//   sharing the same draws (common random numbers).
+// Per path at maturity: S_T = S0 e^{x_T} (AssetPathExponential) and the payoff
+// terms of each strike.  Reduction over paths (Sec. 6): a transposed warp
+// butterfly in FP32 sums 32 paths per strike in 31 shuffle-add steps for 32
+// strikes at once, then one FP64 add per lane into per-warp shared-memory
+// accumulators; per block the warps are summed in FP64 in fixed order into a
+// partial row in global scratch, and the last block to finish (atomic ticket)
+// sums the rows in block order and normalises.  No path data touches HBM.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "simr_device.cuh"
+#include "simr_internal.h"
+
+namespace simr {
+namespace {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// In-place transposed butterfly: on entry vals[j] is this lane's term for strike
+// j of the tile; on exit vals[0] of lane l is the sum over the 32 lanes for strike l.
+__device__ __forceinline__ void butterfly32(float (&vals)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < o; ++j) {
+      const float send = upper ? vals[j] : vals[j + o];
+      const float keep = upper ? vals[j + o] : vals[j];
+      vals[j] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+struct StrikeConst {
+  float K, Km, Wr, pad;  // strike; K e^{-h_r T}; K e^{h_r T} - K e^{-h_r T}
+};
+
+// Per-path term of accumulator `a` for one strike (call or put), given the
+// terminal spots of all scenarios.  a = 0: payoff f; 1: f^2; then per Greek bit.
+template <int NS>
+__device__ __forceinline__ float acc_term(const PathLaunch& L, int greek_bit, int a,
+                                          const StrikeConst& k, const float (&S)[NS]) {
+  const float s = S[0];
+  const bool put = L.is_put != 0;
+  const float f = put ? fmaxf(k.K - s, 0.0f) : fmaxf(s - k.K, 0.0f);
+  if (a == 0) return f;
+  if (a == 1) return f * f;
+  const float h = L.h_s;
+  switch (greek_bit) {
+    case 0: {  // delta: f(S(1+h)) - f(S(1-h)) = min(max(S(1+h)-K, 0), 2hS) for a call
+      const float w = 2.0f * h * s;
+      return put ? -fminf(fmaxf(fmaf(h, s, k.K - s), 0.0f), w) : fminf(fmaxf(fmaf(h, s, s - k.K), 0.0f), w);
+    }
+    case 1:  // gamma: f(S(1+h)) - 2 f(S) + f(S(1-h)) = max(0, hS - |K - S|)
+      return fmaxf(fmaf(h, s, -fabsf(k.K - s)), 0.0f);
+    case 4:  // rho: e^{-hT} f(S e^{hT}) - e^{hT} f(S e^{-hT}) = f(S; K e^{-hT}) - f(S; K e^{hT})
+      return put ? -fminf(fmaxf(k.Km + k.Wr - s, 0.0f), k.Wr) : fminf(fmaxf(s - k.Km, 0.0f), k.Wr);
+    default:
+      break;
+  }
+  return 0.0f;
+}
+
+template <int NS>
+__device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn, const StrikeConst& k,
+                                            const float (&S)[NS]) {
+  float su = 0.0f, sd = 0.0f;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (s == up) su = S[s];
+    if (s == dn) sd = S[s];
+  }
+  const bool put = L.is_put != 0;
+  const float fu = put ? fmaxf(k.K - su, 0.0f) : fmaxf(su - k.K, 0.0f);
+  const float fd = put ? fmaxf(k.K - sd, 0.0f) : fmaxf(sd - k.K, 0.0f);
+  return L.sc[up].ratio * fu - L.sc[dn].ratio * fd;
+}
+
+// One time step for all NS scenarios from the two words (w_v, w_x) of the step.
+// NS scenarios in registers; DYN: only the first L.n_scen of them are live.
+template <int NS, bool DYN>
+__device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
+                                         float (&x)[NS], float (&c)[NS]) {
+  const float xv = centered_uniform(w_v);
+  const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
+  const float zv = norminv_centered(xv);
+  const float zx = norminv_centered(centered_uniform(w_x));
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (DYN && s >= L.n_scen) break;
+    float vn, dl;
+    qe_variance_step(L.sc[s], v[s], omu, zv, vn, dl);
+    log_spot_step(L.sc[s], v[s], vn, dl, zx, x[s], c[s]);
+    v[s] = vn;
+  }
+}
+
+template <int NS, bool DYN>
+__device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, float (&v)[NS], float (&x)[NS],
+                                         float (&c)[NS]) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    v[s] = L.sc[s].v0;
+    x[s] = 0.0f;
+    c[s] = 0.0f;
+  }
+  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+  const uint32_t pairs = L.steps >> 1;
+  for (uint32_t i = 0; i < pairs; ++i) {
+    const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
+    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
+    step_all<NS, DYN>(L, w.z, w.w, v, x, c);
+  }
+  if (L.steps & 1u) {
+    const uint4 w = philox4x32_10(pairs, plo, phi, L.option_index, L.rk);
+    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
+  }
+}
+
+// Results of strike k from its n_acc sums (sum_a = s[a * stride]): the price
+// e^{-rT} sum f / n, its standard error, and each Greek e^{-rT} sum / (n denom);
+// or, in raw mode, the sums themselves.  FP64.
+// A strike flagged `bad` (not finite and > 0) gets NaN results.
+__device__ __forceinline__ void write_results(const PathLaunch& L, int k, const double* s, int stride,
+                                              const PathOutputs& out, bool bad) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  if (L.raw_sums) {
+    for (int a = 0; a < L.n_acc; ++a) out.sums[(size_t)k * L.n_acc + a] = bad ? nan : s[(size_t)a * stride];
+    return;
+  }
+  if (bad) {
+    out.price[k] = nan;
+    if (out.stderr_) out.stderr_[k] = nan;
+    if (out.greeks)
+      for (int g = 0; g < L.n_acc - 2; ++g) out.greeks[(size_t)k * (L.n_acc - 2) + g] = nan;
+    return;
+  }
+  const double n = L.paths_total, inv_n = 1.0 / n;
+  const double mean = s[0] * inv_n;
+  out.price[k] = L.disc * mean;
+  if (out.stderr_) {
+    const double var = n > 1.0 ? (s[stride] * inv_n - mean * mean) / (n - 1.0) : 0.0;
+    out.stderr_[k] = L.disc * sqrt(var > 0.0 ? var : 0.0);
+  }
+  if (out.greeks) {
+    const int ng = L.n_acc - 2;
+    for (int g = 0; g < ng; ++g)
+      out.greeks[(size_t)k * ng + g] = L.disc * s[(size_t)(2 + g) * stride] * inv_n / L.denom[g];
+  }
+}
+
+// Fused price / Greeks kernel.  TILE = 1 (single strike) or 32 (strike tiles).
+// Dynamic shared memory: accumulators [warps][n_acc][nk_pad] (FP64), then the
+// strike constants [nk_pad] (StrikeConst), then a flag word.
+template <int NS, int TILE, bool DYN>
+__global__ void __launch_bounds__(256) heston_paths_kernel(const __grid_constant__ PathLaunch L,
+                                                           const double* __restrict__ strikes,
+                                                           PathOutputs out, double* __restrict__ partials,
+                                                           unsigned int* __restrict__ ticket) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warps = blockDim.x / kWarp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = L.n_acc * L.nk_pad;
+  double* acc = reinterpret_cast<double*>(smem_raw);
+  StrikeConst* ks = reinterpret_cast<StrikeConst*>(acc + (size_t)warps * row);
+  int* s_last = reinterpret_cast<int*>(ks + L.nk_pad);
+
+  for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
+  for (int j = threadIdx.x; j < L.nk_pad; j += blockDim.x) {
+    StrikeConst k{0.0f, 0.0f, 0.0f, 0.0f};
+    if (j < L.n_strikes) {
+      const double K = strikes[j];
+      if (!(K > 0.0) || !isfinite(K)) atomicOr(out.status, 1);  // reported by simr_sync
+      k.K = (float)K;
+      k.Km = (float)(K * (double)L.rho_em);
+      k.Wr = (float)(K * (double)L.rho_ep - K * (double)L.rho_em);
+    }
+    ks[j] = k;
+  }
+  __syncthreads();
+
+  double* my_acc = acc + (size_t)warp * row;
+  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  const uint64_t total_warps = (uint64_t)gridDim.x * warps;
+  for (uint64_t b = (uint64_t)blockIdx.x * warps + warp; b < batches; b += total_warps) {
+    const uint64_t local = b * kWarp + lane;
+    const bool active = local < L.path_count;
+    float v[NS], x[NS], c[NS];
+    simulate<NS, DYN>(L, L.path_begin + local, v, x, c);
+    float S[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) S[s] = terminal_spot(L.S0, x[s], c[s]);
+
+    // accumulator list: 0 f, 1 f^2, then set Greek bits in order
+    int a = 0, r = 0;
+    for (int bit = -2; bit < kMaxGreeks; ++bit) {
+      if (bit >= 0 && !((L.greek_mask >> bit) & 1u)) continue;
+      const bool resim = bit == 2 || bit == 3 || bit >= 5;
+      const int up = resim ? L.resim_up[r] : 0, dn = resim ? L.resim_dn[r] : 0;
+      if (TILE == 1) {
+        float t = resim ? resim_term<NS>(L, up, dn, ks[0], S) : acc_term<NS>(L, bit, a, ks[0], S);
+        t = warp_sum(active ? t : 0.0f);
+        if (lane == 0) my_acc[a] += (double)t;
+      } else {
+        for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
+          float vals[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const StrikeConst k = ks[t0 + j];
+            const float t = resim ? resim_term<NS>(L, up, dn, k, S) : acc_term<NS>(L, bit, a, k, S);
+            vals[j] = active ? t : 0.0f;
+          }
+          butterfly32(vals, lane);
+          my_acc[(size_t)a * L.nk_pad + t0 + lane] += (double)vals[0];
+        }
+      }
+      if (resim) ++r;
+      ++a;
+    }
+  }
+  __syncthreads();
+
+  // block partial: sum the warps in order
+  double* my_row = partials + (size_t)blockIdx.x * row;
+  for (int i = threadIdx.x; i < row; i += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < warps; ++w) s += acc[(size_t)w * row + i];
+    my_row[i] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+
+  // last block: sum the partial rows in block order, then normalise per strike
+  for (int i = threadIdx.x; i < row; i += blockDim.x) {
+    double s = 0.0;
+    for (unsigned bidx = 0; bidx < gridDim.x; ++bidx) s += __ldcg(partials + (size_t)bidx * row + i);
+    acc[i] = s;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < L.n_strikes; k += blockDim.x) {
+    const double K = strikes[k];
+    write_results(L, k, acc + k, L.nk_pad, out, !(K > 0.0) || !isfinite(K));
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Normalise sums of a sharded run: sums[k][n_acc] -> outputs.
+__global__ void finalize_sums_kernel(const __grid_constant__ PathLaunch L, const double* __restrict__ sums,
+                                     PathOutputs out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < L.n_strikes) write_results(L, k, sums + (size_t)k * L.n_acc, 1, out, false);
+}
+
+__global__ void __launch_bounds__(256) heston_terminal_kernel(const __grid_constant__ PathLaunch L,
+                                                              float* __restrict__ x_T, float* __restrict__ v_T) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.path_count) return;
+  float v[1], x[1], c[1];
+  simulate<1, false>(L, L.path_begin + i, v, x, c);
+  x_T[i] = x[0] - c[0];
+  if (v_T) v_T[i] = v[0];
+}
+
+template <int NS, int TILE, bool DYN>
+cudaError_t launch_t(const PathLaunch& L, const double* strikes, const PathOutputs& out, const Scratch& s,
+                     int num_sms, cudaStream_t stream, int* grid_used) {
+  const int tpb = 256, warps = tpb / kWarp;
+  const size_t row = (size_t)L.n_acc * L.nk_pad;
+  const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16;
+  auto kern = heston_paths_kernel<NS, TILE, DYN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  uint64_t grid = (uint64_t)num_sms * per_sm;
+  const uint64_t need = (batches + warps - 1) / warps;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  if ((size_t)grid * row > s.partial_doubles) return cudaErrorMemoryAllocation;
+  *grid_used = (int)grid;
+  kern<<<(unsigned)grid, tpb, smem, stream>>>(L, strikes, out, s.partials, s.ticket);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t paths_scratch_doubles(const PathLaunch& L, int num_sms) {
+  // at most 8 resident blocks of 256 threads per SM
+  return (size_t)num_sms * 8 * (size_t)L.n_acc * L.nk_pad;
+}
+
+cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathOutputs& out, const Scratch& s,
+                         int num_sms, cudaStream_t stream, int* grid_used) {
+  const bool one = L.nk_pad == 1;
+  switch (L.n_scen) {
+    case 1:
+      return one ? launch_t<1, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
+                 : launch_t<1, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+    case 3:
+      return one ? launch_t<3, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
+                 : launch_t<3, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+    case 5:
+      return one ? launch_t<5, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
+                 : launch_t<5, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+    default:
+      if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
+      return one ? launch_t<kMaxScen, 1, true>(L, strikes, out, s, num_sms, stream, grid_used)
+                 : launch_t<kMaxScen, 32, true>(L, strikes, out, s, num_sms, stream, grid_used);
+  }
+}
+
+cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathOutputs& out, cudaStream_t stream) {
+  const int tpb = 128;
+  finalize_sums_kernel<<<(L.n_strikes + tpb - 1) / tpb, tpb, 0, stream>>>(L, sums, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream) {
+  const int tpb = 256;
+  const uint64_t grid = (L.path_count + tpb - 1) / tpb;
+  heston_terminal_kernel<<<(unsigned)grid, tpb, 0, stream>>>(L, x_T, v_T);
+  return cudaGetLastError();
+}
+
+}  // namespace simr

@@ -1,0 +1,76 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol include/*.h declares (no GPU)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"^SIMR_API\s+[\w\s\*]+?\b(simr_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2402_12111_gb300 import build
+
+    try:
+        return build.build()
+    except RuntimeError as e:
+        if "nvcc not found" in str(e):
+            pytest.skip("no CUDA toolkit")
+        raise
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for required in ("simr_price", "simr_greeks_fd", "simr_create", "simr_destroy", "simr_last_error", "simr_sync"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (simr_\w+)", out))
+    assert _declared() <= exported
+    # nothing but the declared C entry points leaks out of the library
+    assert exported == _declared()
+
+
+def test_binding_loads_without_gpu(libpath):
+    import paper_2402_12111_gb300 as simr
+
+    L = simr.load(build_if_missing=False)
+    assert L.simr_version() >= 100
+    assert L.simr_last_error() == b""
+
+
+def test_no_context_without_gpu(libpath):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2402_12111_gb300 as simr
+    from paper_2402_12111_gb300 import _simr
+
+    with pytest.raises(simr.SimrError):
+        _simr.context(0)
+
+
+def test_product_path_does_not_import_oracle():
+    # The package must not reach the CPU oracle (no fallback); only tests, smoke and bench may.
+    for path in glob.glob(os.path.join(ROOT, "paper_2402_12111_gb300", "**", "*.py"), recursive=True):
+        src = open(path).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
+    for path in glob.glob(os.path.join(ROOT, "paper_2402_12111_gb300", "csrc", "*")):
+        assert "simr_oracle" not in open(path).read(), path
