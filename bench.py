@@ -1,0 +1,358 @@
+"""Benchmark: Heston path-steps/s for price + bump-and-revalue Greeks on GB300.
+
+A step is one pass of the whole hot path over one batch: simr_greeks_fd on the
+32-strike grid workload (252 steps, 2^20 paths, delta/gamma/vega/theta/rho,
+relative bump 1e-4) -- Philox draws, inverse normals, QE variance and log-spot
+steps for the base and the four re-simulated scenarios, payoffs and the FP64
+reduction, one kernel launch.  value = underlying path-steps (paths x time
+steps) priced with Greeks per second, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank prices its own path range [rank P, (rank+1) P)
+(weak scaling, no collective in the timed loop); the shards' FP64 sums are
+combined once afterwards.  --impl reference times the FP64 CPU oracle on the
+host cores on a bounded path sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "Heston path-steps/s (price+Greeks) on 1 GB300; % FP32 peak; adjoint vs FD speedup"
+UNIT = "path-steps/s"
+FP32_LANES_PER_SM = 128
+# FP32 flops per path-step, FMA = 2, as the kernel's formulas compute them:
+#   shared per step: two inverse normals (2 x 22) + two uniforms (2 x 2)          = 48
+#   per simulated scenario: QE variance step 25 + log-spot step with its Kahan
+#   compensation 16                                                               = 41
+FLOPS_SHARED = 48
+FLOPS_PER_SCENARIO = 41
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def greek_list(w):
+    return list(w.greeks)
+
+
+def simulated_scenarios(greeks) -> int:
+    """Base + up/down for each re-simulated Greek (delta, gamma, rho reuse the base path)."""
+    return 1 + 2 * sum(g in ("vega", "theta", "kappa", "lrvar", "volvol", "corr") for g in greeks)
+
+
+def flops_per_path_step(greeks) -> int:
+    return FLOPS_SHARED + FLOPS_PER_SCENARIO * simulated_scenarios(greeks)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_12111_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(sha: str):
+    """DRAM bytes per launch of the path kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "heston_paths_grid32_252x1048576.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != sha:
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.out = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.out:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_run(w, paths_sample: int):
+    """One oracle pass (price + the same FD Greeks) on paths [0, paths_sample) of the workload."""
+    import oracle
+
+    bits = {"delta": oracle.G_DELTA, "gamma": oracle.G_GAMMA, "vega": oracle.G_VEGA, "theta": oracle.G_THETA,
+            "rho": oracle.G_RHO}
+    mask = sum(bits[g] for g in w.greeks)
+    t0 = time.perf_counter()
+    oracle.greeks_fd(w.model, w.strikes, w.is_put, w.steps, paths_sample, w.seed, w.rel_bump, mask)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, paths_sample: int = 1 << 16):
+    import oracle
+
+    oracle.build()
+    cores = oracle.max_threads()
+    dt = cpu_oracle_run(w, paths_sample)
+    return {"value": paths_sample * w.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{w.name}: paths [0, {paths_sample}) of {w.paths}, all {w.steps} steps, all "
+                      f"{len(w.strikes)} strikes and the same Greeks; {dt:.2f} s wall on {cores} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workloads.grid()
+    import oracle
+
+    oracle.build()
+    cores = oracle.max_threads()
+    sample = 1 << 13
+    for _ in range(args.warmup):
+        cpu_oracle_run(w, sample)
+    times = [cpu_oracle_run(w, sample) for _ in range(args.steps)]
+    total = sum(times)
+    value = args.steps * sample * w.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "paths": w.paths, "time_steps": w.steps, "strikes": len(w.strikes),
+                       "greeks": greek_list(w), "rel_bump": w.rel_bump, "seed": w.seed,
+                       "sample_paths_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"paths [0, {sample}) of {w.paths} per step, all {w.steps} steps, "
+                                       f"{len(w.strikes)} strikes, same Greeks"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+
+    import paper_2402_12111_gb300 as simr
+
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    w = workloads.grid()
+    if args.paths:
+        w.paths = args.paths
+        w.name = f"{w.name}_paths{args.paths}"
+    greeks = greek_list(w)
+    mask = simr.greek_mask(greeks)
+    K = torch.as_tensor(w.strikes, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    path_begin = rank * w.paths
+
+    def step():
+        if world == 1:
+            return simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=mask, rel_bump=w.rel_bump)
+        return simr.path_sums(w.model, K, w.is_put, w.steps, path_begin, w.paths, seed=w.seed, greeks=mask,
+                              rel_bump=w.rel_bump)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+        flush.zero_()
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            starts[i].record(stream)
+            out = step()
+            ends[i].record(stream)
+            flush.zero_()
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if pg is not None:
+        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
+        sums = out.clone()
+        pg.all_reduce(sums)
+    ms = float(ms_t.item())
+    path_steps = w.paths * w.steps
+    value = world * path_steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers (pinned strikes in, results out)
+    e2e = None
+    if not args.no_e2e:
+        K_host = torch.as_tensor(w.strikes, dtype=torch.float64).pin_memory()
+        e2e_steps = max(5, min(args.steps, 20))
+        simr.greeks_fd(w.model, K_host, w.is_put, w.steps, w.paths, w.seed, greeks=mask, rel_bump=w.rel_bump,
+                       device=dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            p_h, g_h = simr.greeks_fd(w.model, K_host, w.is_put, w.steps, w.paths, w.seed, greeks=mask,
+                                      rel_bump=w.rel_bump, device=dev)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if pg is not None:
+            pg.all_reduce(e2e_t, op=pg.ReduceOp.MAX)
+        e2e = {"value": world * path_steps / float(e2e_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": K_host.numel() * 8, "d2h_bytes_per_step": (p_h.numel() + g_h.numel()) * 8,
+               "steps": e2e_steps}
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops_step = flops_per_path_step(greeks)
+    achieved_tflops = flops_step * path_steps / (ms * 1e-3) / 1e12  # per GPU, one launch per step
+    sha = kernel_source_sha()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "paths": w.paths, "time_steps": w.steps, "strikes": len(w.strikes),
+                   "greeks": greeks, "rel_bump": w.rel_bump, "seed": w.seed,
+                   "simulated_scenarios": simulated_scenarios(greeks),
+                   "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
+                   "parallelism": f"paths sharded over {world} rank(s)"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp32_peak_tflops, "traffic": profiled_traffic(sha),
+                     "peak_kind": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                  f"x {sm_max:.0f} MHz (FMA = 2 flops)",
+                     "flops_per_path_step": flops_step},
+        "fp32_peak_frac": achieved_tflops / fp32_peak_tflops,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "kernel_source_sha": sha,
+        "wall_s_timed_region": t_wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -89,28 +89,60 @@ int ensure(T** buf, size_t* cap, size_t n, const char* what) {
   return SIMR_OK;
 }
 
-// FP64 -> FP32 constants of one scenario (formulas in simr_device.cuh).
-ScenConst scen_const(const simr_heston& m, uint32_t steps, double T_base) {
+// FP64 constants of one scenario (formulas in simr_device.cuh), in the order
+// E, thE, c1, c2, C0, Cv, Cd, Cdl, sK3.
+void scen_const64(const simr_heston& m, uint32_t steps, double out[9]) {
   const double dt = m.T / (double)steps;
   const double kdt = m.kappa * dt;
   const double E = std::exp(-kdt);
   const double omE = -std::expm1(-kdt);
   const double s2 = m.sigma * m.sigma;
   const double rs = m.rho / m.sigma;
-  ScenConst c;
-  c.E = (float)E;
-  c.thE = (float)(m.theta * omE);
-  c.c1 = (float)(s2 * E * omE / m.kappa);
-  c.c2 = (float)(m.theta * s2 * omE * omE / (2.0 * m.kappa));
-  c.C0 = (float)(m.r * dt);
-  c.Cv = (float)(-0.25 * dt);
-  c.Cd = (float)(rs * (omE - 0.5 * kdt * (1.0 + E)));
-  c.Cdl = (float)(rs * (1.0 + 0.5 * kdt));
-  c.sK3 = (float)std::sqrt(0.5 * dt * (1.0 - m.rho * m.rho));
-  c.theta = (float)m.theta;
-  c.ratio = (float)std::exp(-m.r * (m.T - T_base));
-  c.v0 = (float)m.v0;
-  return c;
+  const double Cd = rs * (omE - 0.5 * kdt * (1.0 + E));
+  out[0] = E;
+  out[1] = m.theta * omE;
+  out[2] = s2 * E * omE / m.kappa;
+  out[3] = m.theta * s2 * omE * omE / (2.0 * m.kappa);
+  out[4] = m.r * dt + Cd * m.theta;
+  out[5] = -0.25 * dt;
+  out[6] = Cd;
+  out[7] = rs * (1.0 + 0.5 * kdt);
+  out[8] = std::sqrt(0.5 * dt * (1.0 - m.rho * m.rho));
+}
+
+ScenConst pack(const double c[9], double ratio, double v0) {
+  ScenConst s;
+  s.E = (float)c[0];
+  s.thE = (float)c[1];
+  s.c1 = (float)c[2];
+  s.c2 = (float)c[3];
+  s.C0 = (float)c[4];
+  s.Cv = (float)c[5];
+  s.Cd = (float)c[6];
+  s.Cdl = (float)c[7];
+  s.sK3 = (float)c[8];
+  s.ratio = (float)ratio;
+  s.v0 = (float)v0;
+  s.pad = 0.0f;
+  return s;
+}
+
+// Base scenario: full constants.
+ScenConst base_const(const simr_heston& m, uint32_t steps) {
+  double c[9];
+  scen_const64(m, steps, c);
+  return pack(c, 1.0, m.v0);
+}
+
+// Bumped scenario: FP64 deltas to the FP32-ROUNDED base constants, so that
+// base + delta reproduces the bumped constant to FP32 relative precision of the delta.
+ScenConst bumped_const(const simr_heston& base, const simr_heston& bumped, uint32_t steps) {
+  double cb[9], cs[9], d[9];
+  scen_const64(base, steps, cb);
+  scen_const64(bumped, steps, cs);
+  for (int i = 0; i < 9; ++i) d[i] = cs[i] - (double)(float)cb[i];
+  const double ratio_m1 = std::expm1(-bumped.r * bumped.T + base.r * base.T);
+  return pack(d, ratio_m1, bumped.v0 - (double)(float)base.v0);
 }
 
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2]) {
@@ -149,7 +181,7 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
   L->h_s = (float)rel_bump;
   L->disc = std::exp(-m->r * m->T);
   L->paths_total = (double)paths_total;
-  L->sc[0] = scen_const(*m, steps, m->T);
+  L->sc[0] = base_const(*m, steps);
   int ns = 1, r = 0, g = 0;
   for (int bit = 0; bit < kMaxGreeks; ++bit) {
     if (!((mask >> bit) & 1u)) continue;
@@ -162,8 +194,8 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
     } else if (b == SIMR_G_RHO) {
       double h = rel_bump * std::fabs(m->r);
       if (h == 0.0) h = rel_bump;
-      L->rho_em = (float)std::exp(-h * m->T);
-      L->rho_ep = (float)std::exp(h * m->T);
+      L->rho_em = std::exp(-h * m->T);
+      L->rho_w = 2.0 * std::sinh(h * m->T);
       denom = 2.0 * h;
     } else {
       // re-simulated: field selection
@@ -198,12 +230,12 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
       double hu = 0.0, hd = 0.0;
       if (up_ok) {
         iu = ns;
-        L->sc[ns++] = scen_const(up, steps, m->T);
+        L->sc[ns++] = bumped_const(*m, up, steps);
         hu = h;
       }
       if (dn_ok) {
         id = ns;
-        L->sc[ns++] = scen_const(dn, steps, m->T);
+        L->sc[ns++] = bumped_const(*m, dn, steps);
         hd = h;
       }
       L->resim_up[r] = iu;

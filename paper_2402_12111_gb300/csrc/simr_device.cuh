@@ -20,15 +20,24 @@ constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
 //   s^2 = v c1 + c2
 //   x' = x + K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X, rewritten without
 //   the large cancelling rho/sigma terms as
-//   x' = x + C0 + Cv (v + v') + Cd (theta - v) + Cdl (v' - m) + sK3 sqrt(v + v') Z_X
-// with C0 = r dt, Cv = -dt/4, Cd = (rho/sigma)((1-E) - kappa dt (1+E)/2),
-// Cdl = (rho/sigma)(1 + kappa dt/2), sK3 = sqrt(dt (1 - rho^2)/2): the same
-// polynomial in (v, v'), since v' - v = (theta - v)(1 - E) + (v' - m).
+//   x' = x + C0 + Cv (v + v') - Cd v + Cdl (v' - m) + sK3 sqrt(v + v') Z_X
+// with Cd = (rho/sigma)((1-E) - kappa dt (1+E)/2), C0 = r dt + Cd theta,
+// Cv = -dt/4, Cdl = (rho/sigma)(1 + kappa dt/2), sK3 = sqrt(dt (1 - rho^2)/2):
+// the same polynomial in (v, v'), since v' - v = (theta - v)(1 - E) + (v' - m).
+//
+// A bumped scenario (bump-and-revalue) stores DELTAS to the base scenario's
+// constants instead (dE = E_s - E_0 etc., differences taken in FP64): a 1e-4
+// bump moves E or Cdl by only a few FP32 ulps, so rounding the bumped constants
+// on their own would bias the finite difference.  Each use adds the delta
+// product to the base product inside an FMA, and v0's delta enters the first
+// step as a low-order term; the only rounding left is per step and per path.
 struct ScenConst {
   float E, thE, c1, c2;
   float C0, Cv, Cd, Cdl;
-  float sK3, theta, ratio;  // ratio = discount of this scenario / base discount
-  float v0;                 // initial variance of this scenario
+  float sK3;
+  float ratio;  // base: 1; bumped: (discount of this scenario / base discount) - 1
+  float v0;     // base: v0; bumped: v0_s - v0
+  float pad;
 };
 
 // ---------------------------------------------------------------- PTX ----
@@ -114,7 +123,8 @@ __device__ __forceinline__ float norminv_centered(float x) {
 #undef SIMR_S2
 
 // ------------------------------------------------------------ QE step ----
-// VariancePathQE (paper Sec. 4) with Andersen's QE rule, psi_c = 1.5:
+// VariancePathQE (paper Sec. 4) with Andersen's QE rule, psi_c = 1.5, given
+// m = E[v'|v] and s2 = Var[v'|v]:
 //   psi = s^2/m^2 <= 1.5 : v' = a (b + Z_V)^2, b^2 = t - 1 + sqrt(t (t - 1)),
 //                          t = 2/psi, a = m / (1 + b^2)
 //   psi > 1.5            : p = (psi-1)/(psi+1); v' = 0 if U_V <= p,
@@ -124,10 +134,8 @@ __device__ __forceinline__ float norminv_centered(float x) {
 // innovation the log-spot step needs) without cancellation in the quadratic
 // branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1) since m = a (1 + b^2).
 // omu = 1 - U_V (exact), zv = Phi^-1(U_V).
-__device__ __forceinline__ void qe_variance_step(const ScenConst& c, float v, float omu, float zv,
-                                                 float& v_next, float& dl) {
-  const float m = fmaf(v, c.E, c.thE);
-  const float s2 = fmaf(v, c.c1, c.c2);
+__device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, float zv, float& v_next,
+                                                float& dl) {
   const float m2 = m * m;
   if (s2 <= 1.5f * m2 && m2 > 0.0f) {
     const float t = 2.0f * m2 * rcp_approx(s2);
@@ -154,18 +162,56 @@ __device__ __forceinline__ void qe_variance_step(const ScenConst& c, float v, fl
   }
 }
 
-// LogPricePathQE (paper Sec. 5) for one scenario, Kahan-compensated in x.
-__device__ __forceinline__ void log_spot_step(const ScenConst& c, float v, float v_next, float dl,
-                                              float zx, float& x, float& comp) {
-  const float s = v + v_next;
+// One step of the base scenario: QE variance step, then LogPricePathQE (paper
+// Sec. 5), Kahan-compensated in x.
+__device__ __forceinline__ void step_base(const ScenConst& c, float omu, float zv, float zx, float& v, float& x,
+                                          float& comp) {
+  float vn, dl;
+  qe_from_moments(fmaf(v, c.E, c.thE), fmaf(v, c.c1, c.c2), omu, zv, vn, dl);
+  const float s = v + vn;
   float inc = fmaf(c.Cv, s, c.C0);
-  inc = fmaf(c.Cd, c.theta - v, inc);
+  inc = fmaf(-c.Cd, v, inc);
   inc = fmaf(c.Cdl, dl, inc);
   inc = fmaf(c.sK3 * sqrt_approx(s), zx, inc);
   const float y = inc - comp;
   const float t = x + y;
   comp = (t - x) - y;
   x = t;
+  v = vn;
+}
+
+// One step of a bumped scenario: base constants b plus deltas d.  v_lo is the
+// low-order part of the variance state (v0's bump on the first step, else 0).
+template <bool FIRST>
+__device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float v_lo, float omu,
+                                            float zv, float zx, float& v, float& x, float& comp) {
+  float small_m = fmaf(v, d.E, d.thE);
+  float small_s = fmaf(v, d.c1, d.c2);
+  if (FIRST) {
+    small_m = fmaf(b.E + d.E, v_lo, small_m);
+    small_s = fmaf(b.c1 + d.c1, v_lo, small_s);
+  }
+  const float m = fmaf(v, b.E, b.thE) + small_m;
+  const float s2 = fmaf(v, b.c1, b.c2) + small_s;
+  float vn, dl;
+  qe_from_moments(m, s2, omu, zv, vn, dl);
+  const float s = FIRST ? (v + vn) + v_lo : v + vn;
+  const float vv = FIRST ? v + v_lo : v;
+  const float q = sqrt_approx(s);
+  float inc = fmaf(b.Cv, s, b.C0);
+  inc = fmaf(-b.Cd, vv, inc);
+  inc = fmaf(b.Cdl, dl, inc);
+  inc = fmaf(b.sK3 * q, zx, inc);
+  float sm = fmaf(d.Cv, s, d.C0);
+  sm = fmaf(-d.Cd, vv, sm);
+  sm = fmaf(d.Cdl, dl, sm);
+  sm = fmaf(d.sK3 * q, zx, sm);
+  inc += sm;
+  const float y = inc - comp;
+  const float t = x + y;
+  comp = (t - x) - y;
+  x = t;
+  v = vn;
 }
 
 // AssetPathExponential (paper Sec. 5): S_T = S0 e^{x} with the Kahan remainder

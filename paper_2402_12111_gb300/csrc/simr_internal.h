@@ -29,7 +29,8 @@ struct PathLaunch {
   uint32_t greek_mask;
   float S0;
   float h_s;              // relative S0 bump (delta, gamma)
-  float rho_em, rho_ep;   // e^{-h_r T}, e^{+h_r T}: strikes of the r-shifted revaluation
+  double rho_em;          // e^{-h_r T}: strike factor of the r-up revaluation
+  double rho_w;           // e^{h_r T} - e^{-h_r T} = 2 sinh(h_r T): band width factor
   int32_t resim_up[kMaxResim], resim_dn[kMaxResim];  // scenario of each re-simulated Greek
   ScenConst sc[kMaxScen];
   // finalisation (FP64)

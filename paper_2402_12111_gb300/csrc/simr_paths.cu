@@ -77,6 +77,7 @@ __device__ __forceinline__ float acc_term(const PathLaunch& L, int greek_bit, in
   return 0.0f;
 }
 
+// ratio_up f_up - ratio_dn f_dn with ratio = 1 + delta (delta exact in FP32).
 template <int NS>
 __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn, const StrikeConst& k,
                                             const float (&S)[NS]) {
@@ -89,25 +90,25 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
   const bool put = L.is_put != 0;
   const float fu = put ? fmaxf(k.K - su, 0.0f) : fmaxf(su - k.K, 0.0f);
   const float fd = put ? fmaxf(k.K - sd, 0.0f) : fmaxf(sd - k.K, 0.0f);
-  return L.sc[up].ratio * fu - L.sc[dn].ratio * fd;
+  const float ru = up ? L.sc[up].ratio : 0.0f, rd = dn ? L.sc[dn].ratio : 0.0f;
+  return fmaf(ru, fu, fmaf(-rd, fd, fu - fd));
 }
 
 // One time step for all NS scenarios from the two words (w_v, w_x) of the step.
 // NS scenarios in registers; DYN: only the first L.n_scen of them are live.
-template <int NS, bool DYN>
+// FIRST: the first step, where a bumped v0 enters as a low-order term.
+template <int NS, bool DYN, bool FIRST>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
   const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
   const float zv = norminv_centered(xv);
   const float zx = norminv_centered(centered_uniform(w_x));
+  step_base(L.sc[0], omu, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
+  for (int s = 1; s < NS; ++s) {
     if (DYN && s >= L.n_scen) break;
-    float vn, dl;
-    qe_variance_step(L.sc[s], v[s], omu, zv, vn, dl);
-    log_spot_step(L.sc[s], v[s], vn, dl, zx, x[s], c[s]);
-    v[s] = vn;
+    step_bumped<FIRST>(L.sc[0], L.sc[s], FIRST ? L.sc[s].v0 : 0.0f, omu, zv, zx, v[s], x[s], c[s]);
   }
 }
 
@@ -116,20 +117,25 @@ __device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, flo
                                          float (&c)[NS]) {
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    v[s] = L.sc[s].v0;
+    v[s] = L.sc[0].v0;  // bumped scenarios add their v0 delta in the first step
     x[s] = 0.0f;
     c[s] = 0.0f;
   }
   const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
   const uint32_t pairs = L.steps >> 1;
-  for (uint32_t i = 0; i < pairs; ++i) {
-    const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
-    step_all<NS, DYN>(L, w.z, w.w, v, x, c);
+  {
+    const uint4 w = philox4x32_10(0u, plo, phi, L.option_index, L.rk);
+    step_all<NS, DYN, true>(L, w.x, w.y, v, x, c);
+    if (L.steps > 1) step_all<NS, DYN, false>(L, w.z, w.w, v, x, c);
   }
-  if (L.steps & 1u) {
+  for (uint32_t i = 1; i < pairs; ++i) {
+    const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
+    step_all<NS, DYN, false>(L, w.x, w.y, v, x, c);
+    step_all<NS, DYN, false>(L, w.z, w.w, v, x, c);
+  }
+  if ((L.steps & 1u) && pairs > 0) {
     const uint4 w = philox4x32_10(pairs, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
+    step_all<NS, DYN, false>(L, w.x, w.y, v, x, c);
   }
 }
 
@@ -188,8 +194,8 @@ __global__ void __launch_bounds__(256) heston_paths_kernel(const __grid_constant
       const double K = strikes[j];
       if (!(K > 0.0) || !isfinite(K)) atomicOr(out.status, 1);  // reported by simr_sync
       k.K = (float)K;
-      k.Km = (float)(K * (double)L.rho_em);
-      k.Wr = (float)(K * (double)L.rho_ep - K * (double)L.rho_em);
+      k.Km = (float)(K * L.rho_em);
+      k.Wr = (float)(K * L.rho_w);
     }
     ks[j] = k;
   }
