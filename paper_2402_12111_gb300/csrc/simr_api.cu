@@ -135,14 +135,15 @@ ScenConst base_const(const simr_heston& m, uint32_t steps) {
 }
 
 // Bumped scenario: FP64 deltas to the FP32-ROUNDED base constants, so that
-// base + delta reproduces the bumped constant to FP32 relative precision of the delta.
+// base + delta reproduces the bumped constant to FP32 relative precision of the
+// delta; v0 is the scenario's own FP32 initial variance.
 ScenConst bumped_const(const simr_heston& base, const simr_heston& bumped, uint32_t steps) {
   double cb[9], cs[9], d[9];
   scen_const64(base, steps, cb);
   scen_const64(bumped, steps, cs);
   for (int i = 0; i < 9; ++i) d[i] = cs[i] - (double)(float)cb[i];
   const double ratio_m1 = std::expm1(-bumped.r * bumped.T + base.r * base.T);
-  return pack(d, ratio_m1, bumped.v0 - (double)(float)base.v0);
+  return pack(d, ratio_m1, bumped.v0);
 }
 
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2]) {
@@ -228,15 +229,18 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
       if (unit && *fu > 1.0) up_ok = false;
       int iu = 0, id = 0;
       double hu = 0.0, hd = 0.0;
+      // v0 is only the initial state: the kernel starts each scenario from its
+      // FP32 value, so the realised bump is the difference of those values.
+      const double v0f = (double)(float)m->v0;
       if (up_ok) {
         iu = ns;
         L->sc[ns++] = bumped_const(*m, up, steps);
-        hu = h;
+        hu = (b == SIMR_G_VEGA) ? (double)(float)up.v0 - v0f : h;
       }
       if (dn_ok) {
         id = ns;
         L->sc[ns++] = bumped_const(*m, dn, steps);
-        hd = h;
+        hd = (b == SIMR_G_VEGA) ? v0f - (double)(float)dn.v0 : h;
       }
       L->resim_up[r] = iu;
       L->resim_dn[r] = id;
@@ -576,3 +580,4 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
 }
 
 }  // extern "C"
+

@@ -27,16 +27,19 @@ constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
 //
 // A bumped scenario (bump-and-revalue) stores DELTAS to the base scenario's
 // constants instead (dE = E_s - E_0 etc., differences taken in FP64): a 1e-4
-// bump moves E or Cdl by only a few FP32 ulps, so rounding the bumped constants
-// on their own would bias the finite difference.  Each use adds the delta
-// product to the base product inside an FMA, and v0's delta enters the first
-// step as a low-order term; the only rounding left is per step and per path.
+// bump moves E or Cdl by only a few FP32 ulps, so bumped constants rounded on
+// their own would bias the finite difference.  Each delta is added inside an
+// FMA whose product varies from path to path (so its rounding is unbiased),
+// and every scenario adds the base constants in the same order, so the
+// systematic part of their rounding is common to all scenarios and cancels in
+// the difference.  The initial variance is not a delta: each scenario starts
+// from its own FP32 v0, and the host divides by the realised FP32 bump.
 struct ScenConst {
   float E, thE, c1, c2;
   float C0, Cv, Cd, Cdl;
   float sK3;
   float ratio;  // base: 1; bumped: (discount of this scenario / base discount) - 1
-  float v0;     // base: v0; bumped: v0_s - v0
+  float v0;     // initial variance of this scenario (FP32 value)
   float pad;
 };
 
@@ -163,11 +166,16 @@ __device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, fl
 }
 
 // One step of the base scenario: QE variance step, then LogPricePathQE (paper
-// Sec. 5), Kahan-compensated in x.
+// Sec. 5), Kahan-compensated in x.  CRN: with bumped scenarios alongside, the
+// moments are formed in the bumped scenarios' rounding order (product, then
+// the additive constant) so the two share their systematic rounding.
+template <bool CRN>
 __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float zv, float zx, float& v, float& x,
                                           float& comp) {
   float vn, dl;
-  qe_from_moments(fmaf(v, c.E, c.thE), fmaf(v, c.c1, c.c2), omu, zv, vn, dl);
+  const float m = CRN ? v * c.E + c.thE : fmaf(v, c.E, c.thE);
+  const float s2 = CRN ? v * c.c1 + c.c2 : fmaf(v, c.c1, c.c2);
+  qe_from_moments(m, s2, omu, zv, vn, dl);
   const float s = v + vn;
   float inc = fmaf(c.Cv, s, c.C0);
   inc = fmaf(-c.Cd, v, inc);
@@ -180,30 +188,21 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
   v = vn;
 }
 
-// One step of a bumped scenario: base constants b plus deltas d.  v_lo is the
-// low-order part of the variance state (v0's bump on the first step, else 0).
-template <bool FIRST>
-__device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float v_lo, float omu,
-                                            float zv, float zx, float& v, float& x, float& comp) {
-  float small_m = fmaf(v, d.E, d.thE);
-  float small_s = fmaf(v, d.c1, d.c2);
-  if (FIRST) {
-    small_m = fmaf(b.E + d.E, v_lo, small_m);
-    small_s = fmaf(b.c1 + d.c1, v_lo, small_s);
-  }
-  const float m = fmaf(v, b.E, b.thE) + small_m;
-  const float s2 = fmaf(v, b.c1, b.c2) + small_s;
+// One step of a bumped scenario: base constants b plus deltas d.
+__device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float omu, float zv, float zx,
+                                            float& v, float& x, float& comp) {
+  const float m = fmaf(v, b.E, fmaf(v, d.E, d.thE)) + b.thE;
+  const float s2 = fmaf(v, b.c1, fmaf(v, d.c1, d.c2)) + b.c2;
   float vn, dl;
   qe_from_moments(m, s2, omu, zv, vn, dl);
-  const float s = FIRST ? (v + vn) + v_lo : v + vn;
-  const float vv = FIRST ? v + v_lo : v;
+  const float s = v + vn;
   const float q = sqrt_approx(s);
   float inc = fmaf(b.Cv, s, b.C0);
-  inc = fmaf(-b.Cd, vv, inc);
+  inc = fmaf(-b.Cd, v, inc);
   inc = fmaf(b.Cdl, dl, inc);
   inc = fmaf(b.sK3 * q, zx, inc);
   float sm = fmaf(d.Cv, s, d.C0);
-  sm = fmaf(-d.Cd, vv, sm);
+  sm = fmaf(-d.Cd, v, sm);
   sm = fmaf(d.Cdl, dl, sm);
   sm = fmaf(d.sK3 * q, zx, sm);
   inc += sm;

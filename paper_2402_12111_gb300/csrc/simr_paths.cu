@@ -96,19 +96,18 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
 
 // One time step for all NS scenarios from the two words (w_v, w_x) of the step.
 // NS scenarios in registers; DYN: only the first L.n_scen of them are live.
-// FIRST: the first step, where a bumped v0 enters as a low-order term.
-template <int NS, bool DYN, bool FIRST>
+template <int NS, bool DYN>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
   const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
   const float zv = norminv_centered(xv);
   const float zx = norminv_centered(centered_uniform(w_x));
-  step_base(L.sc[0], omu, zv, zx, v[0], x[0], c[0]);
+  step_base<(NS > 1)>(L.sc[0], omu, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
   for (int s = 1; s < NS; ++s) {
     if (DYN && s >= L.n_scen) break;
-    step_bumped<FIRST>(L.sc[0], L.sc[s], FIRST ? L.sc[s].v0 : 0.0f, omu, zv, zx, v[s], x[s], c[s]);
+    step_bumped(L.sc[0], L.sc[s], omu, zv, zx, v[s], x[s], c[s]);
   }
 }
 
@@ -117,25 +116,20 @@ __device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, flo
                                          float (&c)[NS]) {
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    v[s] = L.sc[0].v0;  // bumped scenarios add their v0 delta in the first step
+    v[s] = (DYN && s >= L.n_scen) ? 0.0f : L.sc[s].v0;
     x[s] = 0.0f;
     c[s] = 0.0f;
   }
   const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
   const uint32_t pairs = L.steps >> 1;
-  {
-    const uint4 w = philox4x32_10(0u, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN, true>(L, w.x, w.y, v, x, c);
-    if (L.steps > 1) step_all<NS, DYN, false>(L, w.z, w.w, v, x, c);
-  }
-  for (uint32_t i = 1; i < pairs; ++i) {
+  for (uint32_t i = 0; i < pairs; ++i) {
     const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN, false>(L, w.x, w.y, v, x, c);
-    step_all<NS, DYN, false>(L, w.z, w.w, v, x, c);
+    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
+    step_all<NS, DYN>(L, w.z, w.w, v, x, c);
   }
-  if ((L.steps & 1u) && pairs > 0) {
+  if (L.steps & 1u) {
     const uint4 w = philox4x32_10(pairs, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN, false>(L, w.x, w.y, v, x, c);
+    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
   }
 }
 
