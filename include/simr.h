@@ -174,6 +174,32 @@ SIMR_API int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const d
                        double* greeks, void* stream);
 
 /*
+ * simr_price without any allocation: the paper has no counterpart to this entry
+ * point.  It is for callers that cannot let a library allocate device memory --
+ * code running while a CUDA graph is being captured (cudaMalloc is not a
+ * stream operation and synchronises the device), serving loops that must never
+ * block on the allocator, and host applications that hand out all device
+ * memory themselves.  It needs no context and calls no cudaMalloc, cudaFree or
+ * allocating library routine: its reduction scratch is one file-scope device
+ * array of 1 MiB + 256 B, which every GPU that loads libsimr holds until the
+ * process exits.
+ *   strikes[n_strikes], price[n_strikes], stderr_out[n_strikes] (nullable):
+ *   DEVICE pointers of the current device only (host pointers: SIMR_EINVAL);
+ *   n_strikes in [1, 32] (larger: SIMR_EINVAL).  Arguments and results are
+ *   those of simr_price with the same seed, option_index and sizes.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Calls on one device share the array, which keeps the last call's
+ * contents (each call clears the words that must start at zero): calls that
+ * overlap on the GPU -- on different streams, or from several host threads --
+ * race and must be serialised by the caller.  A device strike that is not
+ * finite and > 0 gives NaN results for that strike.  Asynchronous on `stream`.
+ */
+SIMR_API int simr_price_noalloc(const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+                                uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index,
+                                double* price, double* stderr_out, void* stream);
+
+/*
  * Wait for `stream` and report any asynchronous device error as a status; also
  * reports (and clears) a device-side argument error such as a device-resident
  * strike that is not finite and > 0 (SIMR_EINVAL).

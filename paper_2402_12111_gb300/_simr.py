@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         L.simr_finalize_sums.argtypes = [vp, H, dp, c_int, c_int, u32, u64, ctypes.c_double, u32, dp, dp, dp, dp,
                                          vp]
         L.simr_sync.argtypes = [vp, vp]
+        L.simr_price_noalloc.argtypes = [H, dp, c_int, c_int, u32, u64, u64, u32, dp, dp, vp]
         _lib = L
         return L
 

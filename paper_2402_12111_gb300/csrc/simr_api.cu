@@ -581,3 +581,30 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
 
 }  // extern "C"
 
+// Helpers shared with other translation units of the library (simr_internal.h).
+namespace simr {
+
+int internal_fail(int code, const char* message) { return fail(code, "%s", message); }
+
+int internal_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+int internal_check_price_args(const simr_heston* model, const double* strikes, int n_strikes, int max_strikes,
+                              uint32_t steps, uint64_t paths) {
+  int rc = check_model(model);
+  if (rc) return rc;
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (paths < 1) return fail(SIMR_EINVAL, "paths must be >= 1");
+  if (!strikes) return fail(SIMR_EINVAL, "strikes is NULL");
+  if (n_strikes < 1 || n_strikes > max_strikes)
+    return fail(SIMR_EINVAL, "n_strikes must lie in [1, %d]", max_strikes);
+  return SIMR_OK;
+}
+
+bool internal_is_device_ptr(const void* p) { return is_device_ptr(p); }
+
+int internal_build_price_launch(const simr_heston* model, int n_strikes, int is_put, uint32_t steps, uint64_t paths,
+                                uint64_t seed, uint32_t option_index, PathLaunch* L) {
+  return build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, 1e-4, 0u, L);
+}
+
+}  // namespace simr

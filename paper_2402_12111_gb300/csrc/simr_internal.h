@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "simr.h"
 #include "simr_device.cuh"
 
 namespace simr {
@@ -66,5 +67,15 @@ cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathO
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);
+
+// Validation and launch building of the C ABI (simr_api.cu), for the other
+// entry points of the library.  They set the thread-local error message.
+int internal_fail(int code, const char* message);
+int internal_cuda_fail(cudaError_t e, const char* what);
+int internal_check_price_args(const simr_heston* model, const double* strikes, int n_strikes, int max_strikes,
+                              uint32_t steps, uint64_t paths);
+bool internal_is_device_ptr(const void* p);
+int internal_build_price_launch(const simr_heston* model, int n_strikes, int is_put, uint32_t steps, uint64_t paths,
+                                uint64_t seed, uint32_t option_index, PathLaunch* L);
 
 }  // namespace simr
