@@ -146,6 +146,32 @@ ScenConst bumped_const(const simr_heston& base, const simr_heston& bumped, uint3
   return pack(d, ratio_m1, bumped.v0);
 }
 
+// FP64 step-0 quantities of a scenario starting from v0 (formulas in simr_device.cuh):
+// out = {a, b, q, C, L, m0, K0p}, returns the branch.
+int first_step64(const simr_heston& m, uint32_t steps, double v0, double out[7]) {
+  double c[9];
+  scen_const64(m, steps, c);
+  const double E = c[0], thE = c[1], c1 = c[2], c2 = c[3], C0 = c[4], Cv = c[5], Cd = c[6];
+  const double m0 = thE + v0 * E, s20 = v0 * c1 + c2;
+  for (int i = 0; i < 7; ++i) out[i] = 0.0;
+  out[5] = m0;
+  out[6] = C0 + (Cv - Cd) * v0;
+  if (!(m0 > 0.0)) return 2;
+  const double psi = s20 / (m0 * m0);
+  if (psi <= 1.5) {
+    const double t = 2.0 / psi;
+    const double b2 = t - 1.0 + std::sqrt(t) * std::sqrt(t - 1.0);
+    out[0] = m0 / (1.0 + b2);
+    out[1] = std::sqrt(b2);
+    return 0;
+  }
+  const double q = 2.0 / (psi + 1.0);
+  out[2] = q;
+  out[3] = m0 / q;
+  out[4] = std::log(q);
+  return 1;
+}
+
 void philox_round_keys(uint64_t seed, uint32_t rk[10][2]) {
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int i = 0; i < 10; ++i) {
@@ -183,6 +209,8 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
   L->disc = std::exp(-m->r * m->T);
   L->paths_total = (double)paths_total;
   L->sc[0] = base_const(*m, steps);
+  simr_heston scen_model[kMaxScen];
+  scen_model[0] = *m;
   int ns = 1, r = 0, g = 0;
   for (int bit = 0; bit < kMaxGreeks; ++bit) {
     if (!((mask >> bit) & 1u)) continue;
@@ -234,11 +262,13 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
       const double v0f = (double)(float)m->v0;
       if (up_ok) {
         iu = ns;
+        scen_model[ns] = up;
         L->sc[ns++] = bumped_const(*m, up, steps);
         hu = (b == SIMR_G_VEGA) ? (double)(float)up.v0 - v0f : h;
       }
       if (dn_ok) {
         id = ns;
+        scen_model[ns] = dn;
         L->sc[ns++] = bumped_const(*m, dn, steps);
         hd = (b == SIMR_G_VEGA) ? v0f - (double)(float)dn.v0 : h;
       }
@@ -251,6 +281,30 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
     L->denom[g++] = denom;
   }
   L->n_scen = ns;
+  // step-0 constants: base full values, bumped scenarios deltas to the base's FP32 values
+  double fb[7];
+  const int br0 = first_step64(*m, steps, (double)L->sc[0].v0, fb);
+  L->first_split = ns > 1 ? 1 : 0;
+  for (int s = 0; s < ns; ++s) {
+    double f[7];
+    const int br = s == 0 ? br0 : first_step64(scen_model[s], steps, (double)L->sc[s].v0, f);
+    if (s == 0) {
+      for (int i = 0; i < 7; ++i) f[i] = fb[i];
+    } else {
+      if (br != br0) L->first_split = 0;  // a bump moved step 0 across a branch: plain step 0
+      for (int i = 0; i < 7; ++i)
+        if (i != 2) f[i] -= (double)(float)fb[i];
+    }
+    FirstConst& fc = L->f0[s];
+    fc.a = (float)f[0];
+    fc.b = (float)f[1];
+    fc.q = (float)f[2];
+    fc.C = (float)f[3];
+    fc.L = (float)f[4];
+    fc.m0 = (float)f[5];
+    fc.K0p = (float)f[6];
+    fc.branch = br;
+  }
   return SIMR_OK;
 }
 

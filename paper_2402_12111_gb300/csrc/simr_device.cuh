@@ -43,6 +43,18 @@ struct ScenConst {
   float pad;
 };
 
+// First-step constants of a scenario (all paths share v0, so every step-0
+// quantity except the draws is a per-scenario constant).  Computed on the host
+// in FP64: base scenario full values, bumped scenarios deltas to the base's
+// FP32 values -- except q (decision threshold) and v0, which are full values.
+//   quadratic: v1 = a (b + Z_V)^2, v1 - m0 = a (Z_V (Z_V + 2b) - 1)
+//   exponential: v1 = 0 if 1 - U_V >= q, else C (L - ln(1 - U_V)), C = m0/q, L = ln q
+//   increment: x1 = K0p + Cv v1 + Cdl (v1 - m0) + sK3 sqrt(v0 + v1) Z_X, K0p = C0 + (Cv - Cd) v0
+struct FirstConst {
+  float a, b, q, C, L, m0, K0p;
+  int branch;  // 0 quadratic, 1 exponential, 2 zero mean
+};
+
 // ---------------------------------------------------------------- PTX ----
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -211,6 +223,56 @@ __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst&
   comp = (t - x) - y;
   x = t;
   v = vn;
+}
+
+// a + b rounded, plus the exact rounding error (Knuth's TwoSum; plain adds only).
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// Step 0 of a scenario in a common-random-number launch: base first-step
+// constants fb plus deltas fd (zero for the base scenario itself), base step
+// constants b plus deltas d.  Each delta enters through the exact rounding
+// error of a sum with a path-dependent operand, so no quantisation of the
+// bump is shared by all paths.
+__device__ __forceinline__ void step0_crn(const FirstConst& fb, const FirstConst& fd, const ScenConst& b,
+                                          const ScenConst& d, float v0, float omu, float zv, float zx, float& v,
+                                          float& x, float& comp) {
+  float v1 = 0.0f, dl = 0.0f;
+  if (fb.branch == 0) {
+    float e;
+    const float hi = two_sum(fb.b, zv, e);
+    const float bz = hi + (e + fd.b);
+    const float bz2 = bz * bz;
+    v1 = fmaf(fb.a, bz2, fd.a * bz2);
+    float g = fmaf(zv, zv + 2.0f * fb.b, -1.0f);
+    g = fmaf(2.0f * fd.b, zv, g);
+    dl = fmaf(fb.a, g, fd.a * g);
+  } else if (fb.branch == 1) {
+    if (omu < fd.q) {  // fd.q: this scenario's own threshold
+      const float lnomu = 0.69314718055994531f * lg2_approx(omu);
+      float e;
+      const float hi = two_sum(fb.L, -lnomu, e);
+      const float w = hi + (e + fd.L);
+      v1 = fmaf(fb.C, w, fd.C * w);
+    }
+    float e;
+    const float hi = two_sum(v1, -fb.m0, e);
+    dl = hi + (e - fd.m0);
+  }
+  const float q = sqrt_approx(v0 + v1);
+  float inc = fmaf(b.Cv, v1, fb.K0p);
+  inc = fmaf(b.Cdl, dl, inc);
+  inc = fmaf(b.sK3 * q, zx, inc);
+  float sm = fmaf(d.Cv, v1, fd.K0p);
+  sm = fmaf(d.Cdl, dl, sm);
+  sm = fmaf(d.sK3 * q, zx, sm);
+  x = inc + sm;
+  comp = 0.0f;
+  v = v1;
 }
 
 // AssetPathExponential (paper Sec. 5): S_T = S0 e^{x} with the Kahan remainder

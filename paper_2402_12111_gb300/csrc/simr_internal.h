@@ -34,6 +34,8 @@ struct PathLaunch {
   double rho_w;           // e^{h_r T} - e^{-h_r T} = 2 sinh(h_r T): band width factor
   int32_t resim_up[kMaxResim], resim_dn[kMaxResim];  // scenario of each re-simulated Greek
   ScenConst sc[kMaxScen];
+  FirstConst f0[kMaxScen];  // step-0 constants (used when first_split != 0)
+  int32_t first_split;      // 1: step 0 of every scenario through step0_crn
   // finalisation (FP64)
   double disc;            // e^{-rT}
   double paths_total;     // denominator of the mean

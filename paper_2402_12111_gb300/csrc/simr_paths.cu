@@ -111,6 +111,25 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
   }
 }
 
+// Step 0 of every scenario of a common-random-number launch (see step0_crn).
+template <int NS, bool DYN>
+__device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
+                                          float (&x)[NS], float (&c)[NS]) {
+  const float xv = centered_uniform(w_v);
+  const float omu = 0.5f * (1.0f - xv);
+  const float zv = norminv_centered(xv);
+  const float zx = norminv_centered(centered_uniform(w_x));
+  const ScenConst zero{};
+  FirstConst fz = L.f0[0];
+  fz.a = fz.b = fz.C = fz.L = fz.m0 = fz.K0p = 0.0f;  // base: zero deltas, its own threshold
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (DYN && s >= L.n_scen) break;
+    step0_crn(L.f0[0], s == 0 ? fz : L.f0[s], L.sc[0], s == 0 ? zero : L.sc[s], L.sc[s].v0, omu, zv, zx, v[s],
+              x[s], c[s]);
+  }
+}
+
 template <int NS, bool DYN>
 __device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, float (&v)[NS], float (&x)[NS],
                                          float (&c)[NS]) {
@@ -122,12 +141,19 @@ __device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, flo
   }
   const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
   const uint32_t pairs = L.steps >> 1;
-  for (uint32_t i = 0; i < pairs; ++i) {
+  uint32_t i0 = 0;
+  if (NS > 1 && L.first_split) {
+    const uint4 w = philox4x32_10(0u, plo, phi, L.option_index, L.rk);
+    step0_all<NS, DYN>(L, w.x, w.y, v, x, c);
+    if (L.steps > 1) step_all<NS, DYN>(L, w.z, w.w, v, x, c);
+    i0 = 1;
+  }
+  for (uint32_t i = i0; i < pairs; ++i) {
     const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
     step_all<NS, DYN>(L, w.x, w.y, v, x, c);
     step_all<NS, DYN>(L, w.z, w.w, v, x, c);
   }
-  if (L.steps & 1u) {
+  if ((L.steps & 1u) && pairs >= i0) {  // odd last step (step 0 itself when steps == 1 without the split)
     const uint4 w = philox4x32_10(pairs, plo, phi, L.option_index, L.rk);
     step_all<NS, DYN>(L, w.x, w.y, v, x, c);
   }
@@ -169,7 +195,7 @@ __device__ __forceinline__ void write_results(const PathLaunch& L, int k, const 
 // Dynamic shared memory: accumulators [warps][n_acc][nk_pad] (FP64), then the
 // strike constants [nk_pad] (StrikeConst), then a flag word.
 template <int NS, int TILE, bool DYN>
-__global__ void __launch_bounds__(256) heston_paths_kernel(const __grid_constant__ PathLaunch L,
+__global__ void __launch_bounds__(256, (NS <= 3 ? 4 : NS <= 5 ? 3 : 2)) heston_paths_kernel(const __grid_constant__ PathLaunch L,
                                                            const double* __restrict__ strikes,
                                                            PathOutputs out, double* __restrict__ partials,
                                                            unsigned int* __restrict__ ticket) {
