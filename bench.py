@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
     return ap.parse_args()
 
@@ -306,6 +307,38 @@ def run_native(args):
                "h2d_bytes_per_step": K_host.numel() * 8, "d2h_bytes_per_step": (p_h.numel() + g_h.numel()) * 8,
                "steps": e2e_steps}
 
+    # adjoint vs bump-and-revalue on the same GPU and workload (the adjoint workload:
+    # 7 sensitivities d/d{S0, v0, kappa, theta, sigma, rho, r}, checkpoint every 16 steps)
+    adj = None
+    if not args.no_adjoint:
+        fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
+        legs = {
+            "price_ms": lambda: simr.price(w.model, K, w.is_put, w.steps, w.paths, w.seed),
+            "fd7_ms": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=fd7,
+                                             rel_bump=w.rel_bump),
+            "adjoint_ms": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed, ckpt_every=16),
+        }
+        adj = {}
+        reps = max(3, min(args.steps, 10))
+        for name, fn in legs.items():
+            for _ in range(3):
+                fn()
+                flush.zero_()
+            times = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                flush.zero_()
+                times.append((a, b))
+            torch.cuda.synchronize()
+            adj[name] = sum(x.elapsed_time(y) for x, y in times) / reps
+        adj["speedup_vs_fd"] = adj["fd7_ms"] / adj["adjoint_ms"]
+        adj["cost_vs_price"] = adj["adjoint_ms"] / adj["price_ms"]
+        adj["ckpt_every"] = 16
+        adj["sensitivities"] = list(fd7)
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -336,6 +369,7 @@ def run_native(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": args.steps,
+        "adjoint_vs_fd": adj,
         "kernel_source_sha": sha,
         "wall_s_timed_region": t_wall,
     }

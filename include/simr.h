@@ -143,6 +143,42 @@ SIMR_API int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const doubl
                    void* stream);
 
 /*
+ * Pathwise adjoint (reverse-mode) Greeks: the price and its sensitivities to
+ * (S0, v0, kappa, theta, sigma, rho, r) per strike from ONE kernel launch.  Per
+ * path, a forward pass (the paper's VariancePathQE and LogPricePathQE stages,
+ * Sec. 4-5) keeps the variance every ckpt_every steps; a reverse sweep
+ * recomputes each segment from its checkpoint (regenerating the segment's
+ * Philox draws) and differentiates the steps backwards with the forward
+ * branches held fixed.  dP/dq = e^{-rT} mean[f'(S_T) S_T dx_T/dq] with
+ * f' = 1{S_T > K} (call) or -1{S_T < K} (put); dP/dS0 = e^{-rT} mean[f' S_T/S0];
+ * dP/dr = e^{-rT} mean[f' S_T T] - T P.  Pathwise derivatives miss the jump of
+ * the QE map where a bump would switch a path's branch, so they differ from
+ * bump-and-revalue by that (small) term.
+ *   ckpt_every   in   even number of steps per checkpoint segment, in [2, 1024];
+ *                     0 = about sqrt(steps).  Shared memory bounds
+ *                     (steps/ckpt_every + ckpt_every); SIMR_EUNSUPPORTED beyond it.
+ *   price[n_strikes], stderr_out[n_strikes] (nullable)   out
+ *   grad[n_strikes * 7]   out  row-major [strike][S0, v0, kappa, theta, sigma, rho, r]
+ * n_strikes in [1, 256].  The rho column is NaN when |rho| = 1 (the pathwise
+ * derivative of sqrt(1 - rho^2) does not exist there).
+ */
+SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes,
+                                 int is_put, uint32_t steps, uint64_t paths, uint64_t seed,
+                                 uint32_t option_index, uint32_t ckpt_every, double* price, double* stderr_out,
+                                 double* grad, void* stream);
+
+/*
+ * Per-path pathwise derivatives: for paths [path_begin, path_begin + n_paths),
+ * x_T[i] = ln(S_T/S0) and grad[i * 5 + j] = d x_T / d(v0, kappa, theta, sigma,
+ * rho)[j] (FP32), by the same forward pass and reverse sweep as
+ * simr_greeks_adjoint (dx_T/dS0 = 0 and dx_T/dr = T need no sweep).  Custom
+ * payoffs g(S_T) get dE[g]/dq = E[g'(S_T) S_T dx_T/dq].  Device pointers only.
+ */
+SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin,
+                                uint64_t n_paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,
+                                float* x_T, float* grad, void* stream);
+
+/*
  * Terminal state of paths [path_begin, path_begin + n_paths): x_T = ln(S_T/S0)
  * and v_T per path, FP32, the state the paper's writeLongstaffSchwartzPath stage
  * writes out (Sec. 5).  x_T[n_paths], v_T[n_paths] out; v_T may be NULL.

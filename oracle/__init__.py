@@ -74,6 +74,7 @@ def lib():
             L.oracle_qe_step.restype = ctypes.c_double
             L.oracle_qe_step_array.argtypes = [H, u32, ctypes.c_double, dp, dp, i64]
             L.oracle_terminal.argtypes = [H, u32, u64, u32, u64, i64, dp, dp, dp]
+            L.oracle_terminal_diag.argtypes = [H, u32, u64, u32, u64, i64, dp, dp, dp, dp]
             L.oracle_price.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
             L.oracle_greeks_fd.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, ctypes.c_double, u32, dp, dp]
             L.oracle_path_grad_reverse.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
@@ -161,6 +162,16 @@ def terminal(model, steps: int, seed: int, path_begin: int, n_paths: int, option
     if rc != 0:
         raise ValueError(f"oracle_terminal failed ({rc})")
     return x, v, mg
+
+
+def terminal_diag(model, steps: int, seed: int, path_begin: int, n_paths: int, option_index: int = 0):
+    """(x_T, v_T, margin, cond) per path; cond = min |b + Z_V| / (1 + b) over quadratic steps."""
+    x, v, mg, cd = (np.empty(n_paths) for _ in range(4))
+    rc = lib().oracle_terminal_diag(ctypes.byref(_model(model)), steps, seed, option_index, path_begin, n_paths,
+                                    _dp(x), _dp(v), _dp(mg), _dp(cd))
+    if rc != 0:
+        raise ValueError(f"oracle_terminal_diag failed ({rc})")
+    return x, v, mg, cd
 
 
 def price(model, strikes, is_put: bool, steps: int, paths: int, seed: int, option_index: int = 0):

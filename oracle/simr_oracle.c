@@ -195,9 +195,14 @@ void oracle_qe_constants(const oracle_heston* m, uint32_t steps, double out[9]) 
  * *branch receives 0 (quadratic), 1 (exponential, v' > 0), 2 (exponential, v' = 0)
  * or 3 (m = 0: zero mean and variance, v' = 0).  *margin receives the distance of
  * the branch decisions from their thresholds: |psi - psi_c| / psi_c, and in the
- * exponential branch also |U_V - p|.
+ * exponential branch also |U_V - p|.  *cond (may be NULL) receives, in the
+ * quadratic branch, |b + Z_V| / (1 + b): small values mean v' = a (b + Z_V)^2 is
+ * a cancellation that a lower-precision evaluation resolves poorly (diagnostic
+ * only, +inf in the other branches).
  */
-double oracle_qe_variance_step(double v, double u_v, const double* k, int* branch, double* margin) {
+double oracle_qe_variance_step(double v, double u_v, const double* k, int* branch, double* margin,
+                               double* cond) {
+  if (cond) *cond = INFINITY;
   const double theta_ = k[9];  /* theta is appended after the 9 constants */
   double E = k[1], c1 = k[2], c2 = k[3];
   double m = theta_ + (v - theta_) * E;
@@ -217,6 +222,7 @@ double oracle_qe_variance_step(double v, double u_v, const double* k, int* branc
     double zv = oracle_norminv(u_v);
     *branch = 0;
     *margin = mg;
+    if (cond) *cond = fabs(b + zv) / (1.0 + b);
     return a * (b + zv) * (b + zv);
   }
   double p = (psi - 1.0) / (psi + 1.0);
@@ -243,15 +249,16 @@ static void step_constants(const oracle_heston* m, uint32_t steps, double k[10])
  */
 static void simulate_path(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
                           uint32_t option_index, uint64_t path, double* x_out, double* v_out,
-                          double* margin_out) {
-  double v = m->v0, x = 0.0, min_margin = INFINITY;
+                          double* margin_out, double* cond_out) {
+  double v = m->v0, x = 0.0, min_margin = INFINITY, min_cond = INFINITY;
   for (uint32_t n = 0; n < steps; ++n) {
     double u_v, u_x;
     oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
     int branch;
-    double mg;
-    double v_next = oracle_qe_variance_step(v, u_v, k, &branch, &mg);
+    double mg, cd;
+    double v_next = oracle_qe_variance_step(v, u_v, k, &branch, &mg, &cd);
     if (mg < min_margin) min_margin = mg;
+    if (cd < min_cond) min_cond = cd;
     /* LogPricePathQE: x += K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X */
     double z_x = oracle_norminv(u_x);
     x += k[4] + k[5] * v + k[6] * v_next + sqrt(k[7] * v + k[8] * v_next) * z_x;
@@ -260,6 +267,7 @@ static void simulate_path(const oracle_heston* m, const double* k, uint32_t step
   *x_out = x;
   *v_out = v;
   if (margin_out) *margin_out = min_margin;
+  if (cond_out) *cond_out = min_cond;
 }
 
 int oracle_max_threads(void) {
@@ -291,7 +299,23 @@ int oracle_terminal(const oracle_heston* m, uint32_t steps, uint64_t seed, uint3
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n_paths; ++i) {
     simulate_path(m, k, steps, seed, option_index, path_begin + (uint64_t)i, &x_T[i], &v_T[i],
-                  margin ? &margin[i] : NULL);
+                  margin ? &margin[i] : NULL, NULL);
+  }
+  return 0;
+}
+
+/* As oracle_terminal, plus the per-path conditioning diagnostic cond (the
+ * smallest |b + Z_V| / (1 + b) over the path's quadratic-branch steps). */
+int oracle_terminal_diag(const oracle_heston* m, uint32_t steps, uint64_t seed, uint32_t option_index,
+                         uint64_t path_begin, int64_t n_paths, double* x_T, double* v_T, double* margin,
+                         double* cond) {
+  if (steps == 0 || n_paths < 0) return -1;
+  double k[10];
+  step_constants(m, steps, k);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_paths; ++i) {
+    simulate_path(m, k, steps, seed, option_index, path_begin + (uint64_t)i, &x_T[i], &v_T[i], &margin[i],
+                  &cond[i]);
   }
   return 0;
 }
@@ -468,7 +492,7 @@ static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps
     double u_v, u_x, mg;
     int br;
     oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
-    double vn = oracle_qe_variance_step(v, u_v, k, &br, &mg);
+    double vn = oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
     x += k[4] + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
     v = vn;
     v_hist[n + 1] = v;
@@ -562,7 +586,7 @@ static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps
 double oracle_qe_step(const oracle_heston* m, uint32_t steps, double v, double u_v, int* branch) {
   double k[10], mg;
   step_constants(m, steps, k);
-  return oracle_qe_variance_step(v, u_v, k, branch, &mg);
+  return oracle_qe_variance_step(v, u_v, k, branch, &mg, NULL);
 }
 
 /* The step applied to one variance v and many uniforms (moment checks). */
@@ -574,7 +598,7 @@ void oracle_qe_step_array(const oracle_heston* m, uint32_t steps, double v, cons
   for (int64_t i = 0; i < n; ++i) {
     int br;
     double mg;
-    v_next[i] = oracle_qe_variance_step(v, u_v[i], k, &br, &mg);
+    v_next[i] = oracle_qe_variance_step(v, u_v[i], k, &br, &mg, NULL);
   }
 }
 

@@ -5,7 +5,10 @@ libsimr.so's sm_103a kernels behind the C ABI of include/simr.h):
 
   price(model, strikes, ...)            -> (price, stderr)      simr_price
   greeks_fd(model, strikes, ...)        -> (price, greeks)      simr_greeks_fd
+  greeks_adjoint(model, strikes, ...)   -> (price, se, grad)    simr_greeks_adjoint
+  heston_price(params, strikes, T, ...) differentiable price    torch.autograd.Function over the adjoint
   paths_terminal(model, steps, ...)     -> (x_T, v_T)           simr_paths_terminal
+  paths_adjoint(model, steps, ...)      -> (x_T, dx_T/dparams)  simr_paths_adjoint
   path_sums / finalize_sums                                     sharded runs
   sharded.price_greeks(...)             multi-rank path sharding (torch.distributed)
 
@@ -13,9 +16,10 @@ libsimr.so's sm_103a kernels behind the C ABI of include/simr.h):
 Tensors on a CUDA device give an asynchronous call on the current stream; CPU
 tensors or sequences give a synchronous call with host buffers.
 """
-from .api import finalize_sums, greeks_fd, path_sums, paths_terminal, price, sync  # noqa: F401
+from .api import (ADJOINT_COLUMNS, HestonAdjoint, finalize_sums, greeks_adjoint, greeks_fd,  # noqa: F401
+                  heston_price, path_sums, paths_adjoint, paths_terminal, price, sync)
 from ._simr import (G_ALL, G_CORR, G_DELTA, G_GAMMA, G_KAPPA, G_LRVAR, G_RHO, G_THETA, G_VEGA,  # noqa: F401
                     G_VOLVOL, GREEK_BITS, Heston, SimrError, greek_mask, load)
 
-__all__ = ["price", "greeks_fd", "paths_terminal", "path_sums", "finalize_sums", "sync", "Heston", "SimrError",
+__all__ = ["price", "greeks_fd", "greeks_adjoint", "heston_price", "HestonAdjoint", "ADJOINT_COLUMNS", "paths_terminal", "paths_adjoint", "path_sums", "finalize_sums", "sync", "Heston", "SimrError",
            "greek_mask", "load", "GREEK_BITS"]

@@ -71,6 +71,70 @@ def greeks_fd(model, strikes, is_put: bool = False, steps: int = 64, paths: int 
     return p, g
 
 
+ADJOINT_COLUMNS = ("S0", "v0", "kappa", "theta", "sigma", "rho", "r")
+
+
+def greeks_adjoint(model, strikes, is_put: bool = False, steps: int = 64, paths: int = 65536, seed: int = 1,
+                   ckpt_every: int = 0, option_index: int = 0, stderr: bool = True, device=None, stream=None):
+    """simr_greeks_adjoint: (price[n_K], stderr[n_K] or None, grad[n_K, 7]) with grad columns
+    d/d(S0, v0, kappa, theta, sigma, rho, r), from one pathwise reverse-mode launch."""
+    K = _as_f64(strikes)
+    p = torch.empty(K.numel(), dtype=torch.float64, device=K.device)
+    se = torch.empty_like(p) if stderr else None
+    g = torch.empty(K.numel(), 7, dtype=torch.float64, device=K.device)
+    L = S.load()
+    ctx = S.context(_device_index(K, device))
+    S.check(L.simr_greeks_adjoint(ctx, ctypes.byref(S.as_heston(model)), _ptr(K), K.numel(), int(bool(is_put)),
+                                  int(steps), int(paths), int(seed), int(option_index), int(ckpt_every), _ptr(p),
+                                  _ptr(se), _ptr(g), _stream(K, stream)))
+    return p, se, g
+
+
+class HestonAdjoint(torch.autograd.Function):
+    """Monte Carlo price as a differentiable function of the model parameters.
+
+    forward(params, strikes, T, is_put, steps, paths, seed, ckpt_every) with
+    params = (S0, v0, kappa, theta, sigma, rho, r) returns the price per strike;
+    the same launch computes the pathwise adjoint Jacobian d price / d params,
+    so backward is grad_out @ J (no second pass over the paths).
+    """
+
+    @staticmethod
+    def forward(ctx, params, strikes, T, is_put=False, steps=64, paths=65536, seed=1, ckpt_every=0):
+        vals = params.detach().double().cpu().tolist()
+        model = dict(zip(ADJOINT_COLUMNS, vals))
+        model["T"] = float(T)
+        price, _, jac = greeks_adjoint(model, strikes, is_put, steps, paths, seed, ckpt_every, stderr=False)
+        ctx.save_for_backward(jac)
+        ctx.params_meta = (params.dtype, params.device)
+        return price
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (jac,) = ctx.saved_tensors
+        g = grad_out.to(jac.dtype).to(jac.device) @ jac
+        dtype, device = ctx.params_meta
+        return g.to(device=device, dtype=dtype), None, None, None, None, None, None, None
+
+
+def heston_price(params, strikes, T, is_put=False, steps=64, paths=65536, seed=1, ckpt_every=0):
+    """Differentiable price per strike (see HestonAdjoint)."""
+    return HestonAdjoint.apply(params, strikes, T, is_put, steps, paths, seed, ckpt_every)
+
+
+def paths_adjoint(model, steps: int, path_begin: int, n_paths: int, seed: int = 1, ckpt_every: int = 0,
+                  option_index: int = 0, device="cuda", stream=None):
+    """simr_paths_adjoint: (x_T[n], grad[n, 5]) FP32, grad = d x_T / d(v0, kappa, theta, sigma, rho)."""
+    dev = torch.device(device)
+    x = torch.empty(int(n_paths), dtype=torch.float32, device=dev)
+    g = torch.empty(int(n_paths), 5, dtype=torch.float32, device=dev)
+    L = S.load()
+    ctx = S.context(_device_index(x, device))
+    S.check(L.simr_paths_adjoint(ctx, ctypes.byref(S.as_heston(model)), int(steps), int(path_begin), int(n_paths),
+                                 int(seed), int(option_index), int(ckpt_every), _ptr(x), _ptr(g), _stream(x, stream)))
+    return x, g
+
+
 def paths_terminal(model, steps: int, path_begin: int, n_paths: int, seed: int = 1, option_index: int = 0,
                    device="cuda", with_variance: bool = True, stream=None):
     """simr_paths_terminal: (x_T, v_T) FP32 per path, x_T = ln(S_T/S0)."""

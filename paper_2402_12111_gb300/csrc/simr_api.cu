@@ -308,6 +308,45 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
   return SIMR_OK;
 }
 
+// Checkpoint interval and the FP64-derived parameter-map constants of the
+// adjoint kernel (formulas beside the kernel in simr_adjoint.cu).
+int build_adjoint(const simr_heston& m, uint32_t steps, uint32_t ckpt_every, AdjConst* A) {
+  uint32_t k = ckpt_every;
+  if (k == 0) {  // about sqrt(steps) steps per segment, even
+    k = 2;
+    while ((uint64_t)k * k < steps) k += 2;
+  }
+  if ((k & 1u) || k < 2 || k > 1024) return fail(SIMR_EINVAL, "ckpt_every must be 0 or an even number in [2, 1024]");
+  const double dt = m.T / (double)steps, kdt = m.kappa * dt;
+  const double E = std::exp(-kdt), omE = -std::expm1(-kdt), s2 = m.sigma * m.sigma, rs = m.rho / m.sigma;
+  const double dE_dk = -dt * E;
+  const double D = omE - 0.5 * kdt * (1.0 + E);
+  const double B = 1.0 + 0.5 * kdt;
+  const double sK3 = std::sqrt(0.5 * dt * (1.0 - m.rho * m.rho));
+  A->ckpt_every = (int32_t)k;
+  A->n_seg = (int32_t)((steps + k - 1) / k);
+  A->theta = (float)m.theta;
+  A->invS0 = (float)(1.0 / m.S0);
+  A->T = (float)m.T;
+  A->dE_dk = dE_dk;
+  A->omE = omE;
+  A->dc1_dk = s2 * ((1.0 - 2.0 * E) * dE_dk / m.kappa - E * omE / (m.kappa * m.kappa));
+  A->dc2_dk = m.theta * s2 * (-omE * dE_dk / m.kappa - omE * omE / (2.0 * m.kappa * m.kappa));
+  A->dc2_dth = s2 * omE * omE / (2.0 * m.kappa);
+  A->dCd_dk = rs * (-dE_dk - 0.5 * dt * (1.0 + E) - 0.5 * kdt * dE_dk);
+  A->dCdl_dk = rs * 0.5 * dt;
+  A->N_Cd = (double)steps * rs * D;
+  A->two_over_sigma = 2.0 / m.sigma;
+  A->c1 = s2 * E * omE / m.kappa;
+  A->c2 = m.theta * s2 * omE * omE / (2.0 * m.kappa);
+  A->Cd_over_sigma = rs * D / m.sigma;
+  A->Cdl_over_sigma = rs * B / m.sigma;
+  A->D_over_sigma = D / m.sigma;
+  A->B_over_sigma = B / m.sigma;
+  A->dsK3_drho = sK3 > 0.0 ? -m.rho * dt / (2.0 * sK3) : __builtin_nan("");
+  return SIMR_OK;
+}
+
 int check_common(simr_ctx* ctx, const simr_heston* m, const double* strikes, int n_strikes, int max_strikes,
                  uint32_t steps, uint64_t paths) {
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
@@ -533,6 +572,67 @@ int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strike
   o.n[2] = (size_t)n_strikes * popcount9(greek_mask);
   if ((rc = stage_outputs(ctx, &o))) return rc;
   return run_paths(ctx, L, ks, o, st);
+}
+
+int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
+                        uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,
+                        double* price, double* stderr_out, double* grad, void* stream) {
+  int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
+  if (rc) return rc;
+  if (!price || !grad) return fail(SIMR_EINVAL, "price and grad must be non-NULL");
+  AdjConst A;
+  if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  PathLaunch L;
+  if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, 1e-4, 0u, &L)))
+    return rc;
+  L.n_acc = 9;  // the adjoint's accumulators: f, f^2 and 7 sensitivities per strike
+  if (adjoint_smem_bytes(L, A) > 200 * 1024)
+    return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
+                A.ckpt_every, steps);
+  const double* ks = nullptr;
+  if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_strikes;
+  o.user[1] = stderr_out;
+  o.n[1] = n_strikes;
+  o.user[2] = grad;
+  o.n[2] = (size_t)n_strikes * 7;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  if ((rc = ensure(&ctx->partials, &ctx->partial_doubles, adjoint_scratch_doubles(L, ctx->num_sms),
+                   "reduction scratch")))
+    return rc;
+  AdjOutputs out{o.dev[0], o.dev[1], o.dev[2], ctx->status};
+  Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles};
+  cudaError_t e = launch_adjoint(L, A, ks, out, sc, ctx->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernel");
+  return finish_outputs(ctx, o, st);
+}
+
+int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin, uint64_t n_paths,
+                       uint64_t seed, uint32_t option_index, uint32_t ckpt_every, float* x_T, float* grad,
+                       void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  int rc = check_model(model);
+  if (rc) return rc;
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (n_paths < 1 || n_paths > (1ull << 31)) return fail(SIMR_EINVAL, "n_paths must lie in [1, 2^31]");
+  if (!x_T || !grad) return fail(SIMR_EINVAL, "x_T and grad must be non-NULL");
+  if (!is_device_ptr(x_T) || !is_device_ptr(grad)) return fail(SIMR_EINVAL, "x_T and grad must be device pointers");
+  AdjConst A;
+  if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
+  if ((size_t)(A.n_seg + 3 * A.ckpt_every) * 128 * sizeof(float) > 200 * 1024)
+    return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
+                A.ckpt_every, steps);
+  if ((rc = with_device(ctx))) return rc;
+  PathLaunch L;
+  if ((rc = build_launch(model, 1, 0, steps, path_begin, n_paths, n_paths, seed, option_index, 1e-4, 0u, &L)))
+    return rc;
+  cudaError_t e = launch_paths_adjoint(L, A, x_T, grad, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the per-path adjoint kernel");
+  return SIMR_OK;
 }
 
 int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,

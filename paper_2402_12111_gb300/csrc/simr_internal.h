@@ -51,6 +51,27 @@ struct PathOutputs {
   int* status;     // device status word: bit 0 = invalid strike seen
 };
 
+// Constants of the adjoint kernel: checkpointing, and the FP64-derived
+// derivatives of the per-step constants with respect to the parameters.
+// The map from the sweep's sums to the parameters runs once per path in FP64:
+// the kappa sensitivity, for one, is a small residual of much larger terms.
+struct AdjConst {
+  int32_t ckpt_every;  // even, >= 2
+  int32_t n_seg;       // ceil(steps / ckpt_every)
+  float theta, invS0, T;
+  double dE_dk, omE, dc1_dk, dc2_dk, dc2_dth;
+  double dCd_dk, dCdl_dk, N_Cd;
+  double two_over_sigma, c1, c2, Cd_over_sigma, Cdl_over_sigma;
+  double D_over_sigma, B_over_sigma, dsK3_drho;
+};
+
+struct AdjOutputs {
+  double* price;    // [n_strikes]
+  double* stderr_;  // [n_strikes] or null
+  double* grad;     // [n_strikes][7]: S0, v0, kappa, theta, sigma, rho, r
+  int* status;
+};
+
 struct Scratch {
   double* partials;      // [grid][n_acc * nk_pad]
   unsigned int* ticket;  // zero between launches
@@ -66,6 +87,14 @@ size_t paths_scratch_doubles(const PathLaunch& L, int num_sms);
 
 // Normalise combined raw sums [n_strikes][n_acc] into the outputs.
 cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathOutputs& out, cudaStream_t stream);
+
+// Pathwise adjoint Greeks (price + 7 sensitivities per strike).
+cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
+                           const Scratch& s, int num_sms, cudaStream_t stream);
+size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms);
+size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A);
+// Per-path x_T and d x_T / d(v0, kappa, theta, sigma, rho) ([n][5]).
+cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream);
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);
