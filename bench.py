@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
+    ap.add_argument("--no-book", action="store_true", help="skip the 1,024-option heterogeneous book leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
     return ap.parse_args()
 
@@ -339,6 +340,28 @@ def run_native(args):
         adj["ckpt_every"] = 16
         adj["sensitivities"] = list(fd7)
 
+    # heterogeneous book: 1,024 options (log-uniform steps and paths), one persistent launch
+    # per submission, replayed from a captured CUDA graph; prices, then prices + adjoint Greeks
+    book = None
+    if not args.no_book:
+        opts = workloads.book()
+        ps_book = sum(o["steps"] * o["paths"] for o in opts)
+        book = {"options": len(opts), "path_steps": ps_book}
+        for name, adj_flag in (("price", False), ("adjoint", True)):
+            simr.batch(opts, seed=1, adjoint=adj_flag, graph=True)  # autotune + capture
+            simr.batch(opts, seed=1, adjoint=adj_flag, graph=True)
+            torch.cuda.synchronize()
+            reps = 3
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                simr.batch(opts, seed=1, adjoint=adj_flag, graph=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_b = a.elapsed_time(b) / reps
+            book[f"{name}_ms"] = ms_b
+            book[f"{name}_path_steps_per_s"] = ps_book / (ms_b * 1e-3)
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -370,6 +393,7 @@ def run_native(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "adjoint_vs_fd": adj,
+        "book": book,
         "kernel_source_sha": sha,
         "wall_s_timed_region": t_wall,
     }

@@ -83,6 +83,20 @@ typedef struct {
   double rho;   /* spot/variance correlation     */
 } simr_heston;
 
+/* One option of a batched book (simr_batch_submit). */
+typedef struct {
+  simr_heston m;   /* model and market                */
+  double K;        /* strike                           */
+  int32_t is_put;  /* 0 call, 1 put                    */
+  uint32_t steps;  /* time steps                       */
+  uint64_t paths;  /* Monte Carlo paths                */
+} simr_option;
+
+/* simr_batch_submit flags */
+#define SIMR_BATCH_ADJOINT (1u << 0)      /* also the 7 pathwise sensitivities per option       */
+#define SIMR_BATCH_GRAPH (1u << 1)        /* capture the launch in a CUDA graph; replay on repeat */
+#define SIMR_BATCH_NO_AUTOTUNE (1u << 2)  /* skip the first-call chunk-size search              */
+
 /* Greek selection bits for simr_greeks_fd; output columns follow bit order. */
 #define SIMR_G_DELTA (1u << 0)  /* d/dS0, analytic S-bump on the same path   */
 #define SIMR_G_GAMMA (1u << 1)  /* d2/dS0^2, same path                       */
@@ -166,6 +180,27 @@ SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const 
                                  int is_put, uint32_t steps, uint64_t paths, uint64_t seed,
                                  uint32_t option_index, uint32_t ckpt_every, double* price, double* stderr_out,
                                  double* grad, void* stream);
+
+/*
+ * A heterogeneous book of European options in one persistent launch: every
+ * option has its own model, strike, steps and paths; option i uses Philox
+ * counter word 3 = i (so its paths are those of simr_price with option_index i).
+ * The library cuts each option's paths into work items of `chunk` paths,
+ * longest options first; the kernel's warps take items from an atomic queue
+ * (the paper's multi-CU replication, Sec. 6, as dynamic load balancing over one
+ * GPU's SMs) and a second kernel sums each option's item rows in a fixed order.
+ *   opts[n_opts]   in   HOST array; n_opts in [1, 2^22]
+ *   flags          in   SIMR_BATCH_* (0 = prices only)
+ *   price[n_opts], stderr_out[n_opts] (nullable)   out, caller's order
+ *   grad[n_opts * 7]   out (SIMR_BATCH_ADJOINT): d/d{S0, v0, kappa, theta, sigma, rho, r}
+ * chunk is chosen by timing three candidates on the first submission of each
+ * book shape (a book's size class, cached in the context): that first call
+ * prices the book three more times.  With SIMR_BATCH_GRAPH the upload-free part
+ * of the call (queue reset, batch kernel, reduction) is captured once per
+ * (book, seed, flags, output buffers) and replayed afterwards.
+ */
+SIMR_API int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64_t seed, uint32_t flags,
+                               double* price, double* stderr_out, double* grad, void* stream);
 
 /*
  * Per-path pathwise derivatives: for paths [path_begin, path_begin + n_paths),

@@ -38,6 +38,16 @@ class Heston(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in MODEL_FIELDS]
 
 
+class Option(ctypes.Structure):
+    """simr_option: model, strike, put flag, steps, paths."""
+
+    _fields_ = [("m", Heston), ("K", ctypes.c_double), ("is_put", ctypes.c_int32), ("steps", ctypes.c_uint32),
+                ("paths", ctypes.c_uint64)]
+
+
+BATCH_ADJOINT, BATCH_GRAPH, BATCH_NO_AUTOTUNE = 1, 2, 4
+
+
 def as_heston(model) -> Heston:
     if isinstance(model, Heston):
         return model
@@ -90,6 +100,7 @@ def load(build_if_missing: bool = True):
                                          vp]
         L.simr_greeks_adjoint.argtypes = [vp, H, dp, c_int, c_int, u32, u64, u64, u32, u32, dp, dp, dp, vp]
         L.simr_paths_adjoint.argtypes = [vp, H, u32, u64, u64, u64, u32, u32, dp, dp, vp]
+        L.simr_batch_submit.argtypes = [vp, ctypes.POINTER(Option), c_int, u64, u32, dp, dp, dp, vp]
         L.simr_sync.argtypes = [vp, vp]
         L.simr_price_noalloc.argtypes = [H, dp, c_int, c_int, u32, u64, u64, u32, dp, dp, vp]
         _lib = L

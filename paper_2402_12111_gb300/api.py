@@ -122,6 +122,33 @@ def heston_price(params, strikes, T, is_put=False, steps=64, paths=65536, seed=1
     return HestonAdjoint.apply(params, strikes, T, is_put, steps, paths, seed, ckpt_every)
 
 
+def batch(options, seed: int = 1, adjoint: bool = False, graph: bool = False, autotune: bool = True,
+          device=None, stream=None, out_device=None):
+    """simr_batch_submit over a book: options is a sequence of dicts with keys
+    model (dict), K, is_put, steps, paths.  Returns (price[n], stderr[n], grad[n, 7] or None)
+    in the book's order, on `out_device` (default: the CUDA device)."""
+    n = len(options)
+    arr = (S.Option * n)()
+    for i, o in enumerate(options):
+        arr[i].m = S.as_heston(o["model"])
+        arr[i].K = float(o["K"])
+        arr[i].is_put = int(bool(o["is_put"]))
+        arr[i].steps = int(o["steps"])
+        arr[i].paths = int(o["paths"])
+    dev_index = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    odev = torch.device("cuda", dev_index) if out_device is None else torch.device(out_device)
+    p = torch.empty(n, dtype=torch.float64, device=odev)
+    se = torch.empty_like(p)
+    g = torch.empty(n, 7, dtype=torch.float64, device=odev) if adjoint else None
+    flags = (S.BATCH_ADJOINT if adjoint else 0) | (S.BATCH_GRAPH if graph else 0) | \
+        (0 if autotune else S.BATCH_NO_AUTOTUNE)
+    L = S.load()
+    ctx = S.context(dev_index)
+    st = _stream(p, stream) if p.is_cuda else ctypes.c_void_p(None)
+    S.check(L.simr_batch_submit(ctx, arr, n, int(seed), flags, _ptr(p), _ptr(se), _ptr(g), st))
+    return p, se, g
+
+
 def paths_adjoint(model, steps: int, path_begin: int, n_paths: int, seed: int = 1, ckpt_every: int = 0,
                   option_index: int = 0, device="cuda", stream=None):
     """simr_paths_adjoint: (x_T[n], grad[n, 5]) FP32, grad = d x_T / d(v0, kappa, theta, sigma, rho)."""

@@ -1,0 +1,191 @@
+// simr_adjoint_path.cuh -- per-path pathwise adjoint of the Heston QE path (forward pass
+// with checkpoints, reverse sweep), shared by the per-strike adjoint kernel and
+// the batched book kernel.  See simr_adjoint.cu for the method.
+#pragma once
+
+#include <cstdint>
+
+#include "simr_device.cuh"
+#include "simr_internal.h"
+
+namespace simr {
+namespace {
+
+// One QE variance step from v given the step's draws (no log-spot update).
+__device__ __forceinline__ float qe_only(const ScenConst& c, float v, float omu, float zv) {
+  float vn, dl;
+  qe_from_moments(fmaf(v, c.E, c.thE), fmaf(v, c.c1, c.c2), omu, zv, vn, dl);
+  return vn;
+}
+
+struct AdjSums {
+  float vbar, Am, Amv, As, Asv, Ad, Adl, Ak3;
+};
+
+// Reverse step n: state vc -> vn (both known), the step's stored draw d (Z_V in
+// the quadratic branch, 1 - U_V in the exponential one; the branch follows from
+// vc) and Z_X; vbar holds the adjoint of v_{n+1} on entry and of v_n on exit.
+// Each square root and its reciprocal come from one rsqrt.
+__device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, float vc, float vn, float d, float zx,
+                                             AdjSums& a) {
+  const float m = fmaf(vc, c.E, c.thE);
+  const float s2 = fmaf(vc, c.c1, c.c2);
+  const float m2 = m * m;
+  const float s = vc + vn;
+  const float rq = rsqrt_approx(s);
+  const float q = s > 0.0f ? s * rq : 0.0f;
+  const float hz = s > 0.0f ? 0.5f * c.sK3 * zx * rq : 0.0f;  // d(sK3 sqrt(s) Z)/ds
+  const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
+  const float dlbar = c.Cdl;
+  float mbar = 0.0f, s2bar = 0.0f, dl = 0.0f;
+  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
+    const float zv = d;
+    const float rs2 = rcp_approx(s2);
+    const float t = 2.0f * m2 * rs2;
+    const float tt = fmaf(t, t, -t);
+    const float rroot = rsqrt_approx(tt);
+    const float root = tt * rroot;
+    const float b2 = (t - 1.0f) + root;
+    const float rb = rsqrt_approx(b2);
+    const float b = b2 * rb;
+    const float ropb2 = rcp_approx(t + root);  // 1 / (1 + b^2)
+    const float am = m * ropb2;
+    const float bz = b + zv;
+    const float g = fmaf(zv, zv + 2.0f * b, -1.0f);
+    dl = am * g;
+    const float abar = fmaf(vnbar, bz * bz, dlbar * g);
+    const float bbar = 2.0f * am * fmaf(vnbar, bz, dlbar * zv);
+    const float b2bar = fmaf(0.5f * bbar, rb, -abar * am * ropb2);
+    mbar = abar * ropb2;
+    const float tbar = b2bar * fmaf(2.0f * t - 1.0f, 0.5f * rroot, 1.0f);
+    mbar = fmaf(tbar * 4.0f * m, rs2, mbar);
+    s2bar = -tbar * t * rs2;
+  } else if (m > 0.0f) {
+    const float omu = d;
+    const float ms = m2 + s2;
+    const float W = omu * ms;
+    if (W >= 2.0f * m2) {
+      dl = -m;
+      mbar = -dlbar;
+    } else {
+      const float rm = rcp_approx(m), rms = rcp_approx(ms);
+      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
+      const float A = 0.5f * ms * rm;
+      const float dA_dm = 0.5f * (m2 - s2) * rm * rm;
+      const float dL_dm = 2.0f * rm - 2.0f * m * rms;
+      const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
+      const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
+      dl = vn - m;
+      mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
+      s2bar = (vnbar + dlbar) * dv_ds;
+    }
+  }
+  a.vbar = (c.Cv - c.Cd + hz) + fmaf(mbar, c.E, s2bar * c.c1);
+  a.Am += mbar;
+  a.Amv = fmaf(mbar, vc - theta, a.Amv);
+  a.As += s2bar;
+  a.Asv = fmaf(s2bar, vc, a.Asv);
+  a.Ad += theta - vc;
+  a.Adl += dl;
+  a.Ak3 = fmaf(q, zx, a.Ak3);
+}
+
+// The draw the reverse step of state v needs: Z_V in the quadratic branch,
+// 1 - U_V otherwise (same branch test as the forward step).
+__device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float omu, float zv) {
+  const float m = fmaf(v, c.E, c.thE);
+  const float s2 = fmaf(v, c.c1, c.c2);
+  return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
+}
+
+// Forward pass with checkpoints, then the reverse sweep, for one path: x_T (with
+// its Kahan remainder) and g = d x_T / d(v0, kappa, theta, sigma, rho).
+// ckpt: [n_seg][bd] and seg: [3][k][bd] shared-memory slices of this block; the
+// recompute pass of a segment keeps the segment's states and draws there, so
+// the reverse sweep regenerates nothing.
+__device__ __forceinline__ void path_adjoint(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
+                                             const uint32_t (&rk)[10][2], uint64_t path, float* ckpt, float* seg,
+                                             int bd, int tid, float& x_out, float& comp_out, float (&g)[5]) {
+  const float theta = A.theta;
+  const uint32_t k = (uint32_t)A.ckpt_every;
+  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+  float* seg_v = seg;
+  float* seg_d = seg + (size_t)k * bd;
+  float* seg_zx = seg + (size_t)2 * k * bd;
+
+  // forward pass with checkpoints (k is even, so checkpoints fall on even steps)
+  float v = c.v0, x = 0.0f, comp = 0.0f;
+  for (uint32_t p = 0; 2 * p < N; ++p) {
+    const uint4 w = philox4x32_10(p, plo, phi, option, rk);
+    const uint32_t n = 2 * p;
+    if (n % k == 0) ckpt[(n / k) * bd + tid] = v;
+    {
+      const float xv = centered_uniform(w.x);
+      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.y)), v, x,
+                       comp);
+    }
+    if (n + 1 < N) {
+      const float xv = centered_uniform(w.z);
+      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.w)), v, x,
+                       comp);
+    }
+  }
+  x_out = x;
+  comp_out = comp;
+
+  // reverse sweep, segment by segment
+  AdjSums as{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int j = A.n_seg - 1; j >= 0; --j) {
+    const uint32_t n0 = (uint32_t)j * k, n1 = min(n0 + k, N);
+    float vv = ckpt[j * bd + tid];
+    for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
+      const uint4 w = philox4x32_10(p, plo, phi, option, rk);
+      const uint32_t i = 2 * p - n0;
+      {
+        const float xv = centered_uniform(w.x);
+        const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
+        seg_v[i * bd + tid] = vv;
+        seg_d[i * bd + tid] = branch_draw(c, vv, omu, zv);
+        seg_zx[i * bd + tid] = norminv_centered(centered_uniform(w.y));
+        vv = qe_only(c, vv, omu, zv);
+      }
+      if (2 * p + 1 < n1) {
+        const float xv = centered_uniform(w.z);
+        const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
+        seg_v[(i + 1) * bd + tid] = vv;
+        seg_d[(i + 1) * bd + tid] = branch_draw(c, vv, omu, zv);
+        seg_zx[(i + 1) * bd + tid] = norminv_centered(centered_uniform(w.w));
+        vv = qe_only(c, vv, omu, zv);
+      }
+    }
+    float vnext = vv;  // v_{n1}
+    for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
+      const float vc = seg_v[i * bd + tid];
+      adjoint_step(c, theta, vc, vnext, seg_d[i * bd + tid], seg_zx[i * bd + tid], as);
+      vnext = vc;
+    }
+  }
+  const double Amv = as.Amv, Asv = as.Asv, As = as.As, Ad = as.Ad, Adl = as.Adl, Am = as.Am, Ak3 = as.Ak3;
+  g[0] = as.vbar;
+  g[1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
+  g[2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
+  g[3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
+  g[4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+}
+
+// Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho, 8 r (before -T P).
+constexpr int kAdjAcc = 9;
+
+__device__ __forceinline__ float adj_term(int a, bool put, float S, float K, const float (&g)[5], float invS0,
+                                          float T) {
+  const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
+  if (a == 0) return f;
+  if (a == 1) return f * f;
+  const float w = put ? (S < K ? -S : 0.0f) : (S > K ? S : 0.0f);
+  if (a == 2) return w * invS0;
+  if (a == 8) return w * T;
+  return w * g[a - 3];
+}
+
+}  // namespace
+}  // namespace simr

@@ -5,8 +5,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
 #include "simr.h"
 #include "simr_internal.h"
@@ -28,6 +32,25 @@ struct simr_ctx {
   size_t out_cap = 0;
   float* dev_f32 = nullptr;
   size_t f32_cap = 0;
+  // batched book: device tables, per-item partial rows, pinned upload staging
+  BatchOption* b_opts = nullptr;
+  size_t b_opts_cap = 0;
+  BatchItem* b_items = nullptr;
+  size_t b_items_cap = 0;
+  double* b_partials = nullptr;
+  size_t b_partials_cap = 0;
+  unsigned char* b_host = nullptr;  // pinned
+  size_t b_host_cap = 0;
+  cudaEvent_t b_uploaded = nullptr;  // the last upload from b_host has completed
+  uint64_t graph_key = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t g_stream = nullptr;  // graphs are captured and launched here (non-blocking)
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  struct Tune {
+    uint64_t key;
+    uint32_t chunk;
+  };
+  std::vector<Tune> tune;
 };
 
 namespace {
@@ -467,6 +490,108 @@ int run_paths(simr_ctx* ctx, const PathLaunch& L, const double* dev_strikes, Out
   return finish_outputs(ctx, o, st);
 }
 
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+// Per-option device records (caller's order) and the longest-first order.
+int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vector<BatchOption>* out,
+                        std::vector<uint32_t>* order, int* smem_floats) {
+  out->resize(n);
+  std::vector<double> cost(n);
+  int smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const simr_option& o = opts[i];
+    int rc = check_model(&o.m);
+    if (rc) {
+      char msg[sizeof(g_err)];
+      std::strncpy(msg, g_err, sizeof(msg) - 1);
+      msg[sizeof(msg) - 1] = 0;
+      return fail(SIMR_EINVAL, "option %d: %s", i, msg);
+    }
+    if (!(o.K > 0.0) || !finite(o.K)) return fail(SIMR_EINVAL, "option %d: strike must be finite and > 0", i);
+    if (o.steps < 1 || o.paths < 1) return fail(SIMR_EINVAL, "option %d: steps and paths must be >= 1", i);
+    if (o.paths > (1ull << 40)) return fail(SIMR_EINVAL, "option %d: paths beyond 2^40", i);
+    BatchOption& b = (*out)[i];
+    std::memset(&b, 0, sizeof(b));
+    b.sc = base_const(o.m, o.steps);
+    if (adjoint) {
+      if ((rc = build_adjoint(o.m, o.steps, 0, &b.A))) return rc;
+      smem = std::max(smem, b.A.n_seg + 3 * b.A.ckpt_every);
+    }
+    b.S0 = (float)o.m.S0;
+    b.K = (float)o.K;
+    b.invS0 = (float)(1.0 / o.m.S0);
+    b.T = (float)o.m.T;
+    b.is_put = o.is_put ? 1 : 0;
+    b.steps = o.steps;
+    b.option_index = (uint32_t)i;
+    b.paths = o.paths;
+    b.disc = std::exp(-o.m.r * o.m.T);
+    cost[i] = (double)o.steps * (double)o.paths;
+  }
+  order->resize(n);
+  std::iota(order->begin(), order->end(), 0u);
+  std::stable_sort(order->begin(), order->end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+  *smem_floats = smem;
+  return SIMR_OK;
+}
+
+// Sorted option table and its items of `chunk` paths, in pinned staging, then uploaded.
+int upload_batch(simr_ctx* ctx, const std::vector<BatchOption>& opts, const std::vector<uint32_t>& order,
+                 uint32_t chunk, cudaStream_t st, uint32_t* n_items_out) {
+  const size_t n = opts.size();
+  uint64_t n_items = 0;
+  for (uint32_t o : order) n_items += (opts[o].paths + chunk - 1) / chunk;
+  if (n_items > 0xffffffffull) return fail(SIMR_EUNSUPPORTED, "book needs more than 2^32 work items");
+  const size_t bytes = n * sizeof(BatchOption) + n_items * sizeof(BatchItem);
+  int rc;
+  if (ctx->b_uploaded) {
+    cudaError_t e = cudaEventSynchronize(ctx->b_uploaded);  // staging still in use by the last upload?
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous upload");
+  }
+  if (ctx->b_host_cap < bytes) {
+    if (ctx->b_host) cudaFreeHost(ctx->b_host);
+    ctx->b_host = nullptr;
+    ctx->b_host_cap = 0;
+    cudaError_t e = cudaHostAlloc((void**)&ctx->b_host, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SIMR_ENOMEM, "pinned staging of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->b_host_cap = bytes;
+  }
+  BatchOption* ho = reinterpret_cast<BatchOption*>(ctx->b_host);
+  BatchItem* hi = reinterpret_cast<BatchItem*>(ctx->b_host + n * sizeof(BatchOption));
+  uint64_t it = 0;
+  for (size_t j = 0; j < n; ++j) {
+    BatchOption b = opts[order[j]];
+    b.item_begin = (uint32_t)it;
+    const uint64_t cnt = (b.paths + chunk - 1) / chunk;
+    b.item_count = (uint32_t)cnt;
+    for (uint64_t q = 0; q < cnt; ++q) {
+      const uint64_t pb = q * chunk;
+      hi[it + q].option = (uint32_t)j;
+      hi[it + q].count = (uint32_t)std::min<uint64_t>(chunk, b.paths - pb);
+      hi[it + q].path_begin = pb;
+    }
+    it += cnt;
+    ho[j] = b;
+  }
+  if ((rc = ensure(&ctx->b_opts, &ctx->b_opts_cap, n, "batch option table"))) return rc;
+  if ((rc = ensure(&ctx->b_items, &ctx->b_items_cap, (size_t)n_items, "batch item table"))) return rc;
+  cudaError_t e = cudaMemcpyAsync(ctx->b_opts, ho, n * sizeof(BatchOption), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->b_items, hi, (size_t)n_items * sizeof(BatchItem), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !ctx->b_uploaded) e = cudaEventCreateWithFlags(&ctx->b_uploaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->b_uploaded, st);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the book");
+  *n_items_out = (uint32_t)n_items;
+  return SIMR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -513,6 +638,15 @@ void simr_destroy(simr_ctx* ctx) {
   cudaFree(ctx->dev_strikes);
   cudaFree(ctx->dev_out);
   cudaFree(ctx->dev_f32);
+  cudaFree(ctx->b_opts);
+  cudaFree(ctx->b_items);
+  cudaFree(ctx->b_partials);
+  if (ctx->b_host) cudaFreeHost(ctx->b_host);
+  if (ctx->b_uploaded) cudaEventDestroy(ctx->b_uploaded);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->g_in) cudaEventDestroy(ctx->g_in);
+  if (ctx->g_out) cudaEventDestroy(ctx->g_out);
+  if (ctx->g_stream) cudaStreamDestroy(ctx->g_stream);
   delete ctx;
 }
 
@@ -699,6 +833,134 @@ int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* st
   out.status = ctx->status;
   cudaError_t e = launch_finalize(L, dsums, out, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the finalize kernel");
+  return finish_outputs(ctx, o, st);
+}
+
+int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64_t seed, uint32_t flags,
+                      double* price, double* stderr_out, double* grad, void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (!opts || n_opts < 1 || n_opts > (1 << 22)) return fail(SIMR_EINVAL, "n_opts must lie in [1, 2^22]");
+  if (flags & ~(SIMR_BATCH_ADJOINT | SIMR_BATCH_GRAPH | SIMR_BATCH_NO_AUTOTUNE))
+    return fail(SIMR_EINVAL, "unknown batch flags");
+  if (is_device_ptr(opts)) return fail(SIMR_EINVAL, "the option table must be in host memory");
+  const bool adjoint = (flags & SIMR_BATCH_ADJOINT) != 0;
+  if (!price) return fail(SIMR_EINVAL, "price is NULL");
+  if (adjoint && !grad) return fail(SIMR_EINVAL, "adjoint books need grad");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<BatchOption> bo;
+  std::vector<uint32_t> order;
+  int smem_floats = 0;
+  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, &order, &smem_floats))) return rc;
+  if ((size_t)smem_floats * 128 * sizeof(float) > 200 * 1024)
+    return fail(SIMR_EUNSUPPORTED, "an option's checkpoints need more shared memory than a block has");
+  BatchLaunch B;
+  std::memset(&B, 0, sizeof(B));
+  philox_round_keys(seed, B.rk);
+  B.n_opts = (uint32_t)n_opts;
+  B.adjoint = adjoint ? 1 : 0;
+  B.smem_floats = smem_floats;
+  const int nacc = adjoint ? 9 : 2;
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_opts;
+  o.user[1] = stderr_out;
+  o.n[1] = n_opts;
+  o.user[2] = adjoint ? grad : nullptr;
+  o.n[2] = (size_t)n_opts * 7;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  BatchOutputs out{o.dev[0], o.dev[1], o.dev[2]};
+  cudaError_t e = prepare_batch(B);
+  if (e != cudaSuccess) return cuda_fail(e, "preparing the batch kernel");
+
+  // chunk (paths per work item): autotuned once per book shape, cached in the context
+  double total = 0.0;
+  for (const BatchOption& b : bo) total += (double)b.steps * (double)b.paths;
+  const uint64_t tkey = (adjoint ? 1ull : 0ull) | ((uint64_t)std::max(0.0, std::log2(total + 1.0)) << 1) |
+                        ((uint64_t)std::log2((double)n_opts) << 16);
+  uint32_t chunk = adjoint ? 1024 : 4096;
+  bool tuned = false;
+  for (const auto& t : ctx->tune)
+    if (t.key == tkey) chunk = t.chunk, tuned = true;
+  const char* env = std::getenv("SIMR_AUTOTUNE");
+  const bool autotune = !(flags & SIMR_BATCH_NO_AUTOTUNE) && !(env && env[0] == '0');
+  if (!tuned && autotune) {
+    const uint32_t cands[3] = {adjoint ? 256u : 1024u, adjoint ? 1024u : 4096u, adjoint ? 4096u : 16384u};
+    float best = 0.0f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+      uint32_t n_items = 0;
+      if ((rc = upload_batch(ctx, bo, order, cands[ci], st, &n_items))) break;
+      B.n_items = n_items;
+      if ((rc = ensure(&ctx->b_partials, &ctx->b_partials_cap, (size_t)n_items * nacc, "batch partial rows"))) break;
+      e = cudaEventRecord(a, st);
+      if (e == cudaSuccess)
+        e = launch_batch(B, ctx->b_opts, ctx->b_items, ctx->ticket + 32, ctx->b_partials, out, ctx->num_sms, st);
+      if (e == cudaSuccess) e = cudaEventRecord(b, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && (ci == 0 || ms < best)) best = ms, chunk = cands[ci];
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotuning the batch kernel");
+    ctx->tune.push_back({tkey, chunk});
+  }
+
+  uint32_t n_items = 0;
+  if ((rc = upload_batch(ctx, bo, order, chunk, st, &n_items))) return rc;
+  B.n_items = n_items;
+  if ((rc = ensure(&ctx->b_partials, &ctx->b_partials_cap, (size_t)n_items * nacc, "batch partial rows"))) return rc;
+  unsigned int* counter = ctx->ticket + 32;  // word at byte 128 of the ticket block
+  if (flags & SIMR_BATCH_GRAPH) {
+    // one captured graph per (book, seed, flags, outputs): repeated submissions replay it.
+    // Captured and launched on the context's own stream, ordered after `st` by events
+    // (capture is not possible on the legacy default stream).
+    if (!ctx->g_stream) {
+      e = cudaStreamCreateWithFlags(&ctx->g_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->g_in, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->g_out, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "creating the graph stream");
+    }
+    cudaStream_t gs = ctx->g_stream;
+    e = cudaEventRecord(ctx->g_in, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, ctx->g_in, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering the graph stream");
+    uint64_t key = fnv1a(bo.data(), bo.size() * sizeof(BatchOption));
+    key = fnv1a(&seed, sizeof(seed), key);
+    key = fnv1a(&flags, sizeof(flags), key);
+    key = fnv1a(&chunk, sizeof(chunk), key);
+    key = fnv1a(&out, sizeof(out), key);
+    if (!(ctx->graph_exec && ctx->graph_key == key)) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t le = launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, gs);
+        e = cudaStreamEndCapture(gs, &g);
+        if (le != cudaSuccess) e = le;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return cuda_fail(e, "capturing the batch graph");
+      }
+      ctx->graph_key = key;
+    }
+    e = cudaGraphLaunch(ctx->graph_exec, gs);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->g_out, gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->g_out, 0);
+  } else {
+    e = launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "launching the batch");
   return finish_outputs(ctx, o, st);
 }
 

@@ -1,0 +1,141 @@
+// simr_batch.cu -- a heterogeneous book of European options in one persistent launch (sm_103a).
+//
+// Each option has its own model, maturity, steps and paths.  The host cuts every
+// option's path range into items of `chunk` paths, longest options first; the
+// persistent kernel's warps take items from an atomic ticket until the queue is
+// empty, simulate their paths (the paper's VariancePathQE / LogPricePathQE /
+// AssetPathExponential stages, Sec. 4-5, one lane per path, the option index as
+// the fourth Philox counter word) and write one FP64 partial row per item; a
+// second kernel sums each option's rows in item order (the reduction over paths
+// of Sec. 6) and normalises.  Adjoint books run the per-path reverse sweep of
+// simr_adjoint_path.cuh instead and add the 7 sensitivities.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "simr_adjoint_path.cuh"
+#include "simr_device.cuh"
+#include "simr_internal.h"
+#include "simr_reduce.cuh"
+
+namespace simr {
+namespace {
+
+template <bool ADJ>
+__global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
+                                                           const BatchOption* __restrict__ opts,
+                                                           const BatchItem* __restrict__ items,
+                                                           unsigned int* __restrict__ counter,
+                                                           double* __restrict__ partials) {
+  extern __shared__ __align__(16) float smem_f[];
+  constexpr int NACC = ADJ ? kAdjAcc : 2;
+  const int lane = threadIdx.x & 31, tid = threadIdx.x, bd = blockDim.x;
+  while (true) {
+    unsigned int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= B.n_items) break;
+    const BatchItem I = items[it];
+    const BatchOption& O = opts[I.option];
+    const ScenConst c = O.sc;
+    const float K = O.K, S0 = O.S0;
+    const bool put = O.is_put != 0;
+    const uint32_t steps = O.steps, oidx = O.option_index;
+    double acc[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+    for (uint32_t b = 0; b < I.count; b += 32) {
+      const bool active = b + lane < I.count;
+      const uint64_t path = I.path_begin + b + lane;
+      float terms[NACC];
+      if (ADJ) {
+        float x, comp, g[5];
+        path_adjoint(c, O.A, steps, oidx, B.rk, path, smem_f, smem_f + (size_t)O.A.n_seg * bd, bd, tid, x, comp, g);
+        const float S = terminal_spot(S0, x, comp);
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) terms[a] = adj_term(a, put, S, K, g, O.invS0, O.T);
+      } else {
+        float x, comp;
+        simulate_one(c, steps, oidx, B.rk, path, x, comp);
+        const float S = terminal_spot(S0, x, comp);
+        const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
+        terms[0] = f;
+        terms[1] = f * f;
+      }
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) {
+        const float t = warp_sum(active ? terms[a] : 0.0f);
+        acc[a] += (double)t;
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) partials[(size_t)it * NACC + a] = acc[a];
+    }
+  }
+}
+
+// One thread per option: sum its items' rows in item order, normalise.
+__global__ void batch_reduce_kernel(const BatchOption* __restrict__ opts, uint32_t n_opts, int nacc,
+                                    const double* __restrict__ partials, BatchOutputs out) {
+  const uint32_t o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_opts) return;
+  const BatchOption& O = opts[o];
+  double s[kAdjAcc];
+  for (int a = 0; a < kAdjAcc; ++a) s[a] = 0.0;
+  for (uint32_t i = O.item_begin; i < O.item_begin + O.item_count; ++i)
+    for (int a = 0; a < nacc; ++a) s[a] += partials[(size_t)i * nacc + a];
+  const double n = (double)O.paths, inv_n = 1.0 / n;
+  const double mean = s[0] * inv_n;
+  const double price = O.disc * mean;
+  const uint32_t u = O.option_index;
+  out.price[u] = price;
+  if (out.stderr_) {
+    const double var = n > 1.0 ? (s[1] * inv_n - mean * mean) / (n - 1.0) : 0.0;
+    out.stderr_[u] = O.disc * sqrt(var > 0.0 ? var : 0.0);
+  }
+  if (out.grad && nacc == kAdjAcc) {
+    for (int c7 = 0; c7 < 7; ++c7) {
+      double g = O.disc * s[2 + c7] * inv_n;
+      if (c7 == 6) g -= (double)O.T * price;
+      out.grad[(size_t)u * 7 + c7] = g;
+    }
+  }
+}
+
+constexpr int kBatchTpb = 128;
+
+size_t batch_smem(const BatchLaunch& B) { return B.adjoint ? (size_t)B.smem_floats * kBatchTpb * sizeof(float) : 0; }
+
+}  // namespace
+
+cudaError_t prepare_batch(const BatchLaunch& B) {
+  if (!B.adjoint) return cudaSuccess;
+  return cudaFuncSetAttribute(heston_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batch_smem(B));
+}
+
+cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
+                         double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream) {
+  const size_t smem = batch_smem(B);
+  int per_sm = 0;
+  cudaError_t e = B.adjoint
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<true>, kBatchTpb, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<false>, kBatchTpb, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned grid = (unsigned)num_sms * (unsigned)per_sm;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return e;
+  if (B.adjoint)
+    heston_batch_kernel<true><<<grid, kBatchTpb, smem, stream>>>(B, opts, items, counter, partials);
+  else
+    heston_batch_kernel<false><<<grid, kBatchTpb, 0, stream>>>(B, opts, items, counter, partials);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nacc = B.adjoint ? kAdjAcc : 2;
+  batch_reduce_kernel<<<(B.n_opts + 127) / 128, 128, 0, stream>>>(opts, B.n_opts, nacc, partials, out);
+  return cudaGetLastError();
+}
+
+}  // namespace simr

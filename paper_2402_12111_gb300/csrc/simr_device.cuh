@@ -280,6 +280,28 @@ __device__ __forceinline__ void step0_crn(const FirstConst& fb, const FirstConst
   v = v1;
 }
 
+// One path of one scenario over all steps: x_T with its Kahan remainder.
+__device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps, uint32_t option,
+                                             const uint32_t (&rk)[10][2], uint64_t path, float& x, float& comp) {
+  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+  float v = c.v0;
+  x = 0.0f;
+  comp = 0.0f;
+  for (uint32_t p = 0; 2 * p < steps; ++p) {
+    const uint4 w = philox4x32_10(p, plo, phi, option, rk);
+    {
+      const float xv = centered_uniform(w.x);
+      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.y)), v, x,
+                       comp);
+    }
+    if (2 * p + 1 < steps) {
+      const float xv = centered_uniform(w.z);
+      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.w)), v, x,
+                       comp);
+    }
+  }
+}
+
 // AssetPathExponential (paper Sec. 5): S_T = S0 e^{x} with the Kahan remainder
 // (true sum = x - comp) applied as S (1 - comp).  expf is the accurate one.
 __device__ __forceinline__ float terminal_spot(float S0, float x, float comp) {

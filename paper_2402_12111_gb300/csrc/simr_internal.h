@@ -72,6 +72,40 @@ struct AdjOutputs {
   int* status;
 };
 
+// One option of a batched book (device table, longest first).
+struct BatchOption {
+  ScenConst sc;             // base scenario constants
+  AdjConst A;               // adjoint constants (adjoint books)
+  float S0, K, invS0, T;
+  int32_t is_put;
+  uint32_t steps;
+  uint32_t option_index;    // position in the caller's array: output slot and Philox counter word
+  uint32_t item_begin, item_count;
+  uint32_t pad;
+  uint64_t paths;
+  double disc;
+};
+
+// A work item: `count` consecutive paths of one option, for one warp.
+struct BatchItem {
+  uint32_t option;  // index into the BatchOption table
+  uint32_t count;
+  uint64_t path_begin;
+};
+
+struct BatchLaunch {
+  uint32_t rk[10][2];
+  uint32_t n_items, n_opts;
+  int32_t adjoint;
+  int32_t smem_floats;  // adjoint: shared floats per thread (max over options of n_seg + 3 ckpt_every)
+};
+
+struct BatchOutputs {
+  double* price;    // [n_opts] in the caller's order
+  double* stderr_;  // [n_opts] or null
+  double* grad;     // [n_opts][7] or null
+};
+
 struct Scratch {
   double* partials;      // [grid][n_acc * nk_pad]
   unsigned int* ticket;  // zero between launches
@@ -95,6 +129,11 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms);
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A);
 // Per-path x_T and d x_T / d(v0, kappa, theta, sigma, rho) ([n][5]).
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream);
+
+// Batched book: queue counter reset, persistent kernel, per-option reduction.
+cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
+                         double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream);
+cudaError_t prepare_batch(const BatchLaunch& B);  // kernel attributes (outside any stream capture)
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);

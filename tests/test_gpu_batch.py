@@ -1,0 +1,86 @@
+"""Batched heterogeneous book (simr_batch_submit) on the GPU.
+
+Option i of a book uses Philox counter word 3 = i, so its estimate is the one
+simr_price / simr_greeks_adjoint give with option_index = i; the two group the
+paths into the same 32-path FP32 sums and differ only in the order of the FP64
+additions that follow (relative 1e-12).  A sample of the book is also checked
+against the FP64 oracle (prices 1e-5 relative + branch-flip allowance).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def simr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_12111_gb300 as simr
+
+    simr.load()
+    return simr
+
+
+@pytest.fixture(scope="module")
+def small_book():
+    # the book generator's distributions, scaled down in paths and steps for test time
+    return workloads.book(n_options=48, seed=3, steps_range=(1, 96), paths_range=(1, 20000))
+
+
+def test_batch_prices_equal_per_option_calls(simr, small_book):
+    p, se, g = simr.batch(small_book, seed=9)
+    assert g is None
+    for i, o in enumerate(small_book):
+        pi, si = simr.price(o["model"], torch.tensor([o["K"]], dtype=torch.float64, device="cuda"), o["is_put"],
+                            o["steps"], o["paths"], 9, option_index=i)
+        torch.testing.assert_close(p[i:i + 1], pi, rtol=1e-12, atol=1e-12)
+        torch.testing.assert_close(se[i:i + 1], si, rtol=1e-9, atol=1e-12)
+
+
+def test_batch_adjoint_equals_per_option_calls(simr, small_book):
+    p, se, g = simr.batch(small_book, seed=4, adjoint=True)
+    for i, o in enumerate(small_book):
+        pi, _, gi = simr.greeks_adjoint(o["model"], torch.tensor([o["K"]], dtype=torch.float64, device="cuda"),
+                                        o["is_put"], o["steps"], o["paths"], 4, ckpt_every=0, option_index=i)
+        torch.testing.assert_close(p[i:i + 1], pi, rtol=1e-12, atol=1e-12)
+        torch.testing.assert_close(g[i:i + 1], gi, rtol=1e-9, atol=1e-9)
+
+
+def test_batch_graph_replay_and_autotune_agree(simr, small_book):
+    ref = simr.batch(small_book, seed=5, autotune=False)[0]
+    a = simr.batch(small_book, seed=5, graph=True)[0]   # capture
+    b = simr.batch(small_book, seed=5, graph=True)[0]   # replay
+    torch.testing.assert_close(a, ref, rtol=1e-12, atol=1e-12)
+    torch.testing.assert_close(b, ref, rtol=1e-12, atol=1e-12)
+    c = simr.batch(small_book[:7], seed=5, graph=True)[0]  # another book: fresh capture
+    torch.testing.assert_close(c, ref[:7], rtol=1e-12, atol=1e-12)
+
+
+def test_batch_sample_matches_oracle(simr, small_book):
+    p, _, _ = simr.batch(small_book, seed=2)
+    p = p.cpu().numpy()
+    for i in range(0, len(small_book), 6):
+        o = small_book[i]
+        po, _ = oracle.price(o["model"], [o["K"]], o["is_put"], o["steps"], o["paths"], 2, option_index=i)
+        x, _, mg = oracle.terminal(o["model"], o["steps"], 2, 0, o["paths"], option_index=i)
+        close = mg < 1e-4
+        S = o["model"]["S0"] * np.exp(x[close])
+        allow = math.exp(-o["model"]["r"] * o["model"]["T"]) * close.sum() * \
+            (o["K"] if o["is_put"] else max(S.max(initial=o["K"]) * 1.5, o["K"])) / o["paths"]
+        assert abs(p[i] - po[0]) <= 1e-5 * abs(po[0]) + allow + 1e-12, (i, p[i], po[0])
+
+
+def test_batch_host_outputs_and_errors(simr, small_book):
+    ph, _, _ = simr.batch(small_book[:5], seed=1, out_device="cpu")
+    pd, _, _ = simr.batch(small_book[:5], seed=1)
+    torch.testing.assert_close(ph, pd.cpu(), rtol=0, atol=0)
+    bad = [dict(small_book[0], K=-1.0)]
+    with pytest.raises(simr.SimrError):
+        simr.batch(bad)
