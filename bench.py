@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
     ap.add_argument("--no-book", action="store_true", help="skip the 1,024-option heterogeneous book leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
+    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book"],
+                    help="only run one call W + K times on the workload (for profilers); prints no JSON")
     return ap.parse_args()
 
 
@@ -219,6 +221,33 @@ def run_reference(args):
                                        f"{len(w.strikes)} strikes, same Greeks"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_leg(args):
+    """One kind of call, W + K times, for an external profiler."""
+    import torch
+
+    import paper_2402_12111_gb300 as simr
+
+    w = workloads.grid()
+    if args.paths:
+        w.paths = args.paths
+    K = torch.as_tensor(w.strikes, dtype=torch.float64, device="cuda")
+    legs = {
+        "fd": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=list(w.greeks),
+                                     rel_bump=w.rel_bump),
+        "price": lambda: simr.price(w.model, K, w.is_put, w.steps, w.paths, w.seed),
+        "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed, ckpt_every=16),
+    }
+    if args.profile_leg == "book":
+        opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))
+        fn = lambda: simr.batch(opts, seed=1, adjoint=True, autotune=False)  # noqa: E731
+    else:
+        fn = legs[args.profile_leg]
+    for _ in range(args.warmup + args.steps):
+        fn()
+    torch.cuda.synchronize()
     return 0
 
 
@@ -409,6 +438,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_leg:
+        return run_profile_leg(args)
     return run_native(args)
 
 

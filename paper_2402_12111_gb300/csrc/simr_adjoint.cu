@@ -28,7 +28,11 @@
 namespace simr {
 namespace {
 
-template <int TILE>
+#ifndef SIMR_ADJ_PPT
+#define SIMR_ADJ_PPT 1  // paths per thread of the per-strike adjoint kernel (2 measured slower)
+#endif
+
+template <int TILE, int PPT>
 __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
@@ -42,8 +46,7 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
   double* acc = reinterpret_cast<double*>(smem_raw);
   StrikeConst* ks = reinterpret_cast<StrikeConst*>(acc + (size_t)warps * row);
   int* s_last = reinterpret_cast<int*>(ks + L.nk_pad);
-  float* ckpt = reinterpret_cast<float*>(s_last + 4);  // [n_seg][bd]
-  float* seg = ckpt + (size_t)A.n_seg * bd;             // [4][k][bd]: v, 1 - U_V, Z_V, Z_X
+  float* ckpt = reinterpret_cast<float*>(s_last + 4);  // path_adjoint_ppt's shared slices
 
   for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
   for (int j = threadIdx.x; j < L.nk_pad; j += blockDim.x) {
@@ -59,28 +62,41 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
 
   const bool put = L.is_put != 0;
   double* my_acc = acc + (size_t)warp * row;
-  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  const uint64_t per_batch = (uint64_t)kWarp * PPT;
+  const uint64_t batches = (L.path_count + per_batch - 1) / per_batch;
   const uint64_t total_warps = (uint64_t)gridDim.x * warps;
   for (uint64_t bt = (uint64_t)blockIdx.x * warps + warp; bt < batches; bt += total_warps) {
-    const uint64_t local = bt * kWarp + lane;
-    const bool active = local < L.path_count;
-    float x, comp, g[5];
-    path_adjoint(L.sc[0], A, L.steps, L.option_index, L.rk, L.path_begin + local, ckpt, seg, bd, tid, x, comp, g);
-    const float S = terminal_spot(L.S0, x, comp);
+    uint64_t pth[PPT];
+    bool act[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const uint64_t local = bt * per_batch + (uint64_t)j * kWarp + lane;
+      act[j] = local < L.path_count;
+      pth[j] = L.path_begin + local;
+    }
+    float x[PPT], comp[PPT], g[PPT][5], S[PPT];
+    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt, bd, tid, x, comp, g);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
-    // per-strike terms, reduced over the warp's 32 paths
+    // per-strike terms, reduced over the warp's paths
     for (int a = 0; a < kAdjAcc; ++a) {
       if (TILE == 1) {
-        float t = adj_term(a, put, S, ks[0].K, g, A.invS0, A.T);
-        t = warp_sum(active ? t : 0.0f);
+        float t = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) t += act[j] ? adj_term(a, put, S[j], ks[0].K, g[j], A.invS0, A.T) : 0.0f;
+        t = warp_sum(t);
         if (lane == 0) my_acc[a] += (double)t;
       } else {
         for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
           float vals[32];
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
-            const float t = adj_term(a, put, S, ks[t0 + jj].K, g, A.invS0, A.T);
-            vals[jj] = active ? t : 0.0f;
+            float t = 0.0f;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+              t += act[j] ? adj_term(a, put, S[j], ks[t0 + jj].K, g[j], A.invS0, A.T) : 0.0f;
+            vals[jj] = t;
           }
           butterfly32(vals, lane);
           my_acc[(size_t)a * L.nk_pad + t0 + lane] += (double)vals[0];
@@ -137,31 +153,32 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bd = blockDim.x, tid = threadIdx.x;
   float* ckpt = reinterpret_cast<float*>(smem_raw);
-  float* seg = ckpt + (size_t)A.n_seg * bd;
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.path_count) return;  // no block-wide synchronisation below
-  float x, comp, g[5];
-  path_adjoint(L.sc[0], A, L.steps, L.option_index, L.rk, L.path_begin + i, ckpt, seg, bd, tid, x, comp, g);
-  x_T[i] = x - comp;
+  float x[1], comp[1], g[1][5];
+  const uint64_t pth[1] = {L.path_begin + i};
+  path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt, bd, tid, x, comp, g);
+  x_T[i] = x[0] - comp[0];
 #pragma unroll
-  for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[j];
+  for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];
 }
 
 template <int TILE>
 cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                              const Scratch& s, int num_sms, cudaStream_t stream) {
+  constexpr int PPT = SIMR_ADJ_PPT;
   const int tpb = 128, warps = tpb / kWarp;
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
   const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-                      (size_t)(A.n_seg + 3 * A.ckpt_every) * tpb * sizeof(float);
-  auto kern = heston_adjoint_kernel<TILE>;
+                      adjoint_floats_per_thread(A, PPT) * tpb * sizeof(float);
+  auto kern = heston_adjoint_kernel<TILE, PPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  const uint64_t batches = (L.path_count + (uint64_t)kWarp * PPT - 1) / ((uint64_t)kWarp * PPT);
   uint64_t grid = (uint64_t)num_sms * per_sm;
   const uint64_t need = (batches + warps - 1) / warps;
   if (grid > need) grid = need;
@@ -180,12 +197,12 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A) {
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
   return 4 * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-         (size_t)(A.n_seg + 3 * A.ckpt_every) * 128 * sizeof(float);
+         adjoint_floats_per_thread(A, SIMR_ADJ_PPT) * 128 * sizeof(float);
 }
 
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream) {
   const int tpb = 128;
-  const size_t smem = (size_t)(A.n_seg + 3 * A.ckpt_every) * tpb * sizeof(float);
+  const size_t smem = adjoint_floats_per_thread(A, 1) * tpb * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(heston_paths_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -20,6 +20,7 @@ __device__ __forceinline__ float qe_only(const ScenConst& c, float v, float omu,
 
 struct AdjSums {
   float vbar, Am, Amv, As, Asv, Ad, Adl, Ak3;
+  float x, comp;  // x_T accumulated over the reverse sweep (Kahan-compensated)
 };
 
 // Reverse step n: state vc -> vn (both known), the step's stored draw d (Z_V in
@@ -80,6 +81,16 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
       s2bar = (vnbar + dlbar) * dv_ds;
     }
   }
+  // the step's log-spot increment (LogPricePathQE), summed into x_T here rather
+  // than in the forward pass
+  float inc = fmaf(c.Cv, s, c.C0);
+  inc = fmaf(-c.Cd, vc, inc);
+  inc = fmaf(c.Cdl, dl, inc);
+  inc = fmaf(c.sK3 * q, zx, inc);
+  const float y = inc - a.comp;
+  const float tx = a.x + y;
+  a.comp = (tx - a.x) - y;
+  a.x = tx;
   a.vbar = (c.Cv - c.Cd + hz) + fmaf(mbar, c.E, s2bar * c.c1);
   a.Am += mbar;
   a.Amv = fmaf(mbar, vc - theta, a.Amv);
@@ -98,79 +109,131 @@ __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float 
   return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
 }
 
-// Forward pass with checkpoints, then the reverse sweep, for one path: x_T (with
-// its Kahan remainder) and g = d x_T / d(v0, kappa, theta, sigma, rho).
-// ckpt: [n_seg][bd] and seg: [3][k][bd] shared-memory slices of this block; the
-// recompute pass of a segment keeps the segment's states and draws there, so
-// the reverse sweep regenerates nothing.
-__device__ __forceinline__ void path_adjoint(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
-                                             const uint32_t (&rk)[10][2], uint64_t path, float* ckpt, float* seg,
-                                             int bd, int tid, float& x_out, float& comp_out, float (&g)[5]) {
+// Forward pass with checkpoints, then the reverse sweep, for PPT paths in
+// lockstep (independent dependency chains for the scheduler to interleave):
+// x_T (with its Kahan remainder) and g = d x_T / d(v0, kappa, theta, sigma, rho)
+// per path.  The forward pass runs the variance recursion only (x_T is not
+// needed before the sweep ends); the reverse sweep adds up the log-spot
+// increments as it goes.  Shared memory, per thread column tid of a block of bd:
+// ckpt[(slot * PPT + j) * bd + tid] (n_seg slots) and, after it, the segment's
+// states, branch draws and Z_X: seg[((q * k + i) * PPT + j) * bd + tid], q = 0..2;
+// the recompute pass of a segment keeps them there, so the reverse sweep
+// regenerates nothing.
+template <int PPT>
+__device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
+                                                 const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT],
+                                                 float* ckpt, int bd, int tid, float (&x_out)[PPT],
+                                                 float (&comp_out)[PPT], float (&g)[PPT][5]) {
   const float theta = A.theta;
   const uint32_t k = (uint32_t)A.ckpt_every;
-  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
-  float* seg_v = seg;
-  float* seg_d = seg + (size_t)k * bd;
-  float* seg_zx = seg + (size_t)2 * k * bd;
+  const int stride = PPT * bd;  // between consecutive slots / steps of one thread's column
+  float* ck = ckpt + tid;
+  float* s0 = ckpt + A.n_seg * stride + tid;  // states
+  float* s1 = s0 + (int)k * stride;           // branch draws
+  float* s2 = s1 + (int)k * stride;           // Z_X
+  uint32_t plo[PPT], phi[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    plo[j] = (uint32_t)path[j];
+    phi[j] = (uint32_t)(path[j] >> 32);
+  }
+#define SIMR_CK(slot, j) ck[(int)(slot) * stride + (j) * bd]
+#define SIMR_SG(q, i, j) s##q[(int)(i) * stride + (j) * bd]
 
-  // forward pass with checkpoints (k is even, so checkpoints fall on even steps)
-  float v = c.v0, x = 0.0f, comp = 0.0f;
+  // forward pass: the variance recursion with checkpoints (k is even, so
+  // checkpoints fall on even steps)
+  float v[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) v[j] = c.v0;
   for (uint32_t p = 0; 2 * p < N; ++p) {
-    const uint4 w = philox4x32_10(p, plo, phi, option, rk);
     const uint32_t n = 2 * p;
-    if (n % k == 0) ckpt[(n / k) * bd + tid] = v;
-    {
-      const float xv = centered_uniform(w.x);
-      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.y)), v, x,
-                       comp);
+    uint4 w[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
+    if (n % k == 0) {
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) SIMR_CK(n / k, j) = v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const float xv = centered_uniform(w[j].x);
+      v[j] = qe_only(c, v[j], 0.5f * (1.0f - xv), norminv_centered(xv));
     }
     if (n + 1 < N) {
-      const float xv = centered_uniform(w.z);
-      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.w)), v, x,
-                       comp);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const float xv = centered_uniform(w[j].z);
+        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xv), norminv_centered(xv));
+      }
     }
   }
-  x_out = x;
-  comp_out = comp;
 
   // reverse sweep, segment by segment
-  AdjSums as{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  for (int j = A.n_seg - 1; j >= 0; --j) {
-    const uint32_t n0 = (uint32_t)j * k, n1 = min(n0 + k, N);
-    float vv = ckpt[j * bd + tid];
+  AdjSums as[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) as[j] = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int sgi = A.n_seg - 1; sgi >= 0; --sgi) {
+    const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
+    float vv[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) vv[j] = SIMR_CK(sgi, j);
     for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
-      const uint4 w = philox4x32_10(p, plo, phi, option, rk);
       const uint32_t i = 2 * p - n0;
-      {
-        const float xv = centered_uniform(w.x);
+      uint4 w[PPT];
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const float xv = centered_uniform(w[j].x);
         const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
-        seg_v[i * bd + tid] = vv;
-        seg_d[i * bd + tid] = branch_draw(c, vv, omu, zv);
-        seg_zx[i * bd + tid] = norminv_centered(centered_uniform(w.y));
-        vv = qe_only(c, vv, omu, zv);
+        SIMR_SG(0, i, j) = vv[j];
+        SIMR_SG(1, i, j) = branch_draw(c, vv[j], omu, zv);
+        SIMR_SG(2, i, j) = norminv_centered(centered_uniform(w[j].y));
+        vv[j] = qe_only(c, vv[j], omu, zv);
       }
       if (2 * p + 1 < n1) {
-        const float xv = centered_uniform(w.z);
-        const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
-        seg_v[(i + 1) * bd + tid] = vv;
-        seg_d[(i + 1) * bd + tid] = branch_draw(c, vv, omu, zv);
-        seg_zx[(i + 1) * bd + tid] = norminv_centered(centered_uniform(w.w));
-        vv = qe_only(c, vv, omu, zv);
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const float xv = centered_uniform(w[j].z);
+          const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
+          SIMR_SG(0, i + 1, j) = vv[j];
+          SIMR_SG(1, i + 1, j) = branch_draw(c, vv[j], omu, zv);
+          SIMR_SG(2, i + 1, j) = norminv_centered(centered_uniform(w[j].w));
+          vv[j] = qe_only(c, vv[j], omu, zv);
+        }
       }
     }
-    float vnext = vv;  // v_{n1}
+    float vnext[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) vnext[j] = vv[j];  // v_{n1}
     for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-      const float vc = seg_v[i * bd + tid];
-      adjoint_step(c, theta, vc, vnext, seg_d[i * bd + tid], seg_zx[i * bd + tid], as);
-      vnext = vc;
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const float vc = SIMR_SG(0, i, j);
+        adjoint_step(c, theta, vc, vnext[j], SIMR_SG(1, i, j), SIMR_SG(2, i, j), as[j]);
+        vnext[j] = vc;
+      }
     }
   }
-  const double Amv = as.Amv, Asv = as.Asv, As = as.As, Ad = as.Ad, Adl = as.Adl, Am = as.Am, Ak3 = as.Ak3;
-  g[0] = as.vbar;
-  g[1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
-  g[2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
-  g[3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
-  g[4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+#undef SIMR_CK
+#undef SIMR_SG
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    x_out[j] = as[j].x;
+    comp_out[j] = as[j].comp;
+    const double Amv = as[j].Amv, Asv = as[j].Asv, As = as[j].As, Ad = as[j].Ad, Adl = as[j].Adl, Am = as[j].Am,
+                 Ak3 = as[j].Ak3;
+    g[j][0] = as[j].vbar;
+    g[j][1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
+    g[j][2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
+    g[j][3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
+    g[j][4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+  }
+}
+
+// Shared floats per thread of path_adjoint_ppt.
+__host__ __device__ inline size_t adjoint_floats_per_thread(const AdjConst& A, int ppt) {
+  return (size_t)(A.n_seg + 3 * A.ckpt_every) * ppt;
 }
 
 // Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho, 8 r (before -T P).

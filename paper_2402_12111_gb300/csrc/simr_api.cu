@@ -157,14 +157,15 @@ ScenConst base_const(const simr_heston& m, uint32_t steps) {
   return pack(c, 1.0, m.v0);
 }
 
-// Bumped scenario: FP64 deltas to the FP32-ROUNDED base constants, so that
-// base + delta reproduces the bumped constant to FP32 relative precision of the
-// delta; v0 is the scenario's own FP32 initial variance.
+// Bumped scenario: the FP64 difference of the exact constants, added in the
+// kernel to the base scenario's FP32 constants -- the bumped scenario is the
+// base scenario's FP32 model moved by the exact bump (so a v0-only bump has zero
+// deltas); v0 is the scenario's own FP32 initial variance.
 ScenConst bumped_const(const simr_heston& base, const simr_heston& bumped, uint32_t steps) {
   double cb[9], cs[9], d[9];
   scen_const64(base, steps, cb);
   scen_const64(bumped, steps, cs);
-  for (int i = 0; i < 9; ++i) d[i] = cs[i] - (double)(float)cb[i];
+  for (int i = 0; i < 9; ++i) d[i] = cs[i] - cb[i];
   const double ratio_m1 = std::expm1(-bumped.r * bumped.T + base.r * base.T);
   return pack(d, ratio_m1, bumped.v0);
 }
@@ -304,7 +305,10 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
     L->denom[g++] = denom;
   }
   L->n_scen = ns;
-  // step-0 constants: base full values, bumped scenarios deltas to the base's FP32 values
+  // vega is the first re-simulated Greek in bit order, so its two-sided bump occupies
+  // scenarios 1 and 2 when present
+  L->n_v0_scen = ((mask & SIMR_G_VEGA) && L->resim_up[0] == 1 && L->resim_dn[0] == 2) ? 2 : 0;
+  // step-0 constants: base full values, bumped scenarios the exact differences to them
   double fb[7];
   const int br0 = first_step64(*m, steps, (double)L->sc[0].v0, fb);
   L->first_split = ns > 1 ? 1 : 0;
@@ -316,7 +320,7 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
     } else {
       if (br != br0) L->first_split = 0;  // a bump moved step 0 across a branch: plain step 0
       for (int i = 0; i < 7; ++i)
-        if (i != 2) f[i] -= (double)(float)fb[i];
+        if (i != 2) f[i] -= fb[i];
     }
     FirstConst& fc = L->f0[s];
     fc.a = (float)f[0];

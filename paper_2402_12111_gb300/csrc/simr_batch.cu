@@ -44,29 +44,35 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
     double acc[NACC];
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
-    for (uint32_t b = 0; b < I.count; b += 32) {
-      const bool active = b + lane < I.count;
-      const uint64_t path = I.path_begin + b + lane;
+    // paths b + lane and b + 32 + lane of each 64-path step (price mode): the
+    // grouping of simr_price's two-paths-per-thread kernel, so both form the
+    // same FP32 sums of 64 paths
+    constexpr uint32_t STEP = ADJ ? 32u : 64u;
+    for (uint32_t b = 0; b < I.count; b += STEP) {
       float terms[NACC];
       if (ADJ) {
-        float x, comp, g[5];
-        path_adjoint(c, O.A, steps, oidx, B.rk, path, smem_f, smem_f + (size_t)O.A.n_seg * bd, bd, tid, x, comp, g);
-        const float S = terminal_spot(S0, x, comp);
+        const bool active = b + lane < I.count;
+        float x[1], comp[1], g[1][5];
+        const uint64_t pth[1] = {I.path_begin + b + lane};
+        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f, bd, tid, x, comp, g);
+        const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) terms[a] = adj_term(a, put, S, K, g, O.invS0, O.T);
+        for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
       } else {
-        float x, comp;
-        simulate_one(c, steps, oidx, B.rk, path, x, comp);
-        const float S = terminal_spot(S0, x, comp);
-        const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
-        terms[0] = f;
-        terms[1] = f * f;
+        terms[0] = terms[1] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const bool active = b + 32 * j + lane < I.count;
+          float x, comp;
+          simulate_one(c, steps, oidx, B.rk, I.path_begin + b + 32 * j + lane, x, comp);
+          const float S = terminal_spot(S0, x, comp);
+          const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
+          terms[0] += active ? f : 0.0f;
+          terms[1] += active ? f * f : 0.0f;
+        }
       }
 #pragma unroll
-      for (int a = 0; a < NACC; ++a) {
-        const float t = warp_sum(active ? terms[a] : 0.0f);
-        acc[a] += (double)t;
-      }
+      for (int a = 0; a < NACC; ++a) acc[a] += (double)warp_sum(terms[a]);
     }
     if (lane == 0) {
 #pragma unroll

@@ -26,7 +26,8 @@ constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
 // the same polynomial in (v, v'), since v' - v = (theta - v)(1 - E) + (v' - m).
 //
 // A bumped scenario (bump-and-revalue) stores DELTAS to the base scenario's
-// constants instead (dE = E_s - E_0 etc., differences taken in FP64): a 1e-4
+// constants instead (dE = E_s - E_0 etc., exact differences taken in FP64 and
+// added to the base's FP32 constants): a 1e-4
 // bump moves E or Cdl by only a few FP32 ulps, so bumped constants rounded on
 // their own would bias the finite difference.  Each delta is added inside an
 // FMA whose product varies from path to path (so its rounding is unbiased),
@@ -45,8 +46,8 @@ struct ScenConst {
 
 // First-step constants of a scenario (all paths share v0, so every step-0
 // quantity except the draws is a per-scenario constant).  Computed on the host
-// in FP64: base scenario full values, bumped scenarios deltas to the base's
-// FP32 values -- except q (decision threshold) and v0, which are full values.
+// in FP64: base scenario full values, bumped scenarios their exact differences
+// to the base's -- except q (decision threshold) and v0, which are full values.
 //   quadratic: v1 = a (b + Z_V)^2, v1 - m0 = a (Z_V (Z_V + 2b) - 1)
 //   exponential: v1 = 0 if 1 - U_V >= q, else C (L - ln(1 - U_V)), C = m0/q, L = ln q
 //   increment: x1 = K0p + Cv v1 + Cdl (v1 - m0) + sK3 sqrt(v0 + v1) Z_X, K0p = C0 + (Cv - Cd) v0
@@ -190,8 +191,10 @@ template <bool CRN>
 __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float zv, float zx, float& v, float& x,
                                           float& comp) {
   float vn, dl;
-  const float m = CRN ? v * c.E + c.thE : fmaf(v, c.E, c.thE);
-  const float s2 = CRN ? v * c.c1 + c.c2 : fmaf(v, c.c1, c.c2);
+  // CRN: round(round(v E) + thE), exactly the bumped scenarios' sequence with zero
+  // deltas (__fmul_rn / __fadd_rn are never contracted into an FMA)
+  const float m = CRN ? __fadd_rn(__fmul_rn(v, c.E), c.thE) : fmaf(v, c.E, c.thE);
+  const float s2 = CRN ? __fadd_rn(__fmul_rn(v, c.c1), c.c2) : fmaf(v, c.c1, c.c2);
   qe_from_moments(m, s2, omu, zv, vn, dl);
   const float s = v + vn;
   float inc = fmaf(c.Cv, s, c.C0);
@@ -205,11 +208,15 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
   v = vn;
 }
 
+#ifndef SIMR_KAHAN_BUMPED
+#define SIMR_KAHAN_BUMPED 1  // Kahan-compensate x in bumped scenarios too
+#endif
+
 // One step of a bumped scenario: base constants b plus deltas d.
 __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float omu, float zv, float zx,
                                             float& v, float& x, float& comp) {
-  const float m = fmaf(v, b.E, fmaf(v, d.E, d.thE)) + b.thE;
-  const float s2 = fmaf(v, b.c1, fmaf(v, d.c1, d.c2)) + b.c2;
+  const float m = __fadd_rn(fmaf(v, b.E, fmaf(v, d.E, d.thE)), b.thE);
+  const float s2 = __fadd_rn(fmaf(v, b.c1, fmaf(v, d.c1, d.c2)), b.c2);
   float vn, dl;
   qe_from_moments(m, s2, omu, zv, vn, dl);
   const float s = v + vn;
@@ -223,10 +230,14 @@ __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst&
   sm = fmaf(d.Cdl, dl, sm);
   sm = fmaf(d.sK3 * q, zx, sm);
   inc += sm;
+#if SIMR_KAHAN_BUMPED
   const float y = inc - comp;
   const float t = x + y;
   comp = (t - x) - y;
   x = t;
+#else
+  x += inc;
+#endif
   v = vn;
 }
 

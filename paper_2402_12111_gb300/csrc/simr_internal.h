@@ -36,6 +36,7 @@ struct PathLaunch {
   ScenConst sc[kMaxScen];
   FirstConst f0[kMaxScen];  // step-0 constants (used when first_split != 0)
   int32_t first_split;      // 1: step 0 of every scenario through step0_crn
+  int32_t n_v0_scen;        // 2: scenarios 1 and 2 are the up/down v0 bumps (no constant deltas)
   // finalisation (FP64)
   double disc;            // e^{-rT}
   double paths_total;     // denominator of the mean

@@ -21,6 +21,19 @@
 #include "simr_internal.h"
 #include "simr_reduce.cuh"
 
+// Tuning knobs (compile-time): resident 256-thread blocks per SM the 5-scenario
+// kernel is register-budgeted for.
+#ifndef SIMR_FD5_BLOCKS_PER_SM
+#define SIMR_FD5_BLOCKS_PER_SM 3
+#endif
+// paths per thread of the pricing (one scenario) and bump-and-revalue kernels
+#ifndef SIMR_PRICE_PPT
+#define SIMR_PRICE_PPT 2
+#endif
+#ifndef SIMR_FD_PPT
+#define SIMR_FD_PPT 1
+#endif
+
 namespace simr {
 namespace {
 
@@ -69,7 +82,9 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
 
 // One time step for all NS scenarios from the two words (w_v, w_x) of the step.
 // NS scenarios in registers; DYN: only the first L.n_scen of them are live.
-template <int NS, bool DYN>
+// Scenarios 1 .. NV differ from the base only in v0 (all constant deltas zero):
+// they take the base step, which is the bumped step's arithmetic with zero deltas.
+template <int NS, int NV, bool DYN>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
@@ -80,7 +95,10 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
 #pragma unroll
   for (int s = 1; s < NS; ++s) {
     if (DYN && s >= L.n_scen) break;
-    step_bumped(L.sc[0], L.sc[s], omu, zv, zx, v[s], x[s], c[s]);
+    if (s <= NV)
+      step_base<true>(L.sc[0], omu, zv, zx, v[s], x[s], c[s]);
+    else
+      step_bumped(L.sc[0], L.sc[s], omu, zv, zx, v[s], x[s], c[s]);
   }
 }
 
@@ -103,32 +121,56 @@ __device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uin
   }
 }
 
-template <int NS, bool DYN>
-__device__ __forceinline__ void simulate(const PathLaunch& L, uint64_t path, float (&v)[NS], float (&x)[NS],
-                                         float (&c)[NS]) {
+// PPT paths per thread, simulated step by step in lockstep: independent
+// dependency chains the scheduler can interleave (instruction-level
+// parallelism at the same occupancy).
+template <int NS, int NV, bool DYN, int PPT>
+__device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t (&path)[PPT], float (&v)[PPT][NS],
+                                             float (&x)[PPT][NS], float (&c)[PPT][NS]) {
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    v[s] = (DYN && s >= L.n_scen) ? 0.0f : L.sc[s].v0;
-    x[s] = 0.0f;
-    c[s] = 0.0f;
+  for (int j = 0; j < PPT; ++j) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      v[j][s] = (DYN && s >= L.n_scen) ? 0.0f : L.sc[s].v0;
+      x[j][s] = 0.0f;
+      c[j][s] = 0.0f;
+    }
   }
-  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+  uint32_t plo[PPT], phi[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    plo[j] = (uint32_t)path[j];
+    phi[j] = (uint32_t)(path[j] >> 32);
+  }
   const uint32_t pairs = L.steps >> 1;
   uint32_t i0 = 0;
   if (NS > 1 && L.first_split) {
-    const uint4 w = philox4x32_10(0u, plo, phi, L.option_index, L.rk);
-    step0_all<NS, DYN>(L, w.x, w.y, v, x, c);
-    if (L.steps > 1) step_all<NS, DYN>(L, w.z, w.w, v, x, c);
+    uint4 w[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(0u, plo[j], phi[j], L.option_index, L.rk);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) step0_all<NS, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
+    if (L.steps > 1) {
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
+    }
     i0 = 1;
   }
   for (uint32_t i = i0; i < pairs; ++i) {
-    const uint4 w = philox4x32_10(i, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
-    step_all<NS, DYN>(L, w.z, w.w, v, x, c);
+    uint4 w[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(i, plo[j], phi[j], L.option_index, L.rk);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
   }
   if ((L.steps & 1u) && pairs >= i0) {  // odd last step (step 0 itself when steps == 1 without the split)
-    const uint4 w = philox4x32_10(pairs, plo, phi, L.option_index, L.rk);
-    step_all<NS, DYN>(L, w.x, w.y, v, x, c);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const uint4 w = philox4x32_10(pairs, plo[j], phi[j], L.option_index, L.rk);
+      step_all<NS, NV, DYN>(L, w.x, w.y, v[j], x[j], c[j]);
+    }
   }
 }
 
@@ -167,8 +209,8 @@ __device__ __forceinline__ void write_results(const PathLaunch& L, int k, const 
 // Fused price / Greeks kernel.  TILE = 1 (single strike) or 32 (strike tiles).
 // Dynamic shared memory: accumulators [warps][n_acc][nk_pad] (FP64), then the
 // strike constants [nk_pad] (StrikeConst), then a flag word.
-template <int NS, int TILE, bool DYN>
-__global__ void __launch_bounds__(256, (NS <= 3 ? 4 : NS <= 5 ? 3 : 2)) heston_paths_kernel(const __grid_constant__ PathLaunch L,
+template <int NS, int NV, int TILE, bool DYN, int PPT>
+__global__ void __launch_bounds__(256, (NS * PPT <= 3 ? 4 : NS * PPT <= 5 ? SIMR_FD5_BLOCKS_PER_SM : 2)) heston_paths_kernel(const __grid_constant__ PathLaunch L,
                                                            const double* __restrict__ strikes,
                                                            PathOutputs out, double* __restrict__ partials,
                                                            unsigned int* __restrict__ ticket) {
@@ -195,16 +237,25 @@ __global__ void __launch_bounds__(256, (NS <= 3 ? 4 : NS <= 5 ? 3 : 2)) heston_p
   __syncthreads();
 
   double* my_acc = acc + (size_t)warp * row;
-  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  const uint64_t per_batch = (uint64_t)kWarp * PPT;
+  const uint64_t batches = (L.path_count + per_batch - 1) / per_batch;
   const uint64_t total_warps = (uint64_t)gridDim.x * warps;
   for (uint64_t b = (uint64_t)blockIdx.x * warps + warp; b < batches; b += total_warps) {
-    const uint64_t local = b * kWarp + lane;
-    const bool active = local < L.path_count;
-    float v[NS], x[NS], c[NS];
-    simulate<NS, DYN>(L, L.path_begin + local, v, x, c);
-    float S[NS];
+    uint64_t pth[PPT];
+    bool act[PPT];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) S[s] = terminal_spot(L.S0, x[s], c[s]);
+    for (int j = 0; j < PPT; ++j) {
+      const uint64_t local = b * per_batch + (uint64_t)j * kWarp + lane;
+      act[j] = local < L.path_count;
+      pth[j] = L.path_begin + local;
+    }
+    float v[PPT][NS], x[PPT][NS], c[PPT][NS];
+    simulate_ppt<NS, NV, DYN, PPT>(L, pth, v, x, c);
+    float S[PPT][NS];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) S[j][s] = terminal_spot(L.S0, x[j][s], c[j][s]);
 
     // accumulator list: 0 f, 1 f^2, then set Greek bits in order
     int a = 0, r = 0;
@@ -213,17 +264,27 @@ __global__ void __launch_bounds__(256, (NS <= 3 ? 4 : NS <= 5 ? 3 : 2)) heston_p
       const bool resim = bit == 2 || bit == 3 || bit >= 5;
       const int up = resim ? L.resim_up[r] : 0, dn = resim ? L.resim_dn[r] : 0;
       if (TILE == 1) {
-        float t = resim ? resim_term<NS>(L, up, dn, ks[0], S) : acc_term<NS>(L, bit, a, ks[0], S);
-        t = warp_sum(active ? t : 0.0f);
+        float t = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const float tj = resim ? resim_term<NS>(L, up, dn, ks[0], S[j]) : acc_term<NS>(L, bit, a, ks[0], S[j]);
+          t += act[j] ? tj : 0.0f;
+        }
+        t = warp_sum(t);
         if (lane == 0) my_acc[a] += (double)t;
       } else {
         for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
           float vals[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const StrikeConst k = ks[t0 + j];
-            const float t = resim ? resim_term<NS>(L, up, dn, k, S) : acc_term<NS>(L, bit, a, k, S);
-            vals[j] = active ? t : 0.0f;
+          for (int jj = 0; jj < 32; ++jj) {
+            const StrikeConst k = ks[t0 + jj];
+            float t = 0.0f;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+              const float tj = resim ? resim_term<NS>(L, up, dn, k, S[j]) : acc_term<NS>(L, bit, a, k, S[j]);
+              t += act[j] ? tj : 0.0f;
+            }
+            vals[jj] = t;
           }
           butterfly32(vals, lane);
           my_acc[(size_t)a * L.nk_pad + t0 + lane] += (double)vals[0];
@@ -274,26 +335,27 @@ __global__ void __launch_bounds__(256) heston_terminal_kernel(const __grid_const
                                                               float* __restrict__ x_T, float* __restrict__ v_T) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.path_count) return;
-  float v[1], x[1], c[1];
-  simulate<1, false>(L, L.path_begin + i, v, x, c);
-  x_T[i] = x[0] - c[0];
-  if (v_T) v_T[i] = v[0];
+  float v[1][1], x[1][1], c[1][1];
+  const uint64_t pth[1] = {L.path_begin + i};
+  simulate_ppt<1, 0, false, 1>(L, pth, v, x, c);
+  x_T[i] = x[0][0] - c[0][0];
+  if (v_T) v_T[i] = v[0][0];
 }
 
-template <int NS, int TILE, bool DYN>
+template <int NS, int NV, int TILE, bool DYN, int PPT = (NS == 1 ? SIMR_PRICE_PPT : SIMR_FD_PPT)>
 cudaError_t launch_t(const PathLaunch& L, const double* strikes, const PathOutputs& out, const Scratch& s,
                      int num_sms, cudaStream_t stream, int* grid_used) {
   const int tpb = 256, warps = tpb / kWarp;
   const size_t row = (size_t)L.n_acc * L.nk_pad;
   const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16;
-  auto kern = heston_paths_kernel<NS, TILE, DYN>;
+  auto kern = heston_paths_kernel<NS, NV, TILE, DYN, PPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t batches = (L.path_count + kWarp - 1) / kWarp;
+  const uint64_t batches = (L.path_count + (uint64_t)kWarp * PPT - 1) / ((uint64_t)kWarp * PPT);
   uint64_t grid = (uint64_t)num_sms * per_sm;
   const uint64_t need = (batches + warps - 1) / warps;
   if (grid > need) grid = need;
@@ -314,21 +376,22 @@ size_t paths_scratch_doubles(const PathLaunch& L, int num_sms) {
 cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathOutputs& out, const Scratch& s,
                          int num_sms, cudaStream_t stream, int* grid_used) {
   const bool one = L.nk_pad == 1;
+  const bool v2 = L.n_v0_scen == 2;  // scenarios 1, 2 are the v0 bumps (constant deltas zero)
+#define SIMR_LAUNCH(NS_, NV_, DYN_)                                                                \
+  (one ? launch_t<NS_, NV_, 1, DYN_>(L, strikes, out, s, num_sms, stream, grid_used)               \
+       : launch_t<NS_, NV_, 32, DYN_>(L, strikes, out, s, num_sms, stream, grid_used))
   switch (L.n_scen) {
     case 1:
-      return one ? launch_t<1, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
-                 : launch_t<1, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+      return SIMR_LAUNCH(1, 0, false);
     case 3:
-      return one ? launch_t<3, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
-                 : launch_t<3, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+      return v2 ? SIMR_LAUNCH(3, 2, false) : SIMR_LAUNCH(3, 0, false);
     case 5:
-      return one ? launch_t<5, 1, false>(L, strikes, out, s, num_sms, stream, grid_used)
-                 : launch_t<5, 32, false>(L, strikes, out, s, num_sms, stream, grid_used);
+      return v2 ? SIMR_LAUNCH(5, 2, false) : SIMR_LAUNCH(5, 0, false);
     default:
       if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
-      return one ? launch_t<kMaxScen, 1, true>(L, strikes, out, s, num_sms, stream, grid_used)
-                 : launch_t<kMaxScen, 32, true>(L, strikes, out, s, num_sms, stream, grid_used);
+      return v2 ? SIMR_LAUNCH(kMaxScen, 2, true) : SIMR_LAUNCH(kMaxScen, 0, true);
   }
+#undef SIMR_LAUNCH
 }
 
 cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathOutputs& out, cudaStream_t stream) {
