@@ -387,6 +387,8 @@ cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathO
       return v2 ? SIMR_LAUNCH(3, 2, false) : SIMR_LAUNCH(3, 0, false);
     case 5:
       return v2 ? SIMR_LAUNCH(5, 2, false) : SIMR_LAUNCH(5, 0, false);
+    case 11:  // all five re-simulated model-parameter Greeks
+      return v2 ? SIMR_LAUNCH(11, 2, false) : SIMR_LAUNCH(11, 0, false);
     default:
       if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
       return v2 ? SIMR_LAUNCH(kMaxScen, 2, true) : SIMR_LAUNCH(kMaxScen, 0, true);
