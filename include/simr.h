@@ -169,8 +169,12 @@ SIMR_API int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const doubl
  * the QE map where a bump would switch a path's branch, so they differ from
  * bump-and-revalue by that (small) term.
  *   ckpt_every   in   even number of steps per checkpoint segment, in [2, 1024];
- *                     0 = about sqrt(steps).  Shared memory bounds
- *                     (steps/ckpt_every + ckpt_every); SIMR_EUNSUPPORTED beyond it.
+ *                     0 = about sqrt(steps / 3); values above steps act as steps
+ *                     (rounded up to even).  Each resident thread keeps
+ *                     steps/ckpt_every checkpoints in a context-owned device
+ *                     buffer (at most 2^30 floats in all) and 3 ckpt_every
+ *                     floats of shared memory (at most 200 KB per 128-thread
+ *                     block with the accumulators); SIMR_EUNSUPPORTED beyond.
  *   price[n_strikes], stderr_out[n_strikes] (nullable)   out
  *   grad[n_strikes * 7]   out  row-major [strike][S0, v0, kappa, theta, sigma, rho, r]
  * n_strikes in [1, 256].  The rho column is NaN when |rho| = 1 (the pathwise

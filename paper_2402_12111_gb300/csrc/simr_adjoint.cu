@@ -31,13 +31,22 @@ namespace {
 #ifndef SIMR_ADJ_PPT
 #define SIMR_ADJ_PPT 1  // paths per thread of the per-strike adjoint kernel (2 measured slower)
 #endif
+#ifndef SIMR_ADJ_GCKPT
+#define SIMR_ADJ_GCKPT 1  // checkpoints in global memory (L2-resident), segment buffers in shared memory
+#endif
+
+// Shared floats per thread of the per-strike kernel.
+inline size_t adjoint_thread_smem_floats(const AdjConst& A, int ppt) {
+  return adjoint_seg_floats(A, ppt) + (SIMR_ADJ_GCKPT ? 0 : adjoint_ckpt_floats(A, ppt));
+}
 
 template <int TILE, int PPT>
 __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
                                                              double* __restrict__ partials,
-                                                             unsigned int* __restrict__ ticket) {
+                                                             unsigned int* __restrict__ ticket,
+                                                             float* __restrict__ gckpt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warps = blockDim.x / kWarp;
   const int bd = blockDim.x;
@@ -46,7 +55,13 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
   double* acc = reinterpret_cast<double*>(smem_raw);
   StrikeConst* ks = reinterpret_cast<StrikeConst*>(acc + (size_t)warps * row);
   int* s_last = reinterpret_cast<int*>(ks + L.nk_pad);
-  float* ckpt = reinterpret_cast<float*>(s_last + 4);  // path_adjoint_ppt's shared slices
+  float* sbuf = reinterpret_cast<float*>(s_last + 4);  // path_adjoint_ppt's shared slices
+  // checkpoints: this thread's column of a [slot][grid threads] global array,
+  // or of the shared slices ahead of the segment buffer
+  const int gthreads = (int)(gridDim.x * blockDim.x);
+  float* ck = SIMR_ADJ_GCKPT ? gckpt + (int)blockIdx.x * bd + tid : sbuf + tid;
+  const int ck_stride = SIMR_ADJ_GCKPT ? gthreads : bd;
+  float* seg = SIMR_ADJ_GCKPT ? sbuf + tid : sbuf + (A.n_seg - 1) * PPT * bd + tid;
 
   for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
   for (int j = threadIdx.x; j < L.nk_pad; j += blockDim.x) {
@@ -75,7 +90,7 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
       pth[j] = L.path_begin + local;
     }
     float x[PPT], comp[PPT], g[PPT][5], S[PPT];
-    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt, bd, tid, x, comp, g);
+    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride, seg, bd, x, comp, g);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
@@ -157,7 +172,8 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   if (i >= L.path_count) return;  // no block-wide synchronisation below
   float x[1], comp[1], g[1][5];
   const uint64_t pth[1] = {L.path_begin + i};
-  path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt, bd, tid, x, comp, g);
+  path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt + tid, bd,
+                      ckpt + (A.n_seg - 1) * bd + tid, bd, x, comp, g);
   x_T[i] = x[0] - comp[0];
 #pragma unroll
   for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];
@@ -170,7 +186,7 @@ cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const doubl
   const int tpb = 128, warps = tpb / kWarp;
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
   const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-                      adjoint_floats_per_thread(A, PPT) * tpb * sizeof(float);
+                      adjoint_thread_smem_floats(A, PPT) * tpb * sizeof(float);
   auto kern = heston_adjoint_kernel<TILE, PPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -184,7 +200,9 @@ cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const doubl
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   if ((size_t)grid * row > s.partial_doubles) return cudaErrorMemoryAllocation;
-  kern<<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket);
+  if (SIMR_ADJ_GCKPT && (size_t)grid * tpb * adjoint_ckpt_floats(A, PPT) > s.ckpt_floats)
+    return cudaErrorMemoryAllocation;
+  kern<<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket, s.ckpt);
   return cudaGetLastError();
 }
 
@@ -197,12 +215,17 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A) {
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
   return 4 * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-         adjoint_floats_per_thread(A, SIMR_ADJ_PPT) * 128 * sizeof(float);
+         adjoint_thread_smem_floats(A, SIMR_ADJ_PPT) * 128 * sizeof(float);
+}
+
+size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms) {
+  // at most 16 resident blocks of 128 threads per SM
+  return SIMR_ADJ_GCKPT ? (size_t)num_sms * 16 * 128 * adjoint_ckpt_floats(A, SIMR_ADJ_PPT) : 0;
 }
 
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream) {
   const int tpb = 128;
-  const size_t smem = adjoint_floats_per_thread(A, 1) * tpb * sizeof(float);
+  const size_t smem = (size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * tpb * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(heston_paths_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

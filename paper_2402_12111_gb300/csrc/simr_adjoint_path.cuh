@@ -109,131 +109,144 @@ __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float 
   return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
 }
 
+// The stored data of one step (recompute pass): state, branch draw, Z_X.
+__device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, uint32_t wx, float* bv, float* bd_,
+                                          float* bz, float& v) {
+  const float omu = 0.5f * (1.0f - xv_v), zv = norminv_centered(xv_v);
+  *bv = v;
+  *bd_ = branch_draw(c, v, omu, zv);
+  *bz = norminv_centered(centered_uniform(wx));
+  v = qe_only(c, v, omu, zv);
+}
+
+// The FP64 map of the sweep's sums onto d x_T / d(v0, kappa, theta, sigma, rho).
+__device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a, float (&g)[5]) {
+  const double Amv = a.Amv, Asv = a.Asv, As = a.As, Ad = a.Ad, Adl = a.Adl, Am = a.Am, Ak3 = a.Ak3;
+  g[0] = a.vbar;
+  g[1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
+  g[2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
+  g[3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
+  g[4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+}
+
 // Forward pass with checkpoints, then the reverse sweep, for PPT paths in
 // lockstep (independent dependency chains for the scheduler to interleave):
 // x_T (with its Kahan remainder) and g = d x_T / d(v0, kappa, theta, sigma, rho)
-// per path.  The forward pass runs the variance recursion only (x_T is not
-// needed before the sweep ends); the reverse sweep adds up the log-spot
-// increments as it goes.  Shared memory, per thread column tid of a block of bd:
-// ckpt[(slot * PPT + j) * bd + tid] (n_seg slots) and, after it, the segment's
-// states, branch draws and Z_X: seg[((q * k + i) * PPT + j) * bd + tid], q = 0..2;
-// the recompute pass of a segment keeps them there, so the reverse sweep
+// per path.  The forward pass runs the variance recursion only, and only up to
+// the last checkpoint (x_T is not needed before the sweep ends; the last
+// segment is recomputed from its checkpoint anyway); the reverse sweep adds up
+// the log-spot increments as it goes.  Checkpoint (slot, path j) of this thread
+// at ck[(slot * PPT + j) * ck_stride] (n_seg - 1 slots; shared or global memory);
+// the segment's states, branch draws and Z_X in this thread's column of a
+// shared buffer of bd columns: seg[((q * k + i) * PPT + j) * bd], q = 0..2.
+// The recompute pass of a segment keeps them there, so the reverse sweep
 // regenerates nothing.
 template <int PPT>
 __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
-                                                 const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT],
-                                                 float* ckpt, int bd, int tid, float (&x_out)[PPT],
+                                                 const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
+                                                 int ck_stride, float* seg, int bd, float (&x_out)[PPT],
                                                  float (&comp_out)[PPT], float (&g)[PPT][5]) {
   const float theta = A.theta;
   const uint32_t k = (uint32_t)A.ckpt_every;
-  const int stride = PPT * bd;  // between consecutive slots / steps of one thread's column
-  float* ck = ckpt + tid;
-  float* s0 = ckpt + A.n_seg * stride + tid;  // states
-  float* s1 = s0 + (int)k * stride;           // branch draws
-  float* s2 = s1 + (int)k * stride;           // Z_X
+  const int n_seg = A.n_seg;
+  const int stride = PPT * bd;  // between consecutive steps of one thread's segment column
   uint32_t plo[PPT], phi[PPT];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     plo[j] = (uint32_t)path[j];
     phi[j] = (uint32_t)(path[j] >> 32);
   }
-#define SIMR_CK(slot, j) ck[(int)(slot) * stride + (j) * bd]
-#define SIMR_SG(q, i, j) s##q[(int)(i) * stride + (j) * bd]
+#define SIMR_CK(slot, j) ck[((int)(slot) * PPT + (j)) * ck_stride]
 
-  // forward pass: the variance recursion with checkpoints (k is even, so
-  // checkpoints fall on even steps)
+  // forward pass: the variance recursion up to the last checkpoint, (n_seg - 1) k
+  // < N; k is even, so every pair of steps below it is whole
   float v[PPT];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) v[j] = c.v0;
-  for (uint32_t p = 0; 2 * p < N; ++p) {
-    const uint32_t n = 2 * p;
-    uint4 w[PPT];
+  for (int sg = 0; sg < n_seg - 1; ++sg) {
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
-    if (n % k == 0) {
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) SIMR_CK(n / k, j) = v[j];
-    }
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const float xv = centered_uniform(w[j].x);
-      v[j] = qe_only(c, v[j], 0.5f * (1.0f - xv), norminv_centered(xv));
-    }
-    if (n + 1 < N) {
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const float xv = centered_uniform(w[j].z);
-        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xv), norminv_centered(xv));
-      }
-    }
-  }
-
-  // reverse sweep, segment by segment
-  AdjSums as[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) as[j] = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  for (int sgi = A.n_seg - 1; sgi >= 0; --sgi) {
-    const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
-    float vv[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) vv[j] = SIMR_CK(sgi, j);
-    for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
-      const uint32_t i = 2 * p - n0;
+    for (int j = 0; j < PPT; ++j) SIMR_CK(sg, j) = v[j];
+    const uint32_t p0 = (uint32_t)sg * (k / 2);
+    for (uint32_t p = p0; p < p0 + k / 2; ++p) {
       uint4 w[PPT];
 #pragma unroll
       for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
-        const float xv = centered_uniform(w[j].x);
-        const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
-        SIMR_SG(0, i, j) = vv[j];
-        SIMR_SG(1, i, j) = branch_draw(c, vv[j], omu, zv);
-        SIMR_SG(2, i, j) = norminv_centered(centered_uniform(w[j].y));
-        vv[j] = qe_only(c, vv[j], omu, zv);
-      }
-      if (2 * p + 1 < n1) {
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-          const float xv = centered_uniform(w[j].z);
-          const float omu = 0.5f * (1.0f - xv), zv = norminv_centered(xv);
-          SIMR_SG(0, i + 1, j) = vv[j];
-          SIMR_SG(1, i + 1, j) = branch_draw(c, vv[j], omu, zv);
-          SIMR_SG(2, i + 1, j) = norminv_centered(centered_uniform(w[j].w));
-          vv[j] = qe_only(c, vv[j], omu, zv);
-        }
-      }
-    }
-    float vnext[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) vnext[j] = vv[j];  // v_{n1}
-    for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const float vc = SIMR_SG(0, i, j);
-        adjoint_step(c, theta, vc, vnext[j], SIMR_SG(1, i, j), SIMR_SG(2, i, j), as[j]);
-        vnext[j] = vc;
+        const float xa = centered_uniform(w[j].x);
+        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xa), norminv_centered(xa));
+        const float xb = centered_uniform(w[j].z);
+        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xb), norminv_centered(xb));
       }
     }
   }
-#undef SIMR_CK
+
+  AdjSums as[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) as[j] = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+
+  {
+    float* s0 = seg;                   // states
+    float* s1 = s0 + (int)k * stride;  // branch draws
+    float* s2 = s1 + (int)k * stride;  // Z_X
+#define SIMR_SG(q, i, j) s##q[(int)(i) * stride + (j) * bd]
+    // the last checkpoint is the forward pass's final state; each earlier one is
+    // loaded a segment ahead of its use
+    float ck_next[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) ck_next[j] = v[j];
+    for (int sgi = n_seg - 1; sgi >= 0; --sgi) {
+      const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
+      float vv[PPT];
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) vv[j] = ck_next[j];
+      if (sgi > 0) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) ck_next[j] = SIMR_CK(sgi - 1, j);
+      }
+      for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
+        const uint32_t i = 2 * p - n0;
+        uint4 w[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+          keep_step(c, centered_uniform(w[j].x), w[j].y, &SIMR_SG(0, i, j), &SIMR_SG(1, i, j), &SIMR_SG(2, i, j),
+                    vv[j]);
+        if (2 * p + 1 < n1) {
+#pragma unroll
+          for (int j = 0; j < PPT; ++j)
+            keep_step(c, centered_uniform(w[j].z), w[j].w, &SIMR_SG(0, i + 1, j), &SIMR_SG(1, i + 1, j),
+                      &SIMR_SG(2, i + 1, j), vv[j]);
+        }
+      }
+      float vnext[PPT];
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) vnext[j] = vv[j];  // v_{n1}
+      for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const float vc = SIMR_SG(0, i, j);
+          adjoint_step(c, theta, vc, vnext[j], SIMR_SG(1, i, j), SIMR_SG(2, i, j), as[j]);
+          vnext[j] = vc;
+        }
+      }
+    }
 #undef SIMR_SG
+  }
+#undef SIMR_CK
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     x_out[j] = as[j].x;
     comp_out[j] = as[j].comp;
-    const double Amv = as[j].Amv, Asv = as[j].Asv, As = as[j].As, Ad = as[j].Ad, Adl = as[j].Adl, Am = as[j].Am,
-                 Ak3 = as[j].Ak3;
-    g[j][0] = as[j].vbar;
-    g[j][1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
-    g[j][2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
-    g[j][3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
-    g[j][4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+    adjoint_map(A, as[j], g[j]);
   }
 }
 
-// Shared floats per thread of path_adjoint_ppt.
-__host__ __device__ inline size_t adjoint_floats_per_thread(const AdjConst& A, int ppt) {
-  return (size_t)(A.n_seg + 3 * A.ckpt_every) * ppt;
+// Floats per thread of path_adjoint_ppt: checkpoints and the segment buffer.
+__host__ __device__ inline size_t adjoint_ckpt_floats(const AdjConst& A, int ppt) { return (size_t)A.n_seg * ppt; }
+__host__ __device__ inline size_t adjoint_seg_floats(const AdjConst& A, int ppt) {
+  return (size_t)3 * A.ckpt_every * ppt;
 }
 
 // Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho, 8 r (before -T P).

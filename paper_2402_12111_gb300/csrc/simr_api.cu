@@ -24,6 +24,8 @@ struct simr_ctx {
   double* partials = nullptr;
   size_t partial_doubles = 0;
   unsigned int* ticket = nullptr;  // 256-byte block: ticket word at 0, status word at 64
+  float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]
+  size_t ckpt_floats = 0;
   int* status = nullptr;
   // staging for host-pointer arguments
   double* dev_strikes = nullptr;
@@ -339,11 +341,12 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
 // adjoint kernel (formulas beside the kernel in simr_adjoint.cu).
 int build_adjoint(const simr_heston& m, uint32_t steps, uint32_t ckpt_every, AdjConst* A) {
   uint32_t k = ckpt_every;
-  if (k == 0) {  // about sqrt(steps) steps per segment, even
+  if (k == 0) {  // the even k near sqrt(steps / 3) that minimises steps / k + 3 k shared floats
     k = 2;
-    while ((uint64_t)k * k < steps) k += 2;
+    while (3ull * k * k < steps) k += 2;
   }
   if ((k & 1u) || k < 2 || k > 1024) return fail(SIMR_EINVAL, "ckpt_every must be 0 or an even number in [2, 1024]");
+  if (k > steps) k = steps + (steps & 1u);  // one segment either way; size its buffer to the path
   const double dt = m.T / (double)steps, kdt = m.kappa * dt;
   const double E = std::exp(-kdt), omE = -std::expm1(-kdt), s2 = m.sigma * m.sigma, rs = m.rho / m.sigma;
   const double dE_dk = -dt * E;
@@ -523,7 +526,7 @@ int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vecto
     b.sc = base_const(o.m, o.steps);
     if (adjoint) {
       if ((rc = build_adjoint(o.m, o.steps, 0, &b.A))) return rc;
-      smem = std::max(smem, b.A.n_seg + 3 * b.A.ckpt_every);
+      smem = std::max(smem, adjoint_thread_floats(b.A.n_seg, b.A.ckpt_every, 1));
     }
     b.S0 = (float)o.m.S0;
     b.K = (float)o.K;
@@ -638,6 +641,7 @@ void simr_destroy(simr_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   cudaFree(ctx->partials);
+  cudaFree(ctx->ckpt);
   cudaFree(ctx->ticket);
   cudaFree(ctx->dev_strikes);
   cudaFree(ctx->dev_out);
@@ -729,6 +733,9 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   if (adjoint_smem_bytes(L, A) > 200 * 1024)
     return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
                 A.ckpt_every, steps);
+  if (adjoint_ckpt_scratch_floats(A, ctx->num_sms) > (1ull << 30))
+    return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps gives more than 2^30 checkpoint floats",
+                A.ckpt_every, steps);
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
   OutStage o;
@@ -742,8 +749,10 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   if ((rc = ensure(&ctx->partials, &ctx->partial_doubles, adjoint_scratch_doubles(L, ctx->num_sms),
                    "reduction scratch")))
     return rc;
+  if ((rc = ensure(&ctx->ckpt, &ctx->ckpt_floats, adjoint_ckpt_scratch_floats(A, ctx->num_sms), "checkpoints")))
+    return rc;
   AdjOutputs out{o.dev[0], o.dev[1], o.dev[2], ctx->status};
-  Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles};
+  Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles, ctx->ckpt, ctx->ckpt_floats};
   cudaError_t e = launch_adjoint(L, A, ks, out, sc, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernel");
   return finish_outputs(ctx, o, st);
@@ -761,7 +770,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   if (!is_device_ptr(x_T) || !is_device_ptr(grad)) return fail(SIMR_EINVAL, "x_T and grad must be device pointers");
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
-  if ((size_t)(A.n_seg + 3 * A.ckpt_every) * 128 * sizeof(float) > 200 * 1024)
+  if ((size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * 128 * sizeof(float) > 200 * 1024)
     return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
                 A.ckpt_every, steps);
   if ((rc = with_device(ctx))) return rc;

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         const bool active = b + lane < I.count;
         float x[1], comp[1], g[1][5];
         const uint64_t pth[1] = {I.path_begin + b + lane};
-        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f, bd, tid, x, comp, g);
+        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd, smem_f + (O.A.n_seg - 1) * bd + tid, bd,
+                            x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;

@@ -66,6 +66,11 @@ struct AdjConst {
   double D_over_sigma, B_over_sigma, dsK3_drho;
 };
 
+// Shared floats per thread of the per-path adjoint with checkpoints in shared
+// memory: n_seg checkpoints and a segment buffer of 3 k floats (state, branch
+// draw, Z_X) per path.
+__host__ __device__ inline int adjoint_thread_floats(int n_seg, int k, int ppt) { return (n_seg + 3 * k) * ppt; }
+
 struct AdjOutputs {
   double* price;    // [n_strikes]
   double* stderr_;  // [n_strikes] or null
@@ -111,6 +116,8 @@ struct Scratch {
   double* partials;      // [grid][n_acc * nk_pad]
   unsigned int* ticket;  // zero between launches
   size_t partial_doubles;
+  float* ckpt = nullptr;  // adjoint checkpoints in global memory
+  size_t ckpt_floats = 0;
 };
 
 // Launch the fused price / Greeks kernel; returns a cudaError_t.
@@ -128,6 +135,7 @@ cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double*
                            const Scratch& s, int num_sms, cudaStream_t stream);
 size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms);
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A);
+size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms);
 // Per-path x_T and d x_T / d(v0, kappa, theta, sigma, rho) ([n][5]).
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream);
 
