@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
     ap.add_argument("--no-book", action="store_true", help="skip the 1,024-option heterogeneous book leg")
+    ap.add_argument("--no-headline", action="store_true",
+                    help="skip the 8-underlying, 1,024-step, 2^26-path adjoint vs bump-and-revalue leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
     ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book"],
                     help="only run one call W + K times on the workload (for profilers); prints no JSON")
@@ -391,6 +393,42 @@ def run_native(args):
             book[f"{name}_ms"] = ms_b
             book[f"{name}_path_steps_per_s"] = ps_book / (ms_b * 1e-3)
 
+    # large-scale headline: 8 underlyings (book-style parameters), 32 strikes each,
+    # 1,024 steps, 2^26 paths; price, adjoint Greeks (checkpoint every 32 steps) and
+    # CRN bump-and-revalue of the same 7 sensitivities, one timed pass each
+    head = None
+    if not args.no_headline:
+        hw = workloads.headline()
+        fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
+        ps_head = sum(u.steps * u.paths for u in hw)
+        head = {"underlyings": len(hw), "time_steps": hw[0].steps, "paths": hw[0].paths,
+                "strikes": len(hw[0].strikes), "ckpt_every": hw[0].ckpt_every, "path_steps": ps_head,
+                "sensitivities": list(fd7)}
+        Kh = [torch.as_tensor(u.strikes, dtype=torch.float64, device=dev) for u in hw]
+        legs = {
+            "price": lambda u, k: simr.price(u.model, k, u.is_put, u.steps, u.paths, u.seed),
+            "adjoint": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
+                                                        ckpt_every=u.ckpt_every),
+            "fd7": lambda u, k: simr.greeks_fd(u.model, k, u.is_put, u.steps, u.paths, u.seed, greeks=fd7,
+                                               rel_bump=u.rel_bump),
+        }
+        for name, fn in legs.items():
+            u0 = hw[0]
+            small = workloads.Workload(u0.name, u0.model, u0.strikes, u0.steps, 1 << 16, ckpt_every=u0.ckpt_every)
+            fn(small, Kh[0])  # warm-up (context scratch, module load)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for u, k in zip(hw, Kh):
+                fn(u, k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) * 1e-3
+            head[f"{name}_s"] = sec
+            head[f"{name}_path_steps_per_s"] = ps_head / sec
+        head["adjoint_speedup_vs_fd"] = head["fd7_s"] / head["adjoint_s"]
+        head["adjoint_cost_vs_price"] = head["adjoint_s"] / head["price_s"]
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -423,6 +461,7 @@ def run_native(args):
         "gpu_launches": args.steps,
         "adjoint_vs_fd": adj,
         "book": book,
+        "headline": head,
         "kernel_source_sha": sha,
         "wall_s_timed_region": t_wall,
     }

@@ -31,16 +31,19 @@ namespace {
 #ifndef SIMR_ADJ_PPT
 #define SIMR_ADJ_PPT 1  // paths per thread of the per-strike adjoint kernel (2 measured slower)
 #endif
-#ifndef SIMR_ADJ_GCKPT
-#define SIMR_ADJ_GCKPT 1  // checkpoints in global memory (L2-resident), segment buffers in shared memory
-#endif
-
-// Shared floats per thread of the per-strike kernel.
-inline size_t adjoint_thread_smem_floats(const AdjConst& A, int ppt) {
-  return adjoint_seg_floats(A, ppt) + (SIMR_ADJ_GCKPT ? 0 : adjoint_ckpt_floats(A, ppt));
+// Dynamic shared memory of the per-strike kernel: strike constants, the
+// last-block flag, then the segment buffers; the per-warp FP64 accumulator rows
+// come first when they live in shared memory throughout (RACC false), or reuse
+// the segment buffers' space once the path loop has ended (RACC true: lane l
+// accumulates strike l of the one 32-strike tile in registers).
+inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int tpb, int ppt, bool racc) {
+  const size_t acc_bytes = (size_t)(tpb / kWarp) * kAdjAcc * L.nk_pad * sizeof(double);
+  const size_t buf_bytes = adjoint_seg_floats(A, ppt) * tpb * sizeof(float);
+  const size_t head = L.nk_pad * sizeof(StrikeConst) + 16;
+  return racc ? head + (buf_bytes > acc_bytes ? buf_bytes : acc_bytes) : acc_bytes + head + buf_bytes;
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool RACC>
 __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
@@ -52,18 +55,22 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
   const int bd = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
   const int row = kAdjAcc * L.nk_pad;
-  double* acc = reinterpret_cast<double*>(smem_raw);
-  StrikeConst* ks = reinterpret_cast<StrikeConst*>(acc + (size_t)warps * row);
+  const size_t acc_bytes = (size_t)warps * row * sizeof(double);
+  const size_t ks_off = RACC ? 0 : acc_bytes;
+  StrikeConst* ks = reinterpret_cast<StrikeConst*>(smem_raw + ks_off);
   int* s_last = reinterpret_cast<int*>(ks + L.nk_pad);
-  float* sbuf = reinterpret_cast<float*>(s_last + 4);  // path_adjoint_ppt's shared slices
-  // checkpoints: this thread's column of a [slot][grid threads] global array,
-  // or of the shared slices ahead of the segment buffer
-  const int gthreads = (int)(gridDim.x * blockDim.x);
-  float* ck = SIMR_ADJ_GCKPT ? gckpt + (int)blockIdx.x * bd + tid : sbuf + tid;
-  const int ck_stride = SIMR_ADJ_GCKPT ? gthreads : bd;
-  float* seg = SIMR_ADJ_GCKPT ? sbuf + tid : sbuf + (A.n_seg - 1) * PPT * bd + tid;
+  float* sbuf = reinterpret_cast<float*>(s_last + 4);  // path_adjoint_ppt's segment buffers
+  double* acc = RACC ? reinterpret_cast<double*>(sbuf) : reinterpret_cast<double*>(smem_raw);
+  // checkpoints: this thread's column of a [slot][grid threads] global array
+  float* ck = gckpt + (int)blockIdx.x * bd + tid;
+  const int ck_stride = (int)(gridDim.x * blockDim.x);
+  float* seg = sbuf + tid;
+  double racc[RACC ? kAdjAcc : 1];
+#pragma unroll
+  for (int a = 0; a < (RACC ? kAdjAcc : 1); ++a) racc[a] = 0.0;
 
-  for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
+  if (!RACC)
+    for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
   for (int j = threadIdx.x; j < L.nk_pad; j += blockDim.x) {
     StrikeConst k{0.0f, 0.0f, 0.0f, 0.0f};
     if (j < L.n_strikes) {
@@ -95,6 +102,21 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
     // per-strike terms, reduced over the warp's paths
+    if (RACC) {
+#pragma unroll
+      for (int a = 0; a < kAdjAcc; ++a) {
+        float vals[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          float t = 0.0f;
+#pragma unroll
+          for (int j = 0; j < PPT; ++j) t += act[j] ? adj_term(a, put, S[j], ks[jj].K, g[j], A.invS0, A.T) : 0.0f;
+          vals[jj] = t;
+        }
+        butterfly32(vals, lane);
+        racc[a] += (double)vals[0];
+      }
+    } else
     for (int a = 0; a < kAdjAcc; ++a) {
       if (TILE == 1) {
         float t = 0.0f;
@@ -120,6 +142,11 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
     }
   }
   __syncthreads();
+  if (RACC) {  // the segment buffers are free now: spill the lanes' sums into the rows
+#pragma unroll
+    for (int a = 0; a < kAdjAcc; ++a) my_acc[(size_t)a * L.nk_pad + lane] = racc[a];
+    __syncthreads();
+  }
 
   double* my_row = partials + (size_t)blockIdx.x * row;
   for (int i = threadIdx.x; i < row; i += blockDim.x) {
@@ -179,15 +206,14 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];
 }
 
-template <int TILE>
+template <int TILE, bool RACC>
 cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                              const Scratch& s, int num_sms, cudaStream_t stream) {
   constexpr int PPT = SIMR_ADJ_PPT;
   const int tpb = 128, warps = tpb / kWarp;
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
-  const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-                      adjoint_thread_smem_floats(A, PPT) * tpb * sizeof(float);
-  auto kern = heston_adjoint_kernel<TILE, PPT>;
+  const size_t smem = adjoint_smem_bytes_t(L, A, tpb, PPT, RACC);
+  auto kern = heston_adjoint_kernel<TILE, PPT, RACC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -200,8 +226,7 @@ cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const doubl
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   if ((size_t)grid * row > s.partial_doubles) return cudaErrorMemoryAllocation;
-  if (SIMR_ADJ_GCKPT && (size_t)grid * tpb * adjoint_ckpt_floats(A, PPT) > s.ckpt_floats)
-    return cudaErrorMemoryAllocation;
+  if ((size_t)grid * tpb * adjoint_ckpt_floats(A, PPT) > s.ckpt_floats) return cudaErrorMemoryAllocation;
   kern<<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket, s.ckpt);
   return cudaGetLastError();
 }
@@ -213,14 +238,12 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
 }
 
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A) {
-  const size_t row = (size_t)kAdjAcc * L.nk_pad;
-  return 4 * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16 +
-         adjoint_thread_smem_floats(A, SIMR_ADJ_PPT) * 128 * sizeof(float);
+  return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32);
 }
 
 size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms) {
   // at most 16 resident blocks of 128 threads per SM
-  return SIMR_ADJ_GCKPT ? (size_t)num_sms * 16 * 128 * adjoint_ckpt_floats(A, SIMR_ADJ_PPT) : 0;
+  return (size_t)num_sms * 16 * 128 * adjoint_ckpt_floats(A, SIMR_ADJ_PPT);
 }
 
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream) {
@@ -236,8 +259,9 @@ cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* 
 
 cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                            const Scratch& s, int num_sms, cudaStream_t stream) {
-  return L.nk_pad == 1 ? launch_adjoint_t<1>(L, A, strikes, out, s, num_sms, stream)
-                       : launch_adjoint_t<32>(L, A, strikes, out, s, num_sms, stream);
+  if (L.nk_pad == 1) return launch_adjoint_t<1, false>(L, A, strikes, out, s, num_sms, stream);
+  if (L.nk_pad == 32) return launch_adjoint_t<32, true>(L, A, strikes, out, s, num_sms, stream);
+  return launch_adjoint_t<32, false>(L, A, strikes, out, s, num_sms, stream);
 }
 
 }  // namespace simr

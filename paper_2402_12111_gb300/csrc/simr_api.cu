@@ -949,6 +949,10 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     key = fnv1a(&flags, sizeof(flags), key);
     key = fnv1a(&chunk, sizeof(chunk), key);
     key = fnv1a(&out, sizeof(out), key);
+    // the captured launches hold the context's device buffers: a reallocation
+    // since the capture makes a new graph
+    const void* bufs[3] = {ctx->b_opts, ctx->b_items, ctx->b_partials};
+    key = fnv1a(bufs, sizeof(bufs), key);
     if (!(ctx->graph_exec && ctx->graph_key == key)) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
       ctx->graph_exec = nullptr;

@@ -63,6 +63,19 @@ def test_batch_graph_replay_and_autotune_agree(simr, small_book):
     torch.testing.assert_close(c, ref[:7], rtol=1e-12, atol=1e-12)
 
 
+def test_batch_graph_recaptured_after_buffer_growth(simr, small_book):
+    # a graph holds the context's device tables; a larger book in between grows
+    # (reallocates) them, and the next replay of the first book must not use the
+    # freed ones
+    ref = simr.batch(small_book, seed=6, autotune=False)[0]
+    a = simr.batch(small_book, seed=6, graph=True)[0]
+    big = workloads.book(n_options=3000, seed=8, steps_range=(1, 4), paths_range=(1, 64))
+    simr.batch(big, seed=6, autotune=False)
+    b = simr.batch(small_book, seed=6, graph=True)[0]
+    torch.testing.assert_close(a, ref, rtol=1e-12, atol=1e-12)
+    torch.testing.assert_close(b, ref, rtol=1e-12, atol=1e-12)
+
+
 def test_batch_sample_matches_oracle(simr, small_book):
     p, _, _ = simr.batch(small_book, seed=2)
     p = p.cpu().numpy()
