@@ -80,6 +80,7 @@ def lib():
             L.oracle_path_grad_reverse.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_path_grad_forward.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_adjoint.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
+            L.oracle_states.argtypes = [H, u32, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_max_threads.restype = c_int
             L.oracle_set_threads.argtypes = [c_int]
             _lib = L
@@ -172,6 +173,21 @@ def terminal_diag(model, steps: int, seed: int, path_begin: int, n_paths: int, o
     if rc != 0:
         raise ValueError(f"oracle_terminal_diag failed ({rc})")
     return x, v, mg, cd
+
+
+def states(model, steps: int, every: int, seed: int, path_begin: int, n_paths: int, option_index: int = 0):
+    """(S, v) of shape [n_paths, steps // every]: spot and variance after steps
+    every, 2 every, ..., steps (the exercise dates of a Bermudan option)."""
+    if every < 1 or steps % every:
+        raise ValueError("every must divide steps")
+    n_ex = steps // every
+    S = np.empty((n_paths, n_ex))
+    v = np.empty((n_paths, n_ex))
+    rc = lib().oracle_states(ctypes.byref(_model(model)), steps, every, seed, option_index, path_begin, n_paths,
+                             _dp(S), _dp(v))
+    if rc != 0:
+        raise ValueError(f"oracle_states failed ({rc})")
+    return S, v
 
 
 def price(model, strikes, is_put: bool, steps: int, paths: int, seed: int, option_index: int = 0):

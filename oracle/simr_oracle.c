@@ -11,6 +11,8 @@
  *   LogPricePathQE         -> log-spot update in simulate_path
  *   AssetPathExponential   -> S_T = S0 * exp(x_N) in the payoff functions
  *   reduction over paths   -> oracle_price (Sec. 6: paths reduced with a cross-path sum)
+ *   writeLongstaffSchwartzPath -> oracle_states (per-path states at the exercise
+ *                             dates; the regression itself is in lsm.py)
  * The per-path state is carried from timestep to timestep exactly as in the
  * paper's asset/timestep/path loop nest (Sec. 5.1, Listing 2): here the path is
  * the outer loop and the timestep the inner one, which changes nothing in the
@@ -245,11 +247,14 @@ static void step_constants(const oracle_heston* m, uint32_t steps, double k[10])
 
 /*
  * Simulate one path for `steps` steps from v = v0, x = ln(S/S0) = 0.
- * Writes x_N, v_N and the smallest decision margin met on the path.
+ * Writes x_N, v_N and the smallest decision margin met on the path; with
+ * every > 0 it also records (x, v) after steps every, 2 every, ... into
+ * x_rec[], v_rec[] (the states at a Bermudan option's exercise dates).
  */
-static void simulate_path(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
-                          uint32_t option_index, uint64_t path, double* x_out, double* v_out,
-                          double* margin_out, double* cond_out) {
+static void simulate_path_rec(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
+                              uint32_t option_index, uint64_t path, double* x_out, double* v_out,
+                              double* margin_out, double* cond_out, uint32_t every, double* x_rec,
+                              double* v_rec) {
   double v = m->v0, x = 0.0, min_margin = INFINITY, min_cond = INFINITY;
   for (uint32_t n = 0; n < steps; ++n) {
     double u_v, u_x;
@@ -263,11 +268,21 @@ static void simulate_path(const oracle_heston* m, const double* k, uint32_t step
     double z_x = oracle_norminv(u_x);
     x += k[4] + k[5] * v + k[6] * v_next + sqrt(k[7] * v + k[8] * v_next) * z_x;
     v = v_next;
+    if (every && (n + 1) % every == 0) {
+      x_rec[(n + 1) / every - 1] = x;
+      v_rec[(n + 1) / every - 1] = v;
+    }
   }
   *x_out = x;
   *v_out = v;
   if (margin_out) *margin_out = min_margin;
   if (cond_out) *cond_out = min_cond;
+}
+
+static void simulate_path(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
+                          uint32_t option_index, uint64_t path, double* x_out, double* v_out,
+                          double* margin_out, double* cond_out) {
+  simulate_path_rec(m, k, steps, seed, option_index, path, x_out, v_out, margin_out, cond_out, 0, NULL, NULL);
 }
 
 int oracle_max_threads(void) {
@@ -316,6 +331,31 @@ int oracle_terminal_diag(const oracle_heston* m, uint32_t steps, uint64_t seed, 
   for (int64_t i = 0; i < n_paths; ++i) {
     simulate_path(m, k, steps, seed, option_index, path_begin + (uint64_t)i, &x_T[i], &v_T[i], &margin[i],
                   &cond[i]);
+  }
+  return 0;
+}
+
+/*
+ * States at the exercise dates of a Bermudan option, for the Longstaff-Schwartz
+ * regression (the paper's longstaffSchwartzPathReduction stage consumes the
+ * per-path states that writeLongstaffSchwartzPath writes out, Sec. 5): dates
+ * t_j = (j + 1) every dt, j = 0 .. n_ex - 1 with n_ex = steps / every (every
+ * must divide steps, so the last date is the maturity).  S[i * n_ex + j] =
+ * S0 exp(x) and v[i * n_ex + j] for path path_begin + i.
+ */
+int oracle_states(const oracle_heston* m, uint32_t steps, uint32_t every, uint64_t seed, uint32_t option_index,
+                  uint64_t path_begin, int64_t n_paths, double* S, double* v) {
+  if (steps == 0 || every == 0 || steps % every != 0 || n_paths < 0) return -1;
+  const int64_t n_ex = steps / every;
+  double k[10];
+  step_constants(m, steps, k);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_paths; ++i) {
+    double xT, vT;
+    double* xs = &S[i * n_ex];
+    simulate_path_rec(m, k, steps, seed, option_index, path_begin + (uint64_t)i, &xT, &vT, NULL, NULL, every, xs,
+                      &v[i * n_ex]);
+    for (int64_t j = 0; j < n_ex; ++j) xs[j] = m->S0 * exp(xs[j]);
   }
   return 0;
 }
