@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
     ap.add_argument("--no-book", action="store_true", help="skip the 1,024-option heterogeneous book leg")
+    ap.add_argument("--no-lsm", action="store_true", help="skip the Longstaff-Schwartz Bermudan put leg")
     ap.add_argument("--no-headline", action="store_true",
                     help="skip the 8-underlying, 1,024-step, 2^26-path adjoint vs bump-and-revalue leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
-    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book"],
+    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "lsm"],
                     help="only run one call W + K times on the workload (for profilers); prints no JSON")
     return ap.parse_args()
 
@@ -185,11 +186,13 @@ def cpu_oracle_run(w, paths_sample: int):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(w, paths_sample: int = 1 << 16):
+def cpu_baseline(w, paths_sample: int = 1 << 20):
+    """The oracle on the host cores; by default the whole workload (2^20 paths, ~12 s on 16 cores)."""
     import oracle
 
     oracle.build()
     cores = oracle.max_threads()
+    paths_sample = min(paths_sample, w.paths)
     dt = cpu_oracle_run(w, paths_sample)
     return {"value": paths_sample * w.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{w.name}: paths [0, {paths_sample}) of {w.paths}, all {w.steps} steps, all "
@@ -245,6 +248,10 @@ def run_profile_leg(args):
     if args.profile_leg == "book":
         opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))
         fn = lambda: simr.batch(opts, seed=1, adjoint=True, autotune=False)  # noqa: E731
+    elif args.profile_leg == "lsm":
+        lw = workloads.lsm()
+        n = args.paths or lw.paths
+        fn = lambda: simr.lsm_price(lw.model, float(lw.strikes[0]), True, lw.steps, 1, n, lw.seed)  # noqa: E731
     else:
         fn = legs[args.profile_leg]
     for _ in range(args.warmup + args.steps):
@@ -429,6 +436,44 @@ def run_native(args):
         head["adjoint_speedup_vs_fd"] = head["fd7_s"] / head["adjoint_s"]
         head["adjoint_cost_vs_price"] = head["adjoint_s"] / head["price_s"]
 
+    # Longstaff-Schwartz Bermudan put (252 steps, exercisable after every step, 2^20
+    # paths): the path kernel, then one kernel per exercise date; the per-date cost is
+    # the difference to a one-date valuation (path kernel + one reduction) over the
+    # remaining dates
+    lsm_leg = None
+    if not args.no_lsm:
+        lw = workloads.lsm()
+        K_l = float(lw.strikes[0])
+        every = lw.extra["exercise_every"]
+        n_ex = lw.steps // every
+
+        def lsm_time(ev, reps=5):
+            simr.lsm_price(lw.model, K_l, True, lw.steps, ev, lw.paths, lw.seed)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                simr.lsm_price(lw.model, K_l, True, lw.steps, ev, lw.paths, lw.seed)
+                b.record(stream)
+                flush.zero_()
+                ts.append((a, b))
+            torch.cuda.synchronize()
+            return sum(x.elapsed_time(y) for x, y in ts) / reps
+
+        ms_all = lsm_time(every)
+        ms_one = lsm_time(lw.steps)
+        per_date_us = 1e3 * (ms_all - ms_one) / max(n_ex - 1, 1)
+        date_bytes = 24 * lw.paths  # per date: S, v of two dates + cash flow and stop per path
+        hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+        lsm_leg = {"workload": lw.name, "exercise_dates": n_ex, "ms": ms_all,
+                   "path_steps_per_s": lw.paths * lw.steps / (ms_all * 1e-3),
+                   "path_kernel_plus_one_date_ms": ms_one, "per_date_us": per_date_us,
+                   "date_kernel_roofline": {"bound": "hbm", "achieved": date_bytes / (per_date_us * 1e-6) / 1e9,
+                                            "peak": hbm, "unit": "GB/s",
+                                            "frac": date_bytes / (per_date_us * 1e-6) / 1e9 / hbm,
+                                            "bytes_per_launch": date_bytes}}
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -462,6 +507,7 @@ def run_native(args):
         "adjoint_vs_fd": adj,
         "book": book,
         "headline": head,
+        "lsm": lsm_leg,
         "kernel_source_sha": sha,
         "wall_s_timed_region": t_wall,
     }

@@ -218,6 +218,37 @@ SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_
                                 float* x_T, float* grad, void* stream);
 
 /*
+ * Longstaff-Schwartz (least-squares Monte Carlo) price of a Bermudan call or
+ * put on paths [0, paths) of the simulation of simr_price (same seed,
+ * option_index and Philox counters) -- the paper's writeLongstaffSchwartzPath and
+ * longstaffSchwartzPathReduction stages (Sec. 5, Fig. 1; a reduction across
+ * paths with dependencies between them, Sec. 6), with the method of Longstaff
+ * and Schwartz (2001):
+ *   exercise dates t_j = (j + 1) exercise_every dt, j = 0 .. n_ex - 1,
+ *   n_ex = steps / exercise_every (none at t = 0; the last is the maturity);
+ *   backwards from t_{n_ex-2}: over the paths with a positive payoff h at t_j,
+ *   least squares of the cash flow they realise later, discounted to t_j, on
+ *   the basis (1, x, x^2, y, x y, y^2), x = S/K - 1, y = v/w - 1,
+ *   w = (v0 + theta)/2 (1 if 0); normal equations by Cholesky in FP64 with a
+ *   basis function left out when its pivot is not above 1e-12 of its diagonal
+ *   entry; fewer than 12 such paths: no exercise at that date; a path
+ *   exercises where h > the fitted continuation value (FP32);
+ *   price = mean of e^{-r t_stop} h(t_stop) (0 if never exercised).
+ *   K, is_put         in   strike (finite, > 0), 0 = call
+ *   exercise_every    in   >= 1, divides steps; n_ex <= 8192
+ *   paths             in   [2, 2^31]; n_ex * paths * 8 bytes of states <= 64 GiB
+ *   price[1], stderr_out[1] (nullable)    out  FP64
+ *   beta[n_ex * 6] (nullable)    out  coefficients per date, row-major; NaN rows
+ *                                     where no regression ran (the maturity's)
+ *   stop[paths] (nullable)       out  int32 exercise date per path, -1 = never
+ * Outputs may be host or device pointers (host: the call synchronises).  The
+ * context owns the per-path states (8 n_ex bytes per path) between calls.
+ */
+SIMR_API int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put, uint32_t steps,
+                            uint32_t exercise_every, uint64_t paths, uint64_t seed, uint32_t option_index,
+                            double* price, double* stderr_out, double* beta, int32_t* stop, void* stream);
+
+/*
  * Terminal state of paths [path_begin, path_begin + n_paths): x_T = ln(S_T/S0)
  * and v_T per path, FP32, the state the paper's writeLongstaffSchwartzPath stage
  * writes out (Sec. 5).  x_T[n_paths], v_T[n_paths] out; v_T may be NULL.

@@ -91,12 +91,15 @@ class LsmResult:
     t: np.ndarray        # [n_ex] exercise times
     S: np.ndarray        # [paths, n_ex]
     v: np.ndarray
+    Y: np.ndarray | None = None  # [paths, n_ex] regression targets at each date (keep_targets)
 
 
 def lsm(model, K: float, is_put: bool, steps: int, every: int, paths: int, seed: int = 1,
-        option_index: int = 0, path_begin: int = 0) -> LsmResult:
+        option_index: int = 0, path_begin: int = 0, keep_targets: bool = False) -> LsmResult:
     """Longstaff-Schwartz price of the Bermudan option over paths
-    [path_begin, path_begin + paths) of the simulation of simr_price."""
+    [path_begin, path_begin + paths) of the simulation of simr_price.  With
+    keep_targets, Y[:, j] holds every path's cash flow discounted to t_j as the
+    regression of date j saw it (NaN at the maturity)."""
     S, v = states(model, steps, every, seed, path_begin, paths, option_index)
     n_ex = steps // every
     r = float(model["r"])
@@ -107,7 +110,10 @@ def lsm(model, K: float, is_put: bool, steps: int, every: int, paths: int, seed:
     stop = np.where(cash > 0.0, n_ex - 1, -1)
     beta = np.full((n_ex, N_BASIS), np.nan)
     margin = np.full((paths, n_ex), np.inf)
+    Yall = np.full((paths, n_ex), np.nan) if keep_targets else None
     for j in range(n_ex - 2, -1, -1):
+        if keep_targets:
+            Yall[:, j] = np.where(stop >= 0, cash * np.exp(-r * (t[np.maximum(stop, 0)] - t[j])), 0.0)
         itm = np.nonzero(h[:, j] > 0.0)[0]
         if itm.size < MIN_ITM:
             continue
@@ -126,4 +132,4 @@ def lsm(model, K: float, is_put: bool, steps: int, every: int, paths: int, seed:
     s2 = float(np.sum(dcf * dcf))
     mean = s1 / paths
     var = (s2 / paths - mean * mean) / (paths - 1) if paths > 1 else 0.0
-    return LsmResult(mean, math.sqrt(max(var, 0.0)), beta, stop, cash, margin, t, S, v)
+    return LsmResult(mean, math.sqrt(max(var, 0.0)), beta, stop, cash, margin, t, S, v, Yall)

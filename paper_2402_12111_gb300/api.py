@@ -149,6 +149,25 @@ def batch(options, seed: int = 1, adjoint: bool = False, graph: bool = False, au
     return p, se, g
 
 
+def lsm_price(model, K: float, is_put: bool = True, steps: int = 64, exercise_every: int = 1, paths: int = 65536,
+              seed: int = 1, option_index: int = 0, with_beta: bool = False, with_stop: bool = False,
+              device="cuda", stream=None):
+    """simr_lsm_price: Longstaff-Schwartz Bermudan price on the paths of simr_price.
+    Returns (price, stderr, beta[n_ex, 6] or None, stop[paths] int32 or None), on `device`."""
+    dev = torch.device(device)
+    n_ex = int(steps) // max(int(exercise_every), 1)
+    p = torch.empty(1, dtype=torch.float64, device=dev)
+    se = torch.empty_like(p)
+    b = torch.empty(max(n_ex, 1), 6, dtype=torch.float64, device=dev) if with_beta else None
+    st = torch.empty(int(paths), dtype=torch.int32, device=dev) if with_stop else None
+    L = S.load()
+    ctx = S.context(_device_index(p, device))
+    S.check(L.simr_lsm_price(ctx, ctypes.byref(S.as_heston(model)), float(K), int(bool(is_put)), int(steps),
+                             int(exercise_every), int(paths), int(seed), int(option_index), _ptr(p), _ptr(se), _ptr(b),
+                             _ptr(st), _stream(p, stream)))
+    return p, se, b, st
+
+
 def paths_adjoint(model, steps: int, path_begin: int, n_paths: int, seed: int = 1, ckpt_every: int = 0,
                   option_index: int = 0, device="cuda", stream=None):
     """simr_paths_adjoint: (x_T[n], grad[n, 5]) FP32, grad = d x_T / d(v0, kappa, theta, sigma, rho)."""

@@ -23,9 +23,27 @@ struct simr_ctx {
   // path-kernel scratch: partial rows + ticket
   double* partials = nullptr;
   size_t partial_doubles = 0;
-  unsigned int* ticket = nullptr;  // 256-byte block: ticket word at 0, status word at 64
+  // 256-byte block: ticket word at 0, status word at 64, batch queue counter at
+  // 128, Longstaff-Schwartz ticket at 192
+  unsigned int* ticket = nullptr;
   float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]
   size_t ckpt_floats = 0;
+  // Longstaff-Schwartz: states at the exercise dates, per-path cash flows,
+  // coefficients, discount table
+  float* lsm_S = nullptr;
+  size_t lsm_S_cap = 0;
+  float* lsm_V = nullptr;
+  size_t lsm_V_cap = 0;
+  float* lsm_cash = nullptr;
+  size_t lsm_cash_cap = 0;
+  int32_t* lsm_stop = nullptr;
+  size_t lsm_stop_cap = 0;
+  double* lsm_beta = nullptr;  // [2][n_ex][6]: reported basis, then the scaled one
+  size_t lsm_beta_cap = 0;
+  float4* lsm_xform = nullptr;
+  size_t lsm_xform_cap = 0;
+  float* lsm_dpow = nullptr;
+  size_t lsm_dpow_cap = 0;
   int* status = nullptr;
   // staging for host-pointer arguments
   double* dev_strikes = nullptr;
@@ -642,6 +660,13 @@ void simr_destroy(simr_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->partials);
   cudaFree(ctx->ckpt);
+  cudaFree(ctx->lsm_S);
+  cudaFree(ctx->lsm_V);
+  cudaFree(ctx->lsm_cash);
+  cudaFree(ctx->lsm_stop);
+  cudaFree(ctx->lsm_beta);
+  cudaFree(ctx->lsm_dpow);
+  cudaFree(ctx->lsm_xform);
   cudaFree(ctx->ticket);
   cudaFree(ctx->dev_strikes);
   cudaFree(ctx->dev_out);
@@ -1010,6 +1035,109 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
   if (e == cudaSuccess && (hx || hv)) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "copying terminal states");
   return SIMR_OK;
+}
+
+int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put, uint32_t steps,
+                   uint32_t exercise_every, uint64_t paths, uint64_t seed, uint32_t option_index, double* price,
+                   double* stderr_out, double* beta, int32_t* stop, void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  int rc = check_model(model);
+  if (rc) return rc;
+  if (!(K > 0.0) || !std::isfinite(K)) return fail(SIMR_EINVAL, "strike must be finite and > 0");
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (exercise_every < 1 || steps % exercise_every != 0)
+    return fail(SIMR_EINVAL, "exercise_every must be >= 1 and divide steps");
+  const uint32_t n_ex = steps / exercise_every;
+  if (n_ex > 8192) return fail(SIMR_EINVAL, "at most 8192 exercise dates");
+  if (paths < 2 || paths > (1ull << 31)) return fail(SIMR_EINVAL, "paths must lie in [2, 2^31]");
+  if ((double)n_ex * (double)paths * 8.0 > 64.0 * (1ull << 30))
+    return fail(SIMR_EUNSUPPORTED, "the states at the exercise dates would exceed 64 GiB");
+  if (!price) return fail(SIMR_EINVAL, "price is NULL");
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nS = (size_t)n_ex * paths;
+  if ((rc = ensure(&ctx->lsm_S, &ctx->lsm_S_cap, nS, "exercise-date spots"))) return rc;
+  if ((rc = ensure(&ctx->lsm_V, &ctx->lsm_V_cap, nS, "exercise-date variances"))) return rc;
+  if ((rc = ensure(&ctx->lsm_cash, &ctx->lsm_cash_cap, (size_t)paths, "cash flows"))) return rc;
+  if ((rc = ensure(&ctx->lsm_stop, &ctx->lsm_stop_cap, (size_t)paths, "exercise dates"))) return rc;
+  if ((rc = ensure(&ctx->lsm_beta, &ctx->lsm_beta_cap, (size_t)n_ex * 12, "regression coefficients"))) return rc;
+  if ((rc = ensure(&ctx->lsm_dpow, &ctx->lsm_dpow_cap, (size_t)n_ex, "discount table"))) return rc;
+  if ((rc = ensure(&ctx->lsm_xform, &ctx->lsm_xform_cap, (size_t)n_ex, "basis scaling"))) return rc;
+  if ((rc = ensure(&ctx->partials, &ctx->partial_doubles, lsm_partial_doubles(ctx->num_sms), "reduction scratch")))
+    return rc;
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = 1;
+  o.user[1] = stderr_out;
+  o.n[1] = 1;
+  o.user[2] = beta;
+  o.n[2] = (size_t)n_ex * 6;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+
+  const double dt_ex = model->T / (double)n_ex;
+  std::vector<float> dpow(n_ex);
+  for (uint32_t k = 0; k < n_ex; ++k) dpow[k] = (float)std::exp(-model->r * dt_ex * (double)k);
+  // per date: xs = (S - F)/sd_S and ys = (v - E v)/sd_v from the model's forward
+  // F = S0 e^{rt}, log-spot spread sqrt(vbar t) (vbar: mean expected variance over
+  // [0, t]) and the CIR mean and variance of v_t
+  std::vector<float4> xf(n_ex);
+  const double kap = model->kappa, th = model->theta, v0 = model->v0, s2 = model->sigma * model->sigma;
+  for (uint32_t j = 0; j < n_ex; ++j) {
+    const double t = dt_ex * (double)(j + 1), E = std::exp(-kap * t), omE = -std::expm1(-kap * t);
+    const double F = model->S0 * std::exp(model->r * t);
+    const double vbar = th + (v0 - th) * omE / (kap * t);
+    const double sdS = F * std::sqrt(std::max(vbar * t, 1e-12));
+    const double Ev = th + (v0 - th) * E;
+    const double varv = v0 * s2 * E * omE / kap + th * s2 * omE * omE / (2.0 * kap);
+    const double sdv = std::max(std::sqrt(std::max(varv, 0.0)), 1e-6 * (Ev + 0.5 * (v0 + th)) + 1e-300);
+    xf[j] = make_float4((float)(1.0 / sdS), (float)(-F / sdS), (float)(1.0 / sdv), (float)(-Ev / sdv));
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->lsm_dpow, dpow.data(), n_ex * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->lsm_xform, xf.data(), n_ex * sizeof(float4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables go out of scope
+  // rows of dates without a regression stay NaN; the maturity row never gets one
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->lsm_beta, 0xff, (size_t)n_ex * 12 * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "preparing the Longstaff-Schwartz tables");
+
+  LsmLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  philox_round_keys(seed, L.rk);
+  L.sc = base_const(*model, steps);
+  L.S0 = (float)model->S0;
+  L.K = (float)K;
+  const double w = 0.5 * (model->v0 + model->theta);
+  L.is_put = is_put ? 1 : 0;
+  L.n_ex = (int32_t)n_ex;
+  L.every = (int32_t)exercise_every;
+  L.min_itm = 12;
+  L.steps = steps;
+  L.option_index = option_index;
+  L.paths = paths;
+  L.disc0 = std::exp(-model->r * dt_ex);
+  L.Kd = K;
+  L.wd = w > 0.0 ? w : 1.0;
+  LsmBuffers B{ctx->lsm_S,
+               ctx->lsm_V,
+               ctx->lsm_cash,
+               ctx->lsm_stop,
+               o.dev[2] ? o.dev[2] : ctx->lsm_beta,
+               ctx->lsm_beta + (size_t)n_ex * 6,
+               ctx->lsm_xform,
+               ctx->lsm_dpow,
+               ctx->partials,
+               ctx->ticket + 48,
+               o.dev[0],
+               o.dev[1]};
+  if (o.dev[2]) e = cudaMemsetAsync(o.dev[2], 0xff, (size_t)n_ex * 6 * sizeof(double), st);
+  if (e == cudaSuccess) e = launch_lsm(L, B, ctx->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the Longstaff-Schwartz kernels");
+  if (stop) {
+    e = cudaMemcpyAsync(stop, ctx->lsm_stop, (size_t)paths * sizeof(int32_t), cudaMemcpyDefault, st);
+    if (e == cudaSuccess && !is_device_ptr(stop)) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the exercise dates");
+  }
+  return finish_outputs(ctx, o, st);
 }
 
 }  // extern "C"

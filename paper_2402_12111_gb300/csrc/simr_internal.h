@@ -147,6 +147,39 @@ cudaError_t prepare_batch(const BatchLaunch& B);  // kernel attributes (outside 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);
 
+// Longstaff-Schwartz (simr_lsm.cu).  Exercise dates t_j = (j + 1) every dt,
+// j = 0 .. n_ex - 1; per-path states at the dates in [date][path] arrays.
+struct LsmLaunch {
+  uint32_t rk[10][2];
+  ScenConst sc;        // base scenario constants (v0 included)
+  float S0, K;         // spot, strike
+  int32_t is_put, n_ex, every, min_itm;
+  uint32_t steps, option_index;
+  uint64_t paths;
+  double disc0;        // e^{-r t_0}
+  double Kd, wd;       // strike and basis scale w in FP64 (coefficient conversion)
+};
+
+struct LsmBuffers {
+  float* S;            // [n_ex][paths]
+  float* V;            // [n_ex][paths]
+  float* cash;         // [paths] payoff at the exercise date (0: never exercised)
+  int32_t* stop;       // [paths] exercise date, -1 = never
+  double* beta;        // [n_ex][6] in the basis (1, x, x^2, y, xy, y^2); NaN row = no regression
+  double* beta_t;      // [n_ex][6] the same fit in the date's scaled basis (what the kernels use)
+  const float4* xform; // [n_ex] scaled coordinates of date j: xs = a S + b, ys = p v + q
+  const float* dpow;   // [n_ex] e^{-r k (t_1 - t_0)}, k = 0 .. n_ex - 1
+  double* partials;    // [grid][21]
+  unsigned int* ticket;
+  double* price;       // [1]
+  double* stderr_;     // [1] or null
+};
+
+// All launches of one Longstaff-Schwartz valuation on `stream`: the path
+// kernel, then one kernel per exercise date (the last also reduces the price).
+cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream);
+size_t lsm_partial_doubles(int num_sms);
+
 // Validation and launch building of the C ABI (simr_api.cu), for the other
 // entry points of the library.  They set the thread-local error message.
 int internal_fail(int code, const char* message);

@@ -71,6 +71,13 @@ def adjoint() -> Workload:
                     ckpt_every=16)
 
 
+def lsm() -> Workload:
+    """Bermudan put, exercisable after every one of 252 steps (a daily-exercise
+    proxy for the American option), 2^20 paths: the Longstaff-Schwartz workload."""
+    return Workload("heston_lsm_put_252x1048576_daily", dict(BASE_MODEL), np.array([100.0]), 252, 1 << 20,
+                    is_put=True, extra={"exercise_every": 1})
+
+
 def _draw_params(rng: np.random.Generator) -> dict:
     """One option's parameters, in a fixed draw order."""
     v0 = rng.uniform(0.01, 0.09)
