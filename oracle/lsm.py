@@ -16,10 +16,15 @@ Readings of what neither source fixes for this model (stated once here):
   * basis 1, x, x^2, y, x y, y^2 with x = S/K - 1, y = v/w - 1, w = (v0 + theta)/2
     (w = 1 when that is 0): the quadratic polynomials in spot and variance;
   * only paths with a positive payoff enter the regression or may exercise;
-  * least squares through the normal equations, solved by Cholesky in basis
-    order with a basis function left out (coefficient 0) when its pivot is not
-    above 1e-12 of its diagonal entry; with fewer than 12 in-the-money paths
-    there is no regression and no exercise at that date (coefficients NaN);
+  * least squares through the normal equations, written in the date's
+    standardised coordinates xs = (S - F)/sd_S, ys = (v - E v)/sd_v (F = S0 e^{rt},
+    sd_S = F sqrt(vbar t) with vbar the mean expected variance over [0, t],
+    E v and sd_v the CIR mean and standard deviation of v_t): the same
+    quadratics as in x, y, with order-one Gram entries.  Cholesky in basis
+    order, a basis function left out (coefficient 0) when its pivot is not
+    above 1e-5 of its diagonal entry (exact or near collinearity); with fewer
+    than 12 in-the-money paths there is no regression and no exercise at that
+    date (coefficients NaN).  Coefficients are reported in x, y;
   * exercise when payoff > continuation (strict);
   * price = mean over paths of e^{-r t_stop} x cash flow (0 if never exercised),
     standard error as for the European estimator.
@@ -35,7 +40,7 @@ from . import states
 
 N_BASIS = 6
 MIN_ITM = 12
-PIVOT_TOL = 1e-12
+PIVOT_TOL = 1e-5
 
 
 def basis_scale(model) -> float:
@@ -48,6 +53,48 @@ def basis(S, v, K: float, w: float) -> np.ndarray:
     x = np.asarray(S, dtype=np.float64) / K - 1.0
     y = np.asarray(v, dtype=np.float64) / w - 1.0
     return np.stack([np.ones_like(x), x, x * x, y, x * y, y * y], axis=-1)
+
+
+def standardise(model, n_ex: int, j: int):
+    """(a, b, p, q) of date j: xs = a S + b, ys = p v + q (see the module docstring)."""
+    T, r, S0 = float(model["T"]), float(model["r"]), float(model["S0"])
+    kap, th, v0, s2 = float(model["kappa"]), float(model["theta"]), float(model["v0"]), float(model["sigma"]) ** 2
+    t = T * (j + 1) / n_ex
+    E = math.exp(-kap * t)
+    omE = -math.expm1(-kap * t)
+    F = S0 * math.exp(r * t)
+    vbar = th + (v0 - th) * omE / (kap * t)
+    sdS = F * math.sqrt(max(vbar * t, 1e-12))
+    Ev = th + (v0 - th) * E
+    varv = v0 * s2 * E * omE / kap + th * s2 * omE * omE / (2.0 * kap)
+    sdv = math.sqrt(max(varv, 1e-24))
+    return 1.0 / sdS, -F / sdS, 1.0 / sdv, -Ev / sdv
+
+
+def basis_std(S, v, coef) -> np.ndarray:
+    """Rows (1, xs, xs^2, ys, xs ys, ys^2) with xs = a S + b, ys = p v + q."""
+    a, b, p, q = coef
+    xs = a * np.asarray(S, dtype=np.float64) + b
+    ys = p * np.asarray(v, dtype=np.float64) + q
+    return np.stack([np.ones_like(xs), xs, xs * xs, ys, xs * ys, ys * ys], axis=-1)
+
+
+def reported(beta_s, coef, K: float, w: float) -> np.ndarray:
+    """Coefficients in (1, x, x^2, y, xy, y^2), x = S/K - 1, y = v/w - 1, of the
+    quadratic with coefficients beta_s in (1, xs, xs^2, ys, xs ys, ys^2):
+    S = K (1 + x) gives xs = kx (x - cx), kx = aK, cx = -(aK + b)/(aK); likewise ys."""
+    a, b, p, q = coef
+    kx, ky = a * K, p * w
+    cx, cy = -(kx + b) / kx, -(ky + q) / ky
+    b0, b1, b2, b3, b4, b5 = beta_s
+    return np.array([
+        b0 - b1 * kx * cx + b2 * kx * kx * cx * cx - b3 * ky * cy + b4 * kx * ky * cx * cy + b5 * ky * ky * cy * cy,
+        b1 * kx - 2.0 * b2 * kx * kx * cx - b4 * kx * ky * cy,
+        b2 * kx * kx,
+        b3 * ky - b4 * kx * ky * cx - 2.0 * b5 * ky * ky * cy,
+        b4 * kx * ky,
+        b5 * ky * ky,
+    ])
 
 
 def solve_normal(G, b, tol: float = PIVOT_TOL):
@@ -119,9 +166,11 @@ def lsm(model, K: float, is_put: bool, steps: int, every: int, paths: int, seed:
             continue
         st = stop[itm]
         Y = np.where(st >= 0, cash[itm] * np.exp(-r * (t[np.maximum(st, 0)] - t[j])), 0.0)
-        Phi = basis(S[itm, j], v[itm, j], K, w)
-        beta[j], _ = solve_normal(Phi.T @ Phi, Phi.T @ Y)
-        C = Phi @ beta[j]
+        coef = standardise(model, n_ex, j)
+        Phi = basis_std(S[itm, j], v[itm, j], coef)
+        beta_s, _ = solve_normal(Phi.T @ Phi, Phi.T @ Y)
+        beta[j] = reported(beta_s, coef, K, w)
+        C = Phi @ beta_s
         hj = h[itm, j]
         margin[itm, j] = np.abs(hj - C)
         ex = hj > C

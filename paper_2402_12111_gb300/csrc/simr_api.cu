@@ -24,7 +24,7 @@ struct simr_ctx {
   double* partials = nullptr;
   size_t partial_doubles = 0;
   // 256-byte block: ticket word at 0, status word at 64, batch queue counter at
-  // 128, Longstaff-Schwartz ticket at 192
+  // 128, Longstaff-Schwartz ticket at 192, its sweep barrier words at 208 and 224
   unsigned int* ticket = nullptr;
   float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]
   size_t ckpt_floats = 0;
@@ -440,6 +440,7 @@ int take_status(simr_ctx* ctx, cudaStream_t st) {
   if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
   if (h & 1) return fail(SIMR_EINVAL, "a device-resident strike was not finite and > 0 (results are NaN)");
+  if (h & 2) return fail(SIMR_ETIMEOUT, "a grid barrier of the Longstaff-Schwartz sweep timed out (results invalid)");
   return SIMR_OK;
 }
 
@@ -1127,6 +1128,7 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
                ctx->lsm_dpow,
                ctx->partials,
                ctx->ticket + 48,
+               ctx->status,
                o.dev[0],
                o.dev[1]};
   if (o.dev[2]) e = cudaMemsetAsync(o.dev[2], 0xff, (size_t)n_ex * 6 * sizeof(double), st);

@@ -169,14 +169,16 @@ struct LsmBuffers {
   double* beta_t;      // [n_ex][6] the same fit in the date's scaled basis (what the kernels use)
   const float4* xform; // [n_ex] scaled coordinates of date j: xs = a S + b, ys = p v + q
   const float* dpow;   // [n_ex] e^{-r k (t_1 - t_0)}, k = 0 .. n_ex - 1
-  double* partials;    // [grid][21]
-  unsigned int* ticket;
+  double* partials;    // [grid][21] (cooperative sweep: [2][grid][21] double-float pairs)
+  unsigned int* ticket;  // last-block ticket; words 4 and 8 after it: sweep barrier count, generation
+  int* status;         // bit 1 set when a sweep barrier wait timed out
   double* price;       // [1]
   double* stderr_;     // [1] or null
 };
 
 // All launches of one Longstaff-Schwartz valuation on `stream`: the path
-// kernel, then one kernel per exercise date (the last also reduces the price).
+// kernel, then the backward induction as one cooperative launch (or, where
+// that is not possible, one kernel per exercise date; the last reduces the price).
 cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream);
 size_t lsm_partial_doubles(int num_sms);
 

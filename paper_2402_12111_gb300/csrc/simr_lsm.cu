@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "simr_device.cuh"
 #include "simr_internal.h"
@@ -163,51 +164,107 @@ __constant__ int c_gram_index[kNB * kNB] = {0, 1, 3, 2,  4,  5,  1, 3,  6,  4,  
 
 // 6x6 normal equations G beta = b from the 15 monomial sums and the 6 products
 // b (tot[15..20]), solved by one warp (lane r < 6 holds row r of G and of the
-// Cholesky factor L; every lane ends with all of beta).  Cholesky in basis
-// order, basis function k left out (coefficient 0) when its pivot d is not
-// above 1e-12 G[k][k]; each dot product runs in ascending index order.
+// Cholesky factor L; every lane ends with all of beta).  In the standardised
+// coordinates G has order-one entries, so the factorisation runs in FP32:
+// Cholesky in basis order, basis function k left out (coefficient 0) when its
+// pivot is not above 1e-5 G[k][k]; then one step of iterative refinement with
+// the residual b - G x formed in FP64 (row r in lane r), which brings the
+// solution to about FP64 accuracy for condition numbers far below 1e7.
 __device__ void lsm_solve_warp(const double* tot, double* beta, int lane) {
-  double g[kNB], l[kNB], rd[kNB], z[kNB];
-  unsigned keep = 0;
   const int row = lane < kNB ? lane : 0;
+  double g[kNB];
+  float gf[kNB], l[kNB], rd[kNB];
+  unsigned keep = 0;
 #pragma unroll
   for (int k = 0; k < kNB; ++k) {
     g[k] = tot[c_gram_index[row * kNB + k]];
-    l[k] = 0.0;
+    gf[k] = (float)g[k];
+    l[k] = 0.0f;
   }
 #pragma unroll
   for (int k = 0; k < kNB; ++k) {
-    double s = 0.0;
+    float s = 0.0f;
 #pragma unroll
-    for (int i = 0; i < k; ++i) s += l[i] * l[i];  // left-out columns hold 0
-    const double d = __shfl_sync(kFull, g[k] - s, k);
-    const double gkk = __shfl_sync(kFull, g[k], k);
-    rd[k] = 0.0;
-    if (!(gkk > 0.0 && d > 1e-12 * gkk)) continue;
+    for (int i = 0; i < k; ++i) s = fmaf(l[i], l[i], s);  // left-out columns hold 0
+    const float d = __shfl_sync(kFull, gf[k] - s, k);
+    const float gkk = __shfl_sync(kFull, gf[k], k);
+    rd[k] = 0.0f;
+    if (!(gkk > 0.0f && d > 1e-5f * gkk)) continue;
     keep |= 1u << k;
-    const double lkk = sqrt(d);
-    rd[k] = 1.0 / lkk;
-    double t = 0.0;
+    const float lkk = __fsqrt_rn(d);
+    rd[k] = __frcp_rn(lkk);
+    float t = 0.0f;
 #pragma unroll
-    for (int i = 0; i < k; ++i) t += l[i] * __shfl_sync(kFull, l[i], k);
-    if (lane > k) l[k] = (g[k] - t) * rd[k];
+    for (int i = 0; i < k; ++i) t = fmaf(l[i], __shfl_sync(kFull, l[i], k), t);
+    if (lane > k) l[k] = (gf[k] - t) * rd[k];
     if (lane == k) l[k] = lkk;
   }
+  // L L^T x = r for r held by every lane; L[k][i] is lane k's l[i]
+  auto solve = [&](const float (&r)[kNB], float (&x)[kNB]) {
+    float z[kNB];
 #pragma unroll
-  for (int k = 0; k < kNB; ++k) {  // L z = b
-    double t = 0.0;
+    for (int k = 0; k < kNB; ++k) {
+      float t = 0.0f;
 #pragma unroll
-    for (int i = 0; i < k; ++i) t += l[i] * z[i];
-    const double zk = ((keep >> k) & 1u) ? (tot[kNMono + k] - t) * rd[k] : 0.0;
-    z[k] = __shfl_sync(kFull, zk, k);
-  }
+      for (int i = 0; i < k; ++i) t = fmaf(l[i], z[i], t);
+      const float zk = ((keep >> k) & 1u) ? (r[k] - t) * rd[k] : 0.0f;
+      z[k] = __shfl_sync(kFull, zk, k);
+    }
 #pragma unroll
-  for (int k = kNB - 1; k >= 0; --k) {  // L^T beta = z; L[i][k] is lane i's l[k]
-    double t = 0.0;
+    for (int k = kNB - 1; k >= 0; --k) {
+      float t = 0.0f;
 #pragma unroll
-    for (int i = k + 1; i < kNB; ++i) t += __shfl_sync(kFull, l[k], i) * beta[i];
-    beta[k] = ((keep >> k) & 1u) ? (z[k] - t) * rd[k] : 0.0;
-  }
+      for (int i = k + 1; i < kNB; ++i) t = fmaf(__shfl_sync(kFull, l[k], i), x[i], t);
+      x[k] = ((keep >> k) & 1u) ? (z[k] - t) * rd[k] : 0.0f;
+    }
+  };
+  float rf[kNB], xf[kNB], dx[kNB];
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) rf[k] = (float)tot[kNMono + k];
+  solve(rf, xf);
+  double res = tot[kNMono + row];
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) res = fma(-g[k], (double)xf[k], res);
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) rf[k] = (float)__shfl_sync(kFull, res, k);
+  solve(rf, dx);
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) beta[k] = ((keep >> k) & 1u) ? (double)xf[k] + (double)dx[k] : 0.0;
+}
+
+// Fitted continuation value in the standardised coordinates (x, y).
+__device__ __forceinline__ float lsm_continuation(const float (&b)[kNB], float x, float y) {
+  float C = fmaf(b[2], x, b[1]);
+  C = fmaf(C, x, b[0]);
+  return fmaf(fmaf(b[5], y, fmaf(b[4], x, b[3])), y, C);
+}
+
+// One in-the-money path's terms of the regression sums: the 15 monomials
+// 1, x, y, x^2, xy, y^2, x^3, x^2y, xy^2, y^3, x^4, x^3y, x^2y^2, xy^3, y^4 and
+// the target Y times the basis (1, x, x^2, y, xy, y^2).
+__device__ __forceinline__ void lsm_accumulate(float (&acc)[kNReg], float x, float y, float Y) {
+  const float x2 = x * x, y2 = y * y, xy = x * y;
+  acc[0] += 1.0f;
+  acc[1] += x;
+  acc[2] += y;
+  acc[3] += x2;
+  acc[4] += xy;
+  acc[5] += y2;
+  acc[6] = fmaf(x2, x, acc[6]);
+  acc[7] = fmaf(x2, y, acc[7]);
+  acc[8] = fmaf(x, y2, acc[8]);
+  acc[9] = fmaf(y2, y, acc[9]);
+  acc[10] = fmaf(x2, x2, acc[10]);
+  acc[11] = fmaf(x2, xy, acc[11]);
+  acc[12] = fmaf(x2, y2, acc[12]);
+  acc[13] = fmaf(xy, y2, acc[13]);
+  acc[14] = fmaf(y2, y2, acc[14]);
+  acc[15] += Y;
+  acc[16] = fmaf(Y, x, acc[16]);
+  acc[17] = fmaf(Y, x2, acc[17]);
+  acc[18] = fmaf(Y, y, acc[18]);
+  acc[19] = fmaf(Y, xy, acc[19]);
+  acc[20] = fmaf(Y, y2, acc[20]);
 }
 
 // Date kernel: exercise rule of date j (UPDATE), then the regression sums of
@@ -271,10 +328,7 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_date_kernel(const __grid_constant
       if (upd) {
         const float h = lsm_payoff(put, Su[k], K);
         if (h > 0.0f) {
-          const float x = fmaf(Su[k], tj.x, tj.y), y = fmaf(Vu[k], tj.z, tj.w);
-          float C = fmaf(bj[2], x, bj[1]);
-          C = fmaf(C, x, bj[0]);
-          C = fmaf(fmaf(bj[5], y, fmaf(bj[4], x, bj[3])), y, C);
+          const float C = lsm_continuation(bj, fmaf(Su[k], tj.x, tj.y), fmaf(Vu[k], tj.z, tj.w));
           if (h > C) {
             cc = h;
             s = j;
@@ -288,28 +342,7 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_date_kernel(const __grid_constant
         if (h > 0.0f) {
           const float x = fmaf(Sg[k], tr.x, tr.y), y = fmaf(Vg[k], tr.z, tr.w);
           const float Y = s >= 0 ? cc * __ldg(dpow + (s - jr)) : 0.0f;
-          const float x2 = x * x, y2 = y * y, xy = x * y;
-          acc[0] += 1.0f;
-          acc[1] += x;
-          acc[2] += y;
-          acc[3] += x2;
-          acc[4] += xy;
-          acc[5] += y2;
-          acc[6] = fmaf(x2, x, acc[6]);
-          acc[7] = fmaf(x2, y, acc[7]);
-          acc[8] = fmaf(x, y2, acc[8]);
-          acc[9] = fmaf(y2, y, acc[9]);
-          acc[10] = fmaf(x2, x2, acc[10]);
-          acc[11] = fmaf(x2, xy, acc[11]);
-          acc[12] = fmaf(x2, y2, acc[12]);
-          acc[13] = fmaf(xy, y2, acc[13]);
-          acc[14] = fmaf(y2, y2, acc[14]);
-          acc[15] += Y;
-          acc[16] = fmaf(Y, x, acc[16]);
-          acc[17] = fmaf(Y, x2, acc[17]);
-          acc[18] = fmaf(Y, y, acc[18]);
-          acc[19] = fmaf(Y, xy, acc[19]);
-          acc[20] = fmaf(Y, y2, acc[20]);
+          if constexpr (REGRESS) lsm_accumulate(acc, x, y, Y);
         }
       } else {
         const float d = s >= 0 ? cc * __ldg(dpow + s) : 0.0f;  // discounted to t_0
@@ -404,6 +437,351 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_date_kernel(const __grid_constant
   }
 }
 
+// The same normal equations from double-float totals, with FP32 arithmetic only
+// (the sweep's critical path): the FP32 Cholesky of lsm_solve_warp on the high
+// parts, then one refinement step whose residual b - G x is formed in
+// double-float (each product G x split exactly by an FMA).  The solution is the
+// pair (x, dx); x + dx in FP32 is what the exercise rule uses.
+__device__ void lsm_solve_df(const DF* tot, float* x_out, float* dx_out, int lane) {
+  const int row = lane < kNB ? lane : 0;
+  DF g[kNB];
+  float l[kNB], rd[kNB];
+  unsigned keep = 0;
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) {
+    g[k] = tot[c_gram_index[row * kNB + k]];
+    l[k] = 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < k; ++i) s = fmaf(l[i], l[i], s);
+    const float d = __shfl_sync(kFull, g[k].hi - s, k);
+    const float gkk = __shfl_sync(kFull, g[k].hi, k);
+    rd[k] = 0.0f;
+    if (!(gkk > 0.0f && d > 1e-5f * gkk)) continue;
+    keep |= 1u << k;
+    const float lkk = __fsqrt_rn(d);
+    rd[k] = __frcp_rn(lkk);
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < k; ++i) t = fmaf(l[i], __shfl_sync(kFull, l[i], k), t);
+    if (lane > k) l[k] = (g[k].hi - t) * rd[k];
+    if (lane == k) l[k] = lkk;
+  }
+  auto solve = [&](const float (&r)[kNB], float (&x)[kNB]) {
+    float z[kNB];
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) {
+      float t = 0.0f;
+#pragma unroll
+      for (int i = 0; i < k; ++i) t = fmaf(l[i], z[i], t);
+      const float zk = ((keep >> k) & 1u) ? (r[k] - t) * rd[k] : 0.0f;
+      z[k] = __shfl_sync(kFull, zk, k);
+    }
+#pragma unroll
+    for (int k = kNB - 1; k >= 0; --k) {
+      float t = 0.0f;
+#pragma unroll
+      for (int i = k + 1; i < kNB; ++i) t = fmaf(__shfl_sync(kFull, l[k], i), x[i], t);
+      x[k] = ((keep >> k) & 1u) ? (z[k] - t) * rd[k] : 0.0f;
+    }
+  };
+  float rf[kNB], x[kNB], dx[kNB];
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) rf[k] = tot[kNMono + k].hi;
+  solve(rf, x);
+  DF res = tot[kNMono + row];
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) {
+    const float p = g[k].hi * x[k];
+    const float pe = fmaf(g[k].hi, x[k], -p);  // exact remainder of the product
+    res = df_add(res, DF{-p, -fmaf(g[k].lo, x[k], pe)});
+  }
+  const float r = res.hi + res.lo;
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) rf[k] = __shfl_sync(kFull, r, k);
+  solve(rf, dx);
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) {
+    x_out[k] = x[k];
+    dx_out[k] = dx[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweep: the whole backward induction in one cooperative launch (all
+// blocks resident, one per SM).  Each date: apply the date's rule to the
+// thread's paths (states kept in registers from the previous date's
+// regression), load the states of the date before, accumulate its regression
+// sums, write the block's row, one grid barrier, then EVERY block sums all
+// rows in block order and solves the same normal equations (identical
+// arithmetic, so identical coefficients everywhere and no second barrier).
+// Rows alternate between two buffers: a block writes a buffer again only after
+// the next barrier, which every block reaches after reading it.
+constexpr int kSweepTpb = 1024;
+constexpr int kSweepWarps = kSweepTpb / kWarp;
+constexpr int kSweepParts = 48;             // threads per quantity in the cross-block sum (a multiple of 8)
+constexpr unsigned kSpinLimit = 1u << 23;   // barrier polls (>= 32 ns apart after 2048): ~0.3 s, then the wait gives up
+
+struct LsmSweep {
+  unsigned int* count;  // arrivals at the current barrier
+  unsigned int* gen;    // barrier generation
+  int* status;          // bit 1: a barrier wait timed out (results invalid)
+  float2* rows;         // [2][grid][kNReg]
+};
+
+// Grid-wide barrier of the cooperative sweep, bounded: a wait that exceeds
+// kSpinLimit polls sets status bit 1 and returns false, and every later barrier
+// returns false at once, so all blocks leave within one time-out.
+__device__ bool lsm_grid_sync(const LsmSweep& Y, int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = (*(volatile int*)Y.status & 2) == 0;
+    if (ok) {
+      const unsigned g = *(volatile unsigned*)Y.gen;
+      if (atomicAdd(Y.count, 1u) == gridDim.x - 1) {
+        atomicExch(Y.count, 0u);
+        __threadfence();
+        atomicAdd(Y.gen, 1u);
+      } else {
+        unsigned it = 0;
+        while (*(volatile unsigned*)Y.gen == g) {
+          if (++it > kSpinLimit) {
+            atomicOr(Y.status, 2);
+            ok = 0;
+            break;
+          }
+          if (it > 2048) __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Block's FP32 warp sums (s_w[warp][q], q < nv) -> one double-float row: four
+// threads per quantity sum 8 warps each, then one sums the four in order.
+__device__ __forceinline__ void sweep_block_row(const float (*s_w)[kNReg], int nv, DF* s_quad, float2* row) {
+  if (threadIdx.x < 4 * nv) {
+    const int q = threadIdx.x % nv, g = threadIdx.x / nv;
+    DF t{0.0f, 0.0f};
+#pragma unroll
+    for (int w = 8 * g; w < 8 * g + 8; ++w) t = df_add(t, DF{s_w[w][q], 0.0f});
+    s_quad[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    DF t{0.0f, 0.0f};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) t = df_add(t, s_quad[g * nv + threadIdx.x]);
+    row[threadIdx.x] = make_float2(t.hi, t.lo);
+  }
+}
+
+// Sum of all blocks' rows in block order into s_tot (double-float): thread
+// (part, q), part < kSweepParts, takes blocks part, part + kSweepParts, ...;
+// then groups of 8 parts, then the groups, each in order.
+__device__ __forceinline__ void sweep_total(const float2* rows, int nv, DF* s_part, DF* s_tot) {
+  if (threadIdx.x < kSweepParts * nv) {
+    const int q = threadIdx.x % nv, part = threadIdx.x / nv;
+    DF t{0.0f, 0.0f};
+#pragma unroll 4
+    for (unsigned b = part; b < gridDim.x; b += kSweepParts) {
+      const float2 r = __ldcg(rows + (size_t)b * kNReg + q);
+      t = df_add(t, DF{r.x, r.y});
+    }
+    s_part[threadIdx.x] = t;
+  }
+  __syncthreads();
+  constexpr int kGroups = kSweepParts / 8;
+  DF t{0.0f, 0.0f};
+  if (threadIdx.x < kGroups * nv) {
+    const int q = threadIdx.x % nv, grp = threadIdx.x / nv;
+#pragma unroll
+    for (int part = 8 * grp; part < 8 * grp + 8; ++part) t = df_add(t, s_part[part * nv + q]);
+  }
+  __syncthreads();
+  if (threadIdx.x < kGroups * nv) s_part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    DF u{0.0f, 0.0f};
+#pragma unroll
+    for (int grp = 0; grp < kGroups; ++grp) u = df_add(u, s_part[grp * nv + threadIdx.x]);
+    s_tot[threadIdx.x] = u;
+  }
+  __syncthreads();
+}
+
+template <int M>
+__global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_constant__ LsmLaunch L,
+                                                                 const LsmBuffers B, const LsmSweep Y) {
+  __shared__ float s_w[kSweepWarps][kNReg];
+  __shared__ DF s_part[kSweepParts * kNReg];
+  __shared__ DF s_tot[kNReg];
+  __shared__ float s_beta[kNB];
+  __shared__ int s_has, s_flag;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t P = L.paths;
+  float2* beta_t = reinterpret_cast<float2*>(B.beta_t);  // [n_ex][6] (x, dx) pairs
+  const uint64_t gt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool put = L.is_put != 0;
+  const float K = L.K;
+  // this thread's paths g0 + m gt: cash flow and exercise date in registers for
+  // the whole sweep (the states are read per date, from L2 after a prefetch)
+  float c[M];
+  int st[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint64_t i = g0 + (uint64_t)m * gt;
+    c[m] = i < P ? B.cash[i] : 0.0f;
+    st[m] = i < P ? B.stop[i] : -1;
+  }
+  if (threadIdx.x == 0) s_has = 0;
+  __syncthreads();
+  for (int d = L.n_ex - 1; d >= 0; --d) {
+    const bool regress = d >= 1;
+    const int nv = regress ? kNReg : 2;
+    // date d's rule (no coefficients at the maturity)
+    if (s_has) {
+      float bj[kNB];
+#pragma unroll
+      for (int k = 0; k < kNB; ++k) bj[k] = s_beta[k];
+      const float4 tj = B.xform[d];
+      const float* Sd = B.S + (size_t)d * P;
+      const float* Vd = B.V + (size_t)d * P;
+      float Su[M], Vu[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {  // all loads first
+        const uint64_t i = g0 + (uint64_t)m * gt;
+        Su[m] = i < P ? __ldcg(Sd + i) : 0.0f;
+        Vu[m] = i < P ? __ldcg(Vd + i) : 0.0f;
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float h = lsm_payoff(put, Su[m], K);
+        if (g0 + (uint64_t)m * gt < P && h > 0.0f &&
+            h > lsm_continuation(bj, fmaf(Su[m], tj.x, tj.y), fmaf(Vu[m], tj.z, tj.w))) {
+          c[m] = h;
+          st[m] = d;
+        }
+      }
+    }
+    float acc[kNReg];
+#pragma unroll
+    for (int k = 0; k < kNReg; ++k) acc[k] = 0.0f;
+    if (regress) {
+      const float* Sr = B.S + (size_t)(d - 1) * P;
+      const float* Vr = B.V + (size_t)(d - 1) * P;
+      float Sn[M], Vn[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {  // all loads first
+        const uint64_t i = g0 + (uint64_t)m * gt;
+        Sn[m] = i < P ? __ldcg(Sr + i) : 0.0f;
+        Vn[m] = i < P ? __ldcg(Vr + i) : 0.0f;
+      }
+      if (d >= 2) {  // the date after next into L2 while this one is reduced and solved
+        const float* Sp = B.S + (size_t)(d - 2) * P;
+        const float* Vp = B.V + (size_t)(d - 2) * P;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const uint64_t i = g0 + (uint64_t)m * gt;
+          if (i < P) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Sp + i));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Vp + i));
+          }
+        }
+      }
+      const float4 tr = B.xform[d - 1];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float h = lsm_payoff(put, Sn[m], K);
+        if (g0 + (uint64_t)m * gt < P && h > 0.0f) {
+          const float Yv = st[m] >= 0 ? c[m] * __ldg(B.dpow + (st[m] - (d - 1))) : 0.0f;
+          lsm_accumulate(acc, fmaf(Sn[m], tr.x, tr.y), fmaf(Vn[m], tr.z, tr.w), Yv);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float dv = st[m] >= 0 ? c[m] * __ldg(B.dpow + st[m]) : 0.0f;  // discounted to t_0
+        acc[0] += dv;
+        acc[1] = fmaf(dv, dv, acc[1]);
+      }
+    }
+    // FP32 over the warp, double-float over warps and blocks
+    {
+      float vals[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) vals[k] = k < kNReg ? acc[k] : 0.0f;
+      butterfly32(vals, lane);
+      if (lane < kNReg) s_w[warp][lane] = vals[0];
+    }
+    __syncthreads();
+    float2* rows = Y.rows + (size_t)(d & 1) * gridDim.x * kNReg;
+    sweep_block_row(s_w, nv, s_part, rows + (size_t)blockIdx.x * kNReg);
+    if (!lsm_grid_sync(Y, &s_flag)) return;
+    sweep_total(rows, nv, s_part, s_tot);
+    if (regress) {
+      // every block: the same solve; block 0 records the coefficients
+      if (warp == 0) {
+        const bool ok = s_tot[0].hi >= (float)L.min_itm;  // an exact count
+        float x[kNB], dx[kNB];
+        if (ok) lsm_solve_df(s_tot, x, dx, lane);
+        if (lane == 0) {
+          s_has = ok ? 1 : 0;
+#pragma unroll
+          for (int k = 0; k < kNB; ++k) s_beta[k] = ok ? x[k] + dx[k] : 0.0f;
+          if (blockIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < kNB; ++k)
+              beta_t[(size_t)(d - 1) * kNB + k] = ok ? make_float2(x[k], dx[k]) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+          }
+        }
+      }
+      __syncthreads();
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const double n = (double)P;
+      const double mean = ((double)s_tot[0].hi + (double)s_tot[0].lo) / n;
+      B.price[0] = L.disc0 * mean;
+      if (B.stderr_) {
+        const double var = n > 1.0 ? (((double)s_tot[1].hi + (double)s_tot[1].lo) / n - mean * mean) / (n - 1.0) : 0.0;
+        B.stderr_[0] = L.disc0 * sqrt(var > 0.0 ? var : 0.0);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint64_t i = g0 + (uint64_t)m * gt;
+    if (i < P) B.stop[i] = st[m];
+  }
+  // the coefficients in x, y: one date per block (block 0's rows are visible
+  // after the last barrier)
+  if (threadIdx.x == 0) {
+    for (int j = blockIdx.x; j < L.n_ex - 1; j += gridDim.x) {
+      const float2* bt = beta_t + (size_t)j * kNB;
+      double* bo = B.beta + (size_t)j * kNB;
+      if (isnan(__ldcg(bt).x)) continue;  // stays NaN
+      double bs[kNB];
+#pragma unroll
+      for (int k = 0; k < kNB; ++k) {
+        const float2 v = __ldcg(bt + k);
+        bs[k] = (double)v.x + (double)v.y;
+      }
+      const float4 tr = B.xform[j];
+      const double kx = (double)tr.x * L.Kd, cx = -(kx + (double)tr.y) / kx;
+      const double ky = (double)tr.z * L.wd, cy = -(ky + (double)tr.w) / ky;
+      lsm_unscale(bs, kx, cx, ky, cy, bo);
+    }
+  }
+}
+
 template <bool U, bool R>
 cudaError_t launch_date(const LsmLaunch& L, const LsmBuffers& B, int j, unsigned grid, cudaStream_t st) {
   lsm_date_kernel<U, R><<<grid, kLsmTpb, 0, st>>>(L, B, j);
@@ -415,6 +793,50 @@ constexpr int kLsmMaxBlocksPerSm = 8;
 }  // namespace
 
 size_t lsm_partial_doubles(int num_sms) { return (size_t)num_sms * kLsmMaxBlocksPerSm * kNReg; }
+
+namespace {
+
+template <int M>
+cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
+                        bool* used) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsm_sweep_kernel<M>, kSweepTpb, 0);
+  if (e != cudaSuccess || per_sm < 1) return e;
+  const uint64_t resident = (uint64_t)num_sms * per_sm;
+  const uint64_t per_block = (uint64_t)M * kSweepTpb;
+  const uint64_t need = (L.paths + per_block - 1) / per_block;
+  if (need > resident || need > (uint64_t)num_sms * kLsmMaxBlocksPerSm / 2) return cudaSuccess;  // M too small
+  const unsigned grid = (unsigned)need;
+  e = cudaMemsetAsync(Y.count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  LsmLaunch Lc = L;
+  LsmBuffers Bc = B;
+  LsmSweep Yc = Y;
+  void* args[] = {&Lc, &Bc, &Yc};
+  e = cudaLaunchCooperativeKernel((const void*)lsm_sweep_kernel<M>, dim3(grid), dim3(kSweepTpb), args, 0, st);
+  if (e == cudaSuccess) *used = true;
+  return e;
+}
+
+// The backward induction as one cooperative launch when the device supports it
+// and the paths fit M <= 7 per thread of the resident blocks; *used reports it.
+cudaError_t try_sweep(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
+                      bool* used) {
+  *used = false;
+  const char* env = std::getenv("SIMR_LSM_SWEEP");
+  if (env && env[0] == '0') return cudaSuccess;
+  int dev = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess || !coop) return e;
+  e = try_sweep_m<1>(L, B, Y, num_sms, st, used);
+  if (e == cudaSuccess && !*used) e = try_sweep_m<2>(L, B, Y, num_sms, st, used);
+  if (e == cudaSuccess && !*used) e = try_sweep_m<4>(L, B, Y, num_sms, st, used);
+  if (e == cudaSuccess && !*used) e = try_sweep_m<7>(L, B, Y, num_sms, st, used);
+  return e;
+}
+
+}  // namespace
 
 cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream) {
   int per_sm = 0;
@@ -428,6 +850,11 @@ cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cud
   lsm_paths_kernel<<<(unsigned)grid, kLsmTpb, 0, stream>>>(L, B.S, B.V, B.cash, B.stop);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+
+  bool swept = false;
+  const LsmSweep Y{B.ticket + 4, B.ticket + 8, B.status, reinterpret_cast<float2*>(B.partials)};
+  e = try_sweep(L, B, Y, num_sms, stream, &swept);
+  if (e != cudaSuccess || swept) return e;
 
   // date kernels: resident blocks on all SMs (at most kLsmMaxBlocksPerSm), at most one path per thread more
   int per_sm2 = 0;

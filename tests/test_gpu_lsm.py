@@ -169,6 +169,63 @@ def test_lsm_full_size_properties(simr):
     assert agree > 0.995, agree
 
 
+def _perturbed_oracle_spread(model, K, is_put, steps, every, paths, seed, n=3):
+    """The oracle's own sensitivity: its price and exercise dates with S and v
+    perturbed by 1e-7 relative (the size of the FP32 path error), n draws.
+    Returns (max |price change|, max fraction of paths whose date changed)."""
+    base = olsm.lsm(model, K, is_put, steps, every, paths, seed)
+    orig = olsm.states
+    dp, ds = 0.0, 0.0
+    for k in range(n):
+        rng = np.random.default_rng(100 + k)
+
+        def noisy(*a, **kw):
+            S, v = orig(*a, **kw)
+            return S * (1 + 1e-7 * rng.standard_normal(S.shape)), v * (1 + 1e-7 * rng.standard_normal(v.shape))
+
+        olsm.states = noisy
+        try:
+            r = olsm.lsm(model, K, is_put, steps, every, paths, seed)
+        finally:
+            olsm.states = orig
+        dp = max(dp, abs(r.price - base.price))
+        ds = max(ds, float(np.mean(r.stop != base.stop)))
+    return base, dp, ds
+
+
+def test_lsm_large_matches_oracle_within_its_own_sensitivity(simr):
+    # With tens of thousands of paths a decision somewhere sits within rounding of
+    # its boundary; its flip moves every earlier fit a little and flips more
+    # near-boundary decisions (the oracle does the same under 1e-7 noise: ~1e-4 of
+    # the price at 2^16 paths).  The GPU must stay within a few times that spread.
+    args = (BASE, 100.0, True, 64, 2, 1 << 16, 4)
+    ref, dp, ds = _perturbed_oracle_spread(*args)
+    p, _, _, stop = simr.lsm_price(*args, with_stop=True)
+    assert abs(p.item() - ref.price) <= 4 * dp + 1e-5 * ref.price, (p.item(), ref.price, dp)
+    assert np.mean(stop.cpu().numpy() != ref.stop) <= 4 * ds + 1e-4
+
+
+@pytest.mark.parametrize("paths", [5003, 1 << 18, 1 << 20])
+def test_cooperative_sweep_and_per_date_launches_agree(simr, paths, monkeypatch):
+    # the backward induction runs as one cooperative launch or as one kernel per
+    # date; they group the FP32 partial sums differently, so their fits differ at
+    # ~1e-7 -- below the estimator's own sensitivity at large path counts (see
+    # above), hence a bound of a small fraction of the standard error there
+    args = (BASE, 100.0, True, 64, 2, paths, 4)
+    a = simr.lsm_price(*args, with_beta=True, with_stop=True)
+    monkeypatch.setenv("SIMR_LSM_SWEEP", "0")
+    b = simr.lsm_price(*args, with_beta=True, with_stop=True)
+    sa, sb = a[3].cpu().numpy(), b[3].cpu().numpy()
+    if paths < 10000:
+        assert a[0].item() == pytest.approx(b[0].item(), rel=1e-6)
+        assert np.mean(sa != sb) <= 1e-3
+    else:
+        assert abs(a[0].item() - b[0].item()) <= 0.1 * a[1].item()
+        assert np.mean(sa != sb) <= 2e-2
+    ba, bb = a[2].cpu().numpy(), b[2].cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(ba), np.isnan(bb))
+
+
 def test_lsm_rejects_bad_arguments(simr):
     with pytest.raises(simr.SimrError):
         simr.lsm_price(BASE, 100.0, True, 64, 5, 1000, 1)   # 5 does not divide 64

@@ -46,6 +46,24 @@ def test_normal_equation_solve_matches_lstsq():
     assert keep0 == [True, True, True, False, False, False]
     ref0 = np.linalg.lstsq(Phi0, Y, rcond=None)[0]
     np.testing.assert_allclose(Phi0 @ beta0, Phi0 @ ref0, rtol=1e-9, atol=1e-9)
+    # constant v in standardised coordinates: ys is a constant, collinear with 1
+    coef = lsm.standardise(dict(workloads.BASE_MODEL), 10, 4)
+    Ps = lsm.basis_std(S, np.full(400, 0.05), coef)
+    bs, keeps = lsm.solve_normal(Ps.T @ Ps, Ps.T @ Y)
+    assert keeps == [True, True, True, False, False, False]
+    np.testing.assert_allclose(Ps @ bs, Phi0 @ ref0, rtol=1e-9, atol=1e-9)
+
+
+def test_standardised_and_reported_coefficients_are_the_same_quadratic():
+    rng = np.random.default_rng(6)
+    m = dict(workloads.BASE_MODEL)
+    S = 100.0 * np.exp(0.2 * rng.standard_normal(50))
+    v = 0.04 * rng.gamma(4.0, 0.25, 50)
+    coef = lsm.standardise(m, 12, 3)
+    bs = rng.standard_normal(6)
+    br = lsm.reported(bs, coef, 95.0, lsm.basis_scale(m))
+    np.testing.assert_allclose(lsm.basis(S, v, 95.0, lsm.basis_scale(m)) @ br, lsm.basis_std(S, v, coef) @ bs,
+                               rtol=1e-9, atol=1e-9)
 
 
 def test_regression_on_simulated_paths_matches_lstsq():
@@ -54,12 +72,11 @@ def test_regression_on_simulated_paths_matches_lstsq():
     h = lsm.payoff(r.S, 100.0, True)
     j = n_ex - 2  # the first regression: targets are the maturity payoffs
     itm = h[:, j] > 0
-    Y = np.where(r.stop[itm] >= 0, 0.0, 0.0)
-    # rebuild the first regression's targets independently: only the maturity cash flow exists
+    # the first regression's targets, rebuilt independently: only the maturity cash flow exists
     Y = h[itm, -1] * math.exp(-BASE["r"] * (r.t[-1] - r.t[j]))
     Phi = lsm.basis(r.S[itm, j], r.v[itm, j], 100.0, lsm.basis_scale(BASE))
     ref = np.linalg.lstsq(Phi, Y, rcond=None)[0]
-    np.testing.assert_allclose(Phi @ r.beta[j], Phi @ ref, rtol=1e-9, atol=1e-9 * np.abs(Y).max())
+    np.testing.assert_allclose(Phi @ r.beta[j], Phi @ ref, rtol=1e-8, atol=1e-8 * np.abs(Y).max())
 
 
 DET = dict(S0=50.0, r=0.1, T=1.0, v0=1e-12, kappa=1.5, theta=1e-12, sigma=1e-4, rho=0.0)
