@@ -81,6 +81,10 @@ def lib():
             L.oracle_path_grad_forward.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_adjoint.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
             L.oracle_states.argtypes = [H, u32, u32, u64, u32, u64, i64, dp, dp]
+            L.oracle_set_scheme.argtypes = [c_int]
+            L.oracle_set_scheme.restype = None
+            L.oracle_step_exp_mean.argtypes = [H, u32, ctypes.c_double]
+            L.oracle_step_exp_mean.restype = ctypes.c_double
             L.oracle_max_threads.restype = c_int
             L.oracle_set_threads.argtypes = [c_int]
             _lib = L
@@ -95,6 +99,31 @@ def _model(model) -> Heston:
     if isinstance(model, Heston):
         return model
     return Heston(**{k: float(model[k]) for k in ("S0", "r", "T", "v0", "kappa", "theta", "sigma", "rho")})
+
+
+SCHEMES = {"qe": 0, "qem": 1}
+
+
+class scheme:
+    """Context manager selecting the log-spot scheme of every oracle call inside:
+    "qe" (Andersen's QE) or "qem" (QE with Andersen's martingale correction)."""
+
+    def __init__(self, name: str):
+        self.code = SCHEMES[name]
+
+    def __enter__(self):
+        lib().oracle_set_scheme(self.code)
+        return self
+
+    def __exit__(self, *exc):
+        lib().oracle_set_scheme(0)
+        return False
+
+
+def step_exp_mean(model, steps: int, v: float) -> float:
+    """E[exp(x(t+dt) - x(t) - r dt) | v(t) = v] of one step, exact over the uniform
+    lattice (1 for a martingale scheme), under the current scheme."""
+    return float(lib().oracle_step_exp_mean(ctypes.byref(_model(model)), int(steps), float(v)))
 
 
 def max_threads() -> int:

@@ -11,6 +11,7 @@
  *   LogPricePathQE         -> log-spot update in simulate_path
  *   AssetPathExponential   -> S_T = S0 * exp(x_N) in the payoff functions
  *   reduction over paths   -> oracle_price (Sec. 6: paths reduced with a cross-path sum)
+ *   QE-M variant           -> oracle_set_scheme(1) (Andersen's martingale correction)
  *   writeLongstaffSchwartzPath -> oracle_states (per-path states at the exercise
  *                             dates; the regression itself is in lsm.py)
  * The per-path state is carried from timestep to timestep exactly as in the
@@ -239,6 +240,50 @@ double oracle_qe_variance_step(double v, double u_v, const double* k, int* branc
   return log((1.0 - p) / (1.0 - u_v)) / beta;
 }
 
+/*
+ * Log-spot scheme: 0 = QE as above; 1 = QE-M, Andersen's martingale correction
+ * (Andersen 2008, the martingale-correction section): with A = K2 + K4/2 the
+ * constant K0 - r dt of the log-spot step is replaced by
+ *   K0* = -ln M - (K1 + K3/2) v,   M = E[exp(A v(t+dt)) | v(t)] under the QE step,
+ *   quadratic branch:    ln M = A b^2 a / (1 - 2 A a) - (1/2) ln(1 - 2 A a)   (needs 2 A a < 1)
+ *   exponential branch:  M = p + beta (1 - p) / (beta - A)                    (needs A < beta)
+ * so that E[exp(x(t+dt) - x(t) - r dt) | v(t)] = 1; where the condition fails
+ * the step keeps K0.  Set for the whole library by oracle_set_scheme (test
+ * infrastructure: read-only while a computation runs).
+ */
+static int g_scheme = 0;
+
+void oracle_set_scheme(int scheme) { g_scheme = scheme; }
+
+/* ln M of the QE-M correction at state v (k: the 9 constants + theta); *ok = 0
+ * where the correction does not exist.  m = 0 gives v' = 0, M = 1. */
+static double qem_log_m(double v, const double* k, int* ok) {
+  const double theta_ = k[9], E = k[1], c1 = k[2], c2 = k[3];
+  const double A = k[6] + 0.5 * k[8];
+  const double m = theta_ + (v - theta_) * E;
+  const double s2 = v * c1 + c2;
+  *ok = 1;
+  if (m <= 0.0) return 0.0;
+  const double psi = s2 / (m * m);
+  if (psi <= PSI_C) {
+    const double two_over_psi = 2.0 / psi;
+    const double b2 = two_over_psi - 1.0 + sqrt(two_over_psi) * sqrt(two_over_psi - 1.0);
+    const double a = m / (1.0 + b2);
+    if (!(2.0 * A * a < 1.0)) {
+      *ok = 0;
+      return 0.0;
+    }
+    return A * b2 * a / (1.0 - 2.0 * A * a) - 0.5 * log(1.0 - 2.0 * A * a);
+  }
+  const double p = (psi - 1.0) / (psi + 1.0);
+  const double beta = (1.0 - p) / m;
+  if (!(A < beta)) {
+    *ok = 0;
+    return 0.0;
+  }
+  return log(p + beta * (1.0 - p) / (beta - A));
+}
+
 /* Constants array used by the step: the 9 QE constants followed by theta. */
 static void step_constants(const oracle_heston* m, uint32_t steps, double k[10]) {
   oracle_qe_constants(m, steps, k);
@@ -266,7 +311,13 @@ static void simulate_path_rec(const oracle_heston* m, const double* k, uint32_t 
     if (cd < min_cond) min_cond = cd;
     /* LogPricePathQE: x += K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X */
     double z_x = oracle_norminv(u_x);
-    x += k[4] + k[5] * v + k[6] * v_next + sqrt(k[7] * v + k[8] * v_next) * z_x;
+    double k0 = k[4];
+    if (g_scheme == 1) { /* QE-M: r dt + K0* in place of K0 */
+      int ok;
+      const double lnM = qem_log_m(v, k, &ok);
+      if (ok) k0 = m->r * k[0] - lnM - (k[5] + 0.5 * k[7]) * v;
+    }
+    x += k0 + k[5] * v + k[6] * v_next + sqrt(k[7] * v + k[8] * v_next) * z_x;
     v = v_next;
     if (every && (n + 1) % every == 0) {
       x_rec[(n + 1) / every - 1] = x;
@@ -358,6 +409,34 @@ int oracle_states(const oracle_heston* m, uint32_t steps, uint32_t every, uint64
     for (int64_t j = 0; j < n_ex; ++j) xs[j] = m->S0 * exp(xs[j]);
   }
   return 0;
+}
+
+/*
+ * E[exp(x(t+dt) - x(t) - r dt) | v(t) = v] of one step under the library's
+ * scheme: the normal Z_X integrated exactly (E exp(s Z) = exp(s^2/2)) and the
+ * variance uniform summed over its whole lattice u = (j + 1/2) 2^-23, the set
+ * of values the generator produces, each equally likely -- so this is the
+ * scheme's exact one-step expectation.  1 for a martingale scheme.
+ */
+double oracle_step_exp_mean(const oracle_heston* m, uint32_t steps, double v) {
+  double k[10];
+  step_constants(m, steps, k);
+  double k0 = k[4] - m->r * k[0];
+  if (g_scheme == 1) {
+    int ok;
+    const double lnM = qem_log_m(v, k, &ok);
+    if (ok) k0 = -lnM - (k[5] + 0.5 * k[7]) * v;
+  }
+  const int64_t n = (int64_t)1 << 23;
+  double sum = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    const double u = ((double)j + 0.5) * 0x1p-23;
+    int br;
+    double mg;
+    const double vn = oracle_qe_variance_step(v, u, k, &br, &mg, NULL);
+    sum += exp(k0 + k[5] * v + k[6] * vn + 0.5 * (k[7] * v + k[8] * vn));
+  }
+  return sum / (double)n;
 }
 
 /* European payoff of a call (is_put = 0) or put; zero at S_T = K. */

@@ -1,0 +1,67 @@
+"""Pins of the oracle's QE-M scheme (QE with Andersen's martingale correction).
+
+The correction is defined by one property: the discounted spot is an exact
+martingale of the discrete scheme, E[exp(x(t+dt) - x(t) - r dt) | v(t)] = 1.
+The oracle's one-step expectation sums the variance uniform over its whole
+lattice (every value the generator can produce) and integrates the normal
+exactly, so it is the scheme's exact expectation; a wrong term in ln M breaks
+it.  Further pins: with rho = 0 the correction vanishes (A = 0, M = 1) and the
+paths are plain QE's bit for bit; where the correction does not exist the step
+falls back to QE; the multi-step martingale holds within Monte Carlo error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+BASE = dict(workloads.BASE_MODEL)
+WILD = dict(BASE, sigma=1.0, rho=-0.9, kappa=0.5, T=2.0)  # coarse steps, strong leverage
+
+
+@pytest.mark.parametrize("model", [BASE, WILD], ids=["base", "wild"])
+def test_one_step_expectation_is_a_martingale(model):
+    for v in (0.0, 0.003, 0.04, 0.3):
+        with oracle.scheme("qem"):
+            assert abs(oracle.step_exp_mean(model, 8, v) - 1.0) < 5e-9
+    # the plain scheme is off by far more on the coarse, strongly correlated model
+    with oracle.scheme("qe"):
+        assert max(abs(oracle.step_exp_mean(WILD, 8, v) - 1.0) for v in (0.0, 0.3)) > 1e-5
+
+
+def test_zero_correlation_reduces_to_plain_qe():
+    m = dict(BASE, rho=0.0)
+    x0, v0, _ = oracle.terminal(m, 40, 3, 0, 2000)
+    with oracle.scheme("qem"):
+        x1, v1, _ = oracle.terminal(m, 40, 3, 0, 2000)
+    np.testing.assert_array_equal(v0, v1)
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-15)
+
+
+def test_correction_falls_back_where_it_does_not_exist():
+    # one 4-year step, rho = 0.99, sigma = 3, v = 2: the exponential branch with
+    # A = K2 + K4/2 above beta = (1 - p)/m, where E[exp(A v')] is infinite
+    m = dict(BASE, T=4.0, rho=0.99, sigma=3.0, kappa=5.0)
+    k = oracle.qe_constants(m, 1)
+    A = k["K2"] + 0.5 * k["K4"]
+    v = 2.0
+    mean = m["theta"] + (v - m["theta"]) * k["E"]
+    s2 = v * k["c1"] + k["c2"]
+    psi = s2 / mean ** 2
+    p = (psi - 1) / (psi + 1)
+    assert psi > 1.5 and A >= (1 - p) / mean
+    with oracle.scheme("qe"):
+        plain = oracle.step_exp_mean(m, 1, v)
+    with oracle.scheme("qem"):
+        assert oracle.step_exp_mean(m, 1, v) == plain
+
+
+def test_multi_step_martingale_within_monte_carlo_error():
+    n = 1 << 18
+    with oracle.scheme("qem"):
+        x, _, _ = oracle.terminal(WILD, 8, 5, 0, n)
+    disc = np.exp(-WILD["r"] * WILD["T"]) * WILD["S0"] * np.exp(x)
+    se = disc.std(ddof=1) / math.sqrt(n)
+    assert abs(disc.mean() - WILD["S0"]) < 3 * se
