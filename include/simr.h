@@ -93,6 +93,10 @@ typedef struct {
 } simr_option;
 
 /* simr_batch_submit flags */
+/* Log-spot schemes (simr_set_scheme). */
+#define SIMR_SCHEME_QE 0   /* Andersen's QE, central weights, no martingale correction (default) */
+#define SIMR_SCHEME_QEM 1  /* QE with Andersen's martingale correction                          */
+
 #define SIMR_BATCH_ADJOINT (1u << 0)      /* also the 7 pathwise sensitivities per option       */
 #define SIMR_BATCH_GRAPH (1u << 1)        /* capture the launch in a CUDA graph; replay on repeat */
 #define SIMR_BATCH_NO_AUTOTUNE (1u << 2)  /* skip the first-call chunk-size search              */
@@ -216,6 +220,23 @@ SIMR_API int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opt
 SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin,
                                 uint64_t n_paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,
                                 float* x_T, float* grad, void* stream);
+
+/*
+ * Select the log-spot scheme of the context's later path simulations.
+ *   SIMR_SCHEME_QE   Andersen (2008) QE, psi_c = 1.5, gamma1 = gamma2 = 1/2 (the
+ *                    stages VariancePathQE / LogPricePathQE of the paper, Sec. 4-5).
+ *   SIMR_SCHEME_QEM  the same variance step; the log-spot step with Andersen's
+ *                    martingale correction: K0 - r dt replaced by
+ *                    K0* = -ln M - (K1 + K3/2) v, M = E[exp(A v(t+dt)) | v(t)],
+ *                    A = K2 + K4/2 (the plain step where M does not exist), so
+ *                    that the discounted spot is an exact martingale of the scheme.
+ * QE-M applies to simr_price, simr_paths_terminal, simr_lsm_price and to
+ * simr_greeks_fd / simr_path_sums with Greeks read off the base path (delta,
+ * gamma, rho); the re-simulated Greeks, the adjoint kernels and the batched book
+ * return SIMR_EUNSUPPORTED under it.  simr_price_noalloc is always QE.
+ * SIMR_EINVAL for an unknown scheme.
+ */
+SIMR_API int simr_set_scheme(simr_ctx* ctx, int scheme);
 
 /*
  * Longstaff-Schwartz (least-squares Monte Carlo) price of a Bermudan call or

@@ -227,6 +227,28 @@ def finalize_sums(model, strikes, is_put: bool, steps: int, paths: int, sums: to
     return p, se, g
 
 
+def set_scheme(name: str, device: int = 0):
+    """simr_set_scheme: "qe" (Andersen's QE) or "qem" (QE with the martingale correction)
+    for the device context's later path simulations."""
+    L = S.load()
+    S.check(L.simr_set_scheme(S.context(device), S.SCHEMES[name]))
+
+
+class scheme:
+    """Context manager: the simulations inside use the given scheme on `device`."""
+
+    def __init__(self, name: str, device: int = 0):
+        self.name, self.device = name, device
+
+    def __enter__(self):
+        set_scheme(self.name, self.device)
+        return self
+
+    def __exit__(self, *exc):
+        set_scheme("qe", self.device)
+        return False
+
+
 def sync(device: int = 0, stream=None):
     """simr_sync on a device's current (or given) stream."""
     L = S.load()

@@ -26,6 +26,7 @@ struct simr_ctx {
   // 256-byte block: ticket word at 0, status word at 64, batch queue counter at
   // 128, Longstaff-Schwartz ticket at 192, its sweep barrier words at 208 and 224
   unsigned int* ticket = nullptr;
+  int scheme = SIMR_SCHEME_QE;  // log-spot scheme of the path simulations (simr_set_scheme)
   float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]
   size_t ckpt_floats = 0;
   // Longstaff-Schwartz: states at the exercise dates, per-path cash flows,
@@ -493,6 +494,31 @@ int with_device(simr_ctx* ctx) {
   return SIMR_OK;
 }
 
+// QE-M constants (FP64 -> FP32): r dt, qa = dt (1 - rho^2)/4 (= K3/2 = K4/2),
+// K2 = dt/2 (kappa rho/sigma - 1/2) + rho/sigma, A = K2 + K4/2 = K2 + qa.
+QemConst qem_const(const simr_heston& m, uint32_t steps) {
+  const double dt = m.T / (double)steps;
+  const double K2 = 0.5 * dt * (m.kappa * m.rho / m.sigma - 0.5) + m.rho / m.sigma;
+  const double qa = 0.25 * dt * (1.0 - m.rho * m.rho);
+  return QemConst{(float)(m.r * dt), (float)qa, (float)K2, (float)(K2 + qa)};
+}
+
+// The context's scheme on a path launch: QE-M runs the base scenario only (price,
+// and the Greeks read off the base path: delta, gamma, rho).
+int apply_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, PathLaunch* L) {
+  if (ctx->scheme == SIMR_SCHEME_QE) return SIMR_OK;
+  if (L->n_scen != 1)
+    return fail(SIMR_EUNSUPPORTED, "scheme QE-M supports prices and the delta, gamma and rho of the base path only");
+  L->scheme = 1;
+  L->qm = qem_const(m, steps);
+  return SIMR_OK;
+}
+
+int require_plain_qe(const simr_ctx* ctx, const char* what) {
+  if (ctx->scheme == SIMR_SCHEME_QE) return SIMR_OK;
+  return fail(SIMR_EUNSUPPORTED, "%s runs the plain QE scheme only (simr_set_scheme)", what);
+}
+
 int ensure_scratch(simr_ctx* ctx, const PathLaunch& L) {
   return ensure(&ctx->partials, &ctx->partial_doubles, paths_scratch_doubles(L, ctx->num_sms), "reduction scratch");
 }
@@ -706,6 +732,7 @@ int simr_price(simr_ctx* ctx, const simr_heston* model, const double* strikes, i
   PathLaunch L;
   if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, 1e-4, 0u, &L)))
     return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
   OutStage o;
@@ -731,6 +758,7 @@ int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strike
   if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, rel_bump,
                          greek_mask, &L)))
     return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
   OutStage o;
@@ -748,6 +776,7 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
   if (rc) return rc;
   if (!price || !grad) return fail(SIMR_EINVAL, "price and grad must be non-NULL");
+  if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
   if ((rc = with_device(ctx))) return rc;
@@ -794,6 +823,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   if (n_paths < 1 || n_paths > (1ull << 31)) return fail(SIMR_EINVAL, "n_paths must lie in [1, 2^31]");
   if (!x_T || !grad) return fail(SIMR_EINVAL, "x_T and grad must be non-NULL");
   if (!is_device_ptr(x_T) || !is_device_ptr(grad)) return fail(SIMR_EINVAL, "x_T and grad must be device pointers");
+  if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
   if ((size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * 128 * sizeof(float) > 200 * 1024)
@@ -823,6 +853,7 @@ int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strike
   if ((rc = build_launch(model, n_strikes, is_put, steps, path_begin, path_count, path_count, seed, option_index,
                          greek_mask ? rel_bump : 1e-4, greek_mask, &L)))
     return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
   L.raw_sums = 1;
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
@@ -884,6 +915,8 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   if (is_device_ptr(opts)) return fail(SIMR_EINVAL, "the option table must be in host memory");
   const bool adjoint = (flags & SIMR_BATCH_ADJOINT) != 0;
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
+  int rc0 = require_plain_qe(ctx, "the batched book");
+  if (rc0) return rc0;
   if (adjoint && !grad) return fail(SIMR_EINVAL, "adjoint books need grad");
   int rc = with_device(ctx);
   if (rc) return rc;
@@ -1021,6 +1054,7 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
   PathLaunch L;
   if ((rc = build_launch(model, 1, 0, steps, path_begin, n_paths, n_paths, seed, option_index, 1e-4, 0u, &L)))
     return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
   const bool hx = !is_device_ptr(x_T), hv = v_T && !is_device_ptr(v_T);
   float* dx = x_T;
   float* dv = v_T;
@@ -1035,6 +1069,13 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
   if (e == cudaSuccess && hv) e = cudaMemcpyAsync(v_T, dv, n_paths * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && (hx || hv)) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "copying terminal states");
+  return SIMR_OK;
+}
+
+int simr_set_scheme(simr_ctx* ctx, int scheme) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (scheme != SIMR_SCHEME_QE && scheme != SIMR_SCHEME_QEM) return fail(SIMR_EINVAL, "unknown scheme %d", scheme);
+  ctx->scheme = scheme;
   return SIMR_OK;
 }
 
@@ -1118,6 +1159,8 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
   L.disc0 = std::exp(-model->r * dt_ex);
   L.Kd = K;
   L.wd = w > 0.0 ? w : 1.0;
+  L.scheme = ctx->scheme == SIMR_SCHEME_QEM ? 1 : 0;
+  L.qm = qem_const(*model, steps);
   LsmBuffers B{ctx->lsm_S,
                ctx->lsm_V,
                ctx->lsm_cash,

@@ -208,6 +208,99 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
   v = vn;
 }
 
+// QE-M (Andersen 2008, martingale correction): the constant K0 - r dt of the
+// log-spot step becomes K0* = -ln M - (K1 + K3/2) v with M = E[exp(A v') | v],
+// A = K2 + K4/2, so that the discounted spot is an exact martingale of the
+// scheme.  Written around the same m and dl as the plain step,
+//   x' - x = r dt - qa (v + m) - lam + K2 (v' - m) + sK3 sqrt(v + v') Z_X,
+// qa = K3/2 = K4/2 = dt (1 - rho^2)/4 and lam = ln M - A m >= 0, which has no
+// large cancelling terms (the rho/sigma parts of K1, K2 cancel exactly).
+struct QemConst {
+  float rdt, qa, K2, A;  // r dt, dt (1 - rho^2)/4, K2, K2 + K4/2
+};
+
+// g(u) = -u - ln(1 - u) = sum_{k >= 2} u^k / k, u < 1: the series to u^8 for
+// |u| < 1/8 (remainder below 6e-8 relative), else the logarithm.
+__device__ __forceinline__ float neg_log1m_tail(float u) {
+  if (fabsf(u) < 0.125f) {
+    float t = fmaf(u, 0.125f, 0.14285714285714285f);
+    t = fmaf(u, t, 0.16666666666666666f);
+    t = fmaf(u, t, 0.2f);
+    t = fmaf(u, t, 0.25f);
+    t = fmaf(u, t, 0.33333333333333333f);
+    t = fmaf(u, t, 0.5f);
+    return u * u * t;
+  }
+  return -u - log1pf(-u);
+}
+
+// lam = ln M - A m of the QE-M correction for the QE step with moments (m, s2);
+// false where M does not exist (quadratic branch: 2 A a >= 1; exponential
+// branch: A >= beta).  Quadratic: lam = 2 (A a)^2 b^2 / (1 - 2 A a) + g(2 A a)/2;
+// exponential: lam = ln(1 + (1 - p) w / (1 - w)) - (1 - p) w with w = A / beta.
+// The branch quantities repeat qe_from_moments' own expressions.
+__device__ __forceinline__ bool qem_lambda(float m, float s2, float A, float& lam) {
+  const float m2 = m * m;
+  lam = 0.0f;
+  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
+    const float t = 2.0f * m2 * rcp_approx(s2);
+    const float root = sqrt_approx(fmaf(t, t, -t));
+    const float b2 = (t - 1.0f) + root;
+    const float a = m * rcp_approx(t + root);
+    const float Aa = A * a;
+    const float u = 2.0f * Aa;
+    if (!(u < 1.0f)) return false;
+    lam = fmaf(0.5f, neg_log1m_tail(u), 2.0f * Aa * Aa * b2 / (1.0f - u));
+    return true;
+  }
+  if (m > 0.0f) {
+    const float ms = m2 + s2;
+    const float onep = 2.0f * m2 / ms;  // 1 - p
+    const float w = A * ms / (2.0f * m);  // A / beta, beta = (1 - p)/m = 2 m / ms
+    if (!(w < 1.0f)) return false;
+    lam = log1pf(onep * w / (1.0f - w)) - onep * w;
+    return true;
+  }
+  return true;  // m = 0: v' = 0, M = 1
+}
+
+// One QE-M step of the base scenario (variance step identical to step_base's);
+// where the correction does not exist the plain QE increment is taken.
+__device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, float omu, float zv, float zx,
+                                         float& v, float& x, float& comp) {
+  float vn, dl, lam;
+  const float m = fmaf(v, c.E, c.thE);
+  const float s2 = fmaf(v, c.c1, c.c2);
+  qe_from_moments(m, s2, omu, zv, vn, dl);
+  const float s = v + vn;
+  float inc;
+  if (qem_lambda(m, s2, q.A, lam)) {
+    inc = fmaf(-q.qa, v + m, q.rdt) - lam;
+    inc = fmaf(q.K2, dl, inc);
+  } else {
+    inc = fmaf(c.Cv, s, c.C0);
+    inc = fmaf(-c.Cd, v, inc);
+    inc = fmaf(c.Cdl, dl, inc);
+  }
+  inc = fmaf(c.sK3 * sqrt_approx(s), zx, inc);
+  const float y = inc - comp;
+  const float t = x + y;
+  comp = (t - x) - y;
+  x = t;
+  v = vn;
+}
+
+// One step of the base scenario under scheme QEM (false: QE) with the CRN
+// rounding order of step_base<CRN> for the plain scheme.
+template <bool CRN, bool QEM>
+__device__ __forceinline__ void step_scheme(const ScenConst& c, const QemConst& q, float omu, float zv, float zx,
+                                            float& v, float& x, float& comp) {
+  if constexpr (QEM)
+    step_qem(c, q, omu, zv, zx, v, x, comp);
+  else
+    step_base<CRN>(c, omu, zv, zx, v, x, comp);
+}
+
 #ifndef SIMR_KAHAN_BUMPED
 #define SIMR_KAHAN_BUMPED 1  // Kahan-compensate x in bumped scenarios too
 #endif
@@ -292,8 +385,10 @@ __device__ __forceinline__ void step0_crn(const FirstConst& fb, const FirstConst
 }
 
 // One path of one scenario over all steps: x_T with its Kahan remainder.
+template <bool QEM = false>
 __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps, uint32_t option,
-                                             const uint32_t (&rk)[10][2], uint64_t path, float& x, float& comp) {
+                                             const uint32_t (&rk)[10][2], uint64_t path, float& x, float& comp,
+                                             const QemConst& q = QemConst{}) {
   const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
   float v = c.v0;
   x = 0.0f;
@@ -302,13 +397,13 @@ __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps,
     const uint4 w = philox4x32_10(p, plo, phi, option, rk);
     {
       const float xv = centered_uniform(w.x);
-      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.y)), v, x,
-                       comp);
+      step_scheme<false, QEM>(c, q, 0.5f * (1.0f - xv), norminv_centered(xv),
+                              norminv_centered(centered_uniform(w.y)), v, x, comp);
     }
     if (2 * p + 1 < steps) {
       const float xv = centered_uniform(w.z);
-      step_base<false>(c, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w.w)), v, x,
-                       comp);
+      step_scheme<false, QEM>(c, q, 0.5f * (1.0f - xv), norminv_centered(xv),
+                              norminv_centered(centered_uniform(w.w)), v, x, comp);
     }
   }
 }

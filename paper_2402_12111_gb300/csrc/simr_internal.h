@@ -42,6 +42,8 @@ struct PathLaunch {
   double paths_total;     // denominator of the mean
   double denom[kMaxGreeks];  // per Greek: bump denominator (sign folded in)
   int32_t raw_sums;       // 1: write raw sums instead of normalised results
+  int32_t scheme;         // 0: QE; 1: QE-M (base scenario only, n_scen == 1)
+  QemConst qm;            // QE-M constants of the base scenario
 };
 
 struct PathOutputs {
@@ -158,6 +160,8 @@ struct LsmLaunch {
   uint64_t paths;
   double disc0;        // e^{-r t_0}
   double Kd, wd;       // strike and basis scale w in FP64 (coefficient conversion)
+  int32_t scheme;      // 0: QE; 1: QE-M
+  QemConst qm;
 };
 
 struct LsmBuffers {

@@ -72,6 +72,7 @@ __device__ __forceinline__ float lsm_payoff(bool put, float S, float K) {
 }
 
 // Path kernel: states at the exercise dates, maturity cash flow.
+template <bool QEM>
 __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constant__ LsmLaunch L,
                                                             float* __restrict__ S_out, float* __restrict__ V_out,
                                                             float* __restrict__ cash, int32_t* __restrict__ stop) {
@@ -112,8 +113,8 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
 #pragma unroll
       for (int j = 0; j < kLsmPpt; ++j) {
         const float xv = centered_uniform(w[j].x);
-        step_base<false>(L.sc, 0.5f * (1.0f - xv), norminv_centered(xv), norminv_centered(centered_uniform(w[j].y)),
-                         v[j], x[j], comp[j]);
+        step_scheme<false, QEM>(L.sc, L.qm, 0.5f * (1.0f - xv), norminv_centered(xv),
+                                norminv_centered(centered_uniform(w[j].y)), v[j], x[j], comp[j]);
       }
       if (++cnt == L.every) {
         cnt = 0;
@@ -123,8 +124,8 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
 #pragma unroll
         for (int j = 0; j < kLsmPpt; ++j) {
           const float xv = centered_uniform(w[j].z);
-          step_base<false>(L.sc, 0.5f * (1.0f - xv), norminv_centered(xv),
-                           norminv_centered(centered_uniform(w[j].w)), v[j], x[j], comp[j]);
+          step_scheme<false, QEM>(L.sc, L.qm, 0.5f * (1.0f - xv), norminv_centered(xv),
+                                  norminv_centered(centered_uniform(w[j].w)), v[j], x[j], comp[j]);
         }
         if (++cnt == L.every) {
           cnt = 0;
@@ -840,14 +841,15 @@ cudaError_t try_sweep(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y
 
 cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsm_paths_kernel, kLsmTpb, 0);
+  auto pk = L.scheme == 1 ? lsm_paths_kernel<true> : lsm_paths_kernel<false>;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, kLsmTpb, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t batches = (L.paths + (uint64_t)kWarp * kLsmPpt - 1) / ((uint64_t)kWarp * kLsmPpt);
   uint64_t grid = (uint64_t)num_sms * per_sm;
   const uint64_t need = (batches + kLsmWarps - 1) / kLsmWarps;
   if (grid > need) grid = need;
-  lsm_paths_kernel<<<(unsigned)grid, kLsmTpb, 0, stream>>>(L, B.S, B.V, B.cash, B.stop);
+  pk<<<(unsigned)grid, kLsmTpb, 0, stream>>>(L, B.S, B.V, B.cash, B.stop);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 

@@ -84,14 +84,15 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
 // NS scenarios in registers; DYN: only the first L.n_scen of them are live.
 // Scenarios 1 .. NV differ from the base only in v0 (all constant deltas zero):
 // they take the base step, which is the bumped step's arithmetic with zero deltas.
-template <int NS, int NV, bool DYN>
+template <int NS, int NV, bool DYN, bool QEM = false>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
   const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
   const float zv = norminv_centered(xv);
   const float zx = norminv_centered(centered_uniform(w_x));
-  step_base<(NS > 1)>(L.sc[0], omu, zv, zx, v[0], x[0], c[0]);
+  static_assert(!QEM || NS == 1, "QE-M runs the base scenario only");
+  step_scheme<(NS > 1), QEM>(L.sc[0], L.qm, omu, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
   for (int s = 1; s < NS; ++s) {
     if (DYN && s >= L.n_scen) break;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uin
 // PPT paths per thread, simulated step by step in lockstep: independent
 // dependency chains the scheduler can interleave (instruction-level
 // parallelism at the same occupancy).
-template <int NS, int NV, bool DYN, int PPT>
+template <int NS, int NV, bool DYN, int PPT, bool QEM = false>
 __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t (&path)[PPT], float (&v)[PPT][NS],
                                              float (&x)[PPT][NS], float (&c)[PPT][NS]) {
 #pragma unroll
@@ -152,7 +153,7 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
     for (int j = 0; j < PPT; ++j) step0_all<NS, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
     if (L.steps > 1) {
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
+      for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
     }
     i0 = 1;
   }
@@ -161,15 +162,15 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
 #pragma unroll
     for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(i, plo[j], phi[j], L.option_index, L.rk);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
+    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
+    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
   }
   if ((L.steps & 1u) && pairs >= i0) {  // odd last step (step 0 itself when steps == 1 without the split)
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const uint4 w = philox4x32_10(pairs, plo[j], phi[j], L.option_index, L.rk);
-      step_all<NS, NV, DYN>(L, w.x, w.y, v[j], x[j], c[j]);
+      step_all<NS, NV, DYN, QEM>(L, w.x, w.y, v[j], x[j], c[j]);
     }
   }
 }
@@ -209,7 +210,7 @@ __device__ __forceinline__ void write_results(const PathLaunch& L, int k, const 
 // Fused price / Greeks kernel.  TILE = 1 (single strike) or 32 (strike tiles).
 // Dynamic shared memory: accumulators [warps][n_acc][nk_pad] (FP64), then the
 // strike constants [nk_pad] (StrikeConst), then a flag word.
-template <int NS, int NV, int TILE, bool DYN, int PPT>
+template <int NS, int NV, int TILE, bool DYN, int PPT, bool QEM>
 __global__ void __launch_bounds__(256, (NS * PPT <= 3 ? 4 : NS * PPT <= 5 ? SIMR_FD5_BLOCKS_PER_SM : 2)) heston_paths_kernel(const __grid_constant__ PathLaunch L,
                                                            const double* __restrict__ strikes,
                                                            PathOutputs out, double* __restrict__ partials,
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256, (NS * PPT <= 3 ? 4 : NS * PPT <= 5 ? SIMR
       pth[j] = L.path_begin + local;
     }
     float v[PPT][NS], x[PPT][NS], c[PPT][NS];
-    simulate_ppt<NS, NV, DYN, PPT>(L, pth, v, x, c);
+    simulate_ppt<NS, NV, DYN, PPT, QEM>(L, pth, v, x, c);
     float S[PPT][NS];
 #pragma unroll
     for (int j = 0; j < PPT; ++j)
@@ -331,24 +332,26 @@ __global__ void finalize_sums_kernel(const __grid_constant__ PathLaunch L, const
   if (k < L.n_strikes) write_results(L, k, sums + (size_t)k * L.n_acc, 1, out, false);
 }
 
+template <bool QEM>
 __global__ void __launch_bounds__(256) heston_terminal_kernel(const __grid_constant__ PathLaunch L,
                                                               float* __restrict__ x_T, float* __restrict__ v_T) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.path_count) return;
   float v[1][1], x[1][1], c[1][1];
   const uint64_t pth[1] = {L.path_begin + i};
-  simulate_ppt<1, 0, false, 1>(L, pth, v, x, c);
+  simulate_ppt<1, 0, false, 1, QEM>(L, pth, v, x, c);
   x_T[i] = x[0][0] - c[0][0];
   if (v_T) v_T[i] = v[0][0];
 }
 
-template <int NS, int NV, int TILE, bool DYN, int PPT = (NS == 1 ? SIMR_PRICE_PPT : SIMR_FD_PPT)>
+template <int NS, int NV, int TILE, bool DYN, bool QEM = false,
+          int PPT = (NS == 1 ? SIMR_PRICE_PPT : SIMR_FD_PPT)>
 cudaError_t launch_t(const PathLaunch& L, const double* strikes, const PathOutputs& out, const Scratch& s,
                      int num_sms, cudaStream_t stream, int* grid_used) {
   const int tpb = 256, warps = tpb / kWarp;
   const size_t row = (size_t)L.n_acc * L.nk_pad;
   const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(StrikeConst) + 16;
-  auto kern = heston_paths_kernel<NS, NV, TILE, DYN, PPT>;
+  auto kern = heston_paths_kernel<NS, NV, TILE, DYN, PPT, QEM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -380,6 +383,11 @@ cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathO
 #define SIMR_LAUNCH(NS_, NV_, DYN_)                                                                \
   (one ? launch_t<NS_, NV_, 1, DYN_>(L, strikes, out, s, num_sms, stream, grid_used)               \
        : launch_t<NS_, NV_, 32, DYN_>(L, strikes, out, s, num_sms, stream, grid_used))
+  if (L.scheme == 1) {  // QE-M: the base scenario alone
+    if (L.n_scen != 1) return cudaErrorInvalidValue;
+    return one ? launch_t<1, 0, 1, false, true>(L, strikes, out, s, num_sms, stream, grid_used)
+               : launch_t<1, 0, 32, false, true>(L, strikes, out, s, num_sms, stream, grid_used);
+  }
   switch (L.n_scen) {
     case 1:
       return SIMR_LAUNCH(1, 0, false);
@@ -405,7 +413,10 @@ cudaError_t launch_finalize(const PathLaunch& L, const double* sums, const PathO
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream) {
   const int tpb = 256;
   const uint64_t grid = (L.path_count + tpb - 1) / tpb;
-  heston_terminal_kernel<<<(unsigned)grid, tpb, 0, stream>>>(L, x_T, v_T);
+  if (L.scheme == 1)
+    heston_terminal_kernel<true><<<(unsigned)grid, tpb, 0, stream>>>(L, x_T, v_T);
+  else
+    heston_terminal_kernel<false><<<(unsigned)grid, tpb, 0, stream>>>(L, x_T, v_T);
   return cudaGetLastError();
 }
 
