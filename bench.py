@@ -419,6 +419,28 @@ def run_native(args):
             book[f"{name}_ms"] = ms_b
             book[f"{name}_path_steps_per_s"] = ps_book / (ms_b * 1e-3)
 
+    # the paper's problem sizes (Table 1: A assets analysed x T steps x P paths), each
+    # as one batched submission of A independent options: elements (A T P) per second
+    paper = None
+    if not args.no_book:
+        paper = {}
+        for size in workloads.PAPER_SIZES:
+            opts = workloads.paper_book(size)
+            simr.batch(opts, seed=1, graph=True)
+            simr.batch(opts, seed=1, graph=True)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            a.record(stream)
+            for _ in range(reps):
+                simr.batch(opts, seed=1, graph=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_p = a.elapsed_time(b) / reps
+            paper[size] = {"A": workloads.PAPER_SIZES[size][0], "T": workloads.PAPER_SIZES[size][1],
+                           "P": workloads.PAPER_SIZES[size][2], "elements": workloads.paper_elements(size),
+                           "ms": ms_p, "elements_per_s": workloads.paper_elements(size) / (ms_p * 1e-3)}
+
     # large-scale headline: 8 underlyings (book-style parameters), 32 strikes each,
     # 1,024 steps, 2^26 paths; price, adjoint Greeks (checkpoint every 32 steps) and
     # CRN bump-and-revalue of the same 7 sensitivities, one timed pass each
@@ -526,6 +548,7 @@ def run_native(args):
         "gpu_launches": args.steps,
         "adjoint_vs_fd": adj,
         "book": book,
+        "paper_sizes": paper,
         "headline": head,
         "lsm": lsm_leg,
         "kernel_source_sha": sha,

@@ -14,6 +14,7 @@ the closed forms and semi-analytic prices that pin the oracle in the tests.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -81,6 +82,7 @@ def lib():
             L.oracle_path_grad_forward.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_adjoint.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
             L.oracle_states.argtypes = [H, u32, u32, u64, u32, u64, i64, dp, dp]
+            L.oracle_basket_terminal.argtypes = [H, c_int, dp, u32, u64, u64, i64, dp]
             L.oracle_set_scheme.argtypes = [c_int]
             L.oracle_set_scheme.restype = None
             L.oracle_step_exp_mean.argtypes = [H, u32, ctypes.c_double]
@@ -217,6 +219,41 @@ def states(model, steps: int, every: int, seed: int, path_begin: int, n_paths: i
     if rc != 0:
         raise ValueError(f"oracle_states failed ({rc})")
     return S, v
+
+
+def basket_terminal(models, corr, steps: int, seed: int, path_begin: int, n_paths: int) -> np.ndarray:
+    """x[n_paths, A] = ln(S_T/S0) of A assets whose log-spot normals have correlation
+    `corr` (via numpy's Cholesky factor); asset k uses the counters of option index k."""
+    A = len(models)
+    arr = (Heston * A)(*[_model(m) for m in models])
+    Lc = np.ascontiguousarray(np.linalg.cholesky(np.asarray(corr, dtype=np.float64)))
+    x = np.empty((n_paths, A))
+    rc = lib().oracle_basket_terminal(arr, A, _dp(Lc), steps, seed, path_begin, n_paths, _dp(x))
+    if rc != 0:
+        raise ValueError(f"oracle_basket_terminal failed ({rc})")
+    return x
+
+
+def basket_price(models, corr, weights, strikes, is_put: bool, steps: int, paths: int, seed: int):
+    """(price[n_K], stderr[n_K]) of the basket option on B_T = sum_k w_k S_T,k:
+    e^{-rT} mean max(+-(B_T - K), 0), serial sums in path order."""
+    x = basket_terminal(models, corr, steps, seed, 0, paths)
+    S0 = np.array([float(m["S0"]) for m in models])
+    B = (np.exp(x) * S0[None, :]) @ np.asarray(weights, dtype=np.float64)
+    K = np.atleast_1d(np.asarray(strikes, dtype=np.float64))
+    disc = math.exp(-float(models[0]["r"]) * float(models[0]["T"]))
+    price, se = np.empty(K.size), np.empty(K.size)
+    for j, k in enumerate(K):
+        f = np.maximum(k - B, 0.0) if is_put else np.maximum(B - k, 0.0)
+        s1, s2 = 0.0, 0.0
+        for val in f:
+            s1 += val
+            s2 += val * val
+        mean = s1 / paths
+        price[j] = disc * mean
+        var = (s2 / paths - mean * mean) / (paths - 1) if paths > 1 else 0.0
+        se[j] = disc * math.sqrt(max(var, 0.0))
+    return price, se
 
 
 def price(model, strikes, is_put: bool, steps: int, paths: int, seed: int, option_index: int = 0):

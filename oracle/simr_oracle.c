@@ -412,6 +412,69 @@ int oracle_states(const oracle_heston* m, uint32_t steps, uint32_t every, uint64
 }
 
 /*
+ * Terminal log-spots of A correlated assets (basket options): asset k runs the
+ * single-asset scheme with its own model and the Philox counters of option
+ * index k, except that its log-spot normal is z_k = sum_{j <= k} Lc[k][j] eps_j,
+ * where eps_j = Phi^-1(U_X) of asset j and Lc is the lower Cholesky factor of
+ * the correlation of the spot drivers (row-major A x A; computed by the caller).
+ * The variance drivers stay independent across assets.  x[i * A + k] =
+ * ln(S_T / S0) of asset k on path path_begin + i.
+ */
+int oracle_basket_terminal(const oracle_heston* models, int n_assets, const double* Lc, uint32_t steps,
+                           uint64_t seed, uint64_t path_begin, int64_t n_paths, double* x_out) {
+  if (steps == 0 || n_assets < 1 || n_assets > 64 || n_paths < 0) return -1;
+  const int A = n_assets;
+  double* k = (double*)malloc(sizeof(double) * 10 * (size_t)A);
+  if (!k) return -2;
+  for (int a = 0; a < A; ++a) step_constants(&models[a], steps, &k[10 * a]);
+  int rc = 0;
+#pragma omp parallel
+  {
+    double* v = (double*)malloc(sizeof(double) * (size_t)A);
+    double* x = (double*)malloc(sizeof(double) * (size_t)A);
+    double* uv = (double*)malloc(sizeof(double) * (size_t)A);
+    double* eps = (double*)malloc(sizeof(double) * (size_t)A);
+    if (!v || !x || !uv || !eps) {
+#pragma omp atomic write
+      rc = -2;
+    } else {
+#pragma omp for schedule(static)
+      for (int64_t i = 0; i < n_paths; ++i) {
+        const uint64_t path = path_begin + (uint64_t)i;
+        for (int a = 0; a < A; ++a) {
+          v[a] = models[a].v0;
+          x[a] = 0.0;
+        }
+        for (uint32_t n = 0; n < steps; ++n) {
+          for (int a = 0; a < A; ++a) {
+            double u_x;
+            oracle_step_uniforms(seed, (uint32_t)a, path, n, &uv[a], &u_x);
+            eps[a] = oracle_norminv(u_x);
+          }
+          for (int a = 0; a < A; ++a) {
+            const double* ka = &k[10 * a];
+            double z = 0.0;
+            for (int j = 0; j <= a; ++j) z += Lc[a * A + j] * eps[j];
+            int br;
+            double mg;
+            const double vn = oracle_qe_variance_step(v[a], uv[a], ka, &br, &mg, NULL);
+            x[a] += ka[4] + ka[5] * v[a] + ka[6] * vn + sqrt(ka[7] * v[a] + ka[8] * vn) * z;
+            v[a] = vn;
+          }
+        }
+        for (int a = 0; a < A; ++a) x_out[i * A + a] = x[a];
+      }
+    }
+    free(v);
+    free(x);
+    free(uv);
+    free(eps);
+  }
+  free(k);
+  return rc;
+}
+
+/*
  * E[exp(x(t+dt) - x(t) - r dt) | v(t) = v] of one step under the library's
  * scheme: the normal Z_X integrated exactly (E exp(s Z) = exp(s^2/2)) and the
  * variance uniform summed over its whole lattice u = (j + 1/2) 2^-23, the set

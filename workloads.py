@@ -129,6 +129,20 @@ def paper_datapoint_bytes(size: str) -> int:
     return 2 * 4 * paper_elements(size)
 
 
+def paper_book(size: str, seed: int = 7):
+    """The paper's problem size as a book: A independent assets (options analysed),
+    each with T time steps and P paths; models drawn like the book's parameters
+    with T fixed to T/252 years, strikes at the money.  Elements = A T P."""
+    A, T, P = PAPER_SIZES[size]
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(A):
+        model = _draw_params(rng)
+        model["T"] = T / 252.0
+        out.append(dict(model=model, K=100.0, is_put=False, steps=T, paths=P))
+    return out
+
+
 def random_models(n: int, seed: int):
     """n model dicts drawn like the book's parameters (for parity sweeps)."""
     rng = np.random.default_rng(seed)
