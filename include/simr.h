@@ -222,6 +222,28 @@ SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_
                                 float* x_T, float* grad, void* stream);
 
 /*
+ * Basket option on n_assets correlated Heston assets: e^{-rT} mean of
+ * max(+-(B_T - K), 0), B_T = sum_k weights[k] S_T,k, per strike.  Each asset runs
+ * the QE scheme of simr_price with its own model and the Philox counters of
+ * option index k (so with the identity correlation asset k's path is simr_price's
+ * path of option k), except that its log-spot normal is
+ * z_k = sum_{j <= k} Lc[k][j] eps_j, eps_j = Phi^-1(U_X) of asset j, Lc the lower
+ * Cholesky factor of corr; the variance drivers stay independent.  The paper's A
+ * assets (Sec. 5, Table 1) are the independent case.
+ *   assets[n_assets]        in  host; all share r and T; n_assets in [1, 16]
+ *   corr[n_assets^2]        in  host, row-major correlation of the spot drivers:
+ *                                symmetric, unit diagonal, positive definite
+ *   weights[n_assets]       in  host, finite (negative allowed: spreads, exchange)
+ *   strikes[n_strikes]      in  host or device, finite and >= 0; n_strikes <= 1024
+ *   price, stderr_out (nullable)  out  [n_strikes], host or device
+ * Plain QE only (SIMR_EUNSUPPORTED under SIMR_SCHEME_QEM).
+ */
+SIMR_API int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
+                               const double* weights, const double* strikes, int n_strikes, int is_put,
+                               uint32_t steps, uint64_t paths, uint64_t seed, double* price, double* stderr_out,
+                               void* stream);
+
+/*
  * Select the log-spot scheme of the context's later path simulations.
  *   SIMR_SCHEME_QE   Andersen (2008) QE, psi_c = 1.5, gamma1 = gamma2 = 1/2 (the
  *                    stages VariancePathQE / LogPricePathQE of the paper, Sec. 4-5).

@@ -82,7 +82,7 @@ def lib():
             L.oracle_path_grad_forward.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_adjoint.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
             L.oracle_states.argtypes = [H, u32, u32, u64, u32, u64, i64, dp, dp]
-            L.oracle_basket_terminal.argtypes = [H, c_int, dp, u32, u64, u64, i64, dp]
+            L.oracle_basket_terminal.argtypes = [H, c_int, dp, u32, u64, u64, i64, dp, dp]
             L.oracle_set_scheme.argtypes = [c_int]
             L.oracle_set_scheme.restype = None
             L.oracle_step_exp_mean.argtypes = [H, u32, ctypes.c_double]
@@ -221,17 +221,19 @@ def states(model, steps: int, every: int, seed: int, path_begin: int, n_paths: i
     return S, v
 
 
-def basket_terminal(models, corr, steps: int, seed: int, path_begin: int, n_paths: int) -> np.ndarray:
+def basket_terminal(models, corr, steps: int, seed: int, path_begin: int, n_paths: int, with_margin: bool = False):
     """x[n_paths, A] = ln(S_T/S0) of A assets whose log-spot normals have correlation
-    `corr` (via numpy's Cholesky factor); asset k uses the counters of option index k."""
+    `corr` (via numpy's Cholesky factor); asset k uses the counters of option index k.
+    With with_margin, also each path's smallest branch-decision margin."""
     A = len(models)
     arr = (Heston * A)(*[_model(m) for m in models])
     Lc = np.ascontiguousarray(np.linalg.cholesky(np.asarray(corr, dtype=np.float64)))
     x = np.empty((n_paths, A))
-    rc = lib().oracle_basket_terminal(arr, A, _dp(Lc), steps, seed, path_begin, n_paths, _dp(x))
+    mg = np.empty(n_paths)
+    rc = lib().oracle_basket_terminal(arr, A, _dp(Lc), steps, seed, path_begin, n_paths, _dp(x), _dp(mg))
     if rc != 0:
         raise ValueError(f"oracle_basket_terminal failed ({rc})")
-    return x
+    return (x, mg) if with_margin else x
 
 
 def basket_price(models, corr, weights, strikes, is_put: bool, steps: int, paths: int, seed: int):

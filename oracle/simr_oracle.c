@@ -418,10 +418,11 @@ int oracle_states(const oracle_heston* m, uint32_t steps, uint32_t every, uint64
  * where eps_j = Phi^-1(U_X) of asset j and Lc is the lower Cholesky factor of
  * the correlation of the spot drivers (row-major A x A; computed by the caller).
  * The variance drivers stay independent across assets.  x[i * A + k] =
- * ln(S_T / S0) of asset k on path path_begin + i.
+ * ln(S_T / S0) of asset k on path path_begin + i; margin[i] (may be NULL) the
+ * smallest branch-decision margin over the path's assets and steps.
  */
 int oracle_basket_terminal(const oracle_heston* models, int n_assets, const double* Lc, uint32_t steps,
-                           uint64_t seed, uint64_t path_begin, int64_t n_paths, double* x_out) {
+                           uint64_t seed, uint64_t path_begin, int64_t n_paths, double* x_out, double* margin) {
   if (steps == 0 || n_assets < 1 || n_assets > 64 || n_paths < 0) return -1;
   const int A = n_assets;
   double* k = (double*)malloc(sizeof(double) * 10 * (size_t)A);
@@ -441,6 +442,7 @@ int oracle_basket_terminal(const oracle_heston* models, int n_assets, const doub
 #pragma omp for schedule(static)
       for (int64_t i = 0; i < n_paths; ++i) {
         const uint64_t path = path_begin + (uint64_t)i;
+        double min_mg = INFINITY;
         for (int a = 0; a < A; ++a) {
           v[a] = models[a].v0;
           x[a] = 0.0;
@@ -458,11 +460,13 @@ int oracle_basket_terminal(const oracle_heston* models, int n_assets, const doub
             int br;
             double mg;
             const double vn = oracle_qe_variance_step(v[a], uv[a], ka, &br, &mg, NULL);
+            if (mg < min_mg) min_mg = mg;
             x[a] += ka[4] + ka[5] * v[a] + ka[6] * vn + sqrt(ka[7] * v[a] + ka[8] * vn) * z;
             v[a] = vn;
           }
         }
         for (int a = 0; a < A; ++a) x_out[i * A + a] = x[a];
+        if (margin) margin[i] = min_mg;
       }
     }
     free(v);

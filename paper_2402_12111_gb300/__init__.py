@@ -11,6 +11,7 @@ libsimr.so's sm_103a kernels behind the C ABI of include/simr.h):
   paths_adjoint(model, steps, ...)      -> (x_T, dx_T/dparams)  simr_paths_adjoint
   batch(options, seed, adjoint, graph)  -> (price, se, grad)    simr_batch_submit (heterogeneous book)
   lsm_price(model, K, ...)              -> (price, se, beta, stop) simr_lsm_price (Longstaff-Schwartz)
+  basket_price(models, corr, weights, K) -> (price, se)          simr_basket_price (correlated assets)
   set_scheme("qe" | "qem") / scheme(...)                        simr_set_scheme (QE-M martingale correction)
   path_sums / finalize_sums                                     sharded runs
   sharded.price_greeks(...)             multi-rank path sharding (torch.distributed)
@@ -19,11 +20,11 @@ libsimr.so's sm_103a kernels behind the C ABI of include/simr.h):
 Tensors on a CUDA device give an asynchronous call on the current stream; CPU
 tensors or sequences give a synchronous call with host buffers.
 """
-from .api import (ADJOINT_COLUMNS, HestonAdjoint, batch, finalize_sums, greeks_adjoint, greeks_fd,  # noqa: F401
+from .api import (ADJOINT_COLUMNS, HestonAdjoint, basket_price, batch, finalize_sums, greeks_adjoint, greeks_fd,  # noqa: F401
                   heston_price, lsm_price, path_sums, paths_adjoint, paths_terminal, price, scheme, set_scheme,
                   sync)
 from ._simr import (G_ALL, G_CORR, G_DELTA, G_GAMMA, G_KAPPA, G_LRVAR, G_RHO, G_THETA, G_VEGA,  # noqa: F401
                     G_VOLVOL, GREEK_BITS, Heston, SimrError, greek_mask, load)
 
-__all__ = ["batch", "lsm_price", "set_scheme", "scheme", "price", "greeks_fd", "greeks_adjoint", "heston_price", "HestonAdjoint", "ADJOINT_COLUMNS", "paths_terminal", "paths_adjoint", "path_sums", "finalize_sums", "sync", "Heston", "SimrError",
+__all__ = ["basket_price", "batch", "lsm_price", "set_scheme", "scheme", "price", "greeks_fd", "greeks_adjoint", "heston_price", "HestonAdjoint", "ADJOINT_COLUMNS", "paths_terminal", "paths_adjoint", "path_sums", "finalize_sums", "sync", "Heston", "SimrError",
            "greek_mask", "load", "GREEK_BITS"]

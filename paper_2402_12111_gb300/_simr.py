@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         L.simr_batch_submit.argtypes = [vp, ctypes.POINTER(Option), c_int, u64, u32, dp, dp, dp, vp]
         L.simr_lsm_price.argtypes = [vp, H, ctypes.c_double, c_int, u32, u32, u64, u64, u32, dp, dp, dp, dp, vp]
         L.simr_set_scheme.argtypes = [vp, c_int]
+        L.simr_basket_price.argtypes = [vp, H, c_int, dp, dp, dp, c_int, c_int, u32, u64, u64, dp, dp, vp]
         L.simr_sync.argtypes = [vp, vp]
         L.simr_price_noalloc.argtypes = [H, dp, c_int, c_int, u32, u64, u64, u32, dp, dp, vp]
         _lib = L

@@ -227,6 +227,25 @@ def finalize_sums(model, strikes, is_put: bool, steps: int, paths: int, sums: to
     return p, se, g
 
 
+def basket_price(models, corr, weights, strikes, is_put: bool = False, steps: int = 64, paths: int = 65536,
+                 seed: int = 1, device=None, stream=None):
+    """simr_basket_price: (price[n_K], stderr[n_K]) of the basket option on
+    sum_k w_k S_T,k of correlated assets (`corr`: correlation of the spot drivers)."""
+    n = len(models)
+    arr = (S.Heston * n)(*[S.as_heston(m) for m in models])
+    C = np.ascontiguousarray(np.asarray(corr, dtype=np.float64).reshape(n, n))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(n))
+    K = _as_f64(strikes)
+    p = torch.empty(K.numel(), dtype=torch.float64, device=K.device)
+    se = torch.empty_like(p)
+    L = S.load()
+    ctx = S.context(_device_index(K, device))
+    S.check(L.simr_basket_price(ctx, arr, n, C.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                _ptr(K), K.numel(), int(bool(is_put)), int(steps), int(paths), int(seed), _ptr(p),
+                                _ptr(se), _stream(K, stream)))
+    return p, se
+
+
 def set_scheme(name: str, device: int = 0):
     """simr_set_scheme: "qe" (Andersen's QE) or "qem" (QE with the martingale correction)
     for the device context's later path simulations."""

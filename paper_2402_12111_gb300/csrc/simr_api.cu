@@ -1072,6 +1072,99 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
   return SIMR_OK;
 }
 
+int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
+                      const double* weights, const double* strikes, int n_strikes, int is_put, uint32_t steps,
+                      uint64_t paths, uint64_t seed, double* price, double* stderr_out, void* stream) {
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (!assets || !corr || !weights) return fail(SIMR_EINVAL, "assets, corr and weights must be non-NULL");
+  if (n_assets < 1 || n_assets > kMaxAssets) return fail(SIMR_EINVAL, "n_assets must lie in [1, %d]", kMaxAssets);
+  if (is_device_ptr(assets) || is_device_ptr(corr) || is_device_ptr(weights))
+    return fail(SIMR_EINVAL, "assets, corr and weights must be host arrays");
+  if (!strikes) return fail(SIMR_EINVAL, "strikes is NULL");
+  if (n_strikes < 1 || n_strikes > 1024) return fail(SIMR_EINVAL, "n_strikes must lie in [1, 1024]");
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
+  if (paths < 1 || paths > (1ull << 40)) return fail(SIMR_EINVAL, "paths must lie in [1, 2^40]");
+  if (!price) return fail(SIMR_EINVAL, "price is NULL");
+  int rc = require_plain_qe(ctx, "the basket kernel");
+  if (rc) return rc;
+  for (int k = 0; k < n_assets; ++k) {
+    if ((rc = check_model(&assets[k]))) {
+      char msg[sizeof(g_err)];
+      std::strncpy(msg, g_err, sizeof(msg) - 1);
+      msg[sizeof(msg) - 1] = 0;
+      return fail(SIMR_EINVAL, "asset %d: %s", k, msg);
+    }
+    if (assets[k].r != assets[0].r || assets[k].T != assets[0].T)
+      return fail(SIMR_EINVAL, "all assets of a basket share r and T");
+    if (!std::isfinite(weights[k])) return fail(SIMR_EINVAL, "weight %d is not finite", k);
+  }
+  // lower Cholesky factor of the correlation (FP64), validated on the way
+  const int A = n_assets;
+  std::vector<double> Lc((size_t)A * A, 0.0);
+  for (int i = 0; i < A; ++i) {
+    for (int j = 0; j < A; ++j) {
+      const double c = corr[i * A + j];
+      if (!std::isfinite(c) || c < -1.0 || c > 1.0 || c != corr[j * A + i])
+        return fail(SIMR_EINVAL, "corr must be a symmetric matrix of values in [-1, 1]");
+    }
+    if (corr[i * A + i] != 1.0) return fail(SIMR_EINVAL, "corr must have a unit diagonal");
+  }
+  for (int i = 0; i < A; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = corr[i * A + j];
+      for (int k = 0; k < j; ++k) s -= Lc[i * A + k] * Lc[j * A + k];
+      if (i == j) {
+        if (!(s > 1e-12)) return fail(SIMR_EINVAL, "corr is not positive definite");
+        Lc[i * A + i] = std::sqrt(s);
+      } else {
+        Lc[i * A + j] = s / Lc[j * A + j];
+      }
+    }
+  }
+  if ((rc = with_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  BasketLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  philox_round_keys(seed, L.rk);
+  for (int k = 0; k < A; ++k) {
+    L.sc[k] = base_const(assets[k], steps);
+    L.S0w[k] = (float)(assets[k].S0 * weights[k]);
+    for (int j = 0; j <= k; ++j) L.Lc[k * (k + 1) / 2 + j] = (float)Lc[k * A + j];
+  }
+  L.n_assets = A;
+  L.n_strikes = n_strikes;
+  L.nk_pad = n_strikes == 1 ? 1 : ((n_strikes + 31) / 32) * 32;
+  L.is_put = is_put ? 1 : 0;
+  L.steps = steps;
+  L.paths = paths;
+  L.disc = std::exp(-assets[0].r * assets[0].T);
+  L.paths_total = (double)paths;
+  const double* ks = strikes;
+  if (!is_device_ptr(strikes)) {
+    for (int k = 0; k < n_strikes; ++k)
+      if (!(strikes[k] >= 0.0) || !std::isfinite(strikes[k]))
+        return fail(SIMR_EINVAL, "strike %d must be finite and >= 0", k);
+    if ((rc = ensure(&ctx->dev_strikes, &ctx->strikes_cap, (size_t)n_strikes, "strike staging"))) return rc;
+    cudaError_t e = cudaMemcpyAsync(ctx->dev_strikes, strikes, n_strikes * sizeof(double), cudaMemcpyHostToDevice,
+                                    st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying strikes");
+    ks = ctx->dev_strikes;
+  }
+  OutStage o;
+  o.user[0] = price;
+  o.n[0] = n_strikes;
+  o.user[1] = stderr_out;
+  o.n[1] = n_strikes;
+  if ((rc = stage_outputs(ctx, &o))) return rc;
+  if ((rc = ensure(&ctx->partials, &ctx->partial_doubles, basket_partial_doubles(L, ctx->num_sms),
+                   "reduction scratch")))
+    return rc;
+  BasketOutputs out{o.dev[0], o.dev[1], ctx->status};
+  cudaError_t e = launch_basket(L, ks, out, ctx->partials, ctx->partial_doubles, ctx->ticket, ctx->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the basket kernel");
+  return finish_outputs(ctx, o, st);
+}
+
 int simr_set_scheme(simr_ctx* ctx, int scheme) {
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   if (scheme != SIMR_SCHEME_QE && scheme != SIMR_SCHEME_QEM) return fail(SIMR_EINVAL, "unknown scheme %d", scheme);

@@ -1,0 +1,206 @@
+// simr_basket.cu -- basket options on correlated Heston assets, sm_103a.
+//
+// The paper's A assets (Sec. 5, Table 1) each run the VariancePathQE /
+// LogPricePathQE / AssetPathExponential stages; here A <= 16 assets of one
+// basket are simulated together, one path per thread: asset k uses its own
+// model and the Philox counters of option index k (so with no correlation it is
+// exactly simr_price's path of option k), except that its log-spot normal is
+// z_k = sum_{j <= k} Lc[k][j] eps_j, eps_j the Phi^-1(U_X) of asset j, Lc the
+// lower Cholesky factor of the correlation of the spot drivers; the variance
+// drivers stay independent.  Payoff on B_T = sum_k w_k S_T,k per strike, and
+// the reduction over paths of the price kernel (FP32 over a warp, FP64 on).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "simr_device.cuh"
+#include "simr_internal.h"
+#include "simr_reduce.cuh"
+
+namespace simr {
+namespace {
+
+constexpr int kBasketTpb = 256;
+
+template <int NA, int TILE>
+__global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_constant__ BasketLaunch L,
+                                                                   const double* __restrict__ strikes,
+                                                                   BasketOutputs out, double* __restrict__ partials,
+                                                                   unsigned int* __restrict__ ticket) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warps = blockDim.x / kWarp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = 2 * L.nk_pad;
+  double* acc = reinterpret_cast<double*>(smem_raw);
+  float* ks = reinterpret_cast<float*>(acc + (size_t)warps * row);
+  int* s_last = reinterpret_cast<int*>(ks + L.nk_pad);
+  for (int i = threadIdx.x; i < warps * row; i += blockDim.x) acc[i] = 0.0;
+  for (int j = threadIdx.x; j < L.nk_pad; j += blockDim.x) {
+    float K = 0.0f;
+    if (j < L.n_strikes) {
+      const double Kd = strikes[j];
+      if (!(Kd >= 0.0) || !isfinite(Kd)) atomicOr(out.status, 1);
+      K = (float)Kd;
+    }
+    ks[j] = K;
+  }
+  __syncthreads();
+
+  const bool put = L.is_put != 0;
+  const int na = L.n_assets;
+  double* my_acc = acc + (size_t)warp * row;
+  const uint64_t batches = (L.paths + kWarp - 1) / kWarp;
+  const uint64_t total_warps = (uint64_t)gridDim.x * warps;
+  for (uint64_t bt = (uint64_t)blockIdx.x * warps + warp; bt < batches; bt += total_warps) {
+    const uint64_t path = bt * kWarp + lane;
+    const bool active = path < L.paths;
+    const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+    float v[NA], x[NA], comp[NA], eps[NA];
+    uint32_t wz[NA], ww[NA];  // the odd step's words of each asset
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      v[k] = L.sc[k].v0;
+      x[k] = 0.0f;
+      comp[k] = 0.0f;
+    }
+    for (uint32_t p = 0; 2 * p < L.steps; ++p) {
+      // even step 2p: draw each asset's words, correlate, step in asset order
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        if (k >= na) break;
+        const uint4 w = philox4x32_10(p, plo, phi, (uint32_t)k, L.rk);
+        wz[k] = w.z;
+        ww[k] = w.w;
+        eps[k] = norminv_centered(centered_uniform(w.y));
+        float z = 0.0f;
+#pragma unroll
+        for (int j = 0; j <= k; ++j) z = fmaf(L.Lc[k * (k + 1) / 2 + j], eps[j], z);
+        const float xv = centered_uniform(w.x);
+        step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v[k], x[k], comp[k]);
+      }
+      if (2 * p + 1 < L.steps) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          if (k >= na) break;
+          eps[k] = norminv_centered(centered_uniform(ww[k]));
+          float z = 0.0f;
+#pragma unroll
+          for (int j = 0; j <= k; ++j) z = fmaf(L.Lc[k * (k + 1) / 2 + j], eps[j], z);
+          const float xv = centered_uniform(wz[k]);
+          step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v[k], x[k], comp[k]);
+        }
+      }
+    }
+    float B = 0.0f;  // sum_k w_k S0_k e^{x_k}
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+      if (k < na) B += terminal_spot(L.S0w[k], x[k], comp[k]);
+
+    if (TILE == 1) {
+      const float f = active ? (put ? fmaxf(ks[0] - B, 0.0f) : fmaxf(B - ks[0], 0.0f)) : 0.0f;
+      const float t0 = warp_sum(f), t1 = warp_sum(f * f);
+      if (lane == 0) {
+        my_acc[0] += (double)t0;
+        my_acc[1] += (double)t1;
+      }
+    } else {
+      for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
+        float vf[32], vq[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const float K = ks[t0 + jj];
+          const float f = active ? (put ? fmaxf(K - B, 0.0f) : fmaxf(B - K, 0.0f)) : 0.0f;
+          vf[jj] = f;
+          vq[jj] = f * f;
+        }
+        butterfly32(vf, lane);
+        butterfly32(vq, lane);
+        my_acc[t0 + lane] += (double)vf[0];
+        my_acc[L.nk_pad + t0 + lane] += (double)vq[0];
+      }
+    }
+  }
+  __syncthreads();
+
+  double* my_row = partials + (size_t)blockIdx.x * row;
+  for (int i = threadIdx.x; i < row; i += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < warps; ++w) s += acc[(size_t)w * row + i];
+    my_row[i] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < row; i += blockDim.x) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + (size_t)b * row + i);
+    acc[i] = s;
+  }
+  __syncthreads();
+  const double inv_n = 1.0 / L.paths_total;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (int k = threadIdx.x; k < L.n_strikes; k += blockDim.x) {
+    const double K = strikes[k];
+    const bool bad = !(K >= 0.0) || !isfinite(K);
+    const double mean = acc[k] * inv_n;
+    out.price[k] = bad ? nan : L.disc * mean;
+    if (out.stderr_) {
+      const double n = L.paths_total;
+      const double var = n > 1.0 ? (acc[L.nk_pad + k] * inv_n - mean * mean) / (n - 1.0) : 0.0;
+      out.stderr_[k] = bad ? nan : L.disc * sqrt(var > 0.0 ? var : 0.0);
+    }
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+template <int NA, int TILE>
+cudaError_t launch_basket_t(const BasketLaunch& L, const double* strikes, const BasketOutputs& out,
+                            double* partials, size_t partial_doubles, unsigned int* ticket, int num_sms,
+                            cudaStream_t stream) {
+  const int warps = kBasketTpb / kWarp;
+  const size_t row = 2 * (size_t)L.nk_pad;
+  const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(float) + 16;
+  auto kern = heston_basket_kernel<NA, TILE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBasketTpb, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t batches = (L.paths + kWarp - 1) / kWarp;
+  uint64_t grid = (uint64_t)num_sms * per_sm;
+  const uint64_t need = (batches + warps - 1) / warps;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  if ((size_t)grid * row > partial_doubles) return cudaErrorMemoryAllocation;
+  kern<<<(unsigned)grid, kBasketTpb, smem, stream>>>(L, strikes, out, partials, ticket);
+  return cudaGetLastError();
+}
+
+template <int NA>
+cudaError_t launch_basket_na(const BasketLaunch& L, const double* strikes, const BasketOutputs& out,
+                             double* partials, size_t partial_doubles, unsigned int* ticket, int num_sms,
+                             cudaStream_t stream) {
+  return L.nk_pad == 1
+             ? launch_basket_t<NA, 1>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream)
+             : launch_basket_t<NA, 32>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+}
+
+}  // namespace
+
+size_t basket_partial_doubles(const BasketLaunch& L, int num_sms) {
+  return (size_t)num_sms * 8 * 2 * (size_t)L.nk_pad;  // at most 8 resident blocks per SM
+}
+
+cudaError_t launch_basket(const BasketLaunch& L, const double* strikes, const BasketOutputs& out, double* partials,
+                          size_t partial_doubles, unsigned int* ticket, int num_sms, cudaStream_t stream) {
+  if (L.n_assets <= 2) return launch_basket_na<2>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+  if (L.n_assets <= 4) return launch_basket_na<4>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+  if (L.n_assets <= 8) return launch_basket_na<8>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+  return launch_basket_na<kMaxAssets>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+}
+
+}  // namespace simr

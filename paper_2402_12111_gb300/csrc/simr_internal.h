@@ -186,6 +186,30 @@ struct LsmBuffers {
 cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream);
 size_t lsm_partial_doubles(int num_sms);
 
+// Basket options on correlated assets (simr_basket.cu).
+constexpr int kMaxAssets = 16;
+
+struct BasketLaunch {
+  uint32_t rk[10][2];
+  ScenConst sc[kMaxAssets];                          // per asset (v0 included)
+  float Lc[kMaxAssets * (kMaxAssets + 1) / 2];       // lower Cholesky factor, rows packed
+  float S0w[kMaxAssets];                             // S0_k w_k
+  int32_t n_assets, n_strikes, nk_pad, is_put;
+  uint32_t steps, pad;
+  uint64_t paths;
+  double disc, paths_total;
+};
+
+struct BasketOutputs {
+  double* price;    // [n_strikes]
+  double* stderr_;  // [n_strikes] or null
+  int* status;      // bit 0: a device strike was not finite and >= 0
+};
+
+cudaError_t launch_basket(const BasketLaunch& L, const double* strikes, const BasketOutputs& out, double* partials,
+                          size_t partial_doubles, unsigned int* ticket, int num_sms, cudaStream_t stream);
+size_t basket_partial_doubles(const BasketLaunch& L, int num_sms);
+
 // Validation and launch building of the C ABI (simr_api.cu), for the other
 // entry points of the library.  They set the thread-local error message.
 int internal_fail(int code, const char* message);
