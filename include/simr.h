@@ -201,9 +201,11 @@ SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const 
  *   flags          in   SIMR_BATCH_* (0 = prices only)
  *   price[n_opts], stderr_out[n_opts] (nullable)   out, caller's order
  *   grad[n_opts * 7]   out (SIMR_BATCH_ADJOINT): d/d{S0, v0, kappa, theta, sigma, rho, r}
- * chunk is chosen by timing three candidates on the first submission of each
- * book shape (a book's size class, cached in the context): that first call
- * prices the book three more times.  With SIMR_BATCH_GRAPH the upload-free part
+ * chunk is chosen by timing four candidates on the first submission of each
+ * book shape (a book's size class, cached in the context): 1024/4096/16384
+ * paths (256/1024/4096 with the adjoint) and the size that gives about two
+ * items per resident warp; that first call prices the book four more times.
+ * Without tuning the chunk is the smaller of 4096 (1024) and that size.  With SIMR_BATCH_GRAPH the upload-free part
  * of the call (queue reset, batch kernel, reduction) is captured once per
  * (book, seed, flags, output buffers) and replayed afterwards.
  */

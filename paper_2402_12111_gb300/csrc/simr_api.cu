@@ -951,19 +951,27 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   for (const BatchOption& b : bo) total += (double)b.steps * (double)b.paths;
   const uint64_t tkey = (adjoint ? 1ull : 0ull) | ((uint64_t)std::max(0.0, std::log2(total + 1.0)) << 1) |
                         ((uint64_t)std::log2((double)n_opts) << 16);
-  uint32_t chunk = adjoint ? 1024 : 4096;
+  // a chunk that fills the GPU: about two items per resident warp (the kernel
+  // runs ~40 warps per SM), a multiple of the paths a warp takes per pass
+  double total_paths = 0.0;
+  for (const BatchOption& b : bo) total_paths += (double)b.paths;
+  const uint32_t quantum = adjoint ? 32u : 64u;
+  const double fill = total_paths / (2.0 * 40.0 * (double)ctx->num_sms);
+  const uint32_t balanced =
+      (uint32_t)std::min(16384.0, std::max((double)quantum, std::ceil(fill / quantum) * quantum));
+  uint32_t chunk = std::min(adjoint ? 1024u : 4096u, balanced);
   bool tuned = false;
   for (const auto& t : ctx->tune)
     if (t.key == tkey) chunk = t.chunk, tuned = true;
   const char* env = std::getenv("SIMR_AUTOTUNE");
   const bool autotune = !(flags & SIMR_BATCH_NO_AUTOTUNE) && !(env && env[0] == '0');
   if (!tuned && autotune) {
-    const uint32_t cands[3] = {adjoint ? 256u : 1024u, adjoint ? 1024u : 4096u, adjoint ? 4096u : 16384u};
+    const uint32_t cands[4] = {adjoint ? 256u : 1024u, adjoint ? 1024u : 4096u, adjoint ? 4096u : 16384u, balanced};
     float best = 0.0f;
     cudaEvent_t a = nullptr, b = nullptr;
     e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
       uint32_t n_items = 0;
       if ((rc = upload_batch(ctx, bo, order, cands[ci], st, &n_items))) break;
       B.n_items = n_items;

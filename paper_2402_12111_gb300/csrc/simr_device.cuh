@@ -234,33 +234,49 @@ __device__ __forceinline__ float neg_log1m_tail(float u) {
   return -u - log1pf(-u);
 }
 
-// lam = ln M - A m of the QE-M correction for the QE step with moments (m, s2);
-// false where M does not exist (quadratic branch: 2 A a >= 1; exponential
-// branch: A >= beta).  Quadratic: lam = 2 (A a)^2 b^2 / (1 - 2 A a) + g(2 A a)/2;
-// exponential: lam = ln(1 + (1 - p) w / (1 - w)) - (1 - p) w with w = A / beta.
-// The branch quantities repeat qe_from_moments' own expressions.
-__device__ __forceinline__ bool qem_lambda(float m, float s2, float A, float& lam) {
+// The QE variance step of qe_from_moments (the same expressions, so the same
+// v_next and dl) together with lam = ln M - A m of the QE-M correction; false
+// where M does not exist (quadratic branch: 2 A a >= 1; exponential branch:
+// A >= beta).  Quadratic: lam = 2 (A a)^2 b^2 / (1 - 2 A a) + g(2 A a)/2;
+// exponential: lam = ln(1 + (1 - p) w / (1 - w)) - (1 - p) w with w = A / beta,
+// 1 - p = 2 m^2 / (m^2 + s^2), beta = 2 m / (m^2 + s^2).
+__device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, float zv, float A, float& v_next,
+                                                 float& dl, float& lam) {
   const float m2 = m * m;
   lam = 0.0f;
   if (s2 <= 1.5f * m2 && m2 > 0.0f) {
     const float t = 2.0f * m2 * rcp_approx(s2);
     const float root = sqrt_approx(fmaf(t, t, -t));
     const float b2 = (t - 1.0f) + root;
+    const float b = sqrt_approx(b2);
     const float a = m * rcp_approx(t + root);
+    const float bz = b + zv;
+    v_next = a * bz * bz;
+    dl = a * fmaf(zv, zv + 2.0f * b, -1.0f);
     const float Aa = A * a;
     const float u = 2.0f * Aa;
     if (!(u < 1.0f)) return false;
-    lam = fmaf(0.5f, neg_log1m_tail(u), 2.0f * Aa * Aa * b2 / (1.0f - u));
+    lam = fmaf(0.5f, neg_log1m_tail(u), 2.0f * Aa * Aa * b2 * rcp_approx(1.0f - u));
     return true;
   }
   if (m > 0.0f) {
     const float ms = m2 + s2;
-    const float onep = 2.0f * m2 / ms;  // 1 - p
-    const float w = A * ms / (2.0f * m);  // A / beta, beta = (1 - p)/m = 2 m / ms
+    const float W = omu * ms;
+    if (W >= 2.0f * m2) {
+      v_next = 0.0f;
+    } else {
+      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
+      v_next = 0.5f * ms * rcp_approx(m) * L;
+    }
+    dl = v_next - m;
+    const float onep = 2.0f * m2 * rcp_approx(ms);  // 1 - p
+    const float w = 0.5f * A * ms * rcp_approx(m);  // A / beta
     if (!(w < 1.0f)) return false;
-    lam = log1pf(onep * w / (1.0f - w)) - onep * w;
+    lam = log1pf(onep * w * rcp_approx(1.0f - w)) - onep * w;
     return true;
   }
+  v_next = 0.0f;
+  dl = 0.0f;
   return true;  // m = 0: v' = 0, M = 1
 }
 
@@ -271,10 +287,10 @@ __device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, 
   float vn, dl, lam;
   const float m = fmaf(v, c.E, c.thE);
   const float s2 = fmaf(v, c.c1, c.c2);
-  qe_from_moments(m, s2, omu, zv, vn, dl);
+  const bool ok = qem_from_moments(m, s2, omu, zv, q.A, vn, dl, lam);
   const float s = v + vn;
   float inc;
-  if (qem_lambda(m, s2, q.A, lam)) {
+  if (ok) {
     inc = fmaf(-q.qa, v + m, q.rdt) - lam;
     inc = fmaf(q.K2, dl, inc);
   } else {
