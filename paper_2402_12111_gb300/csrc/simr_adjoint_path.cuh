@@ -109,13 +109,14 @@ __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float 
   return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
 }
 
-// The stored data of one step (recompute pass): state, branch draw, Z_X.
-__device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, uint32_t wx, float* bv, float* bd_,
+// The stored data of one step (recompute pass): state, branch draw, Z_X, from
+// the step's centred variance uniform and its two normals.
+__device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, float zv, float zx, float* bv, float* bd_,
                                           float* bz, float& v) {
-  const float omu = 0.5f * (1.0f - xv_v), zv = norminv_centered(xv_v);
+  const float omu = 0.5f * (1.0f - xv_v);
   *bv = v;
   *bd_ = branch_draw(c, v, omu, zv);
-  *bz = norminv_centered(centered_uniform(wx));
+  *bz = zx;
   v = qe_only(c, v, omu, zv);
 }
 
@@ -172,11 +173,11 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
 #pragma unroll
       for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const float xa = centered_uniform(w[j].x);
-        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xa), norminv_centered(xa));
-        const float xb = centered_uniform(w[j].z);
-        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xb), norminv_centered(xb));
+      for (int j = 0; j < PPT; ++j) {  // the pair's two variance normals together
+        const float xa = centered_uniform(w[j].x), xb = centered_uniform(w[j].z);
+        const float2 zv = norminv_centered2(make_float2(xa, xb));
+        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xa), zv.x);
+        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xb), zv.y);
       }
     }
   }
@@ -210,14 +211,13 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
 #pragma unroll
         for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
 #pragma unroll
-        for (int j = 0; j < PPT; ++j)
-          keep_step(c, centered_uniform(w[j].x), w[j].y, &SIMR_SG(0, i, j), &SIMR_SG(1, i, j), &SIMR_SG(2, i, j),
-                    vv[j]);
-        if (2 * p + 1 < n1) {
-#pragma unroll
-          for (int j = 0; j < PPT; ++j)
-            keep_step(c, centered_uniform(w[j].z), w[j].w, &SIMR_SG(0, i + 1, j), &SIMR_SG(1, i + 1, j),
-                      &SIMR_SG(2, i + 1, j), vv[j]);
+        for (int j = 0; j < PPT; ++j) {  // the pair's normals two at a time
+          const float xa = centered_uniform(w[j].x), xb = centered_uniform(w[j].z);
+          const float2 zv = norminv_centered2(make_float2(xa, xb));
+          const float2 zx = norminv_centered2(make_float2(centered_uniform(w[j].y), centered_uniform(w[j].w)));
+          keep_step(c, xa, zv.x, zx.x, &SIMR_SG(0, i, j), &SIMR_SG(1, i, j), &SIMR_SG(2, i, j), vv[j]);
+          if (2 * p + 1 < n1)
+            keep_step(c, xb, zv.y, zx.y, &SIMR_SG(0, i + 1, j), &SIMR_SG(1, i + 1, j), &SIMR_SG(2, i + 1, j), vv[j]);
         }
       }
       float vnext[PPT];

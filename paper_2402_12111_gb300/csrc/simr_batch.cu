@@ -61,12 +61,13 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
       } else {
         terms[0] = terms[1] = 0.0f;
+        float2 x2, comp2;
+        simulate_two(c, steps, oidx, B.rk, I.path_begin + b + lane, I.path_begin + b + 32 + lane, x2, comp2);
+        const float xs[2] = {x2.x, x2.y}, cs[2] = {comp2.x, comp2.y};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const bool active = b + 32 * j + lane < I.count;
-          float x, comp;
-          simulate_one(c, steps, oidx, B.rk, I.path_begin + b + 32 * j + lane, x, comp);
-          const float S = terminal_spot(S0, x, comp);
+          const float S = terminal_spot(S0, xs[j], cs[j]);
           const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
           terms[0] += active ? f : 0.0f;
           terms[1] += active ? f * f : 0.0f;

@@ -78,6 +78,51 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return r;
 }
 
+// ------------------------------------------------- packed FP32 (f32x2) ----
+// sm_100-family paired FP32 instructions: one instruction computes two lanes,
+// each rounded exactly as the scalar __fmaf_rn / __fmul_rn / __fadd_rn /
+// __fsub_rn (bitwise, checked on the device).  The path kernels are bound by
+// instruction issue, not by the FMA pipe, so pairing two scenarios (or two
+// paths) that run the same arithmetic halves the issue slots of that part.
+// Functions with a "2" suffix below repeat their scalar namesake's operation
+// sequence lane for lane, so a lane's result is the scalar function's, bit for bit.
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 p_bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 p_rcp(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+__device__ __forceinline__ float2 p_sqrt(float2 a) { return make_float2(sqrt_approx(a.x), sqrt_approx(a.y)); }
+__device__ __forceinline__ float2 p_lg2(float2 a) { return make_float2(lg2_approx(a.x), lg2_approx(a.y)); }
+
 // ------------------------------------------------------------- Philox ----
 // Philox4x32-10 (Salmon et al., SC'11).  rk[i] = key + i * (0x9E3779B9, 0xBB67AE85)
 // is precomputed on the host (the key is uniform over the launch), so each round
@@ -113,33 +158,55 @@ __device__ __forceinline__ float centered_uniform(uint32_t w) {
 // multiplied by sqrt(2) (in double, rounded once), so no final scaling is needed.
 // 1 - x^2 is formed by one FMA (exact product, one rounding).
 #define SIMR_S2(c) ((float)((c) * 1.4142135623730951))
+// the tail branch (w >= 5, |x| > 0.9966: about 0.3% of the draws)
+__device__ __forceinline__ float norminv_tail(float w) {
+  w = __fsub_rn(sqrt_approx(w), 3.0f);
+  float p = SIMR_S2(-0.000200214257);
+  p = __fmaf_rn(p, w, SIMR_S2(0.000100950558));
+  p = __fmaf_rn(p, w, SIMR_S2(0.00134934322));
+  p = __fmaf_rn(p, w, SIMR_S2(-0.00367342844));
+  p = __fmaf_rn(p, w, SIMR_S2(0.00573950773));
+  p = __fmaf_rn(p, w, SIMR_S2(-0.0076224613));
+  p = __fmaf_rn(p, w, SIMR_S2(0.00943887047));
+  p = __fmaf_rn(p, w, SIMR_S2(1.00167406));
+  p = __fmaf_rn(p, w, SIMR_S2(2.83297682));
+  return p;
+}
 __device__ __forceinline__ float norminv_centered(float x) {
-  float w = -0.69314718055994531f * lg2_approx(fmaf(-x, x, 1.0f));
+  const float w = __fmul_rn(-0.69314718055994531f, lg2_approx(__fmaf_rn(-x, x, 1.0f)));
   float p;
   if (w < 5.0f) {
-    w = w - 2.5f;
+    const float wc = __fsub_rn(w, 2.5f);
     p = SIMR_S2(2.81022636e-08);
-    p = fmaf(p, w, SIMR_S2(3.43273939e-07));
-    p = fmaf(p, w, SIMR_S2(-3.5233877e-06));
-    p = fmaf(p, w, SIMR_S2(-4.39150654e-06));
-    p = fmaf(p, w, SIMR_S2(0.00021858087));
-    p = fmaf(p, w, SIMR_S2(-0.00125372503));
-    p = fmaf(p, w, SIMR_S2(-0.00417768164));
-    p = fmaf(p, w, SIMR_S2(0.246640727));
-    p = fmaf(p, w, SIMR_S2(1.50140941));
+    p = __fmaf_rn(p, wc, SIMR_S2(3.43273939e-07));
+    p = __fmaf_rn(p, wc, SIMR_S2(-3.5233877e-06));
+    p = __fmaf_rn(p, wc, SIMR_S2(-4.39150654e-06));
+    p = __fmaf_rn(p, wc, SIMR_S2(0.00021858087));
+    p = __fmaf_rn(p, wc, SIMR_S2(-0.00125372503));
+    p = __fmaf_rn(p, wc, SIMR_S2(-0.00417768164));
+    p = __fmaf_rn(p, wc, SIMR_S2(0.246640727));
+    p = __fmaf_rn(p, wc, SIMR_S2(1.50140941));
   } else {
-    w = sqrt_approx(w) - 3.0f;
-    p = SIMR_S2(-0.000200214257);
-    p = fmaf(p, w, SIMR_S2(0.000100950558));
-    p = fmaf(p, w, SIMR_S2(0.00134934322));
-    p = fmaf(p, w, SIMR_S2(-0.00367342844));
-    p = fmaf(p, w, SIMR_S2(0.00573950773));
-    p = fmaf(p, w, SIMR_S2(-0.0076224613));
-    p = fmaf(p, w, SIMR_S2(0.00943887047));
-    p = fmaf(p, w, SIMR_S2(1.00167406));
-    p = fmaf(p, w, SIMR_S2(2.83297682));
+    p = norminv_tail(w);
   }
-  return p * x;
+  return __fmul_rn(p, x);
+}
+// Two inverse normals at once (the central polynomial paired, the rare tail per lane).
+__device__ __forceinline__ float2 norminv_centered2(float2 x) {
+  const float2 w = p_mul(p_bc(-0.69314718055994531f), p_lg2(p_fma(p_mul(x, p_bc(-1.0f)), x, p_bc(1.0f))));
+  const float2 wc = p_sub(w, p_bc(2.5f));
+  float2 p = p_bc(SIMR_S2(2.81022636e-08));
+  p = p_fma(p, wc, p_bc(SIMR_S2(3.43273939e-07)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(-3.5233877e-06)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(-4.39150654e-06)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(0.00021858087)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(-0.00125372503)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(-0.00417768164)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(0.246640727)));
+  p = p_fma(p, wc, p_bc(SIMR_S2(1.50140941)));
+  if (!(w.x < 5.0f)) p.x = norminv_tail(w.x);
+  if (!(w.y < 5.0f)) p.y = norminv_tail(w.y);
+  return p_mul(p, x);
 }
 #undef SIMR_S2
 
@@ -155,32 +222,57 @@ __device__ __forceinline__ float norminv_centered(float x) {
 // innovation the log-spot step needs) without cancellation in the quadratic
 // branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1) since m = a (1 + b^2).
 // omu = 1 - U_V (exact), zv = Phi^-1(U_V).
-__device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, float zv, float& v_next,
-                                                float& dl) {
-  const float m2 = m * m;
-  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
-    const float t = 2.0f * m2 * rcp_approx(s2);
-    const float root = sqrt_approx(fmaf(t, t, -t));
-    const float b2 = (t - 1.0f) + root;
-    const float b = sqrt_approx(b2);
-    const float a = m * rcp_approx(t + root);
-    const float bz = b + zv;
-    v_next = a * bz * bz;
-    dl = a * fmaf(zv, zv + 2.0f * b, -1.0f);
-  } else if (m > 0.0f) {
-    const float ms = m2 + s2;
-    const float W = omu * ms;
-    if (W >= 2.0f * m2) {
+// the exponential branch (and the zero-mean case) of qe_from_moments
+__device__ __forceinline__ void qe_exp_branch(float m, float s2, float m2, float omu, float& v_next, float& dl) {
+  if (m > 0.0f) {
+    const float ms = __fadd_rn(m2, s2);
+    const float W = __fmul_rn(omu, ms);
+    if (W >= __fmul_rn(2.0f, m2)) {
       v_next = 0.0f;
     } else {
-      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
-      v_next = 0.5f * ms * rcp_approx(m) * L;
+      const float L = __fmul_rn(0.69314718055994531f, lg2_approx(__fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(W))));
+      v_next = __fmul_rn(__fmul_rn(__fmul_rn(0.5f, ms), rcp_approx(m)), L);
     }
-    dl = v_next - m;
+    dl = __fsub_rn(v_next, m);
   } else {
     v_next = 0.0f;
     dl = 0.0f;
   }
+}
+
+__device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, float zv, float& v_next,
+                                                float& dl) {
+  const float m2 = __fmul_rn(m, m);
+  if (s2 <= __fmul_rn(1.5f, m2) && m2 > 0.0f) {
+    const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
+    const float root = sqrt_approx(__fmaf_rn(t, t, -t));
+    const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
+    const float b = sqrt_approx(b2);
+    const float a = __fmul_rn(m, rcp_approx(__fadd_rn(t, root)));
+    const float bz = __fadd_rn(b, zv);
+    v_next = __fmul_rn(__fmul_rn(a, bz), bz);
+    dl = __fmul_rn(a, __fmaf_rn(zv, __fadd_rn(zv, __fmul_rn(2.0f, b)), -1.0f));
+  } else {
+    qe_exp_branch(m, s2, m2, omu, v_next, dl);
+  }
+}
+
+// Two QE variance steps: the quadratic branch paired for both lanes, then any
+// lane outside it redone by the scalar exponential branch.
+__device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2, float2 omu, float2 zv, float2& v_next,
+                                                 float2& dl) {
+  const float2 m2 = p_mul(m, m);
+  const float2 lim = p_mul(p_bc(1.5f), m2);
+  const float2 t = p_mul(p_mul(p_bc(2.0f), m2), p_rcp(s2));
+  const float2 root = p_sqrt(p_fma(t, t, p_mul(t, p_bc(-1.0f))));
+  const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+  const float2 b = p_sqrt(b2);
+  const float2 a = p_mul(m, p_rcp(p_add(t, root)));
+  const float2 bz = p_add(b, zv);
+  v_next = p_mul(p_mul(a, bz), bz);
+  dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
+  if (!(s2.x <= lim.x && m2.x > 0.0f)) qe_exp_branch(m.x, s2.x, m2.x, omu.x, v_next.x, dl.x);
+  if (!(s2.y <= lim.y && m2.y > 0.0f)) qe_exp_branch(m.y, s2.y, m2.y, omu.y, v_next.y, dl.y);
 }
 
 // One step of the base scenario: QE variance step, then LogPricePathQE (paper
@@ -193,17 +285,38 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
   float vn, dl;
   // CRN: round(round(v E) + thE), exactly the bumped scenarios' sequence with zero
   // deltas (__fmul_rn / __fadd_rn are never contracted into an FMA)
-  const float m = CRN ? __fadd_rn(__fmul_rn(v, c.E), c.thE) : fmaf(v, c.E, c.thE);
-  const float s2 = CRN ? __fadd_rn(__fmul_rn(v, c.c1), c.c2) : fmaf(v, c.c1, c.c2);
+  const float m = CRN ? __fadd_rn(__fmul_rn(v, c.E), c.thE) : __fmaf_rn(v, c.E, c.thE);
+  const float s2 = CRN ? __fadd_rn(__fmul_rn(v, c.c1), c.c2) : __fmaf_rn(v, c.c1, c.c2);
   qe_from_moments(m, s2, omu, zv, vn, dl);
-  const float s = v + vn;
-  float inc = fmaf(c.Cv, s, c.C0);
-  inc = fmaf(-c.Cd, v, inc);
-  inc = fmaf(c.Cdl, dl, inc);
-  inc = fmaf(c.sK3 * sqrt_approx(s), zx, inc);
-  const float y = inc - comp;
-  const float t = x + y;
-  comp = (t - x) - y;
+  const float s = __fadd_rn(v, vn);
+  float inc = __fmaf_rn(c.Cv, s, c.C0);
+  inc = __fmaf_rn(-c.Cd, v, inc);
+  inc = __fmaf_rn(c.Cdl, dl, inc);
+  inc = __fmaf_rn(__fmul_rn(c.sK3, sqrt_approx(s)), zx, inc);
+  const float y = __fsub_rn(inc, comp);
+  const float t = __fadd_rn(x, y);
+  comp = __fsub_rn(__fsub_rn(t, x), y);
+  x = t;
+  v = vn;
+}
+
+// step_base for two lanes sharing the constants (two paths, or two scenarios
+// that differ only in v0).
+template <bool CRN>
+__device__ __forceinline__ void step_base2(const ScenConst& c, float2 omu, float2 zv, float2 zx, float2& v,
+                                           float2& x, float2& comp) {
+  float2 vn, dl;
+  const float2 m = CRN ? p_add(p_mul(v, p_bc(c.E)), p_bc(c.thE)) : p_fma(v, p_bc(c.E), p_bc(c.thE));
+  const float2 s2 = CRN ? p_add(p_mul(v, p_bc(c.c1)), p_bc(c.c2)) : p_fma(v, p_bc(c.c1), p_bc(c.c2));
+  qe_from_moments2(m, s2, omu, zv, vn, dl);
+  const float2 s = p_add(v, vn);
+  float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
+  inc = p_fma(p_bc(-c.Cd), v, inc);
+  inc = p_fma(p_bc(c.Cdl), dl, inc);
+  inc = p_fma(p_mul(p_bc(c.sK3), p_sqrt(s)), zx, inc);
+  const float2 y = p_sub(inc, comp);
+  const float2 t = p_add(x, y);
+  comp = p_sub(p_sub(t, x), y);
   x = t;
   v = vn;
 }
@@ -324,28 +437,59 @@ __device__ __forceinline__ void step_scheme(const ScenConst& c, const QemConst& 
 // One step of a bumped scenario: base constants b plus deltas d.
 __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float omu, float zv, float zx,
                                             float& v, float& x, float& comp) {
-  const float m = __fadd_rn(fmaf(v, b.E, fmaf(v, d.E, d.thE)), b.thE);
-  const float s2 = __fadd_rn(fmaf(v, b.c1, fmaf(v, d.c1, d.c2)), b.c2);
+  const float m = __fadd_rn(__fmaf_rn(v, b.E, __fmaf_rn(v, d.E, d.thE)), b.thE);
+  const float s2 = __fadd_rn(__fmaf_rn(v, b.c1, __fmaf_rn(v, d.c1, d.c2)), b.c2);
   float vn, dl;
   qe_from_moments(m, s2, omu, zv, vn, dl);
-  const float s = v + vn;
+  const float s = __fadd_rn(v, vn);
   const float q = sqrt_approx(s);
-  float inc = fmaf(b.Cv, s, b.C0);
-  inc = fmaf(-b.Cd, v, inc);
-  inc = fmaf(b.Cdl, dl, inc);
-  inc = fmaf(b.sK3 * q, zx, inc);
-  float sm = fmaf(d.Cv, s, d.C0);
-  sm = fmaf(-d.Cd, v, sm);
-  sm = fmaf(d.Cdl, dl, sm);
-  sm = fmaf(d.sK3 * q, zx, sm);
-  inc += sm;
+  float inc = __fmaf_rn(b.Cv, s, b.C0);
+  inc = __fmaf_rn(-b.Cd, v, inc);
+  inc = __fmaf_rn(b.Cdl, dl, inc);
+  inc = __fmaf_rn(__fmul_rn(b.sK3, q), zx, inc);
+  float sm = __fmaf_rn(d.Cv, s, d.C0);
+  sm = __fmaf_rn(-d.Cd, v, sm);
+  sm = __fmaf_rn(d.Cdl, dl, sm);
+  sm = __fmaf_rn(__fmul_rn(d.sK3, q), zx, sm);
+  inc = __fadd_rn(inc, sm);
 #if SIMR_KAHAN_BUMPED
-  const float y = inc - comp;
-  const float t = x + y;
-  comp = (t - x) - y;
+  const float y = __fsub_rn(inc, comp);
+  const float t = __fadd_rn(x, y);
+  comp = __fsub_rn(__fsub_rn(t, x), y);
   x = t;
 #else
-  x += inc;
+  x = __fadd_rn(x, inc);
+#endif
+  v = vn;
+}
+
+// step_bumped for two scenarios with deltas d0 (lane x) and d1 (lane y).
+__device__ __forceinline__ void step_bumped2(const ScenConst& b, const ScenConst& d0, const ScenConst& d1,
+                                             float2 omu, float2 zv, float2 zx, float2& v, float2& x, float2& comp) {
+  const float2 m = p_add(p_fma(v, p_bc(b.E), p_fma(v, make_float2(d0.E, d1.E), make_float2(d0.thE, d1.thE))),
+                         p_bc(b.thE));
+  const float2 s2 = p_add(p_fma(v, p_bc(b.c1), p_fma(v, make_float2(d0.c1, d1.c1), make_float2(d0.c2, d1.c2))),
+                          p_bc(b.c2));
+  float2 vn, dl;
+  qe_from_moments2(m, s2, omu, zv, vn, dl);
+  const float2 s = p_add(v, vn);
+  const float2 q = p_sqrt(s);
+  float2 inc = p_fma(p_bc(b.Cv), s, p_bc(b.C0));
+  inc = p_fma(p_bc(-b.Cd), v, inc);
+  inc = p_fma(p_bc(b.Cdl), dl, inc);
+  inc = p_fma(p_mul(p_bc(b.sK3), q), zx, inc);
+  float2 sm = p_fma(make_float2(d0.Cv, d1.Cv), s, make_float2(d0.C0, d1.C0));
+  sm = p_fma(make_float2(-d0.Cd, -d1.Cd), v, sm);
+  sm = p_fma(make_float2(d0.Cdl, d1.Cdl), dl, sm);
+  sm = p_fma(p_mul(make_float2(d0.sK3, d1.sK3), q), zx, sm);
+  inc = p_add(inc, sm);
+#if SIMR_KAHAN_BUMPED
+  const float2 y = p_sub(inc, comp);
+  const float2 t = p_add(x, y);
+  comp = p_sub(p_sub(t, x), y);
+  x = t;
+#else
+  x = p_add(x, inc);
 #endif
   v = vn;
 }
@@ -420,6 +564,34 @@ __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps,
       const float xv = centered_uniform(w.z);
       step_scheme<false, QEM>(c, q, 0.5f * (1.0f - xv), norminv_centered(xv),
                               norminv_centered(centered_uniform(w.w)), v, x, comp);
+    }
+  }
+}
+
+// Two paths of one scenario in lockstep (plain QE): simulate_one's arithmetic,
+// paired lane for lane, so each path's x_T and remainder equal simulate_one's.
+__device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps, uint32_t option,
+                                             const uint32_t (&rk)[10][2], uint64_t path0, uint64_t path1,
+                                             float2& x, float2& comp) {
+  const uint32_t plo0 = (uint32_t)path0, phi0 = (uint32_t)(path0 >> 32);
+  const uint32_t plo1 = (uint32_t)path1, phi1 = (uint32_t)(path1 >> 32);
+  float2 v = make_float2(c.v0, c.v0);
+  x = make_float2(0.0f, 0.0f);
+  comp = make_float2(0.0f, 0.0f);
+  for (uint32_t p = 0; 2 * p < steps; ++p) {
+    const uint4 w0 = philox4x32_10(p, plo0, phi0, option, rk);
+    const uint4 w1 = philox4x32_10(p, plo1, phi1, option, rk);
+    {
+      const float xa = centered_uniform(w0.x), xb = centered_uniform(w1.x);
+      const float2 zv = norminv_centered2(make_float2(xa, xb));
+      const float2 zx = norminv_centered2(make_float2(centered_uniform(w0.y), centered_uniform(w1.y)));
+      step_base2<false>(c, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, v, x, comp);
+    }
+    if (2 * p + 1 < steps) {
+      const float xa = centered_uniform(w0.z), xb = centered_uniform(w1.z);
+      const float2 zv = norminv_centered2(make_float2(xa, xb));
+      const float2 zx = norminv_centered2(make_float2(centered_uniform(w0.w), centered_uniform(w1.w)));
+      step_base2<false>(c, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, v, x, comp);
     }
   }
 }

@@ -71,6 +71,30 @@ __device__ __forceinline__ float lsm_payoff(bool put, float S, float K) {
   return put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
 }
 
+// One step of the thread's two paths from their (variance, log-spot) words:
+// paired for plain QE (simulate_two's arithmetic), per path for QE-M.
+template <bool QEM>
+__device__ __forceinline__ void step_two(const LsmLaunch& L, uint32_t wv0, uint32_t wx0, uint32_t wv1, uint32_t wx1,
+                                         float (&v)[kLsmPpt], float (&x)[kLsmPpt], float (&comp)[kLsmPpt]) {
+  static_assert(kLsmPpt == 2, "two paths per thread");
+  const float xa = centered_uniform(wv0), xb = centered_uniform(wv1);
+  const float2 zv = norminv_centered2(make_float2(xa, xb));
+  const float2 zx = norminv_centered2(make_float2(centered_uniform(wx0), centered_uniform(wx1)));
+  if constexpr (QEM) {
+    step_qem(L.sc, L.qm, 0.5f * (1.0f - xa), zv.x, zx.x, v[0], x[0], comp[0]);
+    step_qem(L.sc, L.qm, 0.5f * (1.0f - xb), zv.y, zx.y, v[1], x[1], comp[1]);
+  } else {
+    float2 vv = make_float2(v[0], v[1]), xx = make_float2(x[0], x[1]), cc = make_float2(comp[0], comp[1]);
+    step_base2<false>(L.sc, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, vv, xx, cc);
+    v[0] = vv.x;
+    v[1] = vv.y;
+    x[0] = xx.x;
+    x[1] = xx.y;
+    comp[0] = cc.x;
+    comp[1] = cc.y;
+  }
+}
+
 // Path kernel: states at the exercise dates, maturity cash flow.
 template <bool QEM>
 __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constant__ LsmLaunch L,
@@ -110,23 +134,13 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
       uint4 w[kLsmPpt];
 #pragma unroll
       for (int j = 0; j < kLsmPpt; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], L.option_index, L.rk);
-#pragma unroll
-      for (int j = 0; j < kLsmPpt; ++j) {
-        const float xv = centered_uniform(w[j].x);
-        step_scheme<false, QEM>(L.sc, L.qm, 0.5f * (1.0f - xv), norminv_centered(xv),
-                                norminv_centered(centered_uniform(w[j].y)), v[j], x[j], comp[j]);
-      }
+      step_two<QEM>(L, w[0].x, w[0].y, w[1].x, w[1].y, v, x, comp);
       if (++cnt == L.every) {
         cnt = 0;
         record();
       }
       if (2 * p + 1 < L.steps) {
-#pragma unroll
-        for (int j = 0; j < kLsmPpt; ++j) {
-          const float xv = centered_uniform(w[j].z);
-          step_scheme<false, QEM>(L.sc, L.qm, 0.5f * (1.0f - xv), norminv_centered(xv),
-                                  norminv_centered(centered_uniform(w[j].w)), v[j], x[j], comp[j]);
-        }
+        step_two<QEM>(L, w[0].z, w[0].w, w[1].z, w[1].w, v, x, comp);
         if (++cnt == L.every) {
           cnt = 0;
           record();

@@ -84,22 +84,57 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
 // NS scenarios in registers; DYN: only the first L.n_scen of them are live.
 // Scenarios 1 .. NV differ from the base only in v0 (all constant deltas zero):
 // they take the base step, which is the bumped step's arithmetic with zero deltas.
+// The two inverse normals run paired, and so do the scenarios after the base,
+// two at a time (s, s + 1): the paired functions repeat the scalar ones lane for
+// lane, so every scenario's value is the scalar step's, bit for bit.
 template <int NS, int NV, bool DYN, bool QEM = false>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
   const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
-  const float zv = norminv_centered(xv);
-  const float zx = norminv_centered(centered_uniform(w_x));
+  const float2 z = norminv_centered2(make_float2(xv, centered_uniform(w_x)));
+  const float zv = z.x, zx = z.y;
   static_assert(!QEM || NS == 1, "QE-M runs the base scenario only");
+  static_assert(NS % 2 == 1, "the base scenario plus up/down pairs");
   step_scheme<(NS > 1), QEM>(L.sc[0], L.qm, omu, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
-  for (int s = 1; s < NS; ++s) {
+  for (int s = 1; s + 1 < NS; s += 2) {
     if (DYN && s >= L.n_scen) break;
-    if (s <= NV)
-      step_base<true>(L.sc[0], omu, zv, zx, v[s], x[s], c[s]);
+    float2 vv = make_float2(v[s], v[s + 1]), xx = make_float2(x[s], x[s + 1]), cc = make_float2(c[s], c[s + 1]);
+    if (s + 1 <= NV)
+      step_base2<true>(L.sc[0], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
     else
-      step_bumped(L.sc[0], L.sc[s], omu, zv, zx, v[s], x[s], c[s]);
+      step_bumped2(L.sc[0], L.sc[s], L.sc[s + 1], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
+    v[s] = vv.x;
+    v[s + 1] = vv.y;
+    x[s] = xx.x;
+    x[s + 1] = xx.y;
+    c[s] = cc.x;
+    c[s + 1] = cc.y;
+  }
+}
+
+// One time step of PPT paths.  Pricing with two paths per thread runs the two
+// paths' steps paired (their inverse normals too); otherwise step_all per path.
+template <int NS, int NV, bool DYN, int PPT, bool QEM>
+__device__ __forceinline__ void step_paths(const PathLaunch& L, const uint32_t (&wv)[PPT], const uint32_t (&wx)[PPT],
+                                           float (&v)[PPT][NS], float (&x)[PPT][NS], float (&c)[PPT][NS]) {
+  if constexpr (NS == 1 && PPT == 2 && !QEM) {
+    const float xv0 = centered_uniform(wv[0]), xv1 = centered_uniform(wv[1]);
+    const float2 zv = norminv_centered2(make_float2(xv0, xv1));
+    const float2 zx = norminv_centered2(make_float2(centered_uniform(wx[0]), centered_uniform(wx[1])));
+    const float2 omu = make_float2(0.5f * (1.0f - xv0), 0.5f * (1.0f - xv1));
+    float2 vv = make_float2(v[0][0], v[1][0]), xx = make_float2(x[0][0], x[1][0]), cc = make_float2(c[0][0], c[1][0]);
+    step_base2<false>(L.sc[0], omu, zv, zx, vv, xx, cc);
+    v[0][0] = vv.x;
+    v[1][0] = vv.y;
+    x[0][0] = xx.x;
+    x[1][0] = xx.y;
+    c[0][0] = cc.x;
+    c[1][0] = cc.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, wv[j], wx[j], v[j], x[j], c[j]);
   }
 }
 
@@ -152,26 +187,34 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
 #pragma unroll
     for (int j = 0; j < PPT; ++j) step0_all<NS, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
     if (L.steps > 1) {
+      uint32_t wv[PPT], wx[PPT];
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
+      for (int j = 0; j < PPT; ++j) wv[j] = w[j].z, wx[j] = w[j].w;
+      step_paths<NS, NV, DYN, PPT, QEM>(L, wv, wx, v, x, c);
     }
     i0 = 1;
   }
   for (uint32_t i = i0; i < pairs; ++i) {
     uint4 w[PPT];
+    uint32_t wv[PPT], wx[PPT];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(i, plo[j], phi[j], L.option_index, L.rk);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
+    for (int j = 0; j < PPT; ++j) wv[j] = w[j].x, wx[j] = w[j].y;
+    step_paths<NS, NV, DYN, PPT, QEM>(L, wv, wx, v, x, c);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) step_all<NS, NV, DYN, QEM>(L, w[j].z, w[j].w, v[j], x[j], c[j]);
+    for (int j = 0; j < PPT; ++j) wv[j] = w[j].z, wx[j] = w[j].w;
+    step_paths<NS, NV, DYN, PPT, QEM>(L, wv, wx, v, x, c);
   }
   if ((L.steps & 1u) && pairs >= i0) {  // odd last step (step 0 itself when steps == 1 without the split)
+    uint32_t wv[PPT], wx[PPT];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const uint4 w = philox4x32_10(pairs, plo[j], phi[j], L.option_index, L.rk);
-      step_all<NS, NV, DYN, QEM>(L, w.x, w.y, v[j], x[j], c[j]);
+      wv[j] = w.x;
+      wx[j] = w.y;
     }
+    step_paths<NS, NV, DYN, PPT, QEM>(L, wv, wx, v, x, c);
   }
 }
 
