@@ -43,8 +43,12 @@ inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int t
   return racc ? head + (buf_bytes > acc_bytes ? buf_bytes : acc_bytes) : acc_bytes + head + buf_bytes;
 }
 
+#ifndef SIMR_ADJ_MINB
+#define SIMR_ADJ_MINB 1  // minimum resident blocks per SM requested from the register allocator
+#endif
+
 template <int TILE, int PPT, bool RACC>
-__global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
+__global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
                                                              double* __restrict__ partials,
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
   // checkpoints: this thread's column of a [slot][grid threads] global array
   float* ck = gckpt + (int)blockIdx.x * bd + tid;
   const int ck_stride = (int)(gridDim.x * blockDim.x);
-  float* seg = sbuf + tid;
+  float* seg = sbuf;  // the block's segment buffer (16-byte aligned)
   double racc[RACC ? kAdjAcc : 1];
 #pragma unroll
   for (int a = 0; a < (RACC ? kAdjAcc : 1); ++a) racc[a] = 0.0;
@@ -97,7 +101,8 @@ __global__ void __launch_bounds__(128) heston_adjoint_kernel(const __grid_consta
       pth[j] = L.path_begin + local;
     }
     float x[PPT], comp[PPT], g[PPT][5], S[PPT];
-    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride, seg, bd, x, comp, g);
+    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride, seg, A.ckpt_every, bd, x,
+                          comp, g);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   float x[1], comp[1], g[1][5];
   const uint64_t pth[1] = {L.path_begin + i};
   path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt + tid, bd,
-                      ckpt + (A.n_seg - 1) * bd + tid, bd, x, comp, g);
+                      ckpt + (A.n_seg - 1) * bd, A.ckpt_every, bd, x, comp, g);
   x_T[i] = x[0] - comp[0];
 #pragma unroll
   for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];

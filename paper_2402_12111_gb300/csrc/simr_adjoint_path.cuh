@@ -109,13 +109,12 @@ __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float 
   return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
 }
 
-// The stored data of one step (recompute pass): state, branch draw, Z_X, from
-// the step's centred variance uniform and its two normals.
-__device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, float zv, float zx, float* bv, float* bd_,
-                                          float* bz, float& v) {
+// The stored data of one step (recompute pass): (state, branch draw) as one
+// pair and Z_X, from the step's centred variance uniform and its two normals.
+__device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, float zv, float zx, float2* bvd, float* bz,
+                                          float& v) {
   const float omu = 0.5f * (1.0f - xv_v);
-  *bv = v;
-  *bd_ = branch_draw(c, v, omu, zv);
+  *bvd = make_float2(v, branch_draw(c, v, omu, zv));
   *bz = zx;
   v = qe_only(c, v, omu, zv);
 }
@@ -130,35 +129,75 @@ __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a,
   g[4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
 }
 
-// Forward pass with checkpoints, then the reverse sweep, for PPT paths in
-// lockstep (independent dependency chains for the scheduler to interleave):
-// x_T (with its Kahan remainder) and g = d x_T / d(v0, kappa, theta, sigma, rho)
-// per path.  The forward pass runs the variance recursion only, and only up to
-// the last checkpoint (x_T is not needed before the sweep ends; the last
-// segment is recomputed from its checkpoint anyway); the reverse sweep adds up
-// the log-spot increments as it goes.  Checkpoint (slot, path j) of this thread
-// at ck[(slot * PPT + j) * ck_stride] (n_seg - 1 slots; shared or global memory);
-// the segment's states, branch draws and Z_X in this thread's column of a
-// shared buffer of bd columns: seg[((q * k + i) * PPT + j) * bd], q = 0..2.
-// The recompute pass of a segment keeps them there, so the reverse sweep
-// regenerates nothing.
-template <int PPT>
-__device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
-                                                 const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
-                                                 int ck_stride, float* seg, int bd, float (&x_out)[PPT],
-                                                 float (&comp_out)[PPT], float (&g)[PPT][5]) {
+// Reverse sweep of one path, segment by segment, last first: each segment's
+// states are recomputed from its checkpoint (the last checkpoint is v_last, the
+// forward pass's final state; earlier ones ck[slot * cstride], each loaded a
+// segment ahead of its use) and kept with the step's branch draw and Z_X in this
+// thread's column of the block's shared segment buffer at seg (8-byte aligned,
+// bd columns, krows >= k rows per array, the same for every thread of the block):
+// (state, draw) pairs as a float2 array [i][column], then Z_X as a float array
+// [i][column] -- then the steps are differentiated backwards.  x_T (with its Kahan remainder)
+// is summed on the way; g = d x_T / d(v0, kappa, theta, sigma, rho).
+__device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
+                                           const uint32_t (&rk)[10][2], uint32_t plo, uint32_t phi,
+                                           const float* ck, int cstride, float v_last, float* seg, int krows, int bd,
+                                           float& x_out, float& comp_out, float (&g)[5]) {
   const float theta = A.theta;
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
-  const int stride = PPT * bd;  // between consecutive steps of one thread's segment column
+  AdjSums as = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  float2* s01 = reinterpret_cast<float2*>(seg) + threadIdx.x;  // (state, draw) [i * bd]
+  float* s2 = seg + 2 * krows * bd + threadIdx.x;                // Z_X [i * bd]
+  float ck_next = v_last;
+  for (int sgi = n_seg - 1; sgi >= 0; --sgi) {
+    const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
+    float vv = ck_next;
+    if (sgi > 0) ck_next = ck[(sgi - 1) * cstride];
+    for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
+      const int i = (int)(2 * p - n0) * bd;
+      const uint4 w = philox4x32_10(p, plo, phi, option, rk);
+      const float xa = centered_uniform(w.x), xb = centered_uniform(w.z);
+      const float2 zv = norminv_centered2(make_float2(xa, xb));  // the pair's normals two at a time
+      const float2 zx = norminv_centered2(make_float2(centered_uniform(w.y), centered_uniform(w.w)));
+      keep_step(c, xa, zv.x, zx.x, s01 + i, s2 + i, vv);
+      if (2 * p + 1 < n1) keep_step(c, xb, zv.y, zx.y, s01 + i + bd, s2 + i + bd, vv);
+    }
+    float vnext = vv;  // v_{n1}
+    for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
+      const float2 vd = s01[i * bd];
+      adjoint_step(c, theta, vd.x, vnext, vd.y, s2[i * bd], as);
+      vnext = vd.x;
+    }
+  }
+  x_out = as.x;
+  comp_out = as.comp;
+  adjoint_map(A, as, g);
+}
+
+// Forward pass with checkpoints, then the reverse sweeps, for PPT paths: the
+// forward pass runs the variance recursion only, and only up to the last
+// checkpoint (x_T is not needed before the sweep ends; the last segment is
+// recomputed from its checkpoint anyway), the PPT paths together -- two paths
+// paired (qe_from_moments2, lane for lane the scalar step); the reverse sweeps
+// then run one path at a time through the same shared segment buffer.
+// Checkpoint (slot, path j) of this thread at ck[(slot * PPT + j) * ck_stride]
+// (n_seg - 1 slots; shared or global memory); seg is the block's shared
+// segment buffer (bd columns of 3 krows floats, krows >= k the same for the
+// whole block, 8-byte aligned; this thread's column is threadIdx.x).
+template <int PPT>
+__device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
+                                                 const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
+                                                 int ck_stride, float* seg, int krows, int bd, float (&x_out)[PPT],
+                                                 float (&comp_out)[PPT], float (&g)[PPT][5]) {
+  static_assert(PPT == 1 || PPT == 2, "one or two paths per thread");
+  const uint32_t k = (uint32_t)A.ckpt_every;
+  const int n_seg = A.n_seg;
   uint32_t plo[PPT], phi[PPT];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     plo[j] = (uint32_t)path[j];
     phi[j] = (uint32_t)(path[j] >> 32);
   }
-#define SIMR_CK(slot, j) ck[((int)(slot) * PPT + (j)) * ck_stride]
-
   // forward pass: the variance recursion up to the last checkpoint, (n_seg - 1) k
   // < N; k is even, so every pair of steps below it is whole
   float v[PPT];
@@ -166,87 +205,43 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
   for (int j = 0; j < PPT; ++j) v[j] = c.v0;
   for (int sg = 0; sg < n_seg - 1; ++sg) {
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) SIMR_CK(sg, j) = v[j];
+    for (int j = 0; j < PPT; ++j) ck[(sg * PPT + j) * ck_stride] = v[j];
     const uint32_t p0 = (uint32_t)sg * (k / 2);
     for (uint32_t p = p0; p < p0 + k / 2; ++p) {
       uint4 w[PPT];
 #pragma unroll
       for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {  // the pair's two variance normals together
-        const float xa = centered_uniform(w[j].x), xb = centered_uniform(w[j].z);
+      if constexpr (PPT == 2) {
+        const float xa0 = centered_uniform(w[0].x), xa1 = centered_uniform(w[1].x);
+        const float xb0 = centered_uniform(w[0].z), xb1 = centered_uniform(w[1].z);
+        const float2 za = norminv_centered2(make_float2(xa0, xa1));
+        const float2 zb = norminv_centered2(make_float2(xb0, xb1));
+        float2 vv = make_float2(v[0], v[1]), vn, dl;
+        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.c1), p_bc(c.c2)),
+                         make_float2(0.5f * (1.0f - xa0), 0.5f * (1.0f - xa1)), za, vn, dl);
+        vv = vn;
+        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.c1), p_bc(c.c2)),
+                         make_float2(0.5f * (1.0f - xb0), 0.5f * (1.0f - xb1)), zb, vn, dl);
+        v[0] = vn.x;
+        v[1] = vn.y;
+      } else {  // the pair's two variance normals together
+        const float xa = centered_uniform(w[0].x), xb = centered_uniform(w[0].z);
         const float2 zv = norminv_centered2(make_float2(xa, xb));
-        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xa), zv.x);
-        v[j] = qe_only(c, v[j], 0.5f * (1.0f - xb), zv.y);
+        v[0] = qe_only(c, v[0], 0.5f * (1.0f - xa), zv.x);
+        v[0] = qe_only(c, v[0], 0.5f * (1.0f - xb), zv.y);
       }
     }
   }
-
-  AdjSums as[PPT];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) as[j] = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-
-  {
-    float* s0 = seg;                   // states
-    float* s1 = s0 + (int)k * stride;  // branch draws
-    float* s2 = s1 + (int)k * stride;  // Z_X
-#define SIMR_SG(q, i, j) s##q[(int)(i) * stride + (j) * bd]
-    // the last checkpoint is the forward pass's final state; each earlier one is
-    // loaded a segment ahead of its use
-    float ck_next[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) ck_next[j] = v[j];
-    for (int sgi = n_seg - 1; sgi >= 0; --sgi) {
-      const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
-      float vv[PPT];
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) vv[j] = ck_next[j];
-      if (sgi > 0) {
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) ck_next[j] = SIMR_CK(sgi - 1, j);
-      }
-      for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
-        const uint32_t i = 2 * p - n0;
-        uint4 w[PPT];
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {  // the pair's normals two at a time
-          const float xa = centered_uniform(w[j].x), xb = centered_uniform(w[j].z);
-          const float2 zv = norminv_centered2(make_float2(xa, xb));
-          const float2 zx = norminv_centered2(make_float2(centered_uniform(w[j].y), centered_uniform(w[j].w)));
-          keep_step(c, xa, zv.x, zx.x, &SIMR_SG(0, i, j), &SIMR_SG(1, i, j), &SIMR_SG(2, i, j), vv[j]);
-          if (2 * p + 1 < n1)
-            keep_step(c, xb, zv.y, zx.y, &SIMR_SG(0, i + 1, j), &SIMR_SG(1, i + 1, j), &SIMR_SG(2, i + 1, j), vv[j]);
-        }
-      }
-      float vnext[PPT];
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) vnext[j] = vv[j];  // v_{n1}
-      for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-          const float vc = SIMR_SG(0, i, j);
-          adjoint_step(c, theta, vc, vnext[j], SIMR_SG(1, i, j), SIMR_SG(2, i, j), as[j]);
-          vnext[j] = vc;
-        }
-      }
-    }
-#undef SIMR_SG
-  }
-#undef SIMR_CK
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    x_out[j] = as[j].x;
-    comp_out[j] = as[j].comp;
-    adjoint_map(A, as[j], g[j]);
-  }
+  for (int j = 0; j < PPT; ++j)
+    path_sweep(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], seg, krows, bd,
+               x_out[j], comp_out[j], g[j]);
 }
 
 // Floats per thread of path_adjoint_ppt: checkpoints and the segment buffer.
 __host__ __device__ inline size_t adjoint_ckpt_floats(const AdjConst& A, int ppt) { return (size_t)A.n_seg * ppt; }
-__host__ __device__ inline size_t adjoint_seg_floats(const AdjConst& A, int ppt) {
-  return (size_t)3 * A.ckpt_every * ppt;
+__host__ __device__ inline size_t adjoint_seg_floats(const AdjConst& A, int /*ppt: the sweeps share one buffer*/) {
+  return (size_t)3 * A.ckpt_every;
 }
 
 // Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho, 8 r (before -T P).

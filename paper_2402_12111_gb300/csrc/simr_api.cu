@@ -550,10 +550,10 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
 
 // Per-option device records (caller's order) and the longest-first order.
 int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vector<BatchOption>* out,
-                        std::vector<uint32_t>* order, int* smem_floats) {
+                        std::vector<uint32_t>* order, int* ckpt_rows, int* seg_rows) {
   out->resize(n);
   std::vector<double> cost(n);
-  int smem = 0;
+  int crows = 0, srows = 0;
   for (int i = 0; i < n; ++i) {
     const simr_option& o = opts[i];
     int rc = check_model(&o.m);
@@ -571,7 +571,8 @@ int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vecto
     b.sc = base_const(o.m, o.steps);
     if (adjoint) {
       if ((rc = build_adjoint(o.m, o.steps, 0, &b.A))) return rc;
-      smem = std::max(smem, adjoint_thread_floats(b.A.n_seg, b.A.ckpt_every, 1));
+      crows = std::max(crows, b.A.n_seg - 1);
+      srows = std::max(srows, b.A.ckpt_every);
     }
     b.S0 = (float)o.m.S0;
     b.K = (float)o.K;
@@ -587,7 +588,8 @@ int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vecto
   order->resize(n);
   std::iota(order->begin(), order->end(), 0u);
   std::stable_sort(order->begin(), order->end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
-  *smem_floats = smem;
+  *ckpt_rows = crows + (crows & 1);  // even: the segment pairs stay 8-byte aligned
+  *seg_rows = srows;
   return SIMR_OK;
 }
 
@@ -923,16 +925,17 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<BatchOption> bo;
   std::vector<uint32_t> order;
-  int smem_floats = 0;
-  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, &order, &smem_floats))) return rc;
-  if ((size_t)smem_floats * 128 * sizeof(float) > 200 * 1024)
-    return fail(SIMR_EUNSUPPORTED, "an option's checkpoints need more shared memory than a block has");
+  int ckpt_rows = 0, seg_rows = 0;
+  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, &order, &ckpt_rows, &seg_rows))) return rc;
+  if ((size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > 200 * 1024)
+    return fail(SIMR_EUNSUPPORTED, "the book's checkpoints need more shared memory than a block has");
   BatchLaunch B;
   std::memset(&B, 0, sizeof(B));
   philox_round_keys(seed, B.rk);
   B.n_opts = (uint32_t)n_opts;
   B.adjoint = adjoint ? 1 : 0;
-  B.smem_floats = smem_floats;
+  B.ckpt_rows = ckpt_rows;
+  B.seg_rows = seg_rows;
   const int nacc = adjoint ? 9 : 2;
   OutStage o;
   o.user[0] = price;

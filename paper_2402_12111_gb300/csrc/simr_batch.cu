@@ -54,8 +54,11 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         const bool active = b + lane < I.count;
         float x[1], comp[1], g[1][5];
         const uint64_t pth[1] = {I.path_begin + b + lane};
-        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd, smem_f + (O.A.n_seg - 1) * bd + tid, bd,
-                            x, comp, g);
+        // the block's layout: ckpt_rows checkpoint rows, then the segment
+        // arrays of seg_rows rows (the largest over the book), so threads on
+        // options with different checkpoint intervals never overlap
+        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd, smem_f + B.ckpt_rows * bd, B.seg_rows,
+                            bd, x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
@@ -113,7 +116,9 @@ __global__ void batch_reduce_kernel(const BatchOption* __restrict__ opts, uint32
 
 constexpr int kBatchTpb = 128;
 
-size_t batch_smem(const BatchLaunch& B) { return B.adjoint ? (size_t)B.smem_floats * kBatchTpb * sizeof(float) : 0; }
+size_t batch_smem(const BatchLaunch& B) {
+  return B.adjoint ? (size_t)(B.ckpt_rows + 3 * B.seg_rows) * kBatchTpb * sizeof(float) : 0;
+}
 
 }  // namespace
 

@@ -204,8 +204,10 @@ __device__ __forceinline__ float2 norminv_centered2(float2 x) {
   p = p_fma(p, wc, p_bc(SIMR_S2(-0.00417768164)));
   p = p_fma(p, wc, p_bc(SIMR_S2(0.246640727)));
   p = p_fma(p, wc, p_bc(SIMR_S2(1.50140941)));
-  if (!(w.x < 5.0f)) p.x = norminv_tail(w.x);
-  if (!(w.y < 5.0f)) p.y = norminv_tail(w.y);
+  if (!(w.x < 5.0f && w.y < 5.0f)) {  // one test on the common path
+    if (!(w.x < 5.0f)) p.x = norminv_tail(w.x);
+    if (!(w.y < 5.0f)) p.y = norminv_tail(w.y);
+  }
   return p_mul(p, x);
 }
 #undef SIMR_S2
@@ -271,8 +273,11 @@ __device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2, float2 omu
   const float2 bz = p_add(b, zv);
   v_next = p_mul(p_mul(a, bz), bz);
   dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
-  if (!(s2.x <= lim.x && m2.x > 0.0f)) qe_exp_branch(m.x, s2.x, m2.x, omu.x, v_next.x, dl.x);
-  if (!(s2.y <= lim.y && m2.y > 0.0f)) qe_exp_branch(m.y, s2.y, m2.y, omu.y, v_next.y, dl.y);
+  const bool qx = s2.x <= lim.x && m2.x > 0.0f, qy = s2.y <= lim.y && m2.y > 0.0f;
+  if (!(qx && qy)) {  // one test on the common path
+    if (!qx) qe_exp_branch(m.x, s2.x, m2.x, omu.x, v_next.x, dl.x);
+    if (!qy) qe_exp_branch(m.y, s2.y, m2.y, omu.y, v_next.y, dl.y);
+  }
 }
 
 // One step of the base scenario: QE variance step, then LogPricePathQE (paper

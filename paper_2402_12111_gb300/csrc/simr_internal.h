@@ -105,7 +105,8 @@ struct BatchLaunch {
   uint32_t rk[10][2];
   uint32_t n_items, n_opts;
   int32_t adjoint;
-  int32_t smem_floats;  // adjoint: shared floats per thread (max over options of n_seg + 3 ckpt_every)
+  int32_t ckpt_rows;  // adjoint: checkpoint rows per thread column (max over options of n_seg - 1), even
+  int32_t seg_rows;   // adjoint: rows of each segment array (max over options of ckpt_every)
 };
 
 struct BatchOutputs {
