@@ -243,7 +243,7 @@ def run_profile_leg(args):
         "fd": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=list(w.greeks),
                                      rel_bump=w.rel_bump),
         "price": lambda: simr.price(w.model, K, w.is_put, w.steps, w.paths, w.seed),
-        "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed, ckpt_every=16),
+        "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed),
     }
     if args.profile_leg == "book":
         opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))
@@ -347,7 +347,7 @@ def run_native(args):
                "steps": e2e_steps}
 
     # adjoint vs bump-and-revalue on the same GPU and workload (the adjoint workload:
-    # 7 sensitivities d/d{S0, v0, kappa, theta, sigma, rho, r}, checkpoint every 16 steps)
+    # 7 sensitivities d/d{S0, v0, kappa, theta, sigma, rho, r}, the library's checkpoint interval)
     adj = None
     if not args.no_adjoint:
         fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
@@ -355,7 +355,7 @@ def run_native(args):
             "price_ms": lambda: simr.price(w.model, K, w.is_put, w.steps, w.paths, w.seed),
             "fd7_ms": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=fd7,
                                              rel_bump=w.rel_bump),
-            "adjoint_ms": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed, ckpt_every=16),
+            "adjoint_ms": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed),
         }
         adj = {}
         reps = max(3, min(args.steps, 10))
@@ -394,7 +394,7 @@ def run_native(args):
         adj["qem_cost_vs_qe"] = adj["price_qem_ms"] / adj["price_ms"]
         adj["speedup_vs_fd"] = adj["fd7_ms"] / adj["adjoint_ms"]
         adj["cost_vs_price"] = adj["adjoint_ms"] / adj["price_ms"]
-        adj["ckpt_every"] = 16
+        adj["ckpt_every"] = simr.adjoint_interval(len(w.strikes), w.steps, dev.index or 0)  # the library's choice
         adj["sensitivities"] = list(fd7)
 
     # heterogeneous book: 1,024 options (log-uniform steps and paths), one persistent launch
@@ -470,7 +470,7 @@ def run_native(args):
                   "asset_path_steps_per_s": 8 * 252 * (1 << 20) / (ms_b * 1e-3)}
 
     # large-scale headline: 8 underlyings (book-style parameters), 32 strikes each,
-    # 1,024 steps, 2^26 paths; price, adjoint Greeks (checkpoint every 32 steps) and
+    # 1,024 steps, 2^26 paths; price, adjoint Greeks (the library's checkpoint interval) and
     # CRN bump-and-revalue of the same 7 sensitivities, one timed pass each
     head = None
     if not args.no_headline:
@@ -478,7 +478,9 @@ def run_native(args):
         fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
         ps_head = sum(u.steps * u.paths for u in hw)
         head = {"underlyings": len(hw), "time_steps": hw[0].steps, "paths": hw[0].paths,
-                "strikes": len(hw[0].strikes), "ckpt_every": hw[0].ckpt_every, "path_steps": ps_head,
+                "strikes": len(hw[0].strikes),
+                "ckpt_every": hw[0].ckpt_every or simr.adjoint_interval(len(hw[0].strikes), hw[0].steps, dev.index or 0),
+                "path_steps": ps_head,
                 "sensitivities": list(fd7)}
         Kh = [torch.as_tensor(u.strikes, dtype=torch.float64, device=dev) for u in hw]
         legs = {

@@ -173,8 +173,12 @@ SIMR_API int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const doubl
  * the QE map where a bump would switch a path's branch, so they differ from
  * bump-and-revalue by that (small) term.
  *   ckpt_every   in   even number of steps per checkpoint segment, in [2, 1024];
- *                     0 = about sqrt(steps / 3); values above steps act as steps
- *                     (rounded up to even).  Each resident thread keeps
+ *                     0 = the library's choice for speed: the forward pass runs
+ *                     all segments but the last, so it takes, among the even
+ *                     intervals whose shared memory keeps the kernel's blocks
+ *                     per SM (found once per context by the occupancy API), the
+ *                     one with the longest last segment; values above steps act
+ *                     as steps (rounded up to even).  Each resident thread keeps
  *                     steps/ckpt_every checkpoints in a context-owned device
  *                     buffer (at most 2^30 floats in all) and 3 ckpt_every
  *                     floats of shared memory (at most 200 KB per 128-thread
@@ -188,6 +192,12 @@ SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const 
                                  int is_put, uint32_t steps, uint64_t paths, uint64_t seed,
                                  uint32_t option_index, uint32_t ckpt_every, double* price, double* stderr_out,
                                  double* grad, void* stream);
+
+/*
+ * The checkpoint interval simr_greeks_adjoint takes for ckpt_every = 0 with
+ * n_strikes strikes (in [1, 256]) and `steps` time steps, in *ckpt_every.
+ */
+SIMR_API int simr_adjoint_interval(simr_ctx* ctx, int n_strikes, uint32_t steps, uint32_t* ckpt_every);
 
 /*
  * A heterogeneous book of European options in one persistent launch: every
@@ -218,6 +228,10 @@ SIMR_API int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opt
  * rho)[j] (FP32), by the same forward pass and reverse sweep as
  * simr_greeks_adjoint (dx_T/dS0 = 0 and dx_T/dr = T need no sweep).  Custom
  * payoffs g(S_T) get dE[g]/dq = E[g'(S_T) S_T dx_T/dq].  Device pointers only.
+ * ckpt_every as in simr_greeks_adjoint, except that 0 = the even interval near
+ * sqrt(steps / 3), the one that needs the least shared memory: here the
+ * checkpoints too are kept there (steps/ckpt_every + 3 ckpt_every floats per
+ * thread, at most 200 KB per 128-thread block).
  */
 SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin,
                                 uint64_t n_paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,

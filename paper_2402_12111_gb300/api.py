@@ -90,6 +90,13 @@ def greeks_adjoint(model, strikes, is_put: bool = False, steps: int = 64, paths:
     return p, se, g
 
 
+def adjoint_interval(n_strikes: int, steps: int, device: int = 0) -> int:
+    """simr_adjoint_interval: the checkpoint interval greeks_adjoint takes for ckpt_every=0."""
+    k = ctypes.c_uint32()
+    S.check(S.load().simr_adjoint_interval(S.context(device), int(n_strikes), int(steps), ctypes.byref(k)))
+    return int(k.value)
+
+
 class HestonAdjoint(torch.autograd.Function):
     """Monte Carlo price as a differentiable function of the model parameters.
 

@@ -242,6 +242,38 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
   return (size_t)num_sms * 16 * kAdjAcc * (size_t)L.nk_pad;  // at most 16 resident blocks of 128 threads per SM
 }
 
+cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_max) {
+  // the kernel variant launch_adjoint picks for this strike count
+  const bool racc = L.nk_pad == 32;
+  const void* kern = L.nk_pad == 1 ? (const void*)heston_adjoint_kernel<1, SIMR_ADJ_PPT, false>
+                     : racc      ? (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, true>
+                                 : (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, false>;
+  auto blocks = [&](int k, int* n) -> cudaError_t {
+    AdjConst A{};
+    A.ckpt_every = k;
+    const size_t smem = adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, racc);
+    *n = 0;
+    if (smem > kAdjMaxSmem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, 128, smem);
+  };
+  int best = 0;
+  cudaError_t e = blocks(2, &best);
+  if (e != cudaSuccess) return e;
+  if (best < 1) return cudaErrorInvalidConfiguration;
+  // blocks per SM fall as k grows: the largest even k that keeps `best`
+  int lo = 1, hi = (steps_cap + 1) / 2 + 1;  // k = 2 lo keeps it; k = 2 hi is past the cap
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    int n = 0;
+    if ((e = blocks(2 * mid, &n)) != cudaSuccess) return e;
+    (n >= best ? lo : hi) = mid;
+  }
+  *k_max = 2 * lo;
+  return cudaSuccess;
+}
+
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A) {
   return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32);
 }

@@ -72,6 +72,11 @@ struct simr_ctx {
     uint32_t chunk;
   };
   std::vector<Tune> tune;
+  struct AdjK {  // adjoint_max_ckpt_every per strike tile, found once
+    int32_t nk_pad;
+    int32_t k_max;
+  };
+  std::vector<AdjK> adj_k;
 };
 
 namespace {
@@ -772,6 +777,52 @@ int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strike
   return run_paths(ctx, L, ks, o, st);
 }
 
+// The checkpoint interval the per-strike adjoint runs fastest with.  Its
+// forward pass runs every segment but the last, (n_seg - 1) k = steps - (the
+// last segment's length) steps, while the recompute and reverse passes run all
+// steps whatever k is; so among the even k up to the largest that keeps the
+// kernel's blocks per SM, take the one with the longest last segment (the
+// smallest k on a tie, for the least shared memory).
+int fast_ckpt_every(simr_ctx* ctx, const PathLaunch& L, uint32_t steps, uint32_t* k) {
+  int k_max = 0;
+  for (const auto& t : ctx->adj_k)
+    if (t.nk_pad == L.nk_pad) k_max = t.k_max;
+  if (!k_max) {
+    cudaError_t e = adjoint_max_ckpt_every(L, 1024, &k_max);
+    if (e != cudaSuccess) return cuda_fail(e, "sizing the adjoint's checkpoint interval");
+    ctx->adj_k.push_back({L.nk_pad, k_max});
+  }
+  uint32_t best = 2;
+  uint64_t fwd_best = UINT64_MAX;
+  for (uint32_t c = 2; c <= (uint32_t)k_max; c += 2) {
+    const uint64_t fwd = (uint64_t)((steps + c - 1) / c - 1) * c;
+    if (fwd < fwd_best) {
+      fwd_best = fwd;
+      best = c;
+    }
+    if (c >= steps) break;  // one segment: no forward pass
+  }
+  *k = best;
+  return SIMR_OK;
+}
+
+int simr_adjoint_interval(simr_ctx* ctx, int n_strikes, uint32_t steps, uint32_t* ckpt_every) {
+  if (!ctx || !ckpt_every) return fail(SIMR_EINVAL, "ctx and ckpt_every must be non-NULL");
+  if (n_strikes < 1 || n_strikes > 256) return fail(SIMR_EINVAL, "n_strikes must be in [1, 256]");
+  if (steps < 1) return fail(SIMR_EINVAL, "steps must be positive");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  PathLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_strikes = n_strikes;
+  L.nk_pad = n_strikes == 1 ? 1 : ((n_strikes + 31) / 32) * 32;
+  L.n_acc = 9;
+  uint32_t k = 0;
+  if ((rc = fast_ckpt_every(ctx, L, steps, &k))) return rc;
+  *ckpt_every = k > steps ? steps + (steps & 1u) : k;
+  return SIMR_OK;
+}
+
 int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                         uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,
                         double* price, double* stderr_out, double* grad, void* stream) {
@@ -779,15 +830,17 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   if (rc) return rc;
   if (!price || !grad) return fail(SIMR_EINVAL, "price and grad must be non-NULL");
   if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
-  AdjConst A;
-  if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
   if ((rc = with_device(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   PathLaunch L;
   if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, 1e-4, 0u, &L)))
     return rc;
   L.n_acc = 9;  // the adjoint's accumulators: f, f^2 and 7 sensitivities per strike
-  if (adjoint_smem_bytes(L, A) > 200 * 1024)
+  uint32_t k = ckpt_every;
+  if (k == 0 && (rc = fast_ckpt_every(ctx, L, steps, &k))) return rc;
+  AdjConst A;
+  if ((rc = build_adjoint(*model, steps, k, &A))) return rc;
+  if (adjoint_smem_bytes(L, A) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
                 A.ckpt_every, steps);
   if (adjoint_ckpt_scratch_floats(A, ctx->num_sms) > (1ull << 30))
@@ -828,7 +881,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
-  if ((size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * 128 * sizeof(float) > 200 * 1024)
+  if ((size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * 128 * sizeof(float) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
                 A.ckpt_every, steps);
   if ((rc = with_device(ctx))) return rc;
@@ -927,7 +980,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   std::vector<uint32_t> order;
   int ckpt_rows = 0, seg_rows = 0;
   if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, &order, &ckpt_rows, &seg_rows))) return rc;
-  if ((size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > 200 * 1024)
+  if ((size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "the book's checkpoints need more shared memory than a block has");
   BatchLaunch B;
   std::memset(&B, 0, sizeof(B));

@@ -138,6 +138,13 @@ cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double*
                            const Scratch& s, int num_sms, cudaStream_t stream);
 size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms);
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A);
+// Dynamic shared memory one block of an adjoint kernel may ask for.
+constexpr size_t kAdjMaxSmem = 200 * 1024;
+// The largest even checkpoint interval (at most steps_cap, rounded up to even)
+// at which the per-strike adjoint kernel for L's strike count keeps the blocks
+// per SM it has at interval 2 (its register limit): each thread's segment
+// buffer is 3 k floats of shared memory.
+cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_max);
 size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms);
 // Per-path x_T and d x_T / d(v0, kappa, theta, sigma, rho) ([n][5]).
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream);

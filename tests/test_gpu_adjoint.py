@@ -112,6 +112,26 @@ def test_checkpoint_interval_does_not_change_results(simr):
                                    rtol=0, atol=0)
 
 
+def test_automatic_interval(simr):
+    # the interval taken for ckpt_every=0: even, one segment when it fits, the
+    # same results as any explicit interval
+    for nk, steps in ((1, 252), (32, 252), (33, 100), (32, 7), (1, 1000)):
+        k = simr.adjoint_interval(nk, steps)
+        assert k % 2 == 0 and 2 <= k <= steps + (steps & 1), (nk, steps, k)
+    assert simr.adjoint_interval(32, 7) == 8
+    k = simr.adjoint_interval(32, 252)
+    assert k >= 16
+    K = _dev(workloads.strike_grid())
+    a = simr.greeks_adjoint(CFG, K, False, 252, 4096, 5, ckpt_every=0)
+    b = simr.greeks_adjoint(CFG, K, False, 252, 4096, 5, ckpt_every=k)
+    c = simr.greeks_adjoint(CFG, K, False, 252, 4096, 5, ckpt_every=2)
+    for x, y, z in zip(a, b, c):
+        torch.testing.assert_close(x, y, rtol=0, atol=0)
+        torch.testing.assert_close(x, z, rtol=0, atol=0)
+    with pytest.raises(simr.SimrError):
+        simr.adjoint_interval(0, 10)
+
+
 def test_autograd_function_backward(simr):
     params = torch.tensor([100.0, 0.04, 1.5, 0.04, 0.3, -0.7, 0.05], dtype=torch.float64, requires_grad=True)
     K = _dev(workloads.strike_grid(n=8))

@@ -67,8 +67,7 @@ def grid() -> Workload:
 
 
 def adjoint() -> Workload:
-    return Workload("heston_adjoint_grid32_252x1048576", dict(BASE_MODEL), strike_grid(), 252, 1 << 20,
-                    ckpt_every=16)
+    return Workload("heston_adjoint_grid32_252x1048576", dict(BASE_MODEL), strike_grid(), 252, 1 << 20)
 
 
 def lsm() -> Workload:
@@ -108,9 +107,9 @@ def book(n_options: int = 1024, seed: int = 1, steps_range=(16, 512), paths_rang
 
 def headline(n_underlyings: int = 8, seed: int = 4):
     """8 underlyings with book-style parameters, each on the 32-strike grid,
-    1,024 steps and 2^26 paths, adjoint checkpoint every 32 steps."""
+    1,024 steps and 2^26 paths, the adjoint at the library's checkpoint interval."""
     rng = np.random.default_rng(seed)
-    return [Workload(f"headline_u{i}", _draw_params(rng), strike_grid(), 1024, 1 << 26, ckpt_every=32)
+    return [Workload(f"headline_u{i}", _draw_params(rng), strike_grid(), 1024, 1 << 26)
             for i in range(n_underlyings)]
 
 
