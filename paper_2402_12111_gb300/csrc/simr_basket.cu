@@ -9,6 +9,9 @@
 // lower Cholesky factor of the correlation of the spot drivers; the variance
 // drivers stay independent.  Payoff on B_T = sum_k w_k S_T,k per strike, and
 // the reduction over paths of the price kernel (FP32 over a warp, FP64 on).
+// Assets run in pairs, (k, k + 1) in the two halves of packed FP32 (.f32x2)
+// operations that round lane for lane as the scalar step; an odd count's last
+// asset runs alone in scalar FP32.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -22,11 +25,83 @@ namespace {
 
 constexpr int kBasketTpb = 256;
 
+// The constants of two assets, lane x asset k and lane y asset k + 1.
+struct ScenPair {
+  float2 E, thE, c1, c2, C0, Cv, mCd, Cdl, sK3;
+};
+
+__device__ __forceinline__ ScenPair scen_pair(const ScenConst& a, const ScenConst& b) {
+  ScenPair c;
+  c.E = make_float2(a.E, b.E);
+  c.thE = make_float2(a.thE, b.thE);
+  c.c1 = make_float2(a.c1, b.c1);
+  c.c2 = make_float2(a.c2, b.c2);
+  c.C0 = make_float2(a.C0, b.C0);
+  c.Cv = make_float2(a.Cv, b.Cv);
+  c.mCd = make_float2(-a.Cd, -b.Cd);
+  c.Cdl = make_float2(a.Cdl, b.Cdl);
+  c.sK3 = make_float2(a.sK3, b.sK3);
+  return c;
+}
+
+// step_base<false> of two assets at once in packed FP32, lane for lane the
+// scalar step's operations and rounding.
+__device__ __forceinline__ void step_pair(const ScenPair& c, float2 omu, float2 zv, float2 zx, float2& v, float2& x,
+                                          float2& comp) {
+  float2 vn, dl;
+  qe_from_moments2(p_fma(v, c.E, c.thE), p_fma(v, c.c1, c.c2), omu, zv, vn, dl);
+  const float2 s = p_add(v, vn);
+  float2 inc = p_fma(c.Cv, s, c.C0);
+  inc = p_fma(c.mCd, v, inc);
+  inc = p_fma(c.Cdl, dl, inc);
+  inc = p_fma(p_mul(c.sK3, p_sqrt(s)), zx, inc);
+  const float2 y = p_sub(inc, comp);
+  const float2 t = p_add(x, y);
+  comp = p_sub(p_sub(t, x), y);
+  x = t;
+  v = vn;
+}
+
+// One step of the asset pair (k, k + 1) from their variance uniforms (centred)
+// and spot uniforms' normals eps[0 .. k + 1]: z = Lc eps over the rows k, k + 1,
+// summed in column order as for one asset at a time.
+template <int NA>
+__device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const ScenPair& c, int k, float2 xv,
+                                                 const float (&eps)[NA], float2& v, float2& x, float2& comp) {
+  const float* ra = L.Lc + k * (k + 1) / 2;
+  const float* rb = ra + k + 1;  // row k + 1
+  float2 z = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    if (j > k) break;
+    z = p_fma(make_float2(ra[j], rb[j]), p_bc(eps[j]), z);
+  }
+  z.y = __fmaf_rn(rb[k + 1], eps[k + 1], z.y);
+  const float2 zv = norminv_centered2(xv);
+  step_pair(c, make_float2(0.5f * (1.0f - xv.x), 0.5f * (1.0f - xv.y)), zv, z, v, x, comp);
+}
+
+// One step of the lone last asset k of an odd count (k only known at run
+// time, its state in plain registers) from its variance uniform (centred), the
+// pairs' eps[0 .. k - 1] and its own e, as one lane of basket_pair_step.
+template <int NA>
+__device__ __forceinline__ void basket_lone_step(const BasketLaunch& L, int k, float xv, const float (&eps)[NA],
+                                                 float e, float& v, float& x, float& comp) {
+  const float* ra = L.Lc + k * (k + 1) / 2;
+  float z = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NA; ++j)
+    if (j < k) z = __fmaf_rn(ra[j], eps[j], z);
+  z = __fmaf_rn(ra[k], e, z);
+  step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v, x, comp);
+}
+
 template <int NA, int TILE>
 __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_constant__ BasketLaunch L,
                                                                    const double* __restrict__ strikes,
                                                                    BasketOutputs out, double* __restrict__ partials,
                                                                    unsigned int* __restrict__ ticket) {
+  static_assert(NA % 2 == 0, "assets are stepped in pairs");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warps = blockDim.x / kWarp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -48,6 +123,7 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
 
   const bool put = L.is_put != 0;
   const int na = L.n_assets;
+  const int kl = na - 1;  // the lone last asset when na is odd
   double* my_acc = acc + (size_t)warp * row;
   const uint64_t batches = (L.paths + kWarp - 1) / kWarp;
   const uint64_t total_warps = (uint64_t)gridDim.x * warps;
@@ -55,46 +131,67 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
     const uint64_t path = bt * kWarp + lane;
     const bool active = path < L.paths;
     const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
-    float v[NA], x[NA], comp[NA], eps[NA];
+    float2 v[NA / 2], x[NA / 2], comp[NA / 2];  // the pairs
+    float eps[NA];
     uint32_t wz[NA], ww[NA];  // the odd step's words of each asset
+    float vl = L.sc[kl].v0, xl = 0.0f, cl = 0.0f;  // the lone asset (odd counts)
+    uint32_t wzl = 0u, wwl = 0u;
 #pragma unroll
-    for (int k = 0; k < NA; ++k) {
-      v[k] = L.sc[k].v0;
-      x[k] = 0.0f;
-      comp[k] = 0.0f;
+    for (int q = 0; q < NA / 2; ++q) {
+      v[q] = make_float2(L.sc[2 * q].v0, L.sc[2 * q + 1].v0);
+      x[q] = make_float2(0.0f, 0.0f);
+      comp[q] = make_float2(0.0f, 0.0f);
     }
     for (uint32_t p = 0; 2 * p < L.steps; ++p) {
-      // even step 2p: draw each asset's words, correlate, step in asset order
+      // even step 2p: draw each pair's words, correlate, step in pair order (an
+      // odd count's last asset alone)
 #pragma unroll
-      for (int k = 0; k < NA; ++k) {
-        if (k >= na) break;
-        const uint4 w = philox4x32_10(p, plo, phi, (uint32_t)k, L.rk);
-        wz[k] = w.z;
-        ww[k] = w.w;
-        eps[k] = norminv_centered(centered_uniform(w.y));
-        float z = 0.0f;
-#pragma unroll
-        for (int j = 0; j <= k; ++j) z = fmaf(L.Lc[k * (k + 1) / 2 + j], eps[j], z);
-        const float xv = centered_uniform(w.x);
-        step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v[k], x[k], comp[k]);
+      for (int q = 0; q < NA / 2; ++q) {
+        const int k = 2 * q;
+        if (k + 1 >= na) break;
+        const uint4 wa = philox4x32_10(p, plo, phi, (uint32_t)k, L.rk);
+        const uint4 wb = philox4x32_10(p, plo, phi, (uint32_t)(k + 1), L.rk);
+        wz[k] = wa.z;
+        ww[k] = wa.w;
+        wz[k + 1] = wb.z;
+        ww[k + 1] = wb.w;
+        const float2 e = norminv_centered2(make_float2(centered_uniform(wa.y), centered_uniform(wb.y)));
+        eps[k] = e.x;
+        eps[k + 1] = e.y;
+        basket_pair_step<NA>(L, scen_pair(L.sc[k], L.sc[k + 1]), k,
+                             make_float2(centered_uniform(wa.x), centered_uniform(wb.x)), eps, v[q], x[q], comp[q]);
+      }
+      if (na & 1) {
+        const uint4 w = philox4x32_10(p, plo, phi, (uint32_t)kl, L.rk);
+        wzl = w.z;
+        wwl = w.w;
+        basket_lone_step<NA>(L, kl, centered_uniform(w.x), eps, norminv_centered(centered_uniform(w.y)), vl, xl, cl);
       }
       if (2 * p + 1 < L.steps) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-          if (k >= na) break;
-          eps[k] = norminv_centered(centered_uniform(ww[k]));
-          float z = 0.0f;
-#pragma unroll
-          for (int j = 0; j <= k; ++j) z = fmaf(L.Lc[k * (k + 1) / 2 + j], eps[j], z);
-          const float xv = centered_uniform(wz[k]);
-          step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v[k], x[k], comp[k]);
+        for (int q = 0; q < NA / 2; ++q) {
+          const int k = 2 * q;
+          if (k + 1 >= na) break;
+          const float2 e = norminv_centered2(make_float2(centered_uniform(ww[k]), centered_uniform(ww[k + 1])));
+          eps[k] = e.x;
+          eps[k + 1] = e.y;
+          basket_pair_step<NA>(L, scen_pair(L.sc[k], L.sc[k + 1]), k,
+                               make_float2(centered_uniform(wz[k]), centered_uniform(wz[k + 1])), eps, v[q], x[q],
+                               comp[q]);
         }
+        if (na & 1)
+          basket_lone_step<NA>(L, kl, centered_uniform(wzl), eps, norminv_centered(centered_uniform(wwl)), vl, xl,
+                               cl);
       }
     }
     float B = 0.0f;  // sum_k w_k S0_k e^{x_k}
 #pragma unroll
-    for (int k = 0; k < NA; ++k)
-      if (k < na) B += terminal_spot(L.S0w[k], x[k], comp[k]);
+    for (int q = 0; q < NA / 2; ++q) {
+      if (2 * q + 1 >= na) break;
+      B += terminal_spot(L.S0w[2 * q], x[q].x, comp[q].x);
+      B += terminal_spot(L.S0w[2 * q + 1], x[q].y, comp[q].y);
+    }
+    if (na & 1) B += terminal_spot(L.S0w[kl], xl, cl);
 
     if (TILE == 1) {
       const float f = active ? (put ? fmaxf(ks[0] - B, 0.0f) : fmaxf(B - ks[0], 0.0f)) : 0.0f;
