@@ -24,7 +24,7 @@ struct simr_ctx {
   double* partials = nullptr;
   size_t partial_doubles = 0;
   // 256-byte block: ticket word at 0, status word at 64, batch queue counter at
-  // 128, Longstaff-Schwartz ticket at 192, its sweep barrier words at 208 and 224
+  // 128, Longstaff-Schwartz ticket at 192, its sweep barrier counter at 208
   unsigned int* ticket = nullptr;
   int scheme = SIMR_SCHEME_QE;  // log-spot scheme of the path simulations (simr_set_scheme)
   float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]

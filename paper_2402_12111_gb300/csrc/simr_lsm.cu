@@ -541,36 +541,33 @@ constexpr int kSweepParts = 48;             // threads per quantity in the cross
 constexpr unsigned kSpinLimit = 1u << 23;   // barrier polls (>= 32 ns apart after 2048): ~0.3 s, then the wait gives up
 
 struct LsmSweep {
-  unsigned int* count;  // arrivals at the current barrier
-  unsigned int* gen;    // barrier generation
+  unsigned int* count;  // arrivals at all barriers so far (zeroed before the launch)
   int* status;          // bit 1: a barrier wait timed out (results invalid)
   float2* rows;         // [2][grid][kNReg]
 };
 
-// Grid-wide barrier of the cooperative sweep, bounded: a wait that exceeds
-// kSpinLimit polls sets status bit 1 and returns false, and every later barrier
-// returns false at once, so all blocks leave within one time-out.
-__device__ bool lsm_grid_sync(const LsmSweep& Y, int* s_flag) {
+// Grid-wide barrier number `nb` (0, 1, ...) of the cooperative sweep: every block
+// adds one arrival to a counter that is never reset during the launch and waits
+// until it reaches (nb + 1) blocks -- the last block to arrive has nothing more
+// to do, so the barrier costs one atomic and the polls.  Bounded: a wait that
+// exceeds kSpinLimit polls sets status bit 1 and returns false, and every later
+// barrier returns false at once, so all blocks leave within one time-out.
+__device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, int* s_flag) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = (*(volatile int*)Y.status & 2) == 0;
     if (ok) {
-      const unsigned g = *(volatile unsigned*)Y.gen;
-      if (atomicAdd(Y.count, 1u) == gridDim.x - 1) {
-        atomicExch(Y.count, 0u);
-        __threadfence();
-        atomicAdd(Y.gen, 1u);
-      } else {
-        unsigned it = 0;
-        while (*(volatile unsigned*)Y.gen == g) {
-          if (++it > kSpinLimit) {
-            atomicOr(Y.status, 2);
-            ok = 0;
-            break;
-          }
-          if (it > 2048) __nanosleep(32);
+      const unsigned target = (nb + 1u) * gridDim.x;
+      atomicAdd(Y.count, 1u);
+      unsigned it = 0;
+      while (*(volatile unsigned*)Y.count < target) {
+        if (++it > kSpinLimit) {
+          atomicOr(Y.status, 2);
+          ok = 0;
+          break;
         }
+        if (it > 2048) __nanosleep(32);
       }
       __threadfence();
     }
@@ -636,6 +633,9 @@ __device__ __forceinline__ void sweep_total(const float2* rows, int nv, DF* s_pa
 template <int M>
 __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_constant__ LsmLaunch L,
                                                                  const LsmBuffers B, const LsmSweep Y) {
+  // the states the regression of a date loads, kept for the next date's rule:
+  // [M][thread] S, then [M][thread] v (dynamic shared memory)
+  extern __shared__ float s_keep[];
   __shared__ float s_w[kSweepWarps][kNReg];
   __shared__ DF s_part[kSweepParts * kNReg];
   __shared__ DF s_tot[kNReg];
@@ -664,19 +664,16 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     const bool regress = d >= 1;
     const int nv = regress ? kNReg : 2;
     // date d's rule (no coefficients at the maturity)
-    if (s_has) {
+    if (s_has) {  // (a rule exists only below the last date: date d's states are in s_keep)
       float bj[kNB];
 #pragma unroll
       for (int k = 0; k < kNB; ++k) bj[k] = s_beta[k];
       const float4 tj = B.xform[d];
-      const float* Sd = B.S + (size_t)d * P;
-      const float* Vd = B.V + (size_t)d * P;
       float Su[M], Vu[M];
 #pragma unroll
-      for (int m = 0; m < M; ++m) {  // all loads first
-        const uint64_t i = g0 + (uint64_t)m * gt;
-        Su[m] = i < P ? __ldcg(Sd + i) : 0.0f;
-        Vu[m] = i < P ? __ldcg(Vd + i) : 0.0f;
+      for (int m = 0; m < M; ++m) {
+        Su[m] = s_keep[m * kSweepTpb + threadIdx.x];
+        Vu[m] = s_keep[(M + m) * kSweepTpb + threadIdx.x];
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) {
@@ -700,6 +697,11 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
         const uint64_t i = g0 + (uint64_t)m * gt;
         Sn[m] = i < P ? __ldcg(Sr + i) : 0.0f;
         Vn[m] = i < P ? __ldcg(Vr + i) : 0.0f;
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {  // this thread's own slots: no barrier needed before the next date reads them
+        s_keep[m * kSweepTpb + threadIdx.x] = Sn[m];
+        s_keep[(M + m) * kSweepTpb + threadIdx.x] = Vn[m];
       }
       if (d >= 2) {  // the date after next into L2 while this one is reduced and solved
         const float* Sp = B.S + (size_t)(d - 2) * P;
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     __syncthreads();
     float2* rows = Y.rows + (size_t)(d & 1) * gridDim.x * kNReg;
     sweep_block_row(s_w, nv, s_part, rows + (size_t)blockIdx.x * kNReg);
-    if (!lsm_grid_sync(Y, &s_flag)) return;
+    if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), &s_flag)) return;
     sweep_total(rows, nv, s_part, s_tot);
     if (regress) {
       // every block: the same solve; block 0 records the coefficients
@@ -814,8 +816,11 @@ namespace {
 template <int M>
 cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
                         bool* used) {
+  const size_t smem = (size_t)2 * M * kSweepTpb * sizeof(float);  // s_keep
+  cudaError_t e = cudaFuncSetAttribute(lsm_sweep_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsm_sweep_kernel<M>, kSweepTpb, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsm_sweep_kernel<M>, kSweepTpb, smem);
   if (e != cudaSuccess || per_sm < 1) return e;
   const uint64_t resident = (uint64_t)num_sms * per_sm;
   const uint64_t per_block = (uint64_t)M * kSweepTpb;
@@ -828,7 +833,7 @@ cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep&
   LsmBuffers Bc = B;
   LsmSweep Yc = Y;
   void* args[] = {&Lc, &Bc, &Yc};
-  e = cudaLaunchCooperativeKernel((const void*)lsm_sweep_kernel<M>, dim3(grid), dim3(kSweepTpb), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)lsm_sweep_kernel<M>, dim3(grid), dim3(kSweepTpb), args, smem, st);
   if (e == cudaSuccess) *used = true;
   return e;
 }
@@ -868,7 +873,7 @@ cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cud
   if (e != cudaSuccess) return e;
 
   bool swept = false;
-  const LsmSweep Y{B.ticket + 4, B.ticket + 8, B.status, reinterpret_cast<float2*>(B.partials)};
+  const LsmSweep Y{B.ticket + 4, B.status, reinterpret_cast<float2*>(B.partials)};
   e = try_sweep(L, B, Y, num_sms, stream, &swept);
   if (e != cudaSuccess || swept) return e;
 
