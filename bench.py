@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-headline", action="store_true",
                     help="skip the 8-underlying, 1,024-step, 2^26-path adjoint vs bump-and-revalue leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
-    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "lsm"],
+    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "lsm", "basket"],
                     help="only run one call W + K times on the workload (for profilers); prints no JSON")
     return ap.parse_args()
 
@@ -92,11 +92,16 @@ def measured_peaks():
         return {}
 
 
+# The sources the bench step's kernel (heston_paths_kernel) is compiled from.
+PATH_KERNEL_SOURCES = ("paper_2402_12111_gb300/csrc/simr_paths.cu", "paper_2402_12111_gb300/csrc/simr_device.cuh",
+                       "paper_2402_12111_gb300/csrc/simr_reduce.cuh", "paper_2402_12111_gb300/csrc/simr_internal.h",
+                       "include/simr.h")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2402_12111_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
+    for name in PATH_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -248,6 +253,11 @@ def run_profile_leg(args):
     if args.profile_leg == "book":
         opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))
         fn = lambda: simr.batch(opts, seed=1, adjoint=True, autotune=False)  # noqa: E731
+    elif args.profile_leg == "basket":
+        bm, C, wts, kb, bsteps, bpaths = workloads.basket()
+        Kb = torch.as_tensor(kb, dtype=torch.float64, device="cuda")
+        n = args.paths or bpaths
+        fn = lambda: simr.basket_price(bm, C, wts, Kb, False, bsteps, n, 1)  # noqa: E731
     elif args.profile_leg == "lsm":
         lw = workloads.lsm()
         n = args.paths or lw.paths
@@ -356,6 +366,9 @@ def run_native(args):
             "fd7_ms": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=fd7,
                                              rel_bump=w.rel_bump),
             "adjoint_ms": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed),
+            # the same with a checkpoint every 16 steps (shared-memory segments, forward pass)
+            "adjoint_k16_ms": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed,
+                                                          ckpt_every=16),
         }
         adj = {}
         reps = max(3, min(args.steps, 10))
@@ -394,6 +407,7 @@ def run_native(args):
         adj["qem_cost_vs_qe"] = adj["price_qem_ms"] / adj["price_ms"]
         adj["speedup_vs_fd"] = adj["fd7_ms"] / adj["adjoint_ms"]
         adj["cost_vs_price"] = adj["adjoint_ms"] / adj["price_ms"]
+        adj["k16_cost_vs_price"] = adj["adjoint_k16_ms"] / adj["price_ms"]
         adj["ckpt_every"] = simr.adjoint_interval(len(w.strikes), w.steps, dev.index or 0)  # the library's choice
         adj["sensitivities"] = list(fd7)
 
@@ -445,18 +459,9 @@ def run_native(args):
     # 32 strikes on the equally weighted basket
     basket = None
     if not args.no_book:
-        bm = workloads.random_models(8, 31)
-        for m in bm:
-            m["T"], m["r"] = 1.0, 0.03
-        rng = np.random.default_rng(31)
-        G = rng.standard_normal((8, 10))
-        C = G @ G.T
-        C = C / np.sqrt(np.outer(np.diag(C), np.diag(C)))
-        C = 0.5 * (C + C.T)
-        np.fill_diagonal(C, 1.0)
-        wts = np.full(8, 1.0 / 8)
-        Kb = torch.as_tensor(100.0 * workloads.strike_grid() / 100.0, dtype=torch.float64, device=dev)
-        call = lambda: simr.basket_price(bm, C, wts, Kb, False, 252, 1 << 20, 1)  # noqa: E731
+        bm, C, wts, kb, bsteps, bpaths = workloads.basket()
+        Kb = torch.as_tensor(kb, dtype=torch.float64, device=dev)
+        call = lambda: simr.basket_price(bm, C, wts, Kb, False, bsteps, bpaths, 1)  # noqa: E731
         call()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -487,6 +492,9 @@ def run_native(args):
             "price": lambda u, k: simr.price(u.model, k, u.is_put, u.steps, u.paths, u.seed),
             "adjoint": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
                                                         ckpt_every=u.ckpt_every),
+            # the same with a checkpoint every 32 steps (shared-memory segments, forward pass)
+            "adjoint_k32": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
+                                                            ckpt_every=32),
             "fd7": lambda u, k: simr.greeks_fd(u.model, k, u.is_put, u.steps, u.paths, u.seed, greeks=fd7,
                                                rel_bump=u.rel_bump),
         }
@@ -506,6 +514,7 @@ def run_native(args):
             head[f"{name}_path_steps_per_s"] = ps_head / sec
         head["adjoint_speedup_vs_fd"] = head["fd7_s"] / head["adjoint_s"]
         head["adjoint_cost_vs_price"] = head["adjoint_s"] / head["price_s"]
+        head["adjoint_k32_cost_vs_price"] = head["adjoint_k32_s"] / head["price_s"]
 
     # Longstaff-Schwartz Bermudan put (252 steps, exercisable after every step, 2^20
     # paths): the path kernel, then the backward induction (one cooperative sweep

@@ -173,16 +173,21 @@ SIMR_API int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const doubl
  * the QE map where a bump would switch a path's branch, so they differ from
  * bump-and-revalue by that (small) term.
  *   ckpt_every   in   even number of steps per checkpoint segment, in [2, 1024];
- *                     0 = the library's choice for speed: the forward pass runs
- *                     all segments but the last, so it takes, among the even
- *                     intervals whose shared memory keeps the kernel's blocks
- *                     per SM (found once per context by the occupancy API), the
- *                     one with the longest last segment; values above steps act
- *                     as steps (rounded up to even).  Each resident thread keeps
+ *                     values above steps act as steps (rounded up to even): one
+ *                     segment, no forward pass.  Each resident thread keeps
  *                     steps/ckpt_every checkpoints in a context-owned device
- *                     buffer (at most 2^30 floats in all) and 3 ckpt_every
- *                     floats of shared memory (at most 200 KB per 128-thread
- *                     block with the accumulators); SIMR_EUNSUPPORTED beyond.
+ *                     buffer (at most 2^30 floats in all) and a segment buffer
+ *                     of 3 ckpt_every floats: in shared memory while a
+ *                     128-thread block's buffers and accumulators fit 200 KB,
+ *                     else in a context-owned device buffer (at most 2^31
+ *                     floats in all; SIMR_EUNSUPPORTED beyond).
+ *                     0 = the library's choice for speed (the forward pass runs
+ *                     all segments but the last): one segment of the whole
+ *                     path when its buffer fits shared memory or 2^30 floats of
+ *                     device memory; else, among the even intervals whose
+ *                     shared memory keeps the kernel's blocks per SM (found
+ *                     once per context by the occupancy API), the one with the
+ *                     longest last segment.
  *   price[n_strikes], stderr_out[n_strikes] (nullable)   out
  *   grad[n_strikes * 7]   out  row-major [strike][S0, v0, kappa, theta, sigma, rho, r]
  * n_strikes in [1, 256].  The rho column is NaN when |rho| = 1 (the pathwise

@@ -32,13 +32,15 @@ namespace {
 #define SIMR_ADJ_PPT 1  // paths per thread of the per-strike adjoint kernel (2 measured slower)
 #endif
 // Dynamic shared memory of the per-strike kernel: strike constants, the
-// last-block flag, then the segment buffers; the per-warp FP64 accumulator rows
-// come first when they live in shared memory throughout (RACC false), or reuse
-// the segment buffers' space once the path loop has ended (RACC true: lane l
-// accumulates strike l of the one 32-strike tile in registers).
-inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int tpb, int ppt, bool racc) {
+// last-block flag, then the segment buffers (none when they are in global
+// memory, GSEG); the per-warp FP64 accumulator rows come first when they live in
+// shared memory throughout (RACC false), or reuse the segment buffers' space
+// once the path loop has ended (RACC true: lane l accumulates strike l of the
+// one 32-strike tile in registers).
+inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int tpb, int ppt, bool racc,
+                                   bool gseg = false) {
   const size_t acc_bytes = (size_t)(tpb / kWarp) * kAdjAcc * L.nk_pad * sizeof(double);
-  const size_t buf_bytes = adjoint_seg_floats(A, ppt) * tpb * sizeof(float);
+  const size_t buf_bytes = gseg ? 0 : adjoint_seg_floats(A, ppt) * tpb * sizeof(float);
   const size_t head = L.nk_pad * sizeof(StrikeConst) + 16;
   return racc ? head + (buf_bytes > acc_bytes ? buf_bytes : acc_bytes) : acc_bytes + head + buf_bytes;
 }
@@ -47,13 +49,16 @@ inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int t
 #define SIMR_ADJ_MINB 1  // minimum resident blocks per SM requested from the register allocator
 #endif
 
-template <int TILE, int PPT, bool RACC>
+// GSEG: the segment buffers in global memory, [3 k][grid threads] (for a
+// segment too long for shared memory, in particular one segment of the whole
+// path: no forward pass).
+template <int TILE, int PPT, bool RACC, bool GSEG>
 __global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
                                                              double* __restrict__ partials,
                                                              unsigned int* __restrict__ ticket,
-                                                             float* __restrict__ gckpt) {
+                                                             float* __restrict__ gckpt, float* __restrict__ gseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warps = blockDim.x / kWarp;
   const int bd = blockDim.x;
@@ -68,7 +73,6 @@ __global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(cons
   // checkpoints: this thread's column of a [slot][grid threads] global array
   float* ck = gckpt + (int)blockIdx.x * bd + tid;
   const int ck_stride = (int)(gridDim.x * blockDim.x);
-  float* seg = sbuf;  // the block's segment buffer (16-byte aligned)
   double racc[RACC ? kAdjAcc : 1];
 #pragma unroll
   for (int a = 0; a < (RACC ? kAdjAcc : 1); ++a) racc[a] = 0.0;
@@ -101,8 +105,13 @@ __global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(cons
       pth[j] = L.path_begin + local;
     }
     float x[PPT], comp[PPT], g[PPT][5], S[PPT];
-    path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride, seg, A.ckpt_every, bd, x,
-                          comp, g);
+    if constexpr (GSEG)
+      path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
+                            SegGlobal{gseg, (long long)blockIdx.x * bd + tid, A.ckpt_every, (long long)ck_stride},
+                            x, comp, g);
+    else
+      path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
+                            SegShared{sbuf, A.ckpt_every}, x, comp, g);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
@@ -205,35 +214,56 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   float x[1], comp[1], g[1][5];
   const uint64_t pth[1] = {L.path_begin + i};
   path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt + tid, bd,
-                      ckpt + (A.n_seg - 1) * bd, A.ckpt_every, bd, x, comp, g);
+                      SegShared{ckpt + (A.n_seg - 1) * bd, A.ckpt_every}, x, comp, g);
   x_T[i] = x[0] - comp[0];
 #pragma unroll
   for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];
 }
 
-template <int TILE, bool RACC>
-cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
-                             const Scratch& s, int num_sms, cudaStream_t stream) {
+// The grid of the per-strike kernel variant (resident blocks, at most what the
+// paths need) and its dynamic shared memory.
+template <int TILE, bool RACC, bool GSEG>
+cudaError_t adjoint_grid_t(const PathLaunch& L, const AdjConst& A, int num_sms, uint64_t* grid, size_t* smem) {
   constexpr int PPT = SIMR_ADJ_PPT;
   const int tpb = 128, warps = tpb / kWarp;
-  const size_t row = (size_t)kAdjAcc * L.nk_pad;
-  const size_t smem = adjoint_smem_bytes_t(L, A, tpb, PPT, RACC);
-  auto kern = heston_adjoint_kernel<TILE, PPT, RACC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  *smem = adjoint_smem_bytes_t(L, A, tpb, PPT, RACC, GSEG);
+  auto kern = heston_adjoint_kernel<TILE, PPT, RACC, GSEG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, *smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t batches = (L.path_count + (uint64_t)kWarp * PPT - 1) / ((uint64_t)kWarp * PPT);
-  uint64_t grid = (uint64_t)num_sms * per_sm;
+  uint64_t g = (uint64_t)num_sms * per_sm;
   const uint64_t need = (batches + warps - 1) / warps;
-  if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
+  if (g > need) g = need;
+  *grid = g < 1 ? 1 : g;
+  return cudaSuccess;
+}
+
+template <int TILE, bool RACC, bool GSEG>
+cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
+                             const Scratch& s, int num_sms, cudaStream_t stream) {
+  constexpr int PPT = SIMR_ADJ_PPT;
+  const int tpb = 128;
+  const size_t row = (size_t)kAdjAcc * L.nk_pad;
+  uint64_t grid = 0;
+  size_t smem = 0;
+  cudaError_t e = adjoint_grid_t<TILE, RACC, GSEG>(L, A, num_sms, &grid, &smem);
+  if (e != cudaSuccess) return e;
   if ((size_t)grid * row > s.partial_doubles) return cudaErrorMemoryAllocation;
   if ((size_t)grid * tpb * adjoint_ckpt_floats(A, PPT) > s.ckpt_floats) return cudaErrorMemoryAllocation;
-  kern<<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket, s.ckpt);
+  if (GSEG && (size_t)grid * tpb * adjoint_seg_floats(A, PPT) > s.gseg_floats) return cudaErrorMemoryAllocation;
+  heston_adjoint_kernel<TILE, PPT, RACC, GSEG>
+      <<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket, s.ckpt, s.gseg);
   return cudaGetLastError();
+}
+
+// Whether the segment buffers go to global memory: when 3 k floats per thread
+// do not fit the shared memory of a block.
+bool adjoint_gseg(const PathLaunch& L, const AdjConst& A) {
+  return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32) > kAdjMaxSmem;
 }
 
 }  // namespace
@@ -245,9 +275,9 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
 cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_max) {
   // the kernel variant launch_adjoint picks for this strike count
   const bool racc = L.nk_pad == 32;
-  const void* kern = L.nk_pad == 1 ? (const void*)heston_adjoint_kernel<1, SIMR_ADJ_PPT, false>
-                     : racc      ? (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, true>
-                                 : (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, false>;
+  const void* kern = L.nk_pad == 1 ? (const void*)heston_adjoint_kernel<1, SIMR_ADJ_PPT, false, false>
+                     : racc      ? (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, true, false>
+                                 : (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, false, false>;
   auto blocks = [&](int k, int* n) -> cudaError_t {
     AdjConst A{};
     A.ckpt_every = k;
@@ -275,7 +305,19 @@ cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_ma
 }
 
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A) {
-  return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32);
+  return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32, adjoint_gseg(L, A));
+}
+
+cudaError_t adjoint_gseg_floats(const PathLaunch& L, const AdjConst& A, int num_sms, size_t* floats) {
+  *floats = 0;
+  if (!adjoint_gseg(L, A)) return cudaSuccess;
+  uint64_t grid = 0;
+  size_t smem = 0;
+  cudaError_t e = L.nk_pad == 1    ? adjoint_grid_t<1, false, true>(L, A, num_sms, &grid, &smem)
+                  : L.nk_pad == 32 ? adjoint_grid_t<32, true, true>(L, A, num_sms, &grid, &smem)
+                                   : adjoint_grid_t<32, false, true>(L, A, num_sms, &grid, &smem);
+  if (e == cudaSuccess) *floats = (size_t)grid * 128 * adjoint_seg_floats(A, SIMR_ADJ_PPT);
+  return e;
 }
 
 size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms) {
@@ -296,9 +338,14 @@ cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* 
 
 cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                            const Scratch& s, int num_sms, cudaStream_t stream) {
-  if (L.nk_pad == 1) return launch_adjoint_t<1, false>(L, A, strikes, out, s, num_sms, stream);
-  if (L.nk_pad == 32) return launch_adjoint_t<32, true>(L, A, strikes, out, s, num_sms, stream);
-  return launch_adjoint_t<32, false>(L, A, strikes, out, s, num_sms, stream);
+  if (adjoint_gseg(L, A)) {
+    if (L.nk_pad == 1) return launch_adjoint_t<1, false, true>(L, A, strikes, out, s, num_sms, stream);
+    if (L.nk_pad == 32) return launch_adjoint_t<32, true, true>(L, A, strikes, out, s, num_sms, stream);
+    return launch_adjoint_t<32, false, true>(L, A, strikes, out, s, num_sms, stream);
+  }
+  if (L.nk_pad == 1) return launch_adjoint_t<1, false, false>(L, A, strikes, out, s, num_sms, stream);
+  if (L.nk_pad == 32) return launch_adjoint_t<32, true, false>(L, A, strikes, out, s, num_sms, stream);
+  return launch_adjoint_t<32, false, false>(L, A, strikes, out, s, num_sms, stream);
 }
 
 }  // namespace simr

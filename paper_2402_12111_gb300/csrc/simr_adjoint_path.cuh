@@ -8,6 +8,10 @@
 #include "simr_device.cuh"
 #include "simr_internal.h"
 
+#ifndef SIMR_ADJ_PREFETCH
+#define SIMR_ADJ_PREFETCH 4  // steps ahead the reverse sweep asks global segment data into L2 (4-32 within 2%)
+#endif
+
 namespace simr {
 namespace {
 
@@ -119,6 +123,29 @@ __device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, float 
   v = qe_only(c, v, omu, zv);
 }
 
+// A thread's column of a segment buffer of `stride` columns (8-byte aligned):
+// `rows` (state, draw) float2 pairs at pairs[i * stride], then `rows` Z_X floats
+// at zx[i * stride].  SegShared: the block's buffer in shared memory, column
+// threadIdx.x of blockDim.x; SegGlobal: a grid-wide buffer in global memory,
+// column `col` (the thread's index in the grid) of `stride`.
+struct SegShared {
+  static constexpr bool kGlobal = false;
+  float* base;
+  int rows;
+  __device__ __forceinline__ int stride() const { return (int)blockDim.x; }
+  __device__ __forceinline__ float2* pairs() const { return reinterpret_cast<float2*>(base) + threadIdx.x; }
+  __device__ __forceinline__ float* zx() const { return base + 2 * rows * (int)blockDim.x + threadIdx.x; }
+};
+
+struct SegGlobal {
+  static constexpr bool kGlobal = true;
+  float* base;
+  long long col, rows, cols;
+  __device__ __forceinline__ long long stride() const { return cols; }
+  __device__ __forceinline__ float2* pairs() const { return reinterpret_cast<float2*>(base) + col; }
+  __device__ __forceinline__ float* zx() const { return base + 2 * rows * cols + col; }
+};
+
 // The FP64 map of the sweep's sums onto d x_T / d(v0, kappa, theta, sigma, rho).
 __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a, float (&g)[5]) {
   const double Amv = a.Amv, Asv = a.Asv, As = a.As, Ad = a.Ad, Adl = a.Adl, Am = a.Am, Ak3 = a.Ak3;
@@ -133,28 +160,29 @@ __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a,
 // states are recomputed from its checkpoint (the last checkpoint is v_last, the
 // forward pass's final state; earlier ones ck[slot * cstride], each loaded a
 // segment ahead of its use) and kept with the step's branch draw and Z_X in this
-// thread's column of the block's shared segment buffer at seg (8-byte aligned,
-// bd columns, krows >= k rows per array, the same for every thread of the block):
-// (state, draw) pairs as a float2 array [i][column], then Z_X as a float array
-// [i][column] -- then the steps are differentiated backwards.  x_T (with its Kahan remainder)
-// is summed on the way; g = d x_T / d(v0, kappa, theta, sigma, rho).
+// thread's segment column S (at least k rows) -- then the steps are
+// differentiated backwards.  x_T (with its Kahan remainder) is summed on the
+// way; g = d x_T / d(v0, kappa, theta, sigma, rho).
+template <typename Seg>
 __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                            const uint32_t (&rk)[10][2], uint32_t plo, uint32_t phi,
-                                           const float* ck, int cstride, float v_last, float* seg, int krows, int bd,
+                                           const float* ck, int cstride, float v_last, const Seg& S,
                                            float& x_out, float& comp_out, float (&g)[5]) {
+  using I = decltype(S.stride());
   const float theta = A.theta;
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
   AdjSums as = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  float2* s01 = reinterpret_cast<float2*>(seg) + threadIdx.x;  // (state, draw) [i * bd]
-  float* s2 = seg + 2 * krows * bd + threadIdx.x;                // Z_X [i * bd]
+  float2* s01 = S.pairs();
+  float* s2 = S.zx();
+  const I bd = S.stride();
   float ck_next = v_last;
   for (int sgi = n_seg - 1; sgi >= 0; --sgi) {
     const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
     float vv = ck_next;
     if (sgi > 0) ck_next = ck[(sgi - 1) * cstride];
     for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
-      const int i = (int)(2 * p - n0) * bd;
+      const I i = (I)(2 * p - n0) * bd;
       const uint4 w = philox4x32_10(p, plo, phi, option, rk);
       const float xa = centered_uniform(w.x), xb = centered_uniform(w.z);
       const float2 zv = norminv_centered2(make_float2(xa, xb));  // the pair's normals two at a time
@@ -163,10 +191,33 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
       if (2 * p + 1 < n1) keep_step(c, xb, zv.y, zx.y, s01 + i + bd, s2 + i + bd, vv);
     }
     float vnext = vv;  // v_{n1}
-    for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-      const float2 vd = s01[i * bd];
-      adjoint_step(c, theta, vd.x, vnext, vd.y, s2[i * bd], as);
-      vnext = vd.x;
+    if constexpr (Seg::kGlobal) {
+      // global memory: each step's data loaded one step ahead into registers,
+      // and asked into L2 kPrefetchSteps steps ahead
+      constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
+      int i = (int)(n1 - n0) - 1;
+      float2 vd_n = s01[(I)i * bd];
+      float zx_n = s2[(I)i * bd];
+      for (; i >= 0; --i) {
+        const float2 vd = vd_n;
+        const float zx = zx_n;
+        if (i >= kPrefetchSteps) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - kPrefetchSteps) * bd));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - kPrefetchSteps) * bd));
+        }
+        if (i > 0) {
+          vd_n = s01[(I)(i - 1) * bd];
+          zx_n = s2[(I)(i - 1) * bd];
+        }
+        adjoint_step(c, theta, vd.x, vnext, vd.y, zx, as);
+        vnext = vd.x;
+      }
+    } else {
+      for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
+        const float2 vd = s01[(I)i * bd];
+        adjoint_step(c, theta, vd.x, vnext, vd.y, s2[(I)i * bd], as);
+        vnext = vd.x;
+      }
     }
   }
   x_out = as.x;
@@ -181,13 +232,12 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
 // paired (qe_from_moments2, lane for lane the scalar step); the reverse sweeps
 // then run one path at a time through the same shared segment buffer.
 // Checkpoint (slot, path j) of this thread at ck[(slot * PPT + j) * ck_stride]
-// (n_seg - 1 slots; shared or global memory); seg is the block's shared
-// segment buffer (bd columns of 3 krows floats, krows >= k the same for the
-// whole block, 8-byte aligned; this thread's column is threadIdx.x).
-template <int PPT>
+// (n_seg - 1 slots; shared or global memory); S is this thread's segment column
+// (shared or global memory, at least k rows).
+template <int PPT, typename Seg>
 __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                                  const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
-                                                 int ck_stride, float* seg, int krows, int bd, float (&x_out)[PPT],
+                                                 int ck_stride, const Seg& S, float (&x_out)[PPT],
                                                  float (&comp_out)[PPT], float (&g)[PPT][5]) {
   static_assert(PPT == 1 || PPT == 2, "one or two paths per thread");
   const uint32_t k = (uint32_t)A.ckpt_every;
@@ -234,8 +284,8 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
   }
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
-    path_sweep(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], seg, krows, bd,
-               x_out[j], comp_out[j], g[j]);
+    path_sweep(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], S, x_out[j],
+               comp_out[j], g[j]);
 }
 
 // Floats per thread of path_adjoint_ppt: checkpoints and the segment buffer.

@@ -29,6 +29,8 @@ struct simr_ctx {
   int scheme = SIMR_SCHEME_QE;  // log-spot scheme of the path simulations (simr_set_scheme)
   float* ckpt = nullptr;  // adjoint checkpoints, [slot][resident thread]
   size_t ckpt_floats = 0;
+  float* gseg = nullptr;  // adjoint segment buffers too long for shared memory, [3 k][resident thread]
+  size_t gseg_floats = 0;
   // Longstaff-Schwartz: states at the exercise dates, per-path cash flows,
   // coefficients, discount table
   float* lsm_S = nullptr;
@@ -694,6 +696,7 @@ void simr_destroy(simr_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->partials);
   cudaFree(ctx->ckpt);
+  cudaFree(ctx->gseg);
   cudaFree(ctx->lsm_S);
   cudaFree(ctx->lsm_V);
   cudaFree(ctx->lsm_cash);
@@ -780,10 +783,25 @@ int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strike
 // The checkpoint interval the per-strike adjoint runs fastest with.  Its
 // forward pass runs every segment but the last, (n_seg - 1) k = steps - (the
 // last segment's length) steps, while the recompute and reverse passes run all
-// steps whatever k is; so among the even k up to the largest that keeps the
-// kernel's blocks per SM, take the one with the longest last segment (the
+// steps whatever k is.  So: one segment of the whole path (no forward pass), in
+// shared memory if it fits there, else in global memory if its buffer is at
+// most kAdjAutoGsegFloats; otherwise, among the even k up to the largest that
+// keeps the kernel's blocks per SM, the one with the longest last segment (the
 // smallest k on a tie, for the least shared memory).
 int fast_ckpt_every(simr_ctx* ctx, const PathLaunch& L, uint32_t steps, uint32_t* k) {
+  const uint32_t one = steps + (steps & 1u);
+  if (one <= 1024) {
+    AdjConst A{};
+    A.ckpt_every = (int32_t)one;
+    A.n_seg = 1;
+    size_t floats = 0;
+    cudaError_t e = adjoint_gseg_floats(L, A, ctx->num_sms, &floats);
+    if (e != cudaSuccess) return cuda_fail(e, "sizing the adjoint's segment buffers");
+    if (floats <= kAdjAutoGsegFloats) {
+      *k = one;
+      return SIMR_OK;
+    }
+  }
   int k_max = 0;
   for (const auto& t : ctx->adj_k)
     if (t.nk_pad == L.nk_pad) k_max = t.k_max;
@@ -861,8 +879,16 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
     return rc;
   if ((rc = ensure(&ctx->ckpt, &ctx->ckpt_floats, adjoint_ckpt_scratch_floats(A, ctx->num_sms), "checkpoints")))
     return rc;
+  size_t gseg_need = 0;
+  cudaError_t eg = adjoint_gseg_floats(L, A, ctx->num_sms, &gseg_need);
+  if (eg != cudaSuccess) return cuda_fail(eg, "sizing the adjoint's segment buffers");
+  if (gseg_need > kAdjMaxGsegFloats)
+    return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more than 2^31 floats of segment buffers",
+                A.ckpt_every, steps);
+  if (gseg_need && (rc = ensure(&ctx->gseg, &ctx->gseg_floats, gseg_need, "segment buffers"))) return rc;
   AdjOutputs out{o.dev[0], o.dev[1], o.dev[2], ctx->status};
-  Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles, ctx->ckpt, ctx->ckpt_floats};
+  Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles, ctx->ckpt, ctx->ckpt_floats, ctx->gseg,
+             ctx->gseg_floats};
   cudaError_t e = launch_adjoint(L, A, ks, out, sc, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernel");
   return finish_outputs(ctx, o, st);

@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         // the block's layout: ckpt_rows checkpoint rows, then the segment
         // arrays of seg_rows rows (the largest over the book), so threads on
         // options with different checkpoint intervals never overlap
-        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd, smem_f + B.ckpt_rows * bd, B.seg_rows,
-                            bd, x, comp, g);
+        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
+                            SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;

@@ -121,6 +121,8 @@ struct Scratch {
   size_t partial_doubles;
   float* ckpt = nullptr;  // adjoint checkpoints in global memory
   size_t ckpt_floats = 0;
+  float* gseg = nullptr;  // adjoint segment buffers in global memory (segments too long for shared memory)
+  size_t gseg_floats = 0;
 };
 
 // Launch the fused price / Greeks kernel; returns a cudaError_t.
@@ -140,12 +142,19 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms);
 size_t adjoint_smem_bytes(const PathLaunch& L, const AdjConst& A);
 // Dynamic shared memory one block of an adjoint kernel may ask for.
 constexpr size_t kAdjMaxSmem = 200 * 1024;
+// Largest global segment buffer of the per-strike adjoint (8 GB), and the
+// largest the automatic interval takes (4 GB).
+constexpr size_t kAdjMaxGsegFloats = (size_t)1 << 31;
+constexpr size_t kAdjAutoGsegFloats = (size_t)1 << 30;
 // The largest even checkpoint interval (at most steps_cap, rounded up to even)
 // at which the per-strike adjoint kernel for L's strike count keeps the blocks
 // per SM it has at interval 2 (its register limit): each thread's segment
 // buffer is 3 k floats of shared memory.
 cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_max);
 size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms);
+// Floats of the global segment buffers the per-strike adjoint launch needs (0
+// when its segments fit in shared memory): 3 k per thread of its grid.
+cudaError_t adjoint_gseg_floats(const PathLaunch& L, const AdjConst& A, int num_sms, size_t* floats);
 // Per-path x_T and d x_T / d(v0, kappa, theta, sigma, rho) ([n][5]).
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream);
 

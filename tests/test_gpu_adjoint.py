@@ -112,6 +112,24 @@ def test_checkpoint_interval_does_not_change_results(simr):
                                    rtol=0, atol=0)
 
 
+def test_segments_in_global_memory(simr):
+    # intervals whose segment (3 k floats per thread) exceeds shared memory keep
+    # their segments in global memory: one segment of the whole path (no forward
+    # pass) or a few long ones; the same results bit for bit
+    K = _dev(workloads.strike_grid())
+    for steps, ks in ((200, (200, 150)), (301, (302, 160))):
+        ref = simr.greeks_adjoint(CFG, K, False, steps, 5003, 11, ckpt_every=16)
+        for k in ks:
+            got = simr.greeks_adjoint(CFG, K, False, steps, 5003, 11, ckpt_every=k)
+            for a, b in zip(got, ref):
+                torch.testing.assert_close(a, b, rtol=0, atol=0)
+    K1 = _dev([100.0])
+    ref = simr.greeks_adjoint(CFG, K1, True, 256, 4096, 2, ckpt_every=8)
+    got = simr.greeks_adjoint(CFG, K1, True, 256, 4096, 2, ckpt_every=256)
+    for a, b in zip(got, ref):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
 def test_automatic_interval(simr):
     # the interval taken for ckpt_every=0: even, one segment when it fits, the
     # same results as any explicit interval
@@ -120,7 +138,9 @@ def test_automatic_interval(simr):
         assert k % 2 == 0 and 2 <= k <= steps + (steps & 1), (nk, steps, k)
     assert simr.adjoint_interval(32, 7) == 8
     k = simr.adjoint_interval(32, 252)
-    assert k >= 16
+    assert k == 252  # one segment of the whole path, no forward pass
+    k2 = simr.adjoint_interval(32, 3000)  # longer than one segment may be: shared-memory segments
+    assert k2 % 2 == 0 and 2 <= k2 <= 200
     K = _dev(workloads.strike_grid())
     a = simr.greeks_adjoint(CFG, K, False, 252, 4096, 5, ckpt_every=0)
     b = simr.greeks_adjoint(CFG, K, False, 252, 4096, 5, ckpt_every=k)

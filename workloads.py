@@ -105,6 +105,23 @@ def book(n_options: int = 1024, seed: int = 1, steps_range=(16, 512), paths_rang
     return out
 
 
+def basket(n_assets: int = 8, seed: int = 31):
+    """Correlated basket: n_assets book-style models (T = 1, r = 0.03), a random
+    correlation (normalised Gram matrix of Gaussian rows), equal weights, the
+    32-strike grid, 252 steps, 2^20 paths.  Returns (models, corr, weights,
+    strikes, steps, paths)."""
+    models = random_models(n_assets, seed)
+    for m in models:
+        m["T"], m["r"] = 1.0, 0.03
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n_assets, n_assets + 2))
+    C = G @ G.T
+    C = C / np.sqrt(np.outer(np.diag(C), np.diag(C)))
+    C = 0.5 * (C + C.T)
+    np.fill_diagonal(C, 1.0)
+    return models, C, np.full(n_assets, 1.0 / n_assets), strike_grid(), 252, 1 << 20
+
+
 def headline(n_underlyings: int = 8, seed: int = 4):
     """8 underlyings with book-style parameters, each on the 32-strike grid,
     1,024 steps and 2^26 paths, the adjoint at the library's checkpoint interval."""
