@@ -557,7 +557,7 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
 
 // Per-option device records (caller's order) and the longest-first order.
 int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vector<BatchOption>* out,
-                        std::vector<uint32_t>* order, int* ckpt_rows, int* seg_rows) {
+                        bool one_segment, std::vector<uint32_t>* order, int* ckpt_rows, int* seg_rows) {
   out->resize(n);
   std::vector<double> cost(n);
   int crows = 0, srows = 0;
@@ -577,7 +577,9 @@ int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vecto
     std::memset(&b, 0, sizeof(b));
     b.sc = base_const(o.m, o.steps);
     if (adjoint) {
-      if ((rc = build_adjoint(o.m, o.steps, 0, &b.A))) return rc;
+      // one segment of the whole path (global segments), or the interval near
+      // sqrt(steps / 3) that needs the least shared memory
+      if ((rc = build_adjoint(o.m, o.steps, one_segment ? o.steps + (o.steps & 1u) : 0u, &b.A))) return rc;
       crows = std::max(crows, b.A.n_seg - 1);
       srows = std::max(srows, b.A.ckpt_every);
     }
@@ -1004,10 +1006,27 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<BatchOption> bo;
   std::vector<uint32_t> order;
+  // adjoint books: every option one segment of its whole path in global memory
+  // (no forward pass) when the longest fits 1,024 steps and the buffer
+  // kAdjAutoGsegFloats; else checkpoints and segments in shared memory
+  bool one_segment = false;
+  size_t gseg_floats = 0;
+  if (adjoint) {
+    uint32_t max_steps = 0;
+    for (int i = 0; i < n_opts; ++i) max_steps = std::max(max_steps, opts[i].steps);
+    if (max_steps >= 1 && max_steps <= 1024) {
+      size_t threads = 0;
+      cudaError_t eg = batch_gseg_threads(ctx->num_sms, &threads);
+      if (eg != cudaSuccess) return cuda_fail(eg, "sizing the book's segment buffers");
+      gseg_floats = (size_t)3 * (max_steps + (max_steps & 1u)) * threads;
+      one_segment = gseg_floats <= kAdjAutoGsegFloats;
+    }
+  }
   int ckpt_rows = 0, seg_rows = 0;
-  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, &order, &ckpt_rows, &seg_rows))) return rc;
-  if ((size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > kAdjMaxSmem)
+  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, one_segment, &order, &ckpt_rows, &seg_rows))) return rc;
+  if (!one_segment && (size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "the book's checkpoints need more shared memory than a block has");
+  if (one_segment && (rc = ensure(&ctx->gseg, &ctx->gseg_floats, gseg_floats, "segment buffers"))) return rc;
   BatchLaunch B;
   std::memset(&B, 0, sizeof(B));
   philox_round_keys(seed, B.rk);
@@ -1015,6 +1034,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   B.adjoint = adjoint ? 1 : 0;
   B.ckpt_rows = ckpt_rows;
   B.seg_rows = seg_rows;
+  B.gseg = one_segment ? ctx->gseg : nullptr;
   const int nacc = adjoint ? 9 : 2;
   OutStage o;
   o.user[0] = price;
@@ -1100,7 +1120,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     key = fnv1a(&out, sizeof(out), key);
     // the captured launches hold the context's device buffers: a reallocation
     // since the capture makes a new graph
-    const void* bufs[3] = {ctx->b_opts, ctx->b_items, ctx->b_partials};
+    const void* bufs[4] = {ctx->b_opts, ctx->b_items, ctx->b_partials, B.gseg};
     key = fnv1a(bufs, sizeof(bufs), key);
     if (!(ctx->graph_exec && ctx->graph_key == key)) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);

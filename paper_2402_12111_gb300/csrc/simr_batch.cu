@@ -21,7 +21,9 @@
 namespace simr {
 namespace {
 
-template <bool ADJ>
+// GSEG (adjoint books): every option is one segment of its whole path (no
+// forward pass), kept in a grid-wide buffer in global memory.
+template <bool ADJ, bool GSEG>
 __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
                                                            const BatchOption* __restrict__ opts,
                                                            const BatchItem* __restrict__ items,
@@ -57,8 +59,14 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         // the block's layout: ckpt_rows checkpoint rows, then the segment
         // arrays of seg_rows rows (the largest over the book), so threads on
         // options with different checkpoint intervals never overlap
-        path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
-                            SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
+        if constexpr (GSEG)  // one segment: no checkpoints are read or written
+          path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
+                              SegGlobal{B.gseg, (long long)blockIdx.x * bd + tid, B.seg_rows,
+                                        (long long)gridDim.x * bd},
+                              x, comp, g);
+        else
+          path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
+                              SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
@@ -117,33 +125,38 @@ __global__ void batch_reduce_kernel(const BatchOption* __restrict__ opts, uint32
 constexpr int kBatchTpb = 128;
 
 size_t batch_smem(const BatchLaunch& B) {
-  return B.adjoint ? (size_t)(B.ckpt_rows + 3 * B.seg_rows) * kBatchTpb * sizeof(float) : 0;
+  return B.adjoint && !B.gseg ? (size_t)(B.ckpt_rows + 3 * B.seg_rows) * kBatchTpb * sizeof(float) : 0;
 }
 
 }  // namespace
 
 cudaError_t prepare_batch(const BatchLaunch& B) {
-  if (!B.adjoint) return cudaSuccess;
-  return cudaFuncSetAttribute(heston_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (!B.adjoint || B.gseg) return cudaSuccess;
+  return cudaFuncSetAttribute(heston_batch_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)batch_smem(B));
+}
+
+cudaError_t batch_gseg_threads(int num_sms, size_t* threads) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<true, true>, kBatchTpb, 0);
+  *threads = (size_t)num_sms * (size_t)per_sm * kBatchTpb;
+  return e;
 }
 
 cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
                          double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream) {
   const size_t smem = batch_smem(B);
   int per_sm = 0;
-  cudaError_t e = B.adjoint
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<true>, kBatchTpb, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<false>, kBatchTpb, 0);
+  auto kern = !B.adjoint ? heston_batch_kernel<false, false>
+              : B.gseg   ? heston_batch_kernel<true, true>
+                         : heston_batch_kernel<true, false>;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchTpb, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const unsigned grid = (unsigned)num_sms * (unsigned)per_sm;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), stream);
   if (e != cudaSuccess) return e;
-  if (B.adjoint)
-    heston_batch_kernel<true><<<grid, kBatchTpb, smem, stream>>>(B, opts, items, counter, partials);
-  else
-    heston_batch_kernel<false><<<grid, kBatchTpb, 0, stream>>>(B, opts, items, counter, partials);
+  kern<<<grid, kBatchTpb, smem, stream>>>(B, opts, items, counter, partials);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nacc = B.adjoint ? kAdjAcc : 2;

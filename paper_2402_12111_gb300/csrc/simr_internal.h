@@ -107,6 +107,7 @@ struct BatchLaunch {
   int32_t adjoint;
   int32_t ckpt_rows;  // adjoint: checkpoint rows per thread column (max over options of n_seg - 1), even
   int32_t seg_rows;   // adjoint: rows of each segment array (max over options of ckpt_every)
+  float* gseg;        // adjoint with one segment per path: [3 seg_rows][grid threads] in global memory, else null
 };
 
 struct BatchOutputs {
@@ -162,6 +163,8 @@ cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* 
 cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
                          double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream);
 cudaError_t prepare_batch(const BatchLaunch& B);  // kernel attributes (outside any stream capture)
+// Threads of the adjoint book kernel's grid when its segments are in global memory.
+cudaError_t batch_gseg_threads(int num_sms, size_t* threads);
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);

@@ -53,6 +53,19 @@ def test_batch_adjoint_equals_per_option_calls(simr, small_book):
         torch.testing.assert_close(g[i:i + 1], gi, rtol=1e-9, atol=1e-9)
 
 
+def test_batch_adjoint_long_options_use_shared_segments(simr):
+    # a book whose longest option exceeds 1,024 steps runs the shared-memory
+    # checkpoint layout instead of one global segment per path: the same results
+    book = workloads.book(n_options=6, seed=8, steps_range=(200, 400), paths_range=(300, 3000))
+    book[2]["steps"] = 1500
+    p, _, g = simr.batch(book, seed=6, adjoint=True)
+    for i, o in enumerate(book):
+        pi, _, gi = simr.greeks_adjoint(o["model"], torch.tensor([o["K"]], dtype=torch.float64, device="cuda"),
+                                        o["is_put"], o["steps"], o["paths"], 6, ckpt_every=0, option_index=i)
+        torch.testing.assert_close(p[i:i + 1], pi, rtol=1e-12, atol=1e-12)
+        torch.testing.assert_close(g[i:i + 1], gi, rtol=1e-9, atol=1e-9)
+
+
 def test_batch_graph_replay_and_autotune_agree(simr, small_book):
     ref = simr.batch(small_book, seed=5, autotune=False)[0]
     a = simr.batch(small_book, seed=5, graph=True)[0]   # capture
