@@ -220,7 +220,11 @@ SIMR_API int simr_adjoint_interval(simr_ctx* ctx, int n_strikes, uint32_t steps,
  * book shape (a book's size class, cached in the context): 1024/4096/16384
  * paths (256/1024/4096 with the adjoint) and the size that gives about two
  * items per resident warp; that first call prices the book four more times.
- * Without tuning the chunk is the smaller of 4096 (1024) and that size.  With SIMR_BATCH_GRAPH the upload-free part
+ * Without tuning the chunk is the smaller of 4096 (1024) and that size.  Adjoint books keep every
+ * path whole (one segment, no forward pass) in a context-owned device buffer of 3 x (the longest
+ * option's steps) floats per resident thread when the longest option has at most 1,024 steps and the
+ * buffer fits 2^30 floats; otherwise checkpoints and segments in shared memory as simr_paths_adjoint
+ * chooses them.  With SIMR_BATCH_GRAPH the upload-free part
  * of the call (queue reset, batch kernel, reduction) is captured once per
  * (book, seed, flags, output buffers) and replayed afterwards.
  */

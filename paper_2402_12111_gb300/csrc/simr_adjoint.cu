@@ -1,13 +1,17 @@
 // simr_adjoint.cu -- pathwise adjoint (reverse-mode) Greeks of the Heston QE path, sm_103a.
 //
-// Per path (one lane): a forward pass (Philox draws, QE variance step, log-spot
-// step -- the paper's VariancePathQE and LogPricePathQE, Sec. 4-5) that keeps
-// the variance every `k` steps in shared memory, then a reverse sweep over the
-// segments, last to first: each segment's states are recomputed from its
-// checkpoint (the draws are counter-based, so the segment's draws are
-// regenerated and kept in shared memory with the states) and the steps are
-// differentiated backwards, with the branch taken in the forward pass held
-// fixed (pathwise derivative).  Since x' = x + (terms), the
+// Per path (one lane): a forward pass of the variance recursion (Philox draws,
+// QE variance step -- the paper's VariancePathQE, Sec. 4) that keeps the
+// variance every `k` steps (a global [slot][resident thread] array), then a
+// reverse sweep over the segments, last to first: each segment's states are
+// recomputed from its checkpoint (the draws are counter-based, so the
+// segment's draws are regenerated) and kept with the step's branch draw and Z_X
+// -- in shared memory, or in a global [3 k][resident thread] buffer when the
+// segment is longer than shared memory holds -- and the steps are
+// differentiated backwards (LogPricePathQE's increments summed on the way),
+// with the branch taken in the forward pass held fixed (pathwise derivative).
+// With one segment of the whole path there is no forward pass at all: the
+// recompute of that segment is the path's only simulation.  Since x' = x + (terms), the
 // adjoint of x is 1 throughout; the sweep carries the adjoint of v and seven
 // sums that the parameters enter through:
 //   Am = sum mbar, Amv = sum mbar (v - theta), As = sum s2bar, Asv = sum s2bar v,
