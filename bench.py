@@ -98,11 +98,35 @@ PATH_KERNEL_SOURCES = ("paper_2402_12111_gb300/csrc/simr_paths.cu", "paper_2402_
                        "include/simr.h")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and blank lines (string literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+
+
 def kernel_source_sha() -> str:
+    """Hash of the code (comments aside) the bench step's kernel is compiled from."""
     h = hashlib.sha256()
     for name in PATH_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, name), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
