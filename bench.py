@@ -130,25 +130,43 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(sha: str):
-    """DRAM bytes per launch of the path kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "heston_paths_grid32_252x1048576.txt")
+PATH_KERNEL_PROFILE = os.path.join("profiles", "heston_paths_grid32_252x1048576.txt")
+
+
+def _profile_values(sha: str) -> dict:
+    """The key: value lines of the committed ncu summary of the path kernel, if it was taken on
+    the current kernel sources (else {})."""
     try:
-        lines = open(path).read().splitlines()
+        lines = open(os.path.join(ROOT, PATH_KERNEL_PROFILE)).read().splitlines()
     except OSError:
-        return None
+        return {}
     kv = {}
     for ln in lines:
         if ":" in ln:
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha") != sha:
-        return None
+    return kv if kv.get("kernel_source_sha") == sha else {}
+
+
+def profiled_traffic(sha: str):
+    """DRAM bytes per launch of the path kernel from the committed ncu summary (or None)."""
     try:
-        return float(kv["traffic_bytes_per_launch_full_size"])
+        return float(_profile_values(sha)["traffic_bytes_per_launch_full_size"])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_pipes(sha: str):
+    """The path kernel's ncu pipe utilisation from the committed summary (or None)."""
+    kv = _profile_values(sha)
+    keys = ("fma_pipe_cycles_active_pct_of_active", "xu_pipe_cycles_active_pct_of_elapsed",
+            "issue_active_pct_of_active")
+    try:
+        out = {k: float(kv[k]) for k in keys}
+    except (KeyError, ValueError):
+        return None
+    out["source"] = PATH_KERNEL_PROFILE
+    return out
 
 
 class ClockSampler:
@@ -604,7 +622,10 @@ def run_native(args):
                      "frac": achieved_tflops / fp32_peak_tflops, "traffic": profiled_traffic(sha),
                      "peak_kind": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                   f"x {sm_max:.0f} MHz (FMA = 2 flops)",
-                     "flops_per_path_step": flops_step},
+                     "flops_per_path_step": flops_step,
+                     # the same kernel's FP32 (FMA) and MUFU pipe activity as ncu counts it, from the
+                     # committed summary of this source (None if the sources changed since)
+                     "ncu_pipes": profiled_pipes(sha)},
         "fp32_peak_frac": achieved_tflops / fp32_peak_tflops,
         "clocks": clk.summary(),
         "e2e": e2e,
