@@ -341,13 +341,13 @@ struct QemConst {
 // |u| < 1/8 (remainder below 6e-8 relative), else the logarithm.
 __device__ __forceinline__ float neg_log1m_tail(float u) {
   if (fabsf(u) < 0.125f) {
-    float t = fmaf(u, 0.125f, 0.14285714285714285f);
-    t = fmaf(u, t, 0.16666666666666666f);
-    t = fmaf(u, t, 0.2f);
-    t = fmaf(u, t, 0.25f);
-    t = fmaf(u, t, 0.33333333333333333f);
-    t = fmaf(u, t, 0.5f);
-    return u * u * t;
+    float t = __fmaf_rn(u, 0.125f, 0.14285714285714285f);
+    t = __fmaf_rn(u, t, 0.16666666666666666f);
+    t = __fmaf_rn(u, t, 0.2f);
+    t = __fmaf_rn(u, t, 0.25f);
+    t = __fmaf_rn(u, t, 0.33333333333333333f);
+    t = __fmaf_rn(u, t, 0.5f);
+    return __fmul_rn(__fmul_rn(u, u), t);
   }
   return -u - log1pf(-u);
 }
@@ -360,21 +360,22 @@ __device__ __forceinline__ float neg_log1m_tail(float u) {
 // 1 - p = 2 m^2 / (m^2 + s^2), beta = 2 m / (m^2 + s^2).
 __device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, float zv, float A, float& v_next,
                                                  float& dl, float& lam) {
-  const float m2 = m * m;
+  const float m2 = __fmul_rn(m, m);
   lam = 0.0f;
-  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
-    const float t = 2.0f * m2 * rcp_approx(s2);
-    const float root = sqrt_approx(fmaf(t, t, -t));
-    const float b2 = (t - 1.0f) + root;
+  if (s2 <= __fmul_rn(1.5f, m2) && m2 > 0.0f) {
+    const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
+    const float root = sqrt_approx(__fmaf_rn(t, t, -t));
+    const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
     const float b = sqrt_approx(b2);
-    const float a = m * rcp_approx(t + root);
-    const float bz = b + zv;
-    v_next = a * bz * bz;
-    dl = a * fmaf(zv, zv + 2.0f * b, -1.0f);
-    const float Aa = A * a;
-    const float u = 2.0f * Aa;
+    const float a = __fmul_rn(m, rcp_approx(__fadd_rn(t, root)));
+    const float bz = __fadd_rn(b, zv);
+    v_next = __fmul_rn(__fmul_rn(a, bz), bz);
+    dl = __fmul_rn(a, __fmaf_rn(zv, __fadd_rn(zv, __fmul_rn(2.0f, b)), -1.0f));
+    const float Aa = __fmul_rn(A, a);
+    const float u = __fmul_rn(2.0f, Aa);
     if (!(u < 1.0f)) return false;
-    lam = fmaf(0.5f, neg_log1m_tail(u), 2.0f * Aa * Aa * b2 * rcp_approx(1.0f - u));
+    lam = __fmaf_rn(0.5f, neg_log1m_tail(u),
+                    __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(2.0f, Aa), Aa), b2), rcp_approx(__fsub_rn(1.0f, u))));
     return true;
   }
   if (m > 0.0f) {
@@ -403,23 +404,96 @@ __device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, f
 __device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, float omu, float zv, float zx,
                                          float& v, float& x, float& comp) {
   float vn, dl, lam;
-  const float m = fmaf(v, c.E, c.thE);
-  const float s2 = fmaf(v, c.c1, c.c2);
+  const float m = __fmaf_rn(v, c.E, c.thE);
+  const float s2 = __fmaf_rn(v, c.c1, c.c2);
   const bool ok = qem_from_moments(m, s2, omu, zv, q.A, vn, dl, lam);
-  const float s = v + vn;
+  const float s = __fadd_rn(v, vn);
   float inc;
   if (ok) {
-    inc = fmaf(-q.qa, v + m, q.rdt) - lam;
-    inc = fmaf(q.K2, dl, inc);
+    inc = __fsub_rn(__fmaf_rn(-q.qa, __fadd_rn(v, m), q.rdt), lam);
+    inc = __fmaf_rn(q.K2, dl, inc);
   } else {
-    inc = fmaf(c.Cv, s, c.C0);
-    inc = fmaf(-c.Cd, v, inc);
-    inc = fmaf(c.Cdl, dl, inc);
+    inc = __fmaf_rn(c.Cv, s, c.C0);
+    inc = __fmaf_rn(-c.Cd, v, inc);
+    inc = __fmaf_rn(c.Cdl, dl, inc);
   }
-  inc = fmaf(c.sK3 * sqrt_approx(s), zx, inc);
-  const float y = inc - comp;
-  const float t = x + y;
-  comp = (t - x) - y;
+  inc = __fmaf_rn(__fmul_rn(c.sK3, sqrt_approx(s)), zx, inc);
+  const float y = __fsub_rn(inc, comp);
+  const float t = __fadd_rn(x, y);
+  comp = __fsub_rn(__fsub_rn(t, x), y);
+  x = t;
+  v = vn;
+}
+
+// Two QE-M steps (two paths on the same constants) in packed FP32, lane for
+// lane step_qem: the quadratic branch and the series part of lam paired when
+// both lanes take them, every other case per lane by the scalar functions.
+__device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q, float2 omu, float2 zv, float2 zx,
+                                          float2& v, float2& x, float2& comp) {
+  const float2 m = p_fma(v, p_bc(c.E), p_bc(c.thE));
+  const float2 s2 = p_fma(v, p_bc(c.c1), p_bc(c.c2));
+  const float2 m2 = p_mul(m, m);
+  const float2 lim = p_mul(p_bc(1.5f), m2);
+  float2 vn, dl, lam;
+  bool okx, oky;
+  if (s2.x <= lim.x && m2.x > 0.0f && s2.y <= lim.y && m2.y > 0.0f) {
+    const float2 t = p_mul(p_mul(p_bc(2.0f), m2), p_rcp(s2));
+    const float2 root = p_sqrt(p_fma(t, t, p_mul(t, p_bc(-1.0f))));
+    const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+    const float2 b = p_sqrt(b2);
+    const float2 a = p_mul(m, p_rcp(p_add(t, root)));
+    const float2 bz = p_add(b, zv);
+    vn = p_mul(p_mul(a, bz), bz);
+    dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
+    const float2 Aa = p_mul(p_bc(q.A), a);
+    const float2 u = p_mul(p_bc(2.0f), Aa);
+    okx = u.x < 1.0f;
+    oky = u.y < 1.0f;
+    // g(u) by its series (neg_log1m_tail), the logarithm per lane outside |u| < 1/8
+    float2 g = p_fma(u, p_bc(0.125f), p_bc(0.14285714285714285f));
+    g = p_fma(u, g, p_bc(0.16666666666666666f));
+    g = p_fma(u, g, p_bc(0.2f));
+    g = p_fma(u, g, p_bc(0.25f));
+    g = p_fma(u, g, p_bc(0.33333333333333333f));
+    g = p_fma(u, g, p_bc(0.5f));
+    g = p_mul(p_mul(u, u), g);
+    if (!(fabsf(u.x) < 0.125f && fabsf(u.y) < 0.125f)) {
+      if (!(fabsf(u.x) < 0.125f)) g.x = neg_log1m_tail(u.x);
+      if (!(fabsf(u.y) < 0.125f)) g.y = neg_log1m_tail(u.y);
+    }
+    lam = p_fma(p_bc(0.5f), g, p_mul(p_mul(p_mul(p_mul(p_bc(2.0f), Aa), Aa), b2), p_rcp(p_sub(p_bc(1.0f), u))));
+    if (!okx) lam.x = 0.0f;
+    if (!oky) lam.y = 0.0f;
+  } else {
+    okx = qem_from_moments(m.x, s2.x, omu.x, zv.x, q.A, vn.x, dl.x, lam.x);
+    oky = qem_from_moments(m.y, s2.y, omu.y, zv.y, q.A, vn.y, dl.y, lam.y);
+  }
+  const float2 s = p_add(v, vn);
+  float2 inc;
+  if (okx && oky) {
+    inc = p_sub(p_fma(p_bc(-q.qa), p_add(v, m), p_bc(q.rdt)), lam);
+    inc = p_fma(p_bc(q.K2), dl, inc);
+  } else {
+    const float vv[2] = {v.x, v.y}, mm[2] = {m.x, m.y}, ss[2] = {s.x, s.y}, dd[2] = {dl.x, dl.y},
+                ll[2] = {lam.x, lam.y};
+    const bool ok[2] = {okx, oky};
+    float r[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (ok[j]) {
+        r[j] = __fmaf_rn(q.K2, dd[j], __fsub_rn(__fmaf_rn(-q.qa, __fadd_rn(vv[j], mm[j]), q.rdt), ll[j]));
+      } else {
+        float t = __fmaf_rn(c.Cv, ss[j], c.C0);
+        t = __fmaf_rn(-c.Cd, vv[j], t);
+        r[j] = __fmaf_rn(c.Cdl, dd[j], t);
+      }
+    }
+    inc = make_float2(r[0], r[1]);
+  }
+  inc = p_fma(p_mul(p_bc(c.sK3), p_sqrt(s)), zx, inc);
+  const float2 y = p_sub(inc, comp);
+  const float2 t = p_add(x, y);
+  comp = p_sub(p_sub(t, x), y);
   x = t;
   v = vn;
 }

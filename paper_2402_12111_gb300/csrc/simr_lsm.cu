@@ -71,8 +71,8 @@ __device__ __forceinline__ float lsm_payoff(bool put, float S, float K) {
   return put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
 }
 
-// One step of the thread's two paths from their (variance, log-spot) words:
-// paired for plain QE (simulate_two's arithmetic), per path for QE-M.
+// One step of the thread's two paths from their (variance, log-spot) words,
+// paired in packed FP32 (simulate_two's arithmetic, or step_qem2 for QE-M).
 template <bool QEM>
 __device__ __forceinline__ void step_two(const LsmLaunch& L, uint32_t wv0, uint32_t wx0, uint32_t wv1, uint32_t wx1,
                                          float (&v)[kLsmPpt], float (&x)[kLsmPpt], float (&comp)[kLsmPpt]) {
@@ -80,19 +80,18 @@ __device__ __forceinline__ void step_two(const LsmLaunch& L, uint32_t wv0, uint3
   const float xa = centered_uniform(wv0), xb = centered_uniform(wv1);
   const float2 zv = norminv_centered2(make_float2(xa, xb));
   const float2 zx = norminv_centered2(make_float2(centered_uniform(wx0), centered_uniform(wx1)));
-  if constexpr (QEM) {
-    step_qem(L.sc, L.qm, 0.5f * (1.0f - xa), zv.x, zx.x, v[0], x[0], comp[0]);
-    step_qem(L.sc, L.qm, 0.5f * (1.0f - xb), zv.y, zx.y, v[1], x[1], comp[1]);
-  } else {
-    float2 vv = make_float2(v[0], v[1]), xx = make_float2(x[0], x[1]), cc = make_float2(comp[0], comp[1]);
-    step_base2<false>(L.sc, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, vv, xx, cc);
-    v[0] = vv.x;
-    v[1] = vv.y;
-    x[0] = xx.x;
-    x[1] = xx.y;
-    comp[0] = cc.x;
-    comp[1] = cc.y;
-  }
+  float2 vv = make_float2(v[0], v[1]), xx = make_float2(x[0], x[1]), cc = make_float2(comp[0], comp[1]);
+  const float2 omu = make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb));
+  if constexpr (QEM)
+    step_qem2(L.sc, L.qm, omu, zv, zx, vv, xx, cc);
+  else
+    step_base2<false>(L.sc, omu, zv, zx, vv, xx, cc);
+  v[0] = vv.x;
+  v[1] = vv.y;
+  x[0] = xx.x;
+  x[1] = xx.y;
+  comp[0] = cc.x;
+  comp[1] = cc.y;
 }
 
 // Path kernel: states at the exercise dates, maturity cash flow.

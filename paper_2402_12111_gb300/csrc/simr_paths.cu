@@ -115,17 +115,21 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
 }
 
 // One time step of PPT paths.  Pricing with two paths per thread runs the two
-// paths' steps paired (their inverse normals too); otherwise step_all per path.
+// paths' steps paired (their inverse normals too; QE or QE-M); otherwise
+// step_all per path.
 template <int NS, int NV, bool DYN, int PPT, bool QEM>
 __device__ __forceinline__ void step_paths(const PathLaunch& L, const uint32_t (&wv)[PPT], const uint32_t (&wx)[PPT],
                                            float (&v)[PPT][NS], float (&x)[PPT][NS], float (&c)[PPT][NS]) {
-  if constexpr (NS == 1 && PPT == 2 && !QEM) {
+  if constexpr (NS == 1 && PPT == 2) {
     const float xv0 = centered_uniform(wv[0]), xv1 = centered_uniform(wv[1]);
     const float2 zv = norminv_centered2(make_float2(xv0, xv1));
     const float2 zx = norminv_centered2(make_float2(centered_uniform(wx[0]), centered_uniform(wx[1])));
     const float2 omu = make_float2(0.5f * (1.0f - xv0), 0.5f * (1.0f - xv1));
     float2 vv = make_float2(v[0][0], v[1][0]), xx = make_float2(x[0][0], x[1][0]), cc = make_float2(c[0][0], c[1][0]);
-    step_base2<false>(L.sc[0], omu, zv, zx, vv, xx, cc);
+    if constexpr (QEM)
+      step_qem2(L.sc[0], L.qm, omu, zv, zx, vv, xx, cc);
+    else
+      step_base2<false>(L.sc[0], omu, zv, zx, vv, xx, cc);
     v[0][0] = vv.x;
     v[1][0] = vv.y;
     x[0][0] = xx.x;
