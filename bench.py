@@ -99,7 +99,7 @@ PATH_KERNEL_SOURCES = ("paper_2402_12111_gb300/csrc/simr_paths.cu", "paper_2402_
 
 
 def _code_only(text: str) -> str:
-    """C/C++ source without its comments and blank lines (string literals kept as they are)."""
+    """C/C++ source without its comments, blank lines and indentation (string literals kept as they are)."""
     out, i, n = [], 0, len(text)
     while i < n:
         c = text[i]
@@ -118,7 +118,7 @@ def _code_only(text: str) -> str:
         else:
             out.append(c)
             i += 1
-    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+    return "\n".join(ln.strip() for ln in "".join(out).splitlines() if ln.strip())
 
 
 def kernel_source_sha() -> str:

@@ -74,3 +74,19 @@ def test_product_path_does_not_import_oracle():
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
     for path in glob.glob(os.path.join(ROOT, "paper_2402_12111_gb300", "csrc", "*")):
         assert "simr_oracle" not in open(path).read(), path
+
+
+def test_bench_source_hash_ignores_comments_only():
+    # the profiled-traffic lookup in bench.py keys on the path kernel's code: a
+    # comment edit keeps the key, a code edit changes it
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    code = 'int f(int a) { return a + 1; }  // one\n/* two\n three */ const char* s = "x // y /* z";\n'
+    same = 'int f(int a) { return a + 1; }\n// a different comment\nconst char* s = "x // y /* z";\n'
+    other = 'int f(int a) { return a + 2; }\nconst char* s = "x // y /* z";\n'
+    assert bench._code_only(code) == bench._code_only(same)
+    assert bench._code_only(code) != bench._code_only(other)
+    assert '"x // y /* z"' in bench._code_only(code)
