@@ -44,6 +44,27 @@ struct ScenConst {
   float pad;
 };
 
+// The step constants of two lanes, packed (lane x, lane y): the operands of the
+// paired steps, read from the launch parameters as they are (the same values
+// in both lanes for two paths or the v0 bumps; a bumped pair's own deltas).
+struct ScenConst2 {
+  float2 E, thE, c1, c2, C0, Cv, mCd, Cdl, sK3;  // mCd = -Cd
+};
+
+__host__ __device__ inline ScenConst2 pack_const(const ScenConst& a, const ScenConst& b) {
+  ScenConst2 p;
+  p.E = make_float2(a.E, b.E);
+  p.thE = make_float2(a.thE, b.thE);
+  p.c1 = make_float2(a.c1, b.c1);
+  p.c2 = make_float2(a.c2, b.c2);
+  p.C0 = make_float2(a.C0, b.C0);
+  p.Cv = make_float2(a.Cv, b.Cv);
+  p.mCd = make_float2(-a.Cd, -b.Cd);
+  p.Cdl = make_float2(a.Cdl, b.Cdl);
+  p.sK3 = make_float2(a.sK3, b.sK3);
+  return p;
+}
+
 // First-step constants of a scenario (all paths share v0, so every step-0
 // quantity except the draws is a per-scenario constant).  Computed on the host
 // in FP64: base scenario full values, bumped scenarios their exact differences
@@ -308,22 +329,28 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
 // step_base for two lanes sharing the constants (two paths, or two scenarios
 // that differ only in v0).
 template <bool CRN>
-__device__ __forceinline__ void step_base2(const ScenConst& c, float2 omu, float2 zv, float2 zx, float2& v,
+__device__ __forceinline__ void step_base2(const ScenConst2& c, float2 omu, float2 zv, float2 zx, float2& v,
                                            float2& x, float2& comp) {
   float2 vn, dl;
-  const float2 m = CRN ? p_add(p_mul(v, p_bc(c.E)), p_bc(c.thE)) : p_fma(v, p_bc(c.E), p_bc(c.thE));
-  const float2 s2 = CRN ? p_add(p_mul(v, p_bc(c.c1)), p_bc(c.c2)) : p_fma(v, p_bc(c.c1), p_bc(c.c2));
+  const float2 m = CRN ? p_add(p_mul(v, c.E), c.thE) : p_fma(v, c.E, c.thE);
+  const float2 s2 = CRN ? p_add(p_mul(v, c.c1), c.c2) : p_fma(v, c.c1, c.c2);
   qe_from_moments2(m, s2, omu, zv, vn, dl);
   const float2 s = p_add(v, vn);
-  float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
-  inc = p_fma(p_bc(-c.Cd), v, inc);
-  inc = p_fma(p_bc(c.Cdl), dl, inc);
-  inc = p_fma(p_mul(p_bc(c.sK3), p_sqrt(s)), zx, inc);
+  float2 inc = p_fma(c.Cv, s, c.C0);
+  inc = p_fma(c.mCd, v, inc);
+  inc = p_fma(c.Cdl, dl, inc);
+  inc = p_fma(p_mul(c.sK3, p_sqrt(s)), zx, inc);
   const float2 y = p_sub(inc, comp);
   const float2 t = p_add(x, y);
   comp = p_sub(p_sub(t, x), y);
   x = t;
   v = vn;
+}
+
+template <bool CRN>
+__device__ __forceinline__ void step_base2(const ScenConst& c, float2 omu, float2 zv, float2 zx, float2& v,
+                                           float2& x, float2& comp) {
+  step_base2<CRN>(pack_const(c, c), omu, zv, zx, v, x, comp);
 }
 
 // QE-M (Andersen 2008, martingale correction): the constant K0 - r dt of the
@@ -542,25 +569,24 @@ __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst&
   v = vn;
 }
 
-// step_bumped for two scenarios with deltas d0 (lane x) and d1 (lane y).
-__device__ __forceinline__ void step_bumped2(const ScenConst& b, const ScenConst& d0, const ScenConst& d1,
-                                             float2 omu, float2 zv, float2 zx, float2& v, float2& x, float2& comp) {
-  const float2 m = p_add(p_fma(v, p_bc(b.E), p_fma(v, make_float2(d0.E, d1.E), make_float2(d0.thE, d1.thE))),
-                         p_bc(b.thE));
-  const float2 s2 = p_add(p_fma(v, p_bc(b.c1), p_fma(v, make_float2(d0.c1, d1.c1), make_float2(d0.c2, d1.c2))),
-                          p_bc(b.c2));
+// step_bumped for two scenarios: base constants b (both lanes), deltas d (lane
+// x the first scenario's, lane y the second's).
+__device__ __forceinline__ void step_bumped2(const ScenConst2& b, const ScenConst2& d, float2 omu, float2 zv,
+                                             float2 zx, float2& v, float2& x, float2& comp) {
+  const float2 m = p_add(p_fma(v, b.E, p_fma(v, d.E, d.thE)), b.thE);
+  const float2 s2 = p_add(p_fma(v, b.c1, p_fma(v, d.c1, d.c2)), b.c2);
   float2 vn, dl;
   qe_from_moments2(m, s2, omu, zv, vn, dl);
   const float2 s = p_add(v, vn);
   const float2 q = p_sqrt(s);
-  float2 inc = p_fma(p_bc(b.Cv), s, p_bc(b.C0));
-  inc = p_fma(p_bc(-b.Cd), v, inc);
-  inc = p_fma(p_bc(b.Cdl), dl, inc);
-  inc = p_fma(p_mul(p_bc(b.sK3), q), zx, inc);
-  float2 sm = p_fma(make_float2(d0.Cv, d1.Cv), s, make_float2(d0.C0, d1.C0));
-  sm = p_fma(make_float2(-d0.Cd, -d1.Cd), v, sm);
-  sm = p_fma(make_float2(d0.Cdl, d1.Cdl), dl, sm);
-  sm = p_fma(p_mul(make_float2(d0.sK3, d1.sK3), q), zx, sm);
+  float2 inc = p_fma(b.Cv, s, b.C0);
+  inc = p_fma(b.mCd, v, inc);
+  inc = p_fma(b.Cdl, dl, inc);
+  inc = p_fma(p_mul(b.sK3, q), zx, inc);
+  float2 sm = p_fma(d.Cv, s, d.C0);
+  sm = p_fma(d.mCd, v, sm);
+  sm = p_fma(d.Cdl, dl, sm);
+  sm = p_fma(p_mul(d.sK3, q), zx, sm);
   inc = p_add(inc, sm);
 #if SIMR_KAHAN_BUMPED
   const float2 y = p_sub(inc, comp);
