@@ -1245,6 +1245,7 @@ int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, co
     L.S0w[k] = (float)(assets[k].S0 * weights[k]);
     for (int j = 0; j <= k; ++j) L.Lc[k * (k + 1) / 2 + j] = (float)Lc[k * A + j];
   }
+  for (int q = 0; 2 * q + 1 < A; ++q) L.pk[q] = pack_const(L.sc[2 * q], L.sc[2 * q + 1]);
   L.n_assets = A;
   L.n_strikes = n_strikes;
   L.nk_pad = n_strikes == 1 ? 1 : ((n_strikes + 31) / 32) * 32;

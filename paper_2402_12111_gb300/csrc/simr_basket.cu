@@ -25,28 +25,9 @@ namespace {
 
 constexpr int kBasketTpb = 256;
 
-// The constants of two assets, lane x asset k and lane y asset k + 1.
-struct ScenPair {
-  float2 E, thE, c1, c2, C0, Cv, mCd, Cdl, sK3;
-};
-
-__device__ __forceinline__ ScenPair scen_pair(const ScenConst& a, const ScenConst& b) {
-  ScenPair c;
-  c.E = make_float2(a.E, b.E);
-  c.thE = make_float2(a.thE, b.thE);
-  c.c1 = make_float2(a.c1, b.c1);
-  c.c2 = make_float2(a.c2, b.c2);
-  c.C0 = make_float2(a.C0, b.C0);
-  c.Cv = make_float2(a.Cv, b.Cv);
-  c.mCd = make_float2(-a.Cd, -b.Cd);
-  c.Cdl = make_float2(a.Cdl, b.Cdl);
-  c.sK3 = make_float2(a.sK3, b.sK3);
-  return c;
-}
-
 // step_base<false> of two assets at once in packed FP32, lane for lane the
 // scalar step's operations and rounding.
-__device__ __forceinline__ void step_pair(const ScenPair& c, float2 omu, float2 zv, float2 zx, float2& v, float2& x,
+__device__ __forceinline__ void step_pair(const ScenConst2& c, float2 omu, float2 zv, float2 zx, float2& v, float2& x,
                                           float2& comp) {
   float2 vn, dl;
   qe_from_moments2(p_fma(v, c.E, c.thE), p_fma(v, c.c1, c.c2), omu, zv, vn, dl);
@@ -66,7 +47,7 @@ __device__ __forceinline__ void step_pair(const ScenPair& c, float2 omu, float2 
 // and spot uniforms' normals eps[0 .. k + 1]: z = Lc eps over the rows k, k + 1,
 // summed in column order as for one asset at a time.
 template <int NA>
-__device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const ScenPair& c, int k, float2 xv,
+__device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const ScenConst2& c, int k, float2 xv,
                                                  const float (&eps)[NA], float2& v, float2& x, float2& comp) {
   const float* ra = L.Lc + k * (k + 1) / 2;
   const float* rb = ra + k + 1;  // row k + 1
@@ -158,7 +139,7 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
         const float2 e = norminv_centered2(make_float2(centered_uniform(wa.y), centered_uniform(wb.y)));
         eps[k] = e.x;
         eps[k + 1] = e.y;
-        basket_pair_step<NA>(L, scen_pair(L.sc[k], L.sc[k + 1]), k,
+        basket_pair_step<NA>(L, L.pk[q], k,
                              make_float2(centered_uniform(wa.x), centered_uniform(wb.x)), eps, v[q], x[q], comp[q]);
       }
       if (na & 1) {
@@ -175,7 +156,7 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
           const float2 e = norminv_centered2(make_float2(centered_uniform(ww[k]), centered_uniform(ww[k + 1])));
           eps[k] = e.x;
           eps[k + 1] = e.y;
-          basket_pair_step<NA>(L, scen_pair(L.sc[k], L.sc[k + 1]), k,
+          basket_pair_step<NA>(L, L.pk[q], k,
                                make_float2(centered_uniform(wz[k]), centered_uniform(wz[k + 1])), eps, v[q], x[q],
                                comp[q]);
         }

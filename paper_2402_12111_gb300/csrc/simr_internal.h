@@ -214,6 +214,7 @@ constexpr int kMaxAssets = 16;
 struct BasketLaunch {
   uint32_t rk[10][2];
   ScenConst sc[kMaxAssets];                          // per asset (v0 included)
+  ScenConst2 pk[kMaxAssets / 2];                     // assets (2q, 2q + 1) packed lane by lane
   float Lc[kMaxAssets * (kMaxAssets + 1) / 2];       // lower Cholesky factor, rows packed
   float S0w[kMaxAssets];                             // S0_k w_k
   int32_t n_assets, n_strikes, nk_pad, is_put;
