@@ -102,7 +102,7 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
     if (DYN && s >= L.n_scen) break;
     float2 vv = make_float2(v[s], v[s + 1]), xx = make_float2(x[s], x[s + 1]), cc = make_float2(c[s], c[s + 1]);
     if (s + 1 <= NV)
-      step_base2<true>(L.base2, p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
+      step_base2<true>(L.sc[0], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);  // broadcast: measured faster
     else
       step_bumped2(L.base2, L.pair2[(s - 1) / 2], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
     v[s] = vv.x;
