@@ -334,7 +334,6 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
   }
   L->n_scen = ns;
   // the paired steps' operands, packed once here
-  L->base2 = pack_const(L->sc[0], L->sc[0]);
   for (int k = 0; 2 * k + 1 < ns; ++k)
     L->pair2[k] = pack_const(L->sc[2 * k + 1], L->sc[2 * k + 2 < ns ? 2 * k + 2 : 2 * k + 1]);
   // vega is the first re-simulated Greek in bit order, so its two-sided bump occupies

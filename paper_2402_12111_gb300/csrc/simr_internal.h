@@ -34,7 +34,6 @@ struct PathLaunch {
   double rho_w;           // e^{h_r T} - e^{-h_r T} = 2 sinh(h_r T): band width factor
   int32_t resim_up[kMaxResim], resim_dn[kMaxResim];  // scenario of each re-simulated Greek
   ScenConst sc[kMaxScen];
-  ScenConst2 base2;                // sc[0] in both lanes
   ScenConst2 pair2[kMaxScen / 2];  // scenarios (2k + 1, 2k + 2): their constants (deltas) lane by lane
   FirstConst f0[kMaxScen];  // step-0 constants (used when first_split != 0)
   int32_t first_split;      // 1: step 0 of every scenario through step0_crn
