@@ -99,7 +99,12 @@ typedef struct {
 
 #define SIMR_BATCH_ADJOINT (1u << 0)      /* also the 7 pathwise sensitivities per option       */
 #define SIMR_BATCH_GRAPH (1u << 1)        /* capture the launch in a CUDA graph; replay on repeat */
-#define SIMR_BATCH_NO_AUTOTUNE (1u << 2)  /* skip the first-call chunk-size search              */
+#define SIMR_BATCH_NO_AUTOTUNE (1u << 2)  /* skip the first-call kernel-shape and chunk search   */
+/* Run kernel shape v (0-7) instead of the tuned one (no search): threads per
+ * block 128 / 256 (bit 0); price books: paths per thread 2 / 1 (bit 1) and the
+ * step-pair loop unrolled 1 / 2 times (bit 2); adjoint books: bit 0 only (v < 2).
+ * Every shape gives the same results bit for bit. */
+#define SIMR_BATCH_VARIANT(v) ((((uint32_t)(v) & 7u) + 1u) << 8)
 
 /* Greek selection bits for simr_greeks_fd; output columns follow bit order. */
 #define SIMR_G_DELTA (1u << 0)  /* d/dS0, analytic S-bump on the same path   */
@@ -216,11 +221,16 @@ SIMR_API int simr_adjoint_interval(simr_ctx* ctx, int n_strikes, uint32_t steps,
  *   flags          in   SIMR_BATCH_* (0 = prices only)
  *   price[n_opts], stderr_out[n_opts] (nullable)   out, caller's order
  *   grad[n_opts * 7]   out (SIMR_BATCH_ADJOINT): d/d{S0, v0, kappa, theta, sigma, rho, r}
- * chunk is chosen by timing four candidates on the first submission of each
- * book shape (a book's size class, cached in the context): 1024/4096/16384
- * paths (256/1024/4096 with the adjoint) and the size that gives about two
- * items per resident warp; that first call prices the book four more times.
- * Without tuning the chunk is the smaller of 4096 (1024) and that size.  Adjoint books keep every
+ * The kernel's shape and the chunk are chosen by timing on the first submission
+ * of each book shape (a book's size class): first the eight kernel shapes of
+ * SIMR_BATCH_VARIANT (two for adjoint books) at the default chunk, then, with
+ * the fastest shape, four chunks: 1024/4096/16384 paths (256/1024/4096 with the
+ * adjoint) and the size that gives about two items per resident warp -- that
+ * first call prices the book up to twelve more times.  The choice is cached in
+ * the context and, when the environment variable SIMR_TUNE_CACHE names a file,
+ * appended there as a JSON line {"gpu", "key", "chunk", "variant", ...} and read
+ * back by later processes on a GPU of the same name.  Without tuning: shape 0
+ * and the smaller of 4096 (1024) and that size.  Adjoint books keep every
  * path whole (one segment, no forward pass) in a context-owned device buffer of 3 x (the longest
  * option's steps) floats per resident thread when the longest option has at most 1,024 steps and the
  * buffer fits 2^30 floats; otherwise checkpoints and segments in shared memory as simr_paths_adjoint

@@ -46,6 +46,11 @@ class Option(ctypes.Structure):
 
 
 BATCH_ADJOINT, BATCH_GRAPH, BATCH_NO_AUTOTUNE = 1, 2, 4
+
+
+def batch_variant_flag(v: int) -> int:
+    """SIMR_BATCH_VARIANT(v): run kernel shape v (0-7) of the book kernel."""
+    return ((int(v) & 7) + 1) << 8
 SCHEMES = {"qe": 0, "qem": 1}
 
 

@@ -130,10 +130,11 @@ def heston_price(params, strikes, T, is_put=False, steps=64, paths=65536, seed=1
 
 
 def batch(options, seed: int = 1, adjoint: bool = False, graph: bool = False, autotune: bool = True,
-          device=None, stream=None, out_device=None):
+          device=None, stream=None, out_device=None, variant=None):
     """simr_batch_submit over a book: options is a sequence of dicts with keys
     model (dict), K, is_put, steps, paths.  Returns (price[n], stderr[n], grad[n, 7] or None)
-    in the book's order, on `out_device` (default: the CUDA device)."""
+    in the book's order, on `out_device` (default: the CUDA device).  `variant` (0-7, or
+    None for the tuned one) forces the kernel shape of SIMR_BATCH_VARIANT."""
     n = len(options)
     arr = (S.Option * n)()
     for i, o in enumerate(options):
@@ -148,7 +149,7 @@ def batch(options, seed: int = 1, adjoint: bool = False, graph: bool = False, au
     se = torch.empty_like(p)
     g = torch.empty(n, 7, dtype=torch.float64, device=odev) if adjoint else None
     flags = (S.BATCH_ADJOINT if adjoint else 0) | (S.BATCH_GRAPH if graph else 0) | \
-        (0 if autotune else S.BATCH_NO_AUTOTUNE)
+        (0 if autotune else S.BATCH_NO_AUTOTUNE) | (0 if variant is None else S.batch_variant_flag(variant))
     L = S.load()
     ctx = S.context(dev_index)
     st = _stream(p, stream) if p.is_cuda else ctypes.c_void_p(None)

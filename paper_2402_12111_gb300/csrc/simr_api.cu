@@ -72,8 +72,11 @@ struct simr_ctx {
   struct Tune {
     uint64_t key;
     uint32_t chunk;
+    int32_t variant;  // batch kernel shape (batch_variant)
   };
   std::vector<Tune> tune;
+  bool tune_loaded = false;  // $SIMR_TUNE_CACHE read
+  char gpu_name[256] = "";
   struct AdjK {  // adjoint_max_ckpt_every per strike tile, found once
     int32_t nk_pad;
     int32_t k_max;
@@ -679,10 +682,15 @@ int simr_create(simr_ctx** out, int device) {
   if (!c) return fail(SIMR_ENOMEM, "host allocation failed");
   c->device = device;
   e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceProp prop;
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
   if (e != cudaSuccess) {
     delete c;
-    return cuda_fail(e, "querying the SM count");
+    return cuda_fail(e, "querying the device");
   }
+  std::snprintf(c->gpu_name, sizeof(c->gpu_name), "%s", prop.name);
+  for (char* q = c->gpu_name; *q; ++q)
+    if (*q == '"' || *q == '\\') *q = '_';  // kept out of the cache file's strings
   e = cudaMalloc((void**)&c->ticket, 256);
   if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, 256);
   c->status = reinterpret_cast<int*>(reinterpret_cast<char*>(c->ticket) + 64);
@@ -992,12 +1000,56 @@ int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* st
   return finish_outputs(ctx, o, st);
 }
 
+// Tuned book shapes across processes: $SIMR_TUNE_CACHE names a file of JSON
+// lines {"gpu": name, "key": book size class, "chunk": paths per item,
+// "variant": kernel shape, ...}; this GPU's entries are read once per context,
+// new ones appended (best effort: an unreadable or unwritable file is ignored).
+void load_tune_cache(simr_ctx* ctx) {
+  if (ctx->tune_loaded) return;
+  ctx->tune_loaded = true;
+  const char* path = std::getenv("SIMR_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[1024], gpu[256];
+  unsigned long long key = 0;
+  unsigned chunk = 0;
+  int variant = 0;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (std::sscanf(line, "{\"gpu\": \"%255[^\"]\", \"key\": %llu, \"chunk\": %u, \"variant\": %d", gpu, &key,
+                    &chunk, &variant) != 4)
+      continue;
+    const bool adj = (key & 1ull) != 0;
+    if (std::strcmp(gpu, ctx->gpu_name) != 0 || variant < 0 || variant >= (adj ? 2 : kBatchVariants) ||
+        chunk < 32 || chunk > 16384 || chunk % (adj ? 32u : 64u) != 0)
+      continue;
+    ctx->tune.push_back({(uint64_t)key, (uint32_t)chunk, variant});
+  }
+  std::fclose(f);
+}
+
+void save_tune_entry(const simr_ctx* ctx, const simr_ctx::Tune& t, bool adjoint) {
+  const char* path = std::getenv("SIMR_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  BatchLaunch B{};
+  batch_variant(t.variant, adjoint, &B);
+  std::fprintf(f, "{\"gpu\": \"%s\", \"key\": %llu, \"chunk\": %u, \"variant\": %d, \"tpb\": %d, \"ppt\": %d, "
+               "\"unroll\": %d}\n",
+               ctx->gpu_name, (unsigned long long)t.key, t.chunk, t.variant, B.tpb, B.ppt, B.unroll);
+  std::fclose(f);
+}
+
 int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64_t seed, uint32_t flags,
                       double* price, double* stderr_out, double* grad, void* stream) {
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   if (!opts || n_opts < 1 || n_opts > (1 << 22)) return fail(SIMR_EINVAL, "n_opts must lie in [1, 2^22]");
-  if (flags & ~(SIMR_BATCH_ADJOINT | SIMR_BATCH_GRAPH | SIMR_BATCH_NO_AUTOTUNE))
+  if (flags & ~(SIMR_BATCH_ADJOINT | SIMR_BATCH_GRAPH | SIMR_BATCH_NO_AUTOTUNE | (15u << 8)))
     return fail(SIMR_EINVAL, "unknown batch flags");
+  const int forced = (int)((flags >> 8) & 15u) - 1;  // SIMR_BATCH_VARIANT(v): v, else -1
+  if (forced > 7 || (forced > 1 && (flags & SIMR_BATCH_ADJOINT)))
+    return fail(SIMR_EINVAL, "kernel shape out of range for this book");
   if (is_device_ptr(opts)) return fail(SIMR_EINVAL, "the option table must be in host memory");
   const bool adjoint = (flags & SIMR_BATCH_ADJOINT) != 0;
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
@@ -1048,10 +1100,11 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   o.n[2] = (size_t)n_opts * 7;
   if ((rc = stage_outputs(ctx, &o))) return rc;
   BatchOutputs out{o.dev[0], o.dev[1], o.dev[2]};
-  cudaError_t e = prepare_batch(B);
-  if (e != cudaSuccess) return cuda_fail(e, "preparing the batch kernel");
+  B.gseg_floats = ctx->gseg_floats;
+  cudaError_t e = cudaSuccess;
 
-  // chunk (paths per work item): autotuned once per book shape, cached in the context
+  // kernel shape and chunk (paths per work item): autotuned once per book
+  // shape, cached in the context and in $SIMR_TUNE_CACHE
   double total = 0.0;
   for (const BatchOption& b : bo) total += (double)b.steps * (double)b.paths;
   const uint64_t tkey = (adjoint ? 1ull : 0ull) | ((uint64_t)std::max(0.0, std::log2(total + 1.0)) << 1) |
@@ -1065,37 +1118,63 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   const uint32_t balanced =
       (uint32_t)std::min(16384.0, std::max((double)quantum, std::ceil(fill / quantum) * quantum));
   uint32_t chunk = std::min(adjoint ? 1024u : 4096u, balanced);
+  int variant = 0;
+  load_tune_cache(ctx);
   bool tuned = false;
   for (const auto& t : ctx->tune)
-    if (t.key == tkey) chunk = t.chunk, tuned = true;
+    if (t.key == tkey) chunk = t.chunk, variant = t.variant, tuned = true;
   const char* env = std::getenv("SIMR_AUTOTUNE");
-  const bool autotune = !(flags & SIMR_BATCH_NO_AUTOTUNE) && !(env && env[0] == '0');
+  const bool autotune = forced < 0 && !(flags & SIMR_BATCH_NO_AUTOTUNE) && !(env && env[0] == '0');
+  if (forced >= 0) variant = forced;
   if (!tuned && autotune) {
-    const uint32_t cands[4] = {adjoint ? 256u : 1024u, adjoint ? 1024u : 4096u, adjoint ? 4096u : 16384u, balanced};
-    float best = 0.0f;
     cudaEvent_t a = nullptr, b = nullptr;
     e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
-      uint32_t n_items = 0;
-      if ((rc = upload_batch(ctx, bo, order, cands[ci], st, &n_items))) break;
-      B.n_items = n_items;
-      if ((rc = ensure(&ctx->b_partials, &ctx->b_partials_cap, (size_t)n_items * nacc, "batch partial rows"))) break;
-      e = cudaEventRecord(a, st);
+    uint32_t loaded = 0;  // the chunk the uploaded item table was cut with
+    auto time_one = [&](uint32_t ch, int v, float* ms) -> int {
+      if (ch != loaded) {
+        uint32_t n_items = 0;
+        int r = upload_batch(ctx, bo, order, ch, st, &n_items);
+        if (r) return r;
+        B.n_items = n_items;
+        if ((r = ensure(&ctx->b_partials, &ctx->b_partials_cap, (size_t)n_items * nacc, "batch partial rows")))
+          return r;
+        loaded = ch;
+      }
+      batch_variant(v, adjoint, &B);
+      e = prepare_batch(B);
+      if (e == cudaSuccess) e = cudaEventRecord(a, st);
       if (e == cudaSuccess)
         e = launch_batch(B, ctx->b_opts, ctx->b_items, ctx->ticket + 32, ctx->b_partials, out, ctx->num_sms, st);
       if (e == cudaSuccess) e = cudaEventRecord(b, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+      return SIMR_OK;
+    };
+    float best = 0.0f;
+    const int n_var = adjoint ? 2 : kBatchVariants;
+    for (int v = 0; v < n_var && e == cudaSuccess && !rc; ++v) {  // the kernel shape at the default chunk
       float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e == cudaSuccess && (ci == 0 || ms < best)) best = ms, chunk = cands[ci];
+      rc = time_one(chunk, v, &ms);
+      if (!rc && e == cudaSuccess && (v == 0 || ms < best)) best = ms, variant = v;
+    }
+    const uint32_t cands[4] = {adjoint ? 256u : 1024u, adjoint ? 1024u : 4096u, adjoint ? 4096u : 16384u, balanced};
+    for (int ci = 0; ci < 4 && e == cudaSuccess && !rc; ++ci) {  // then the chunk
+      float ms = 0.0f;
+      rc = time_one(cands[ci], variant, &ms);
+      if (!rc && e == cudaSuccess && (ci == 0 || ms < best)) best = ms, chunk = cands[ci];
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "autotuning the batch kernel");
-    ctx->tune.push_back({tkey, chunk});
+    const simr_ctx::Tune t{tkey, chunk, variant};
+    ctx->tune.push_back(t);
+    save_tune_entry(ctx, t, adjoint);
   }
+  batch_variant(variant, adjoint, &B);
+  e = prepare_batch(B);
+  if (e != cudaSuccess) return cuda_fail(e, "preparing the batch kernel");
 
   uint32_t n_items = 0;
   if ((rc = upload_batch(ctx, bo, order, chunk, st, &n_items))) return rc;
@@ -1120,6 +1199,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     key = fnv1a(&seed, sizeof(seed), key);
     key = fnv1a(&flags, sizeof(flags), key);
     key = fnv1a(&chunk, sizeof(chunk), key);
+    key = fnv1a(&variant, sizeof(variant), key);
     key = fnv1a(&out, sizeof(out), key);
     // the captured launches hold the context's device buffers: a reallocation
     // since the capture makes a new graph

@@ -11,6 +11,7 @@
 // simr_adjoint_path.cuh instead and add the 7 sensitivities.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "simr_adjoint_path.cuh"
@@ -22,9 +23,13 @@ namespace simr {
 namespace {
 
 // GSEG (adjoint books): every option is one segment of its whole path (no
-// forward pass), kept in a grid-wide buffer in global memory.
-template <bool ADJ, bool GSEG>
-__global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
+// forward pass), kept in a grid-wide buffer in global memory.  The tunable
+// shape: TPB threads per block; PPT paths per thread (price books: 2 stepped
+// together in packed FP32, or 1 at a time -- each lane then adds its two paths'
+// terms in the same order, so both give the same sums bit for bit); U, the
+// unrolling of the step-pair loop.
+template <bool ADJ, bool GSEG, int TPB, int PPT, int U>
+__global__ void __launch_bounds__(TPB) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
                                                            const BatchOption* __restrict__ opts,
                                                            const BatchItem* __restrict__ items,
                                                            unsigned int* __restrict__ counter,
@@ -72,9 +77,19 @@ __global__ void __launch_bounds__(128) heston_batch_kernel(const __grid_constant
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
       } else {
         terms[0] = terms[1] = 0.0f;
-        float2 x2, comp2;
-        simulate_two(c, steps, oidx, B.rk, I.path_begin + b + lane, I.path_begin + b + 32 + lane, x2, comp2);
-        const float xs[2] = {x2.x, x2.y}, cs[2] = {comp2.x, comp2.y};
+        float xs[2], cs[2];
+        if constexpr (PPT == 2) {
+          float2 x2, comp2;
+          simulate_two<U>(c, steps, oidx, B.rk, I.path_begin + b + lane, I.path_begin + b + 32 + lane, x2, comp2);
+          xs[0] = x2.x;
+          xs[1] = x2.y;
+          cs[0] = comp2.x;
+          cs[1] = comp2.y;
+        } else {
+#pragma unroll 1
+          for (int j = 0; j < 2; ++j)
+            simulate_one<false, U>(c, steps, oidx, B.rk, I.path_begin + b + 32 * j + lane, xs[j], cs[j]);
+        }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const bool active = b + 32 * j + lane < I.count;
@@ -122,41 +137,72 @@ __global__ void batch_reduce_kernel(const BatchOption* __restrict__ opts, uint32
   }
 }
 
-constexpr int kBatchTpb = 128;
+using BatchKernel = void (*)(BatchLaunch, const BatchOption*, const BatchItem*, unsigned int*, double*);
+
+// The kernel of a book's mode and shape: price books any of the kBatchVariants
+// (threads per block 128 / 256, paths per thread 2 / 1, unroll 1 / 2); adjoint
+// books the thread count only.
+BatchKernel batch_kernel(bool adjoint, bool gseg, int tpb, int ppt, int unroll) {
+  const bool t256 = tpb == 256;
+  if (adjoint) {
+    if (gseg) return t256 ? heston_batch_kernel<true, true, 256, 1, 1> : heston_batch_kernel<true, true, 128, 1, 1>;
+    return t256 ? heston_batch_kernel<true, false, 256, 1, 1> : heston_batch_kernel<true, false, 128, 1, 1>;
+  }
+  const bool p1 = ppt == 1, u2 = unroll == 2;
+  if (t256)
+    return p1 ? (u2 ? heston_batch_kernel<false, false, 256, 1, 2> : heston_batch_kernel<false, false, 256, 1, 1>)
+              : (u2 ? heston_batch_kernel<false, false, 256, 2, 2> : heston_batch_kernel<false, false, 256, 2, 1>);
+  return p1 ? (u2 ? heston_batch_kernel<false, false, 128, 1, 2> : heston_batch_kernel<false, false, 128, 1, 1>)
+            : (u2 ? heston_batch_kernel<false, false, 128, 2, 2> : heston_batch_kernel<false, false, 128, 2, 1>);
+}
+
+BatchKernel batch_kernel(const BatchLaunch& B) {
+  return batch_kernel(B.adjoint != 0, B.gseg != nullptr, B.tpb, B.ppt, B.unroll);
+}
 
 size_t batch_smem(const BatchLaunch& B) {
-  return B.adjoint && !B.gseg ? (size_t)(B.ckpt_rows + 3 * B.seg_rows) * kBatchTpb * sizeof(float) : 0;
+  return B.adjoint && !B.gseg ? (size_t)(B.ckpt_rows + 3 * B.seg_rows) * B.tpb * sizeof(float) : 0;
 }
 
 }  // namespace
 
+void batch_variant(int v, bool adjoint, BatchLaunch* B) {
+  B->tpb = (v & 1) ? 256 : 128;
+  B->ppt = adjoint ? 1 : ((v >> 1) & 1) ? 1 : 2;
+  B->unroll = adjoint ? 1 : ((v >> 2) & 1) ? 2 : 1;
+}
+
 cudaError_t prepare_batch(const BatchLaunch& B) {
   if (!B.adjoint || B.gseg) return cudaSuccess;
-  return cudaFuncSetAttribute(heston_batch_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)batch_smem(B));
+  return cudaFuncSetAttribute(batch_kernel(B), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(B));
 }
 
 cudaError_t batch_gseg_threads(int num_sms, size_t* threads) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_batch_kernel<true, true>, kBatchTpb, 0);
-  *threads = (size_t)num_sms * (size_t)per_sm * kBatchTpb;
-  return e;
+  // the largest grid any adjoint variant runs
+  *threads = 0;
+  for (int tpb = 128; tpb <= 256; tpb *= 2) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(true, true, tpb, 1, 1), tpb, 0);
+    if (e != cudaSuccess) return e;
+    *threads = std::max(*threads, (size_t)num_sms * (size_t)per_sm * tpb);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
                          double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream) {
   const size_t smem = batch_smem(B);
   int per_sm = 0;
-  auto kern = !B.adjoint ? heston_batch_kernel<false, false>
-              : B.gseg   ? heston_batch_kernel<true, true>
-                         : heston_batch_kernel<true, false>;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchTpb, smem);
+  const BatchKernel kern = batch_kernel(B);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B.tpb, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const unsigned grid = (unsigned)num_sms * (unsigned)per_sm;
+  if (B.adjoint && B.gseg && (size_t)grid * B.tpb * 3 * (size_t)B.seg_rows > B.gseg_floats)
+    return cudaErrorMemoryAllocation;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), stream);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kBatchTpb, smem, stream>>>(B, opts, items, counter, partials);
+  kern<<<grid, B.tpb, smem, stream>>>(B, opts, items, counter, partials);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nacc = B.adjoint ? kAdjAcc : 2;

@@ -649,8 +649,9 @@ __device__ __forceinline__ void step0_crn(const FirstConst& fb, const FirstConst
   v = v1;
 }
 
-// One path of one scenario over all steps: x_T with its Kahan remainder.
-template <bool QEM = false>
+// One path of one scenario over all steps: x_T with its Kahan remainder (U:
+// the step-pair loop unrolled U times).
+template <bool QEM = false, int U = 1>
 __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps, uint32_t option,
                                              const uint32_t (&rk)[10][2], uint64_t path, float& x, float& comp,
                                              const QemConst& q = QemConst{}) {
@@ -658,6 +659,7 @@ __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps,
   float v = c.v0;
   x = 0.0f;
   comp = 0.0f;
+#pragma unroll U
   for (uint32_t p = 0; 2 * p < steps; ++p) {
     const uint4 w = philox4x32_10(p, plo, phi, option, rk);
     {
@@ -674,7 +676,9 @@ __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps,
 }
 
 // Two paths of one scenario in lockstep (plain QE): simulate_one's arithmetic,
-// paired lane for lane, so each path's x_T and remainder equal simulate_one's.
+// paired lane for lane, so each path's x_T and remainder equal simulate_one's
+// (U: the step-pair loop unrolled U times).
+template <int U = 1>
 __device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps, uint32_t option,
                                              const uint32_t (&rk)[10][2], uint64_t path0, uint64_t path1,
                                              float2& x, float2& comp) {
@@ -683,6 +687,7 @@ __device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps,
   float2 v = make_float2(c.v0, c.v0);
   x = make_float2(0.0f, 0.0f);
   comp = make_float2(0.0f, 0.0f);
+#pragma unroll U
   for (uint32_t p = 0; 2 * p < steps; ++p) {
     const uint4 w0 = philox4x32_10(p, plo0, phi0, option, rk);
     const uint4 w1 = philox4x32_10(p, plo1, phi1, option, rk);

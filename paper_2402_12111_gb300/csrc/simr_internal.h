@@ -109,6 +109,8 @@ struct BatchLaunch {
   int32_t ckpt_rows;  // adjoint: checkpoint rows per thread column (max over options of n_seg - 1), even
   int32_t seg_rows;   // adjoint: rows of each segment array (max over options of ckpt_every)
   float* gseg;        // adjoint with one segment per path: [3 seg_rows][grid threads] in global memory, else null
+  size_t gseg_floats;  // its capacity
+  int32_t tpb, ppt, unroll;  // the kernel's shape (batch_variant)
 };
 
 struct BatchOutputs {
@@ -164,8 +166,14 @@ cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* 
 cudaError_t launch_batch(const BatchLaunch& B, const BatchOption* opts, const BatchItem* items, unsigned int* counter,
                          double* partials, const BatchOutputs& out, int num_sms, cudaStream_t stream);
 cudaError_t prepare_batch(const BatchLaunch& B);  // kernel attributes (outside any stream capture)
-// Threads of the adjoint book kernel's grid when its segments are in global memory.
+// Threads of the adjoint book kernel's grid when its segments are in global
+// memory (the largest over the kernel shapes).
 cudaError_t batch_gseg_threads(int num_sms, size_t* threads);
+// Kernel shape v of a book, v in [0, kBatchVariants): threads per block 128 /
+// 256 (bit 0); price books: paths per thread 2 / 1 (bit 1), step-pair loop
+// unrolled 1 / 2 times (bit 2); adjoint books use bit 0 only.
+constexpr int kBatchVariants = 8;
+void batch_variant(int v, bool adjoint, BatchLaunch* B);
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);

@@ -7,6 +7,7 @@ additions that follow (relative 1e-12).  A sample of the book is also checked
 against the FP64 oracle (prices 1e-5 relative + branch-flip allowance).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -64,6 +65,51 @@ def test_batch_adjoint_long_options_use_shared_segments(simr):
                                         o["is_put"], o["steps"], o["paths"], 6, ckpt_every=0, option_index=i)
         torch.testing.assert_close(p[i:i + 1], pi, rtol=1e-12, atol=1e-12)
         torch.testing.assert_close(g[i:i + 1], gi, rtol=1e-9, atol=1e-9)
+
+
+def test_every_kernel_shape_gives_the_same_results(simr, small_book):
+    # threads per block, paths per thread and unroll change the schedule, never
+    # the arithmetic or the grouping of the sums: bit for bit the same
+    ref = simr.batch(small_book, seed=12, variant=0)
+    for v in range(1, 8):
+        got = simr.batch(small_book, seed=12, variant=v)
+        torch.testing.assert_close(got[0], ref[0], rtol=0, atol=0)
+        torch.testing.assert_close(got[1], ref[1], rtol=0, atol=0)
+    refa = simr.batch(small_book[:12], seed=12, adjoint=True, variant=0)
+    got = simr.batch(small_book[:12], seed=12, adjoint=True, variant=1)
+    for a, b in zip(got, refa):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+    with pytest.raises(simr.SimrError):
+        simr.batch(small_book[:4], seed=12, adjoint=True, variant=2)  # adjoint books have two shapes
+
+
+def test_tuned_shape_is_written_to_the_cache_file(simr, tmp_path, monkeypatch):
+    import json
+    import subprocess
+    import sys
+
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SIMR_TUNE_CACHE", str(path))
+    # a book size class of its own (so this process tunes it now)
+    book = workloads.book(n_options=3, seed=21, steps_range=(2, 4), paths_range=(7, 9))
+    p0 = simr.batch(book, seed=3)[0]
+    lines = [json.loads(ln) for ln in path.read_text().splitlines()]
+    assert len(lines) == 1
+    e = lines[0]
+    assert set(e) >= {"gpu", "key", "chunk", "variant", "tpb", "ppt", "unroll"}
+    assert 0 <= e["variant"] < 8 and e["tpb"] in (128, 256) and e["ppt"] in (1, 2) and e["unroll"] in (1, 2)
+    assert e["chunk"] % 64 == 0
+    # a fresh process reads the file (a malformed line is skipped) and prices the same book
+    path.write_text("not json\n" + path.read_text())
+    code = ("import sys, torch, workloads, paper_2402_12111_gb300 as simr; "
+            "b = workloads.book(n_options=3, seed=21, steps_range=(2, 4), paths_range=(7, 9)); "
+            "print(repr(simr.batch(b, seed=3)[0].cpu().tolist()))")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root,
+                         env=dict(os.environ, SIMR_TUNE_CACHE=str(path)), timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert eval(out.stdout.strip().splitlines()[-1]) == p0.cpu().tolist()
+    assert len(path.read_text().splitlines()) == 2  # read, nothing re-tuned
 
 
 def test_batch_graph_replay_and_autotune_agree(simr, small_book):
