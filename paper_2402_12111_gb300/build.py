@@ -14,12 +14,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-OUT_DIR = os.path.join(HERE, "_build")
+# SIMR_IEEE=1 in the environment selects the build for error studies: correctly
+# rounded division, square roots and log2f in place of the special-function
+# unit's approximations, in its own directory beside the default one.
+IEEE = os.environ.get("SIMR_IEEE", "0") == "1"
+OUT_DIR = os.path.join(HERE, "_build_ieee" if IEEE else "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libsimr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
+              "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"] + (["-DSIMR_IEEE=1"] if IEEE else [])
 
 
 def nvcc() -> str:

@@ -78,25 +78,47 @@ struct FirstConst {
 };
 
 // ---------------------------------------------------------------- PTX ----
+// The special-function unit's approximations (MUFU), or with SIMR_IEEE=1 (a
+// build for error studies) the correctly rounded division, square root and
+// reciprocal square root and the library's log2f in their place.
+#ifndef SIMR_IEEE
+#define SIMR_IEEE 0
+#endif
 __device__ __forceinline__ float rcp_approx(float x) {
+#if SIMR_IEEE
+  return __frcp_rn(x);
+#else
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+#endif
 }
 __device__ __forceinline__ float sqrt_approx(float x) {
+#if SIMR_IEEE
+  return __fsqrt_rn(x);
+#else
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+#endif
 }
 __device__ __forceinline__ float rsqrt_approx(float x) {
+#if SIMR_IEEE
+  return __frsqrt_rn(x);
+#else
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+#endif
 }
 __device__ __forceinline__ float lg2_approx(float x) {
+#if SIMR_IEEE
+  return log2f(x);
+#else
   float r;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+#endif
 }
 
 // ------------------------------------------------- packed FP32 (f32x2) ----
