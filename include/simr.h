@@ -204,6 +204,18 @@ SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const 
                                  double* grad, void* stream);
 
 /*
+ * Host-side fault injection, for tests of the error paths (nothing reaches the
+ * GPU): the after-th next request of this process for context scratch memory
+ * (what = SIMR_FAULT_ALLOC; allocated or reused) or for a kernel launch (what =
+ * SIMR_FAULT_LAUNCH) fails as if the CUDA call had failed -- the entry point that
+ * meets it returns SIMR_ENOMEM or SIMR_ECUDA and leaves the context usable.
+ * what = 0 disarms.  after in [1, 2^30].  SIMR_EINVAL otherwise.
+ */
+#define SIMR_FAULT_ALLOC 1
+#define SIMR_FAULT_LAUNCH 2
+SIMR_API int simr_inject_fault(int what, int after);
+
+/*
  * The checkpoint interval simr_greeks_adjoint takes for ckpt_every = 0 with
  * n_strikes strikes (in [1, 256]) and `steps` time steps, in *ckpt_every.
  */

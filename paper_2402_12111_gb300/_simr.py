@@ -46,6 +46,7 @@ class Option(ctypes.Structure):
 
 
 BATCH_ADJOINT, BATCH_GRAPH, BATCH_NO_AUTOTUNE = 1, 2, 4
+FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 
 
 def batch_variant_flag(v: int) -> int:
@@ -107,6 +108,7 @@ def load(build_if_missing: bool = True):
         L.simr_greeks_adjoint.argtypes = [vp, H, dp, c_int, c_int, u32, u64, u64, u32, u32, dp, dp, dp, vp]
         L.simr_paths_adjoint.argtypes = [vp, H, u32, u64, u64, u64, u32, u32, dp, dp, vp]
         L.simr_adjoint_interval.argtypes = [vp, c_int, u32, ctypes.POINTER(u32)]
+        L.simr_inject_fault.argtypes = [c_int, c_int]
         L.simr_batch_submit.argtypes = [vp, ctypes.POINTER(Option), c_int, u64, u32, dp, dp, dp, vp]
         L.simr_lsm_price.argtypes = [vp, H, ctypes.c_double, c_int, u32, u32, u64, u64, u32, dp, dp, dp, dp, vp]
         L.simr_set_scheme.argtypes = [vp, c_int]

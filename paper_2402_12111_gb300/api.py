@@ -97,6 +97,13 @@ def adjoint_interval(n_strikes: int, steps: int, device: int = 0) -> int:
     return int(k.value)
 
 
+def inject_fault(what: str, after: int = 1) -> None:
+    """simr_inject_fault: the after-th next scratch request ("alloc") or kernel launch
+    ("launch") of this process fails on the host; "off" disarms."""
+    kinds = {"off": 0, "alloc": S.FAULT_ALLOC, "launch": S.FAULT_LAUNCH}
+    S.check(S.load().simr_inject_fault(kinds[what], int(after)))
+
+
 class HestonAdjoint(torch.autograd.Function):
     """Monte Carlo price as a differentiable function of the model parameters.
 

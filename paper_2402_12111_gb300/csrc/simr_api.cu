@@ -8,9 +8,12 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <numeric>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "simr.h"
 #include "simr_internal.h"
@@ -88,6 +91,18 @@ namespace {
 
 thread_local char g_err[512] = "";
 
+// simr_inject_fault: the armed kind and the requests left until it fires
+std::atomic<int> g_fault_what{0}, g_fault_left{0};
+
+// An NVTX range around a C-ABI call (visible to Nsight Systems and Nsight
+// Compute's NVTX filters; a no-op without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 int fail(int code, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -129,6 +144,8 @@ bool is_device_ptr(const void* p) {
 
 template <typename T>
 int ensure(T** buf, size_t* cap, size_t n, const char* what) {
+  if (take_fault(SIMR_FAULT_ALLOC))
+    return fail(SIMR_ENOMEM, "cudaMalloc of %s (%zu bytes) failed: injected fault", what, n * sizeof(T));
   if (*cap >= n) return SIMR_OK;
   if (*buf) cudaFree(*buf);
   *buf = nullptr;
@@ -550,7 +567,7 @@ int run_paths(simr_ctx* ctx, const PathLaunch& L, const double* dev_strikes, Out
   }
   Scratch s{ctx->partials, ctx->ticket, ctx->partial_doubles};
   int grid = 0;
-  cudaError_t e = launch_paths(L, dev_strikes, out, s, ctx->num_sms, st, &grid);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_paths(L, dev_strikes, out, s, ctx->num_sms, st, &grid);
   if (e != cudaSuccess) return cuda_fail(e, "launching the path kernel");
   return finish_outputs(ctx, o, st);
 }
@@ -663,7 +680,27 @@ int upload_batch(simr_ctx* ctx, const std::vector<BatchOption>& opts, const std:
 
 }  // namespace
 
+bool simr::take_fault(int what) {
+  if (g_fault_what.load(std::memory_order_relaxed) != what) return false;
+  if (g_fault_left.fetch_sub(1) != 1) return false;
+  g_fault_what.store(0);
+  return true;
+}
+
 extern "C" {
+
+int simr_inject_fault(int what, int after) {
+  if (what == 0) {
+    g_fault_what.store(0);
+    return SIMR_OK;
+  }
+  if ((what != SIMR_FAULT_ALLOC && what != SIMR_FAULT_LAUNCH) || after < 1 || after > (1 << 30))
+    return fail(SIMR_EINVAL, "simr_inject_fault: what must be 0, SIMR_FAULT_ALLOC or SIMR_FAULT_LAUNCH, after >= 1");
+  g_fault_what.store(0);
+  g_fault_left.store(after);
+  g_fault_what.store(what);
+  return SIMR_OK;
+}
 
 int simr_version(void) { return 100; }
 
@@ -734,6 +771,7 @@ void simr_destroy(simr_ctx* ctx) {
 }
 
 int simr_sync(simr_ctx* ctx, void* stream) {
+  const NvtxRange nvtx("simr_sync");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   int rc = with_device(ctx);
   if (rc) return rc;
@@ -747,6 +785,7 @@ int simr_sync(simr_ctx* ctx, void* stream) {
 int simr_price(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, double* price,
                double* stderr_out, void* stream) {
+  const NvtxRange nvtx("simr_price");
   int rc = check_common(ctx, model, strikes, n_strikes, 1024, steps, paths);
   if (rc) return rc;
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
@@ -770,6 +809,7 @@ int simr_price(simr_ctx* ctx, const simr_heston* model, const double* strikes, i
 int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                    uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, double rel_bump,
                    uint32_t greek_mask, double* price, double* greeks, void* stream) {
+  const NvtxRange nvtx("simr_greeks_fd");
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
   if (rc) return rc;
   if (!(rel_bump > 0.0 && rel_bump < 0.5)) return fail(SIMR_EINVAL, "rel_bump must lie in (0, 0.5)");
@@ -857,6 +897,7 @@ int simr_adjoint_interval(simr_ctx* ctx, int n_strikes, uint32_t steps, uint32_t
 int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                         uint32_t steps, uint64_t paths, uint64_t seed, uint32_t option_index, uint32_t ckpt_every,
                         double* price, double* stderr_out, double* grad, void* stream) {
+  const NvtxRange nvtx("simr_greeks_adjoint");
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
   if (rc) return rc;
   if (!price || !grad) return fail(SIMR_EINVAL, "price and grad must be non-NULL");
@@ -902,7 +943,7 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   AdjOutputs out{o.dev[0], o.dev[1], o.dev[2], ctx->status};
   Scratch sc{ctx->partials, ctx->ticket, ctx->partial_doubles, ctx->ckpt, ctx->ckpt_floats, ctx->gseg,
              ctx->gseg_floats};
-  cudaError_t e = launch_adjoint(L, A, ks, out, sc, ctx->num_sms, st);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_adjoint(L, A, ks, out, sc, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernel");
   return finish_outputs(ctx, o, st);
 }
@@ -910,6 +951,7 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
 int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin, uint64_t n_paths,
                        uint64_t seed, uint32_t option_index, uint32_t ckpt_every, float* x_T, float* grad,
                        void* stream) {
+  const NvtxRange nvtx("simr_paths_adjoint");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   int rc = check_model(model);
   if (rc) return rc;
@@ -927,7 +969,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   PathLaunch L;
   if ((rc = build_launch(model, 1, 0, steps, path_begin, n_paths, n_paths, seed, option_index, 1e-4, 0u, &L)))
     return rc;
-  cudaError_t e = launch_paths_adjoint(L, A, x_T, grad, (cudaStream_t)stream);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_paths_adjoint(L, A, x_T, grad, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching the per-path adjoint kernel");
   return SIMR_OK;
 }
@@ -935,6 +977,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
 int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                    uint32_t steps, uint64_t path_begin, uint64_t path_count, uint64_t seed, uint32_t option_index,
                    double rel_bump, uint32_t greek_mask, double* sums, void* stream) {
+  const NvtxRange nvtx("simr_path_sums");
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, path_count);
   if (rc) return rc;
   if (greek_mask & ~SIMR_G_ALL) return fail(SIMR_EINVAL, "unknown Greek bits");
@@ -961,6 +1004,7 @@ int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strike
 int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* strikes, int n_strikes, int is_put,
                        uint32_t steps, uint64_t paths, double rel_bump, uint32_t greek_mask, const double* sums,
                        double* price, double* stderr_out, double* greeks, void* stream) {
+  const NvtxRange nvtx("simr_finalize_sums");
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
   if (rc) return rc;
   if (!sums || !price) return fail(SIMR_EINVAL, "sums and price must be non-NULL");
@@ -995,7 +1039,7 @@ int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const double* st
   out.stderr_ = o.dev[1];
   out.greeks = o.dev[2];
   out.status = ctx->status;
-  cudaError_t e = launch_finalize(L, dsums, out, st);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_finalize(L, dsums, out, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the finalize kernel");
   return finish_outputs(ctx, o, st);
 }
@@ -1043,6 +1087,7 @@ void save_tune_entry(const simr_ctx* ctx, const simr_ctx::Tune& t, bool adjoint)
 
 int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64_t seed, uint32_t flags,
                       double* price, double* stderr_out, double* grad, void* stream) {
+  const NvtxRange nvtx("simr_batch_submit");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   if (!opts || n_opts < 1 || n_opts > (1 << 22)) return fail(SIMR_EINVAL, "n_opts must lie in [1, 2^22]");
   if (flags & ~(SIMR_BATCH_ADJOINT | SIMR_BATCH_GRAPH | SIMR_BATCH_NO_AUTOTUNE | (15u << 8)))
@@ -1145,7 +1190,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
       e = prepare_batch(B);
       if (e == cudaSuccess) e = cudaEventRecord(a, st);
       if (e == cudaSuccess)
-        e = launch_batch(B, ctx->b_opts, ctx->b_items, ctx->ticket + 32, ctx->b_partials, out, ctx->num_sms, st);
+        e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_batch(B, ctx->b_opts, ctx->b_items, ctx->ticket + 32, ctx->b_partials, out, ctx->num_sms, st);
       if (e == cudaSuccess) e = cudaEventRecord(b, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
       if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
@@ -1211,7 +1256,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t le = launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, gs);
+        cudaError_t le = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, gs);
         e = cudaStreamEndCapture(gs, &g);
         if (le != cudaSuccess) e = le;
       }
@@ -1227,7 +1272,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     if (e == cudaSuccess) e = cudaEventRecord(ctx->g_out, gs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->g_out, 0);
   } else {
-    e = launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, st);
+    e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_batch(B, ctx->b_opts, ctx->b_items, counter, ctx->b_partials, out, ctx->num_sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "launching the batch");
   return finish_outputs(ctx, o, st);
@@ -1236,6 +1281,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
 int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps, uint64_t path_begin,
                         uint64_t n_paths, uint64_t seed, uint32_t option_index, float* x_T, float* v_T,
                         void* stream) {
+  const NvtxRange nvtx("simr_paths_terminal");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   int rc = check_model(model);
   if (rc) return rc;
@@ -1256,7 +1302,7 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
     if (hx) dx = ctx->dev_f32;
     if (hv) dv = ctx->dev_f32 + n_paths;
   }
-  cudaError_t e = launch_terminal(L, dx, dv, st);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_terminal(L, dx, dv, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the terminal kernel");
   if (hx) e = cudaMemcpyAsync(x_T, dx, n_paths * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && hv) e = cudaMemcpyAsync(v_T, dv, n_paths * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -1268,6 +1314,7 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
 int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
                       const double* weights, const double* strikes, int n_strikes, int is_put, uint32_t steps,
                       uint64_t paths, uint64_t seed, double* price, double* stderr_out, void* stream) {
+  const NvtxRange nvtx("simr_basket_price");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   if (!assets || !corr || !weights) return fail(SIMR_EINVAL, "assets, corr and weights must be non-NULL");
   if (n_assets < 1 || n_assets > kMaxAssets) return fail(SIMR_EINVAL, "n_assets must lie in [1, %d]", kMaxAssets);
@@ -1354,7 +1401,7 @@ int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, co
                    "reduction scratch")))
     return rc;
   BasketOutputs out{o.dev[0], o.dev[1], ctx->status};
-  cudaError_t e = launch_basket(L, ks, out, ctx->partials, ctx->partial_doubles, ctx->ticket, ctx->num_sms, st);
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_basket(L, ks, out, ctx->partials, ctx->partial_doubles, ctx->ticket, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the basket kernel");
   return finish_outputs(ctx, o, st);
 }
@@ -1369,6 +1416,7 @@ int simr_set_scheme(simr_ctx* ctx, int scheme) {
 int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put, uint32_t steps,
                    uint32_t exercise_every, uint64_t paths, uint64_t seed, uint32_t option_index, double* price,
                    double* stderr_out, double* beta, int32_t* stop, void* stream) {
+  const NvtxRange nvtx("simr_lsm_price");
   if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
   int rc = check_model(model);
   if (rc) return rc;
@@ -1462,7 +1510,7 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
                o.dev[0],
                o.dev[1]};
   if (o.dev[2]) e = cudaMemsetAsync(o.dev[2], 0xff, (size_t)n_ex * 6 * sizeof(double), st);
-  if (e == cudaSuccess) e = launch_lsm(L, B, ctx->num_sms, st);
+  if (e == cudaSuccess) e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_lsm(L, B, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the Longstaff-Schwartz kernels");
   if (stop) {
     e = cudaMemcpyAsync(stop, ctx->lsm_stop, (size_t)paths * sizeof(int32_t), cudaMemcpyDefault, st);

@@ -129,6 +129,10 @@ struct Scratch {
   size_t gseg_floats = 0;
 };
 
+// Host-side fault injection (simr_inject_fault): true when this request of the
+// given kind is the one armed to fail (and disarms it).
+bool take_fault(int what);
+
 // Launch the fused price / Greeks kernel; returns a cudaError_t.
 cudaError_t launch_paths(const PathLaunch& L, const double* strikes_dev, const PathOutputs& out,
                          const Scratch& s, int num_sms, cudaStream_t stream, int* grid_used);

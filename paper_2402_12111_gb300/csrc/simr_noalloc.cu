@@ -93,7 +93,8 @@ extern "C" SIMR_API int simr_price_noalloc(const simr_heston* model, const doubl
   out.status = reinterpret_cast<int*>(slot->base + 64);
   simr::Scratch s{reinterpret_cast<double*>(slot->base + kHeaderBytes), ticket, kPartialDoubles};
   int grid = 0;
-  e = simr::launch_paths(L, strikes, out, s, slot->num_sms, st, &grid);
+  e = simr::take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources
+                                          : simr::launch_paths(L, strikes, out, s, slot->num_sms, st, &grid);
   if (e == cudaErrorMemoryAllocation)
     return simr::internal_fail(SIMR_EUNSUPPORTED, "launch needs more partial sums than the static scratch holds");
   if (e != cudaSuccess) return simr::internal_cuda_fail(e, "launching the path kernel");

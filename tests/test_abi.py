@@ -90,3 +90,15 @@ def test_bench_source_hash_ignores_comments_only():
     assert bench._code_only(code) == bench._code_only(same)
     assert bench._code_only(code) != bench._code_only(other)
     assert '"x // y /* z"' in bench._code_only(code)
+
+
+def test_fault_injection_hook_arguments(libpath):
+    # arming and disarming needs no GPU; bad arguments are refused
+    lib = ctypes.CDLL(libpath)
+    lib.simr_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int]
+    assert lib.simr_inject_fault(1, 3) == 0
+    assert lib.simr_inject_fault(0, 0) == 0
+    assert lib.simr_inject_fault(2, 1) == 0
+    assert lib.simr_inject_fault(0, 0) == 0
+    assert lib.simr_inject_fault(3, 1) != 0
+    assert lib.simr_inject_fault(1, 0) != 0

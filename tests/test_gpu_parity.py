@@ -239,3 +239,29 @@ def test_device_strike_error_reported_by_sync(simr):
     assert e.value.code == -1
     assert math.isnan(p[1].item()) and math.isfinite(p[0].item())
     simr.sync(0)  # status was cleared
+
+
+def test_injected_faults_are_reported_and_the_context_survives(simr):
+    # host-side fault injection: the call that meets the fault fails with its
+    # status, nothing reaches the GPU for it, and the next call is unaffected
+    K = _dev([90.0, 100.0, 110.0])
+    ref = simr.price(CFG, K, False, 32, 4096, 3)[0]
+    simr.inject_fault("launch")
+    with pytest.raises(simr.SimrError) as e:
+        simr.price(CFG, K, False, 32, 4096, 3)
+    assert e.value.code == -3  # SIMR_ECUDA
+    torch.testing.assert_close(simr.price(CFG, K, False, 32, 4096, 3)[0], ref, rtol=0, atol=0)
+    simr.inject_fault("alloc")
+    with pytest.raises(simr.SimrError) as e:
+        simr.greeks_adjoint(CFG, K, False, 32, 4096, 3)
+    assert e.value.code == -2  # SIMR_ENOMEM
+    a = simr.greeks_adjoint(CFG, K, False, 32, 4096, 3)
+    torch.testing.assert_close(a[0], ref, rtol=1e-6, atol=1e-9)
+    for name, call in (("launch", lambda: simr.batch([dict(model=CFG, K=100.0, is_put=False, steps=8, paths=999)])),
+                       ("launch", lambda: simr.lsm_price(CFG, 100.0, True, 16, 4, 999, 1)),
+                       ("alloc", lambda: simr.basket_price([CFG, CFG], np.eye(2), [0.5, 0.5], [100.0]))):
+        simr.inject_fault(name)
+        with pytest.raises(simr.SimrError):
+            call()
+        call()
+    simr.inject_fault("off")
