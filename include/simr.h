@@ -43,6 +43,15 @@
  *  - Model validity: S0, K, T > 0; v0, theta >= 0; kappa > 0; sigma > 0 (the
  *    log-spot coefficients divide by sigma); rho in [-1, 1]; all finite;
  *    steps >= 1; paths >= 1.
+ *  - Every compute entry point opens an NVTX range named after itself.
+ *
+ * Environment read at run time: SIMR_AUTOTUNE=0 (books run without the
+ * first-call search of simr_batch_submit), SIMR_TUNE_CACHE=<file> (its tuned
+ * choices persist there), SIMR_LSM_SWEEP=0 (simr_lsm_price runs one kernel per
+ * exercise date instead of the cooperative sweep).  At build time
+ * (paper_2402_12111_gb300/build.py): SIMR_IEEE=1 builds the error-study
+ * library, with correctly rounded division, square roots and log2 in place of
+ * the special-function unit's approximations.
  */
 #ifndef SIMR_H
 #define SIMR_H
