@@ -49,18 +49,49 @@ inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int t
   return racc ? head + (buf_bytes > acc_bytes ? buf_bytes : acc_bytes) : acc_bytes + head + buf_bytes;
 }
 
+// The per-strike terms of a 32-strike tile, lane l owning strike K (the
+// tile's strike l): the warp's paths are broadcast one at a time -- terminal
+// spot and d x_T / d(v0, kappa, theta, sigma, rho) -- and each lane adds its
+// strike's payoff f, f^2, and the in-the-money weight w (S_T for a call above
+// its strike, -S_T for a put below) alone and times each derivative; FP32 over
+// the warp's paths.  out[0..7]: f, f^2, w, w dx/dv0 .. w dx/drho (the S0 and r
+// columns are w / S0 and w T: scaled when added to the FP64 sums).
+template <int PPT>
+__device__ __forceinline__ void strike_tile_terms(bool put, float K, const float (&S)[PPT], const bool (&act)[PPT],
+                                                  const float (&g)[PPT][5], float (&out)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) out[a] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const unsigned live = __ballot_sync(kFull, act[j]);
+#pragma unroll 4
+    for (int p = 0; p < kWarp; ++p) {
+      const float Sp = __shfl_sync(kFull, S[j], p);
+      float gp[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gp[k] = __shfl_sync(kFull, g[j][k], p);
+      if ((live >> p) & 1u) {  // warp-uniform
+        const float f = put ? fmaxf(K - Sp, 0.0f) : fmaxf(Sp - K, 0.0f);
+        const float w = put ? (Sp < K ? -Sp : 0.0f) : (Sp > K ? Sp : 0.0f);
+        out[0] += f;
+        out[1] = fmaf(f, f, out[1]);
+        out[2] += w;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) out[3 + k] = fmaf(w, gp[k], out[3 + k]);
+      }
+    }
+  }
+}
+
 #ifndef SIMR_ADJ_MINB
-#define SIMR_ADJ_MINB 1  // minimum resident blocks per SM asked of the register allocator (32-strike tiles)
-#endif
-#ifndef SIMR_ADJ_MINB_1
-#define SIMR_ADJ_MINB_1 5  // the same for one strike: 5 blocks measured 4.5% faster than the allocator's choice
+#define SIMR_ADJ_MINB 5  // minimum resident blocks per SM asked of the register allocator (measured 4-5% faster than its own choice)
 #endif
 
 // GSEG: the segment buffers in global memory, [3 k][grid threads] (for a
 // segment too long for shared memory, in particular one segment of the whole
 // path: no forward pass).
 template <int TILE, int PPT, bool RACC, bool GSEG>
-__global__ void __launch_bounds__(128, TILE == 1 ? SIMR_ADJ_MINB_1 : SIMR_ADJ_MINB) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
+__global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
                                                              double* __restrict__ partials,
@@ -122,50 +153,43 @@ __global__ void __launch_bounds__(128, TILE == 1 ? SIMR_ADJ_MINB_1 : SIMR_ADJ_MI
 #pragma unroll
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
-    // per-strike terms, reduced over the warp's paths
+    // per-strike terms, summed over the warp's paths
     if (RACC) {
+      float t[8];
+      strike_tile_terms<PPT>(put, ks[lane].K, S, act, g, t);
 #pragma unroll
+      for (int a = 0; a < 8; ++a) racc[a] += (double)t[a];
+    } else if (TILE == 1) {
       for (int a = 0; a < kAdjAcc; ++a) {
-        float vals[32];
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          float t = 0.0f;
-#pragma unroll
-          for (int j = 0; j < PPT; ++j) t += act[j] ? adj_term(a, put, S[j], ks[jj].K, g[j], A.invS0, A.T) : 0.0f;
-          vals[jj] = t;
-        }
-        butterfly32(vals, lane);
-        racc[a] += (double)vals[0];
-      }
-    } else
-    for (int a = 0; a < kAdjAcc; ++a) {
-      if (TILE == 1) {
         float t = 0.0f;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) t += act[j] ? adj_term(a, put, S[j], ks[0].K, g[j], A.invS0, A.T) : 0.0f;
         t = warp_sum(t);
         if (lane == 0) my_acc[a] += (double)t;
-      } else {
-        for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
-          float vals[32];
+      }
+    } else {
+      for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
+        float t[8];
+        strike_tile_terms<PPT>(put, ks[t0 + lane].K, S, act, g, t);
+        double* row = my_acc + t0 + lane;
+        row[0] += (double)t[0];
+        row[(size_t)L.nk_pad] += (double)t[1];
+        row[(size_t)2 * L.nk_pad] += (double)t[2] * (double)A.invS0;
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            float t = 0.0f;
-#pragma unroll
-            for (int j = 0; j < PPT; ++j)
-              t += act[j] ? adj_term(a, put, S[j], ks[t0 + jj].K, g[j], A.invS0, A.T) : 0.0f;
-            vals[jj] = t;
-          }
-          butterfly32(vals, lane);
-          my_acc[(size_t)a * L.nk_pad + t0 + lane] += (double)vals[0];
-        }
+        for (int a = 3; a < 8; ++a) row[(size_t)a * L.nk_pad] += (double)t[a];
+        row[(size_t)8 * L.nk_pad] += (double)t[2] * (double)A.T;
       }
     }
   }
   __syncthreads();
   if (RACC) {  // the segment buffers are free now: spill the lanes' sums into the rows
+    // racc[2] holds the weights w: the S0 column is w / S0, the r column w T
+    my_acc[lane] = racc[0];
+    my_acc[(size_t)L.nk_pad + lane] = racc[1];
+    my_acc[(size_t)2 * L.nk_pad + lane] = racc[2] * (double)A.invS0;
 #pragma unroll
-    for (int a = 0; a < kAdjAcc; ++a) my_acc[(size_t)a * L.nk_pad + lane] = racc[a];
+    for (int a = 3; a < 8; ++a) my_acc[(size_t)a * L.nk_pad + lane] = racc[a];
+    my_acc[(size_t)8 * L.nk_pad + lane] = racc[2] * (double)A.T;
     __syncthreads();
   }
 
