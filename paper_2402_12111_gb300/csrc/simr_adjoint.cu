@@ -19,7 +19,9 @@
 // mapped once per path onto d x_T / d(v0, kappa, theta, sigma, rho) with
 // FP64-derived constants.  Price sensitivities per strike (reduction over paths,
 // Sec. 6): dP/dq = e^{-rT} mean[f'(S_T) S_T dx_T/dq], plus S_T/S0 for S0 and
-// T - T P for r.  Same FP32-butterfly / FP64 reduction as the pricing kernel.
+// T - T P for r.  The terms are summed in FP32 over a warp's paths (one strike
+// per lane for 32-strike tiles, a warp sum for one strike) and in FP64 on, as
+// in the pricing kernel.
 #include <cuda_runtime.h>
 
 #include <cstdint>
