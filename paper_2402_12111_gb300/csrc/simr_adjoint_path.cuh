@@ -43,7 +43,7 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
   const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
   const float dlbar = c.Cdl;
   float mbar = 0.0f, s2bar = 0.0f, dl = 0.0f;
-  if (s2 <= 1.5f * m2 && m2 > 0.0f) {
+  if (s2 < 1.5f * m2) {  // the forward step's branch test
     const float zv = d;
     const float rs2 = rcp_approx(s2);
     const float t = 2.0f * m2 * rs2;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
 __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float omu, float zv) {
   const float m = fmaf(v, c.E, c.thE);
   const float s2 = fmaf(v, c.c1, c.c2);
-  return (s2 <= 1.5f * (m * m) && m * m > 0.0f) ? zv : omu;
+  return s2 < 1.5f * (m * m) ? zv : omu;
 }
 
 // The stored data of one step (recompute pass): (state, branch draw) as one

@@ -262,7 +262,12 @@ __device__ __forceinline__ float2 norminv_centered2(float2 x) {
 //                          t = 2/psi, a = m / (1 + b^2)
 //   psi > 1.5            : p = (psi-1)/(psi+1); v' = 0 if U_V <= p,
 //                          else ((1-p)/m)^-1 ln((1-p)/(1-U_V))
-// The branch test s^2 <= 1.5 m^2 needs no division; U_V <= p is tested as
+// The branch test needs no division: s^2 < 1.5 m^2 in FP32, strictly, so that
+// m = 0 (theta = 0 and v = 0: then s^2 = 0 as well) falls through to the
+// exponential branch's m > 0 test (v' = 0) with no test of its own in the
+// common path; an exact FP32 tie -- at FP32 distance from the threshold, where
+// the FP64 reading psi <= psi_c can go either way anyway -- takes the
+// exponential branch.  U_V <= p is tested as
 // (1 - U_V)(m^2 + s^2) >= 2 m^2.  Besides v' it returns dl = v' - m (the
 // innovation the log-spot step needs) without cancellation in the quadratic
 // branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1) since m = a (1 + b^2).
@@ -288,7 +293,7 @@ __device__ __forceinline__ void qe_exp_branch(float m, float s2, float m2, float
 __device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, float zv, float& v_next,
                                                 float& dl) {
   const float m2 = __fmul_rn(m, m);
-  if (s2 <= __fmul_rn(1.5f, m2) && m2 > 0.0f) {
+  if (s2 < __fmul_rn(1.5f, m2)) {
     const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
     const float root = sqrt_approx(__fmaf_rn(t, t, -t));
     const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
@@ -316,7 +321,7 @@ __device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2, float2 omu
   const float2 bz = p_add(b, zv);
   v_next = p_mul(p_mul(a, bz), bz);
   dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
-  const bool qx = s2.x <= lim.x && m2.x > 0.0f, qy = s2.y <= lim.y && m2.y > 0.0f;
+  const bool qx = s2.x < lim.x, qy = s2.y < lim.y;
   if (!(qx && qy)) {  // one test on the common path
     if (!qx) qe_exp_branch(m.x, s2.x, m2.x, omu.x, v_next.x, dl.x);
     if (!qy) qe_exp_branch(m.y, s2.y, m2.y, omu.y, v_next.y, dl.y);
@@ -411,7 +416,7 @@ __device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, f
                                                  float& dl, float& lam) {
   const float m2 = __fmul_rn(m, m);
   lam = 0.0f;
-  if (s2 <= __fmul_rn(1.5f, m2) && m2 > 0.0f) {
+  if (s2 < __fmul_rn(1.5f, m2)) {
     const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
     const float root = sqrt_approx(__fmaf_rn(t, t, -t));
     const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
@@ -485,7 +490,7 @@ __device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q,
   const float2 lim = p_mul(p_bc(1.5f), m2);
   float2 vn, dl, lam;
   bool okx, oky;
-  if (s2.x <= lim.x && m2.x > 0.0f && s2.y <= lim.y && m2.y > 0.0f) {
+  if (s2.x < lim.x && s2.y < lim.y) {
     const float2 t = p_mul(p_mul(p_bc(2.0f), m2), p_rcp(s2));
     const float2 root = p_sqrt(p_fma(t, t, p_mul(t, p_bc(-1.0f))));
     const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
