@@ -79,6 +79,24 @@ def test_terminal_states_per_path(simr, model, steps, n, begin, xf):
     assert np.quantile(dv, 0.999) < 1e-4, dv.max()
 
 
+@pytest.mark.parametrize("k", [0, 6])
+def test_headline_paths_at_the_end_of_the_range(simr, k):
+    # the headline book's shape at its sampled outputs: 1,024 steps, the last
+    # 2,048 of an underlying's 2^26 paths, one by one against the oracle
+    u = workloads.headline()[k]
+    n, begin = 2048, (1 << 26) - 2048
+    x, v = simr.paths_terminal(u.model, u.steps, begin, n, seed=u.seed)
+    x, v = x.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    xo, vo, mg = oracle.terminal(u.model, u.steps, u.seed, begin, n)
+    ok = mg > FLIP_MARGIN
+    assert ok.mean() > 0.95
+    assert np.all(np.isfinite(x)) and np.all(v >= 0)
+    dx = np.abs(x - xo)[ok]
+    bound = 1.5e-7 * math.sqrt(u.steps) + 1e-6
+    assert np.quantile(dx, 0.999) < bound, (np.quantile(dx, 0.999), dx.max())
+    assert np.mean(dx > bound) <= 0.005
+
+
 # --------------------------------------------------------------- prices ----
 PRICE_CASES = [
     ("cfg_single", CFG, [100.0], False, 64, 65536, 1),
