@@ -256,13 +256,13 @@ def run_reference(args):
     oracle.build()
     cores = oracle.max_threads()
     sample = 1 << 13
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 3)):
         cpu_oracle_run(w, sample)
     times = [cpu_oracle_run(w, sample) for _ in range(args.steps)]
     total = sum(times)
     value = args.steps * sample * w.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "paths": w.paths, "time_steps": w.steps, "strikes": len(w.strikes),
