@@ -27,6 +27,73 @@ struct AdjSums {
   float x, comp;  // x_T accumulated over the reverse sweep (Kahan-compensated)
 };
 
+// The reverse step's quantities of the quadratic branch that do not depend on
+// the adjoint carried in from the later steps (functions of v_n, m, s^2, Z_V).
+struct AdjQuad {
+  float rs2, t, rroot, rb, ropb2, am, bz, g;
+};
+
+__device__ __forceinline__ AdjQuad adj_quad(float m, float m2, float s2, float zv) {
+  AdjQuad Q;
+  Q.rs2 = rcp_approx(s2);
+  Q.t = 2.0f * m2 * Q.rs2;
+  const float tt = fmaf(Q.t, Q.t, -Q.t);
+  Q.rroot = rsqrt_approx(tt);
+  const float root = tt * Q.rroot;
+  const float b2 = (Q.t - 1.0f) + root;
+  Q.rb = rsqrt_approx(b2);
+  const float b = b2 * Q.rb;
+  Q.ropb2 = rcp_approx(Q.t + root);  // 1 / (1 + b^2)
+  Q.am = m * Q.ropb2;
+  Q.bz = b + zv;
+  Q.g = fmaf(zv, zv + 2.0f * b, -1.0f);
+  return Q;
+}
+
+// The end of a reverse step once mbar and s2bar are known: x_T's increment
+// (Kahan-compensated), the adjoint of v_n, and the seven sums.
+__device__ __forceinline__ void adj_tail(const ScenConst& c, float theta, float vc, float q, float zx, float hz,
+                                         float dl, float inc, float mbar, float s2bar, AdjSums& a) {
+  const float y = inc - a.comp;
+  const float tx = a.x + y;
+  a.comp = (tx - a.x) - y;
+  a.x = tx;
+  a.vbar = (c.Cv - c.Cd + hz) + fmaf(mbar, c.E, s2bar * c.c1);
+  a.Am += mbar;
+  a.Amv = fmaf(mbar, vc - theta, a.Amv);
+  a.As += s2bar;
+  a.Asv = fmaf(s2bar, vc, a.Asv);
+  a.Ad += theta - vc;
+  a.Adl += dl;
+  a.Ak3 = fmaf(q, zx, a.Ak3);
+}
+
+// The adjoint chain of a quadratic-branch reverse step: from the adjoint of
+// v_{n+1} through the QE map's derivatives to mbar and s2bar, then adj_tail.
+__device__ __forceinline__ void adj_chain_quad(const ScenConst& c, float theta, float vc, float m, float zv, float q,
+                                               float zx, float hz, float dl, float inc, const AdjQuad& Q,
+                                               AdjSums& a) {
+  const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
+  const float dlbar = c.Cdl;
+  const float abar = fmaf(vnbar, Q.bz * Q.bz, dlbar * Q.g);
+  const float bbar = 2.0f * Q.am * fmaf(vnbar, Q.bz, dlbar * zv);
+  const float b2bar = fmaf(0.5f * bbar, Q.rb, -abar * Q.am * Q.ropb2);
+  float mbar = abar * Q.ropb2;
+  const float tbar = b2bar * fmaf(2.0f * Q.t - 1.0f, 0.5f * Q.rroot, 1.0f);
+  mbar = fmaf(tbar * 4.0f * m, Q.rs2, mbar);
+  const float s2bar = -tbar * Q.t * Q.rs2;
+  adj_tail(c, theta, vc, q, zx, hz, dl, inc, mbar, s2bar, a);
+}
+
+// The step's log-spot increment (LogPricePathQE), summed into x_T in the
+// reverse sweep rather than in the forward pass.
+__device__ __forceinline__ float adj_inc(const ScenConst& c, float s, float vc, float dl, float q, float zx) {
+  float inc = fmaf(c.Cv, s, c.C0);
+  inc = fmaf(-c.Cd, vc, inc);
+  inc = fmaf(c.Cdl, dl, inc);
+  return fmaf(c.sK3 * q, zx, inc);
+}
+
 // Reverse step n: state vc -> vn (both known), the step's stored draw d (Z_V in
 // the quadratic branch, 1 - U_V in the exponential one; the branch follows from
 // vc) and Z_X; vbar holds the adjoint of v_{n+1} on entry and of v_n on exit.
@@ -40,32 +107,16 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
   const float rq = rsqrt_approx(s);
   const float q = s > 0.0f ? s * rq : 0.0f;
   const float hz = s > 0.0f ? 0.5f * c.sK3 * zx * rq : 0.0f;  // d(sK3 sqrt(s) Z)/ds
+  if (s2 < 1.5f * m2) {  // the forward step's branch test
+    const AdjQuad Q = adj_quad(m, m2, s2, d);
+    const float dl = Q.am * Q.g;
+    adj_chain_quad(c, theta, vc, m, d, q, zx, hz, dl, adj_inc(c, s, vc, dl, q, zx), Q, a);
+    return;
+  }
   const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
   const float dlbar = c.Cdl;
   float mbar = 0.0f, s2bar = 0.0f, dl = 0.0f;
-  if (s2 < 1.5f * m2) {  // the forward step's branch test
-    const float zv = d;
-    const float rs2 = rcp_approx(s2);
-    const float t = 2.0f * m2 * rs2;
-    const float tt = fmaf(t, t, -t);
-    const float rroot = rsqrt_approx(tt);
-    const float root = tt * rroot;
-    const float b2 = (t - 1.0f) + root;
-    const float rb = rsqrt_approx(b2);
-    const float b = b2 * rb;
-    const float ropb2 = rcp_approx(t + root);  // 1 / (1 + b^2)
-    const float am = m * ropb2;
-    const float bz = b + zv;
-    const float g = fmaf(zv, zv + 2.0f * b, -1.0f);
-    dl = am * g;
-    const float abar = fmaf(vnbar, bz * bz, dlbar * g);
-    const float bbar = 2.0f * am * fmaf(vnbar, bz, dlbar * zv);
-    const float b2bar = fmaf(0.5f * bbar, rb, -abar * am * ropb2);
-    mbar = abar * ropb2;
-    const float tbar = b2bar * fmaf(2.0f * t - 1.0f, 0.5f * rroot, 1.0f);
-    mbar = fmaf(tbar * 4.0f * m, rs2, mbar);
-    s2bar = -tbar * t * rs2;
-  } else if (m > 0.0f) {
+  if (m > 0.0f) {
     const float omu = d;
     const float ms = m2 + s2;
     const float W = omu * ms;
@@ -85,24 +136,55 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
       s2bar = (vnbar + dlbar) * dv_ds;
     }
   }
-  // the step's log-spot increment (LogPricePathQE), summed into x_T here rather
-  // than in the forward pass
-  float inc = fmaf(c.Cv, s, c.C0);
-  inc = fmaf(-c.Cd, vc, inc);
-  inc = fmaf(c.Cdl, dl, inc);
-  inc = fmaf(c.sK3 * q, zx, inc);
-  const float y = inc - a.comp;
-  const float tx = a.x + y;
-  a.comp = (tx - a.x) - y;
-  a.x = tx;
-  a.vbar = (c.Cv - c.Cd + hz) + fmaf(mbar, c.E, s2bar * c.c1);
-  a.Am += mbar;
-  a.Amv = fmaf(mbar, vc - theta, a.Amv);
-  a.As += s2bar;
-  a.Asv = fmaf(s2bar, vc, a.Asv);
-  a.Ad += theta - vc;
-  a.Adl += dl;
-  a.Ak3 = fmaf(q, zx, a.Ak3);
+  adj_tail(c, theta, vc, q, zx, hz, dl, adj_inc(c, s, vc, dl, q, zx), mbar, s2bar, a);
+}
+
+// Two consecutive reverse steps, n (lane x) then n - 1 (lane y): when both
+// take the quadratic branch, their quantities that do not depend on the
+// carried adjoint -- moments, square roots, the branch's terms, the log-spot
+// increment -- in packed FP32, then the two adjoint chains in order; else two
+// adjoint_step calls.  Lane for lane adjoint_step's operations, so the same
+// sums bit for bit however the steps are paired.
+__device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, float2 vc, float2 vn, float2 d,
+                                              float2 zx, AdjSums& a) {
+  const float2 m = p_fma(vc, p_bc(c.E), p_bc(c.thE));
+  const float2 s2 = p_fma(vc, p_bc(c.c1), p_bc(c.c2));
+  const float2 m2 = p_mul(m, m);
+  const float2 lim = p_mul(p_bc(1.5f), m2);
+  if (!(s2.x < lim.x && s2.y < lim.y)) {
+    adjoint_step(c, theta, vc.x, vn.x, d.x, zx.x, a);
+    adjoint_step(c, theta, vc.y, vn.y, d.y, zx.y, a);
+    return;
+  }
+  const float2 s = p_add(vc, vn);
+  const float2 rq = make_float2(rsqrt_approx(s.x), rsqrt_approx(s.y));
+  const float2 sq = p_mul(s, rq);
+  const float2 hq = p_mul(p_mul(p_bc(0.5f * c.sK3), zx), rq);
+  const float2 q = make_float2(s.x > 0.0f ? sq.x : 0.0f, s.y > 0.0f ? sq.y : 0.0f);
+  const float2 hz = make_float2(s.x > 0.0f ? hq.x : 0.0f, s.y > 0.0f ? hq.y : 0.0f);
+  // adj_quad, paired
+  const float2 rs2 = p_rcp(s2);
+  const float2 t = p_mul(p_mul(p_bc(2.0f), m2), rs2);
+  const float2 tt = p_fma(t, t, p_mul(t, p_bc(-1.0f)));
+  const float2 rroot = make_float2(rsqrt_approx(tt.x), rsqrt_approx(tt.y));
+  const float2 root = p_mul(tt, rroot);
+  const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+  const float2 rb = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
+  const float2 b = p_mul(b2, rb);
+  const float2 ropb2 = p_rcp(p_add(t, root));
+  const float2 am = p_mul(m, ropb2);
+  const float2 bz = p_add(b, d);
+  const float2 g = p_fma(d, p_add(d, p_mul(p_bc(2.0f), b)), p_bc(-1.0f));
+  const float2 dl = p_mul(am, g);
+  // adj_inc, paired
+  float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
+  inc = p_fma(p_bc(-c.Cd), vc, inc);
+  inc = p_fma(p_bc(c.Cdl), dl, inc);
+  inc = p_fma(p_mul(p_bc(c.sK3), q), zx, inc);
+  const AdjQuad Qx{rs2.x, t.x, rroot.x, rb.x, ropb2.x, am.x, bz.x, g.x};
+  const AdjQuad Qy{rs2.y, t.y, rroot.y, rb.y, ropb2.y, am.y, bz.y, g.y};
+  adj_chain_quad(c, theta, vc.x, m.x, d.x, q.x, zx.x, hz.x, dl.x, inc.x, Qx, a);
+  adj_chain_quad(c, theta, vc.y, m.y, d.y, q.y, zx.y, hz.y, dl.y, inc.y, Qy, a);
 }
 
 // The draw the reverse step of state v needs: Z_V in the quadratic branch,
@@ -163,7 +245,7 @@ __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a,
 // thread's segment column S (at least k rows) -- then the steps are
 // differentiated backwards.  x_T (with its Kahan remainder) is summed on the
 // way; g = d x_T / d(v0, kappa, theta, sigma, rho).
-template <typename Seg>
+template <typename Seg, bool PAIRED>
 __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                            const uint32_t (&rk)[10][2], uint32_t plo, uint32_t phi,
                                            const float* ck, int cstride, float v_last, const Seg& S,
@@ -191,32 +273,88 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
       if (2 * p + 1 < n1) keep_step(c, xb, zv.y, zx.y, s01 + i + bd, s2 + i + bd, vv);
     }
     float vnext = vv;  // v_{n1}
-    if constexpr (Seg::kGlobal) {
-      // global memory: each step's data loaded one step ahead into registers,
-      // and asked into L2 kPrefetchSteps steps ahead
-      constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
-      int i = (int)(n1 - n0) - 1;
-      float2 vd_n = s01[(I)i * bd];
-      float zx_n = s2[(I)i * bd];
-      for (; i >= 0; --i) {
-        const float2 vd = vd_n;
-        const float zx = zx_n;
-        if (i >= kPrefetchSteps) {
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - kPrefetchSteps) * bd));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - kPrefetchSteps) * bd));
+    if constexpr (PAIRED) {
+      if constexpr (Seg::kGlobal) {
+        // global memory: the steps in pairs (n, n - 1) from the top, each pair's
+        // data loaded one pair ahead into registers and asked into L2
+        // kPrefetchSteps steps ahead
+        constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
+        int i = (int)(n1 - n0) - 1;
+        float2 pa = s01[(I)i * bd], pb = make_float2(0.0f, 0.0f);
+        float za = s2[(I)i * bd], zb = 0.0f;
+        if (i >= 1) {
+          pb = s01[(I)(i - 1) * bd];
+          zb = s2[(I)(i - 1) * bd];
         }
-        if (i > 0) {
-          vd_n = s01[(I)(i - 1) * bd];
-          zx_n = s2[(I)(i - 1) * bd];
+        for (; i >= 1; i -= 2) {
+          const float2 ca = pa, cb = pb;
+          const float cza = za, czb = zb;
+          if (i - 2 - kPrefetchSteps >= 0) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - 2 - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - 2 - kPrefetchSteps) * bd));
+          }
+          if (i - 3 - kPrefetchSteps >= 0) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - 3 - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - 3 - kPrefetchSteps) * bd));
+          }
+          if (i >= 2) {
+            pa = s01[(I)(i - 2) * bd];
+            za = s2[(I)(i - 2) * bd];
+          }
+          if (i >= 3) {
+            pb = s01[(I)(i - 3) * bd];
+            zb = s2[(I)(i - 3) * bd];
+          }
+          adjoint_step2(c, theta, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
+                        make_float2(cza, czb), as);
+          vnext = cb.x;
         }
-        adjoint_step(c, theta, vd.x, vnext, vd.y, zx, as);
-        vnext = vd.x;
+        if (i == 0) {  // an odd count: the last step alone (loaded as pa)
+          adjoint_step(c, theta, pa.x, vnext, pa.y, za, as);
+          vnext = pa.x;
+        }
+      } else {
+        int i = (int)(n1 - n0) - 1;
+        for (; i >= 1; i -= 2) {
+          const float2 ca = s01[(I)i * bd], cb = s01[(I)(i - 1) * bd];
+          adjoint_step2(c, theta, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
+                        make_float2(s2[(I)i * bd], s2[(I)(i - 1) * bd]), as);
+          vnext = cb.x;
+        }
+        if (i == 0) {
+          const float2 vd = s01[0];
+          adjoint_step(c, theta, vd.x, vnext, vd.y, s2[0], as);
+          vnext = vd.x;
+        }
       }
     } else {
-      for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-        const float2 vd = s01[(I)i * bd];
-        adjoint_step(c, theta, vd.x, vnext, vd.y, s2[(I)i * bd], as);
-        vnext = vd.x;
+      if constexpr (Seg::kGlobal) {
+        // global memory: each step's data loaded one step ahead into registers,
+        // and asked into L2 kPrefetchSteps steps ahead
+        constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
+        int i = (int)(n1 - n0) - 1;
+        float2 vd_n = s01[(I)i * bd];
+        float zx_n = s2[(I)i * bd];
+        for (; i >= 0; --i) {
+          const float2 vd = vd_n;
+          const float zx = zx_n;
+          if (i >= kPrefetchSteps) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - kPrefetchSteps) * bd));
+          }
+          if (i > 0) {
+            vd_n = s01[(I)(i - 1) * bd];
+            zx_n = s2[(I)(i - 1) * bd];
+          }
+          adjoint_step(c, theta, vd.x, vnext, vd.y, zx, as);
+          vnext = vd.x;
+        }
+      } else {
+        for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
+          const float2 vd = s01[(I)i * bd];
+          adjoint_step(c, theta, vd.x, vnext, vd.y, s2[(I)i * bd], as);
+          vnext = vd.x;
+        }
       }
     }
   }
@@ -234,7 +372,7 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
 // Checkpoint (slot, path j) of this thread at ck[(slot * PPT + j) * ck_stride]
 // (n_seg - 1 slots; shared or global memory); S is this thread's segment column
 // (shared or global memory, at least k rows).
-template <int PPT, typename Seg>
+template <int PPT, typename Seg, bool PAIRED = true>
 __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                                  const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
                                                  int ck_stride, const Seg& S, float (&x_out)[PPT],
@@ -284,8 +422,8 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
   }
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
-    path_sweep(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], S, x_out[j],
-               comp_out[j], g[j]);
+    path_sweep<Seg, PAIRED>(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], S,
+                            x_out[j], comp_out[j], g[j]);
 }
 
 // Floats per thread of path_adjoint_ppt: checkpoints and the segment buffer.

@@ -65,12 +65,12 @@ __global__ void __launch_bounds__(TPB) heston_batch_kernel(const __grid_constant
         // arrays of seg_rows rows (the largest over the book), so threads on
         // options with different checkpoint intervals never overlap
         if constexpr (GSEG)  // one segment: no checkpoints are read or written
-          path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
+          path_adjoint_ppt<1, SegGlobal, false>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
                               SegGlobal{B.gseg, (long long)blockIdx.x * bd + tid, B.seg_rows,
                                         (long long)gridDim.x * bd},
                               x, comp, g);
         else
-          path_adjoint_ppt<1>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
+          path_adjoint_ppt<1, SegShared, false>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
                               SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
