@@ -11,8 +11,10 @@ Each test compares the oracle with something other than itself:
     the martingale E[e^{-rT} S_T] = S0;
   * European prices against the Heston semi-analytic price (two Fourier forms
     that agree to 1e-10) and the Black-Scholes limit;
-  * FD and adjoint Greeks against the semi-analytic delta/vega and against each
-    other, and reverse-mode against forward-mode (dual number) per-path tangents.
+  * the standard error against the spread of prices over independent seeds;
+  * FD and adjoint Greeks against the semi-analytic delta/gamma/vega/theta/rho and
+    against each other, and reverse-mode against forward-mode (dual number)
+    per-path tangents.
 The paper itself (Sec. 3-6) prints no option value, so parity with the paper's
 own numbers is unpinned; the harness accounting is pinned to its Tables 1-2.
 """
@@ -153,14 +155,24 @@ def test_qe_step_branches_and_degenerate_cases():
 
 
 # ------------------------------------------------------- multi-step pins ----
+def hard_paths():
+    """2^19 paths of 64 steps of the hard model (coarse steps, both QE branches)."""
+    return oracle.terminal(HARD, 64, 7, 0, 1 << 19)
+
+
+def cfg_paths():
+    """2^19 paths of 64 steps of the base model started away from theta (v0 = 0.09)."""
+    return oracle.terminal(dict(CFG, v0=0.09), 64, 11, 0, 1 << 19)
+
+
 @pytest.fixture(scope="module")
 def terminal_hard():
-    return oracle.terminal(HARD, 64, 7, 0, 1 << 19)
+    return hard_paths()
 
 
 @pytest.fixture(scope="module")
 def terminal_cfg():
-    return oracle.terminal(dict(CFG, v0=0.09), 64, 11, 0, 1 << 19)
+    return cfg_paths()
 
 
 @pytest.mark.parametrize("which", ["hard", "cfg"])
@@ -232,6 +244,20 @@ def test_put_call_parity_on_common_paths():
     np.testing.assert_allclose(c - p, fwd - K * math.exp(-CFG["r"] * CFG["T"]), rtol=0, atol=1e-10)
 
 
+def test_standard_error_matches_the_spread_over_seeds():
+    # stderr estimates the standard deviation of the price estimator itself: over
+    # 128 independent seeds the prices spread by that much.  The sample standard
+    # deviation of 128 draws has a relative error near 1/sqrt(254) = 6%, so the
+    # band [0.8, 1.25] holds comfortably and a factor sqrt(2) falls outside it.
+    K = np.array([80.0, 100.0, 120.0])
+    for is_put in (False, True):
+        runs = [oracle.price(CFG, K, is_put, 16, 8192, s) for s in range(1, 129)]
+        prices = np.array([p for p, _ in runs])
+        errs = np.array([e for _, e in runs])
+        ratio = prices.std(axis=0, ddof=1) / errs.mean(axis=0)
+        assert np.all((ratio > 0.8) & (ratio < 1.25)), ratio
+
+
 def test_counter_independence_of_path_ranges():
     # A path's result depends only on (seed, option, path index): shards agree with the whole.
     xa, va, _ = oracle.terminal(CFG, 16, 3, 0, 4096)
@@ -261,6 +287,18 @@ def test_fd_greeks_against_semi_analytic():
     assert abs(g[0, 3] / rho - 1) < 0.01
     gam = (_cf_call(dict(CFG, S0=100.5)) - 2 * _cf_call(CFG) + _cf_call(dict(CFG, S0=99.5))) / 0.25
     assert abs(g[0, 1] / gam - 1) < 0.25   # FD gamma with a 1e-4 bump is noisy
+
+
+def test_fd_theta_against_semi_analytic():
+    # theta = -dP/dT: the oracle bumps T (and with it dt) on common random numbers
+    K = np.array([90.0, 100.0, 110.0])
+    _, g = oracle.greeks_fd(CFG, K, False, 64, 1 << 18, 1, 1e-4, oracle.G_THETA)
+    h = 1e-4
+    for j, k in enumerate(K):
+        up = A.heston_call_p1p2(k, **dict(CFG, T=CFG["T"] + h))[0]
+        dn = A.heston_call_p1p2(k, **dict(CFG, T=CFG["T"] - h))[0]
+        ref = -(up - dn) / (2 * h)
+        assert abs(g[j, 0] / ref - 1) < 0.015, (k, g[j, 0], ref)
 
 
 def test_reverse_mode_matches_forward_mode_duals():
