@@ -85,17 +85,6 @@ def bs_put(S0, K, r, T, vol):
     return bs_call(S0, K, r, T, vol) - S0 + K * math.exp(-r * T)
 
 
-def bs_delta_call(S0, K, r, T, vol):
-    sd = vol * math.sqrt(T)
-    return float(ndtr((math.log(S0 / K) + (r + 0.5 * vol * vol) * T) / sd))
-
-
-def bs_gamma(S0, K, r, T, vol):
-    sd = vol * math.sqrt(T)
-    d1 = (math.log(S0 / K) + (r + 0.5 * vol * vol) * T) / sd
-    return math.exp(-0.5 * d1 * d1) / math.sqrt(2.0 * math.pi) / (S0 * sd)
-
-
 def cir_mean(t, v0, kappa, theta):
     return theta + (v0 - theta) * math.exp(-kappa * t)
 

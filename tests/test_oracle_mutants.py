@@ -152,6 +152,17 @@ PY_MISTAKES = [
      "return (F - math.sqrt(F * K) * val / math.pi)", pins.test_semi_analytic_forms_agree_and_bs_limit),
     ("put_parity_undiscounted_strike", analytic, "return call - S0 + K * math.exp(-r * T)", "return call - S0 + K",
      _price_pin(True)),
+    ("cir_mean_sign", analytic, "return theta + (v0 - theta) * math.exp(-kappa * t)",
+     "return theta - (v0 - theta) * math.exp(-kappa * t)",
+     lambda: pins.test_closed_form_moments_solve_their_moment_equations(pins.HARD)),
+    ("cir_var_drops_half", analytic, "theta * sigma ** 2 * (1.0 - e) ** 2 / (2.0 * kappa)",
+     "theta * sigma ** 2 * (1.0 - e) ** 2 / kappa",
+     lambda: pins.test_closed_form_moments_solve_their_moment_equations(CFG)),
+    ("log_mean_sign", analytic, "return r * T - 0.5 * (theta * T", "return r * T + 0.5 * (theta * T",
+     lambda: pins.test_closed_form_moments_solve_their_moment_equations(CFG)),
+    ("bs_d1_sign", analytic, "d1 = (math.log(S0 / K) + (r + 0.5 * vol * vol) * T) / sd",
+     "d1 = (math.log(S0 / K) + (r - 0.5 * vol * vol) * T) / sd",
+     pins.test_black_scholes_closed_form_is_the_lognormal_expectation),
 ]
 
 

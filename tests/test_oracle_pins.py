@@ -124,6 +124,47 @@ def test_norminv_against_scipy_and_cdf():
     assert oracle.norminv([0.5])[0] == 0.0
 
 
+# ------------------------------------------------------ the closed forms ----
+@pytest.mark.parametrize("m", [CFG, HARD, dict(CFG, v0=0.0, kappa=4.0, sigma=1.0)])
+def test_closed_form_moments_solve_their_moment_equations(m):
+    # Ito's lemma on dv = kappa (theta - v) dt + sigma sqrt(v) dW gives the moment
+    # equations d/dt E v = kappa (theta - E v) and d/dt Var v = -2 kappa Var v +
+    # sigma^2 E v, and d/dt E ln S = r - E v / 2; integrated numerically here,
+    # they must reproduce the closed forms the oracle is checked against.
+    from scipy.integrate import solve_ivp
+
+    k, th, s = m["kappa"], m["theta"], m["sigma"]
+
+    def rhs(t, y):
+        mean, var, logs = y
+        return [k * (th - mean), -2.0 * k * var + s * s * mean, m["r"] - 0.5 * mean]
+
+    ts = np.linspace(0.0, 2.0, 9)[1:]
+    sol = solve_ivp(rhs, (0.0, 2.0), [m["v0"], 0.0, 0.0], t_eval=ts, rtol=1e-11, atol=1e-14)
+    for j, t in enumerate(ts):
+        assert abs(sol.y[0, j] - A.cir_mean(t, m["v0"], k, th)) < 1e-10
+        assert abs(sol.y[1, j] - A.cir_var(t, m["v0"], k, th, s)) < 1e-10
+        assert abs(sol.y[2, j] - A.heston_log_mean(m["r"], t, m["v0"], k, th)) < 1e-10
+
+
+def test_black_scholes_closed_form_is_the_lognormal_expectation():
+    # e^{-rT} E[(S_T - K)+] with ln S_T ~ N(ln S0 + (r - vol^2/2) T, vol^2 T), by quadrature
+    from scipy import integrate
+
+    for S0, K, r, T, vol in [(100.0, 80.0, 0.05, 1.0, 0.2), (100.0, 120.0, 0.0, 0.25, 0.5), (36.0, 40.0, 0.06, 2.0, 0.3)]:
+        mu, sd = math.log(S0) + (r - 0.5 * vol * vol) * T, vol * math.sqrt(T)
+
+        def density(z, pay):
+            return pay(math.exp(mu + sd * z)) * math.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+        zk = (math.log(K) - mu) / sd
+        # the normal density beyond |z| = 14 is below 1e-42
+        call = math.exp(-r * T) * integrate.quad(density, zk, 14.0, args=(lambda s: s - K,), epsabs=1e-13)[0]
+        put = math.exp(-r * T) * integrate.quad(density, -14.0, zk, args=(lambda s: K - s,), epsabs=1e-13)[0]
+        assert abs(A.bs_call(S0, K, r, T, vol) - call) < 1e-9
+        assert abs(A.bs_put(S0, K, r, T, vol) - put) < 1e-9
+
+
 # --------------------------------------------------------------- QE step ----
 LATTICE = (np.arange(1 << 23, dtype=np.float64) + 0.5) * 2.0 ** -23
 
