@@ -1,0 +1,72 @@
+"""bench.py's output contract, checked on its CPU arm (no GPU).
+
+`bench.py --impl reference` times the FP64 oracle on the host cores and prints
+one JSON line with the same keys as the GPU arm; under torchrun only rank 0
+prints, the other ranks exit 0 without work.  The GPU arm's line (the same
+keys plus roofline, clocks and gpu_launches) needs a GPU and is produced by the
+GPU runs of bench.py.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+COMMON = {"metric": str, "value": float, "unit": str, "n_gpus": int, "steps": int, "warmup": int,
+          "ms_per_step": float, "higher_is_better": bool, "scaling": str, "dtype": str, "data": str,
+          "config": dict, "cpu_baseline": dict, "e2e": dict}
+
+
+def _json_lines(out):
+    return [json.loads(line) for line in out.splitlines() if line.startswith("{")]
+
+
+def _check_reference_line(line, n_gpus):
+    for key, kind in COMMON.items():
+        assert isinstance(line[key], kind), (key, line.get(key))
+    assert line["impl"] == "reference"
+    assert line["n_gpus"] == n_gpus and line["steps"] == 1 and line["warmup"] >= 3
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["dtype"] == "f64" and line["data"] == "synthetic"
+    assert line["config"]["workload"] == "heston_grid32_252x1048576"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_prints_one_contract_line():
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = _json_lines(p.stdout)
+    assert len(lines) == 1, p.stdout
+    _check_reference_line(lines[0], 1)
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "3"]
+    env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = _json_lines(p.stdout)
+    assert len(lines) == 1, p.stdout
+    _check_reference_line(lines[0], 2)
+
+
+@pytest.mark.parametrize("flag", ["--no-e2e", "--no-book", "--no-lsm", "--no-adjoint", "--no-headline"])
+def test_bench_flags_are_accepted(flag):
+    # argument parsing only: --help exits before any work
+    p = subprocess.run([sys.executable, "bench.py", flag, "--help"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert p.returncode == 0 and "--profile-leg" in p.stdout
