@@ -70,3 +70,35 @@ def test_bench_flags_are_accepted(flag):
     p = subprocess.run([sys.executable, "bench.py", flag, "--help"], cwd=ROOT, capture_output=True, text=True,
                        timeout=120)
     assert p.returncode == 0 and "--profile-leg" in p.stdout
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_algorithmic_flops_of_the_bench_step():
+    # 48 flops shared per step (two inverse normals, two uniforms) + 41 per simulated
+    # scenario; the bench step simulates base, v0 +- and T +- (delta, gamma and rho
+    # revalue the base path)
+    b = _bench()
+    g5 = ["delta", "gamma", "vega", "theta", "rho"]
+    assert b.simulated_scenarios(g5) == 5
+    assert b.flops_per_path_step(g5) == 253
+    assert b.simulated_scenarios(["delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr"]) == 11
+
+
+def test_clock_summary_reads_clocks_and_throttle_reasons():
+    b = _bench()
+    s = b.ClockSampler(0)
+    s.out = ["0, 2070, 2070, 910.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2055, 2070, 1101.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 2040, 2070, 1200.5, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+             "garbage line"]
+    out = s.summary()
+    assert out["sm_mhz"] == 2055 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    s.out = []
+    assert s.summary()["reasons"] == ["unsampled"]
