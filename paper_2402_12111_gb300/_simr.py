@@ -52,6 +52,8 @@ FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 def batch_variant_flag(v: int) -> int:
     """SIMR_BATCH_VARIANT(v): run kernel shape v (0-7) of the book kernel."""
     return ((int(v) & 7) + 1) << 8
+
+
 SCHEMES = {"qe": 0, "qem": 1}
 
 
