@@ -102,3 +102,42 @@ def test_fault_injection_hook_arguments(libpath):
     assert lib.simr_inject_fault(0, 0) == 0
     assert lib.simr_inject_fault(3, 1) != 0
     assert lib.simr_inject_fault(1, 0) != 0
+
+
+def test_host_validation_of_the_problem_statement(libpath):
+    # The argument rules are checked on the host before any CUDA call; simr_price_noalloc
+    # needs no context, so they can be exercised here without a GPU.
+    import numpy as np
+
+    from paper_2402_12111_gb300 import _simr as S
+
+    L = S.load(build_if_missing=False)
+    good = dict(S0=100.0, r=0.05, T=1.0, v0=0.04, kappa=1.5, theta=0.04, sigma=0.3, rho=-0.7)
+    K = np.array([100.0] * 33)
+    out = np.zeros(33)
+    kp, op = K.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p)
+
+    def call(model=good, strikes=kp, n=1, steps=64, paths=1024, price=op):
+        rc = L.simr_price_noalloc(ctypes.byref(S.as_heston(model)), strikes, n, 0, steps, paths, 1, 0, price, None,
+                                  None)
+        return rc, L.simr_last_error().decode()
+
+    bad_models = {"S0": 0.0, "T": -1.0, "v0": -1e-3, "theta": -1e-3, "kappa": 0.0, "sigma": 0.0, "rho": 1.5}
+    for field, value in bad_models.items():
+        rc, msg = call(model=dict(good, **{field: value}))
+        assert rc == S.SIMR_EINVAL and msg.startswith(field), (field, msg)
+    rc, msg = call(model=dict(good, r=float("nan")))
+    assert rc == S.SIMR_EINVAL and "non-finite" in msg
+    assert call(steps=0)[0] == S.SIMR_EINVAL and "steps" in call(steps=0)[1]
+    assert call(paths=0)[0] == S.SIMR_EINVAL and "paths" in call(paths=0)[1]
+    assert call(strikes=None)[1] == "strikes is NULL"
+    assert "n_strikes" in call(n=0)[1] and "n_strikes" in call(n=33)[1]
+    assert call(price=None)[1] == "price is NULL"
+    # the edge cases the rules admit: v0 = theta = 0, rho = +-1, r < 0 -- they pass every
+    # model check and stop only at the rule that this entry point takes device memory
+    for edge in (dict(v0=0.0, theta=0.0), dict(rho=1.0), dict(rho=-1.0), dict(r=-0.02)):
+        rc, msg = call(model=dict(good, **edge))
+        assert rc == S.SIMR_EINVAL and "device pointers only" in msg, (edge, msg)
+    # a NULL context is refused by every context call
+    rc = L.simr_price(None, ctypes.byref(S.as_heston(good)), kp, 1, 0, 64, 1024, 1, 0, op, None, None)
+    assert rc == S.SIMR_EINVAL and L.simr_last_error() == b"context is NULL"
