@@ -141,3 +141,21 @@ def test_host_validation_of_the_problem_statement(libpath):
     # a NULL context is refused by every context call
     rc = L.simr_price(None, ctypes.byref(S.as_heston(good)), kp, 1, 0, 64, 1024, 1, 0, op, None, None)
     assert rc == S.SIMR_EINVAL and L.simr_last_error() == b"context is NULL"
+
+
+def test_the_c_abi_from_plain_c(libpath, tmp_path):
+    # include/simr.h compiles as strict C99 and a C program links against libsimr.so;
+    # without a GPU the program reports the library's message for the failed context
+    src = os.path.join(ROOT, "tests", "c", "price_from_c.c")
+    exe = str(tmp_path / "price_from_c")
+    libdir = os.path.dirname(libpath)
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{ROOT}/include", src, "-o",
+                         exe, f"-L{libdir}", "-lsimr", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    if run.returncode == 2:
+        assert run.stdout.startswith("no context: -3 "), run.stdout
+    else:
+        assert run.returncode == 0, run.stdout + run.stderr
+        prices = [float(line.split("price=")[1].split()[0]) for line in run.stdout.splitlines()]
+        assert len(prices) == 3 and all(p > 0 for p in prices) and prices[0] > prices[1] > prices[2]
