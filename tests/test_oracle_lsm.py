@@ -54,9 +54,12 @@ def test_normal_equation_solve_matches_lstsq():
     np.testing.assert_allclose(Ps @ bs, Phi0 @ ref0, rtol=1e-9, atol=1e-9)
 
 
-def test_standardised_and_reported_coefficients_are_the_same_quadratic():
+@pytest.mark.parametrize("v0", [0.04, 0.09])
+def test_standardised_and_reported_coefficients_are_the_same_quadratic(v0):
+    # v0 = theta puts the variance's two centres (E v_t and w) on the same value, so
+    # the coordinate shifts of y vanish; v0 != theta exercises every term of the map
     rng = np.random.default_rng(6)
-    m = dict(workloads.BASE_MODEL)
+    m = dict(workloads.BASE_MODEL, v0=v0)
     S = 100.0 * np.exp(0.2 * rng.standard_normal(50))
     v = 0.04 * rng.gamma(4.0, 0.25, 50)
     coef = lsm.standardise(m, 12, 3)

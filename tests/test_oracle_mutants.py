@@ -147,6 +147,13 @@ PY_MISTAKES = [
      "Y = np.where(st >= 0, cash[itm], 0.0)", lsm_pins.test_regression_on_simulated_paths_matches_lstsq),
     ("lsm_regression_on_every_path", lsm, "itm = np.nonzero(h[:, j] > 0.0)[0]", "itm = np.arange(paths)",
      lsm_pins.test_regression_on_simulated_paths_matches_lstsq),
+    ("lsm_back_substitution_uses_L", lsm, "sum(L[i][k] * beta[i] for i in range(k + 1, n) if keep[i])",
+     "sum(L[k][i] * beta[i] for i in range(k + 1, n) if keep[i])", lsm_pins.test_normal_equation_solve_matches_lstsq),
+    ("lsm_pivot_without_earlier_columns", lsm, "d = G[k][k] - sum(L[k][i] ** 2 for i in range(k) if keep[i])",
+     "d = G[k][k]", lsm_pins.test_normal_equation_solve_matches_lstsq),
+    ("lsm_reported_cross_term", lsm, "b1 * kx - 2.0 * b2 * kx * kx * cx - b4 * kx * ky * cy,",
+     "b1 * kx - 2.0 * b2 * kx * kx * cx + b4 * kx * ky * cy,",
+     lambda: lsm_pins.test_standardised_and_reported_coefficients_are_the_same_quadratic(0.09)),
     ("cf_rho_sign", analytic, "b = kappa - rho * sigma * iu", "b = kappa + rho * sigma * iu", _price_pin(False)),
     ("lewis_undiscounted", analytic, "return math.exp(-r * T) * (F - math.sqrt(F * K) * val / math.pi)",
      "return (F - math.sqrt(F * K) * val / math.pi)", pins.test_semi_analytic_forms_agree_and_bs_limit),
