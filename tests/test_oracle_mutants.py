@@ -91,6 +91,7 @@ C_MISTAKES = [
     ("payoff_call_put_swapped", "double d = is_put ? (K - s_T) : (s_T - K);",
      "double d = is_put ? (s_T - K) : (K - s_T);", pins.test_put_call_parity_on_common_paths),
     ("price_not_discounted", "price[j] = disc * mean;", "price[j] = mean;", pins.test_put_call_parity_on_common_paths),
+    ("stderr_from_first_moment", "s2 += f * f;", "s2 += f;", pins.test_standard_error_matches_the_spread_over_seeds),
     ("stderr_without_sample_size", "(s2 / (double)paths - mean * mean) / (double)(paths - 1)",
      "(s2 / (double)paths - mean * mean)", pins.test_standard_error_matches_the_spread_over_seeds),
     # bump-and-revalue Greeks
@@ -109,6 +110,9 @@ C_MISTAKES = [
      "double dv_dq = (mm / (q * q)) * (1.0 + L);", pins.test_reverse_mode_matches_forward_mode_duals),
     ("adjoint_sigma_map", "grad5[3] = bar_c1 * 2.0 * c1 / sig", "grad5[3] = bar_c1 * c1 / sig",
      pins.test_reverse_mode_matches_forward_mode_duals),
+    ("adjoint_kappa_map_sign", "s2g * ((1.0 - 2.0 * E) * dE_dk / kap - E * (1.0 - E) / (kap * kap))",
+     "s2g * ((1.0 - 2.0 * E) * dE_dk / kap + E * (1.0 - E) / (kap * kap))",
+     pins.test_reverse_mode_matches_forward_mode_duals),
     ("adjoint_theta_through_mean", "bar_th += bar_m * (1.0 - E);", "bar_th += bar_m * E;",
      pins.test_reverse_mode_matches_forward_mode_duals),
     ("dual_quotient_rule", "(a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v)", "(a.d[i] * b.v + a.v * b.d[i]) / (b.v * b.v)",
@@ -124,6 +128,8 @@ C_MISTAKES = [
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.WILD)),
     ("qem_A_definition", "const double A = k[6] + 0.5 * k[8];", "const double A = k[6] + k[8];",
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.BASE)),
+    ("qem_drops_rate", "if (ok) k0 = m->r * k[0] - lnM", "if (ok) k0 = -lnM",
+     qem_pins.test_multi_step_martingale_within_monte_carlo_error),
     # correlated baskets
     ("basket_cholesky_transposed", "z += Lc[a * A + j] * eps[j];", "z += Lc[j * A + a] * eps[j];",
      lambda: basket_pins.test_exchange_option_in_the_black_scholes_limit_is_margrabe(0.6)),
@@ -212,7 +218,8 @@ def test_the_unplanted_copy_passes(monkeypatch, tmp_path):
 def test_c_oracle_mistake_is_caught(monkeypatch, tmp_path, name, site, planted, pin):
     _plant_c(monkeypatch, tmp_path, site, planted)
     with pytest.raises(AssertionError):
-        pin()
+        with np.errstate(all="ignore"):
+            pin()
 
 
 @pytest.mark.parametrize("name,module,site,planted,pin", PY_MISTAKES, ids=[m[0] for m in PY_MISTAKES])
