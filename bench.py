@@ -36,12 +36,16 @@ import workloads  # noqa: E402
 METRIC = "Heston path-steps/s (price+Greeks) on 1 GB300; % FP32 peak; adjoint vs FD speedup"
 UNIT = "path-steps/s"
 FP32_LANES_PER_SM = 128
-# FP32 flops per path-step, FMA = 2, as the kernel's formulas compute them:
-#   shared per step: two inverse normals (2 x 22) + two uniforms (2 x 2)          = 48
-#   per simulated scenario: QE variance step 25 + log-spot step with its Kahan
-#   compensation 16                                                               = 41
-FLOPS_SHARED = 48
-FLOPS_PER_SCENARIO = 41
+# Algorithmic FP32 flops per path-step (FMA = 2 flops; special-function
+# evaluations -- reciprocal, square root, logarithm -- are counted apart, not
+# here), in the method's own operation count:
+#   shared per step: the two inverse normals Z_V, Z_X, 22 each                   = 44
+#   per simulated scenario: QE variance step 16 (moments, psi, b^2, a, v')
+#   + log-spot step 7 (K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X)               = 23
+# Work of this implementation's own choosing is left out: the uniform mapping,
+# the Kahan compensation of x, the CRN scenarios' constant deltas, Philox.
+FLOPS_SHARED = 44
+FLOPS_PER_SCENARIO = 23
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -59,6 +63,9 @@ def parse():
     ap.add_argument("--no-headline", action="store_true",
                     help="skip the 8-underlying, 1,024-step, 2^26-path adjoint vs bump-and-revalue leg")
     ap.add_argument("--paths", type=int, default=0, help="override the path count (profiling small cases)")
+    ap.add_argument("--time-steps", type=int, default=0, help="override the time-step count of --profile-leg")
+    ap.add_argument("--ckpt-every", type=int, default=0,
+                    help="checkpoint interval of --profile-leg adjoint (0: the library's choice)")
     ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "lsm", "basket"],
                     help="only run one call W + K times on the workload (for profilers); prints no JSON")
     return ap.parse_args()
@@ -285,12 +292,15 @@ def run_profile_leg(args):
     w = workloads.grid()
     if args.paths:
         w.paths = args.paths
+    if args.time_steps:
+        w.steps = args.time_steps
     K = torch.as_tensor(w.strikes, dtype=torch.float64, device="cuda")
     legs = {
         "fd": lambda: simr.greeks_fd(w.model, K, w.is_put, w.steps, w.paths, w.seed, greeks=list(w.greeks),
                                      rel_bump=w.rel_bump),
         "price": lambda: simr.price(w.model, K, w.is_put, w.steps, w.paths, w.seed),
-        "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed),
+        "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed,
+                                               ckpt_every=args.ckpt_every),
     }
     if args.profile_leg == "book":
         opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))

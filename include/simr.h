@@ -381,15 +381,15 @@ SIMR_API int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const d
 /*
  * simr_price without any allocation: the paper has no counterpart to this entry
  * point.  It is for callers that cannot let a library allocate device memory --
- * code running while a CUDA graph is being captured (cudaMalloc is not a
- * stream operation and synchronises the device), serving loops that must never
- * block on the allocator, and host applications that hand out all device
+ * serving loops that must never block on the allocator (cudaMalloc can
+ * synchronise the device), and host applications that hand out all device
  * memory themselves.  It needs no context and calls no cudaMalloc, cudaFree or
  * allocating library routine: its reduction scratch is one file-scope device
  * array of 1 MiB + 256 B, which every GPU that loads libsimr holds until the
  * process exits.
  *   strikes[n_strikes], price[n_strikes], stderr_out[n_strikes] (nullable):
- *   DEVICE pointers of the current device only (host pointers: SIMR_EINVAL);
+ *   DEVICE (or managed) pointers of the current device only (host pointers or
+ *   another GPU's memory: SIMR_EINVAL);
  *   n_strikes in [1, 32] (larger: SIMR_EINVAL).  Arguments and results are
  *   those of simr_price with the same seed, option_index and sizes.
  * The first call on a device looks up the array's device address (once per

@@ -85,15 +85,23 @@ __device__ __forceinline__ void strike_tile_terms(bool put, float K, const float
   }
 }
 
-#ifndef SIMR_ADJ_MINB
-#define SIMR_ADJ_MINB 5  // minimum resident blocks per SM asked of the register allocator (measured 4-5% faster than its own choice)
+// Minimum resident blocks per SM asked of the register allocator: 5 for global
+// segments (one segment of the whole path: 4-5% faster than its own choice, 7%
+// faster than 4), 4 for shared-memory segments (which hold a block's segment
+// buffers, 12 k bytes per thread, so that longer segments leave room for 4
+// blocks at most: 11% faster at k = 32 and 1% at k = 16 than with 5).
+#ifndef SIMR_ADJ_MINB_GSEG
+#define SIMR_ADJ_MINB_GSEG 5
+#endif
+#ifndef SIMR_ADJ_MINB_SMEM
+#define SIMR_ADJ_MINB_SMEM 4
 #endif
 
 // GSEG: the segment buffers in global memory, [3 k][grid threads] (for a
 // segment too long for shared memory, in particular one segment of the whole
 // path: no forward pass).
 template <int TILE, int PPT, bool RACC, bool GSEG>
-__global__ void __launch_bounds__(128, SIMR_ADJ_MINB) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
+__global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB_SMEM) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
                                                              double* __restrict__ partials,
@@ -294,7 +302,9 @@ cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const doubl
 }
 
 // Whether the segment buffers go to global memory: when 3 k floats per thread
-// do not fit the shared memory of a block.
+// do not fit the shared memory of a block.  (Shared-memory segments are kept
+// even where they cost resident blocks: at k = 32, 4 blocks per SM with
+// shared-memory segments ran 11% faster than 5 with L2-resident global ones.)
 bool adjoint_gseg(const PathLaunch& L, const AdjConst& A) {
   return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32) > kAdjMaxSmem;
 }

@@ -16,9 +16,9 @@ namespace simr {
 namespace {
 
 // One QE variance step from v given the step's draws (no log-spot update).
-__device__ __forceinline__ float qe_only(const ScenConst& c, float v, float omu, float zv) {
+__device__ __forceinline__ float qe_only(const ScenConst& c, float v, float xv, float zv) {
   float vn, dl;
-  qe_from_moments(fmaf(v, c.E, c.thE), fmaf(v, c.c1, c.c2), omu, zv, vn, dl);
+  qe_from_moments(fmaf(v, c.E, c.thE), fmaf(v, c.h1, c.h2), xv, zv, vn, dl);
   return vn;
 }
 
@@ -27,62 +27,45 @@ struct AdjSums {
   float x, comp;  // x_T accumulated over the reverse sweep (Kahan-compensated)
 };
 
-// The reverse step's quantities of the quadratic branch that do not depend on
-// the adjoint carried in from the later steps (functions of v_n, m, s^2, Z_V).
-struct AdjQuad {
-  float rs2, t, rroot, rb, ropb2, am, bz, g;
+// What a reverse step needs besides the adjoint carried in from the later steps.
+// Common to both branches: the log-spot increment inc and the innovation dl,
+// q = sqrt(v + v'), Z_X, hzc = Cv + d(sK3 q Z_X)/ds (s = v + v'), hzcd = hzc - Cd
+// and tmv = theta - v.  Quadratic branch: the factors of the chain from the
+// adjoint of v' to those of m and s^2 (with t = m^2 / (s^2/2) formed exactly as
+// the forward step forms it, qe_t, so the two take the same branch):
+//   v' = a (b + Z_V)^2, dl = a g, g = Z_V (Z_V + 2b) - 1, a = m / (1 + b^2):
+//   abar = vnbar bz^2 + Cdl g,  bbar = 2 a (vnbar bz + Cdl Z_V),
+//   b2bar = bbar / (2b) - abar a / (1 + b^2),  mbar = abar / (1 + b^2) + tbar 4m / s^2,
+//   tbar = b2bar (1 + (2t - 1) / (2 sqrt(t(t - 1)))),  s2bar = -tbar t / s^2,
+// the factors (bz, bz^2, Cdl g, Cdl Z_V, 2a, 1/(2b), a/(1 + b^2), 1/(1 + b^2), the
+// bracket F, 4m/s^2, t/s^2) all functions of the step's state and draws.
+struct AdjPre {
+  float inc, dl, q, zx, hzc, hzcd, tmv, vc;
+  float bz, bz2, cg, cz, am2, hrb, amr, ropb2, F, m4r, tr;
 };
 
-__device__ __forceinline__ AdjQuad adj_quad(float m, float m2, float s2, float zv) {
-  AdjQuad Q;
-  Q.rs2 = rcp_approx(s2);
-  Q.t = 2.0f * m2 * Q.rs2;
-  const float tt = fmaf(Q.t, Q.t, -Q.t);
-  Q.rroot = rsqrt_approx(tt);
-  const float root = tt * Q.rroot;
-  const float b2 = (Q.t - 1.0f) + root;
-  Q.rb = rsqrt_approx(b2);
-  const float b = b2 * Q.rb;
-  Q.ropb2 = rcp_approx(Q.t + root);  // 1 / (1 + b^2)
-  Q.am = m * Q.ropb2;
-  Q.bz = b + zv;
-  Q.g = fmaf(zv, zv + 2.0f * b, -1.0f);
-  return Q;
-}
-
-// The end of a reverse step once mbar and s2bar are known: x_T's increment
-// (Kahan-compensated), the adjoint of v_n, and the seven sums.
-__device__ __forceinline__ void adj_tail(const ScenConst& c, float theta, float vc, float q, float zx, float hz,
-                                         float dl, float inc, float mbar, float s2bar, AdjSums& a) {
-  const float y = inc - a.comp;
-  const float tx = a.x + y;
-  a.comp = (tx - a.x) - y;
-  a.x = tx;
-  a.vbar = (c.Cv - c.Cd + hz) + fmaf(mbar, c.E, s2bar * c.c1);
-  a.Am += mbar;
-  a.Amv = fmaf(mbar, vc - theta, a.Amv);
-  a.As += s2bar;
-  a.Asv = fmaf(s2bar, vc, a.Asv);
-  a.Ad += theta - vc;
-  a.Adl += dl;
-  a.Ak3 = fmaf(q, zx, a.Ak3);
-}
-
-// The adjoint chain of a quadratic-branch reverse step: from the adjoint of
-// v_{n+1} through the QE map's derivatives to mbar and s2bar, then adj_tail.
-__device__ __forceinline__ void adj_chain_quad(const ScenConst& c, float theta, float vc, float m, float zv, float q,
-                                               float zx, float hz, float dl, float inc, const AdjQuad& Q,
-                                               AdjSums& a) {
-  const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
-  const float dlbar = c.Cdl;
-  const float abar = fmaf(vnbar, Q.bz * Q.bz, dlbar * Q.g);
-  const float bbar = 2.0f * Q.am * fmaf(vnbar, Q.bz, dlbar * zv);
-  const float b2bar = fmaf(0.5f * bbar, Q.rb, -abar * Q.am * Q.ropb2);
-  float mbar = abar * Q.ropb2;
-  const float tbar = b2bar * fmaf(2.0f * Q.t - 1.0f, 0.5f * Q.rroot, 1.0f);
-  mbar = fmaf(tbar * 4.0f * m, Q.rs2, mbar);
-  const float s2bar = -tbar * Q.t * Q.rs2;
-  adj_tail(c, theta, vc, q, zx, hz, dl, inc, mbar, s2bar, a);
+// The quadratic branch's factors from m, t = m^2/(s^2/2), rs2h = 1/(s^2/2), Z_V.
+__device__ __forceinline__ void adj_quad_pre(const ScenConst& c, float m, float t, float rs2h, float zv, AdjPre& P) {
+  const float tt = fmaf(t, t, -t);
+  const float rroot = rsqrt_approx(tt);
+  const float root = tt * rroot;
+  const float b2 = (t - 1.0f) + root;
+  const float rb = rsqrt_approx(b2);
+  const float b = b2 * rb;
+  P.ropb2 = rcp_approx(t + root);  // 1 / (1 + b^2)
+  const float am = m * P.ropb2;
+  P.bz = b + zv;
+  const float g = fmaf(zv, zv + 2.0f * b, -1.0f);
+  P.dl = am * g;
+  P.bz2 = P.bz * P.bz;
+  P.cg = c.Cdl * g;
+  P.cz = c.Cdl * zv;
+  P.am2 = am + am;
+  P.hrb = 0.5f * rb;
+  P.amr = am * P.ropb2;
+  P.F = fmaf(fmaf(2.0f, t, -1.0f), 0.5f * rroot, 1.0f);
+  P.m4r = (m + m) * rs2h;  // 4 m / s^2
+  P.tr = t * (0.5f * rs2h);  // t / s^2
 }
 
 // The step's log-spot increment (LogPricePathQE), summed into x_T in the
@@ -94,34 +77,81 @@ __device__ __forceinline__ float adj_inc(const ScenConst& c, float s, float vc, 
   return fmaf(c.sK3 * q, zx, inc);
 }
 
+// The end of a reverse step once mbar and s2bar are known: x_T's increment
+// (Kahan-compensated), the adjoint of v_n, and the seven sums.
+__device__ __forceinline__ void adj_tail(float E, float c1, const AdjPre& P, float mbar, float s2bar, AdjSums& a) {
+  const float y = P.inc - a.comp;
+  const float tx = a.x + y;
+  a.comp = (tx - a.x) - y;
+  a.x = tx;
+  a.vbar = fmaf(mbar, E, fmaf(s2bar, c1, P.hzcd));
+  a.Am += mbar;
+  a.Amv = fmaf(-mbar, P.tmv, a.Amv);  // + mbar (v - theta)
+  a.As += s2bar;
+  a.Asv = fmaf(s2bar, P.vc, a.Asv);
+  a.Ad += P.tmv;
+  a.Adl += P.dl;
+  a.Ak3 = fmaf(P.q, P.zx, a.Ak3);
+}
+
+// The adjoint chain of a quadratic-branch reverse step: from the adjoint of
+// v_{n+1} through the QE map's derivatives to mbar and s2bar, then adj_tail.
+__device__ __forceinline__ void adj_chain_quad(float E, float c1, const AdjPre& P, AdjSums& a) {
+  const float vnbar = a.vbar + P.hzc;  // total adjoint of v_{n+1}
+  const float abar = fmaf(vnbar, P.bz2, P.cg);
+  const float bbar = P.am2 * fmaf(vnbar, P.bz, P.cz);
+  const float b2bar = fmaf(bbar, P.hrb, -(abar * P.amr));
+  const float tbar = b2bar * P.F;
+  const float mbar = fmaf(tbar, P.m4r, abar * P.ropb2);
+  const float s2bar = -(tbar * P.tr);
+  adj_tail(E, c1, P, mbar, s2bar, a);
+}
+
+// The common part of a reverse step's quantities from vc, vn and Z_X.
+__device__ __forceinline__ void adj_common_pre(const ScenConst& c, float theta, float vc, float vn, float zx,
+                                               AdjPre& P) {
+  const float s = vc + vn;
+  const float rq = rsqrt_approx(s);
+  const float sq = s * rq;
+  const float hq = 0.5f * c.sK3 * zx * rq;
+  P.q = s > 0.0f ? sq : 0.0f;
+  P.zx = zx;
+  P.hzc = (s > 0.0f ? hq : 0.0f) + c.Cv;  // Cv + d(sK3 sqrt(s) Z)/ds
+  P.hzcd = P.hzc - c.Cd;
+  P.tmv = theta - vc;
+  P.vc = vc;
+}
+
 // Reverse step n: state vc -> vn (both known), the step's stored draw d (Z_V in
 // the quadratic branch, 1 - U_V in the exponential one; the branch follows from
 // vc) and Z_X; vbar holds the adjoint of v_{n+1} on entry and of v_n on exit.
 // Each square root and its reciprocal come from one rsqrt.
-__device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, float vc, float vn, float d, float zx,
-                                             AdjSums& a) {
+__device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, float c1, float vc, float vn, float d,
+                                             float zx, AdjSums& a) {
   const float m = fmaf(vc, c.E, c.thE);
-  const float s2 = fmaf(vc, c.c1, c.c2);
+  const float s2h = fmaf(vc, c.h1, c.h2);
   const float m2 = m * m;
-  const float s = vc + vn;
-  const float rq = rsqrt_approx(s);
-  const float q = s > 0.0f ? s * rq : 0.0f;
-  const float hz = s > 0.0f ? 0.5f * c.sK3 * zx * rq : 0.0f;  // d(sK3 sqrt(s) Z)/ds
-  if (s2 < 1.5f * m2) {  // the forward step's branch test
-    const AdjQuad Q = adj_quad(m, m2, s2, d);
-    const float dl = Q.am * Q.g;
-    adj_chain_quad(c, theta, vc, m, d, q, zx, hz, dl, adj_inc(c, s, vc, dl, q, zx), Q, a);
+  const float rs2h = rcp_approx(s2h);
+  const float t = __fmul_rn(m2, rs2h);  // qe_t
+  AdjPre P;
+  adj_common_pre(c, theta, vc, vn, zx, P);
+  if (t > kQuadT) {  // the forward step's branch test
+    adj_quad_pre(c, m, t, rs2h, d, P);
+    P.inc = adj_inc(c, vc + vn, vc, P.dl, P.q, zx);
+    adj_chain_quad(c.E, c1, P, a);
     return;
   }
-  const float vnbar = a.vbar + c.Cv + hz;  // total adjoint of v_{n+1}
+  const float vnbar = a.vbar + P.hzc;  // total adjoint of v_{n+1}
   const float dlbar = c.Cdl;
-  float mbar = 0.0f, s2bar = 0.0f, dl = 0.0f;
+  float mbar = 0.0f, s2bar = 0.0f;
+  P.dl = 0.0f;
   if (m > 0.0f) {
     const float omu = d;
+    const float s2 = s2h + s2h;
     const float ms = m2 + s2;
     const float W = omu * ms;
     if (W >= 2.0f * m2) {
-      dl = -m;
+      P.dl = -m;
       mbar = -dlbar;
     } else {
       const float rm = rcp_approx(m), rms = rcp_approx(ms);
@@ -131,40 +161,43 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
       const float dL_dm = 2.0f * rm - 2.0f * m * rms;
       const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
       const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
-      dl = vn - m;
+      P.dl = vn - m;
       mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
       s2bar = (vnbar + dlbar) * dv_ds;
     }
   }
-  adj_tail(c, theta, vc, q, zx, hz, dl, adj_inc(c, s, vc, dl, q, zx), mbar, s2bar, a);
+  P.inc = adj_inc(c, vc + vn, vc, P.dl, P.q, zx);
+  adj_tail(c.E, c1, P, mbar, s2bar, a);
 }
 
 // Two consecutive reverse steps, n (lane x) then n - 1 (lane y): when both
 // take the quadratic branch, their quantities that do not depend on the
-// carried adjoint -- moments, square roots, the branch's terms, the log-spot
-// increment -- in packed FP32, then the two adjoint chains in order; else two
-// adjoint_step calls.  Lane for lane adjoint_step's operations, so the same
-// sums bit for bit however the steps are paired.
-__device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, float2 vc, float2 vn, float2 d,
-                                              float2 zx, AdjSums& a) {
+// carried adjoint (adj_common_pre, adj_quad_pre, the log-spot increment) in
+// packed FP32, then the two adjoint chains in order; else two adjoint_step
+// calls.  Lane for lane adjoint_step's operations, so the same sums bit for bit
+// however the steps are paired.
+__device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, float c1, float2 vc, float2 vn,
+                                              float2 d, float2 zx, AdjSums& a) {
   const float2 m = p_fma(vc, p_bc(c.E), p_bc(c.thE));
-  const float2 s2 = p_fma(vc, p_bc(c.c1), p_bc(c.c2));
+  const float2 s2h = p_fma(vc, p_bc(c.h1), p_bc(c.h2));
   const float2 m2 = p_mul(m, m);
-  const float2 lim = p_mul(p_bc(1.5f), m2);
-  if (!(s2.x < lim.x && s2.y < lim.y)) {
-    adjoint_step(c, theta, vc.x, vn.x, d.x, zx.x, a);
-    adjoint_step(c, theta, vc.y, vn.y, d.y, zx.y, a);
+  const float2 rs2h = p_rcp(s2h);
+  const float2 t = p_mul(m2, rs2h);  // qe_t, lane for lane
+  if (!(t.x > kQuadT && t.y > kQuadT)) {
+    adjoint_step(c, theta, c1, vc.x, vn.x, d.x, zx.x, a);
+    adjoint_step(c, theta, c1, vc.y, vn.y, d.y, zx.y, a);
     return;
   }
+  // adj_common_pre, paired
   const float2 s = p_add(vc, vn);
   const float2 rq = make_float2(rsqrt_approx(s.x), rsqrt_approx(s.y));
   const float2 sq = p_mul(s, rq);
   const float2 hq = p_mul(p_mul(p_bc(0.5f * c.sK3), zx), rq);
   const float2 q = make_float2(s.x > 0.0f ? sq.x : 0.0f, s.y > 0.0f ? sq.y : 0.0f);
-  const float2 hz = make_float2(s.x > 0.0f ? hq.x : 0.0f, s.y > 0.0f ? hq.y : 0.0f);
-  // adj_quad, paired
-  const float2 rs2 = p_rcp(s2);
-  const float2 t = p_mul(p_mul(p_bc(2.0f), m2), rs2);
+  const float2 hzc = p_add(make_float2(s.x > 0.0f ? hq.x : 0.0f, s.y > 0.0f ? hq.y : 0.0f), p_bc(c.Cv));
+  const float2 hzcd = p_sub(hzc, p_bc(c.Cd));
+  const float2 tmv = p_sub(p_bc(theta), vc);
+  // adj_quad_pre, paired
   const float2 tt = p_fma(t, t, p_mul(t, p_bc(-1.0f)));
   const float2 rroot = make_float2(rsqrt_approx(tt.x), rsqrt_approx(tt.y));
   const float2 root = p_mul(tt, rroot);
@@ -176,33 +209,43 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
   const float2 bz = p_add(b, d);
   const float2 g = p_fma(d, p_add(d, p_mul(p_bc(2.0f), b)), p_bc(-1.0f));
   const float2 dl = p_mul(am, g);
+  const float2 bz2 = p_mul(bz, bz);
+  const float2 cg = p_mul(p_bc(c.Cdl), g);
+  const float2 cz = p_mul(p_bc(c.Cdl), d);
+  const float2 am2 = p_add(am, am);
+  const float2 hrb = p_mul(p_bc(0.5f), rb);
+  const float2 amr = p_mul(am, ropb2);
+  const float2 F = p_fma(p_fma(p_bc(2.0f), t, p_bc(-1.0f)), p_mul(p_bc(0.5f), rroot), p_bc(1.0f));
+  const float2 m4r = p_mul(p_add(m, m), rs2h);
+  const float2 tr = p_mul(t, p_mul(p_bc(0.5f), rs2h));
   // adj_inc, paired
   float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
   inc = p_fma(p_bc(-c.Cd), vc, inc);
   inc = p_fma(p_bc(c.Cdl), dl, inc);
   inc = p_fma(p_mul(p_bc(c.sK3), q), zx, inc);
-  const AdjQuad Qx{rs2.x, t.x, rroot.x, rb.x, ropb2.x, am.x, bz.x, g.x};
-  const AdjQuad Qy{rs2.y, t.y, rroot.y, rb.y, ropb2.y, am.y, bz.y, g.y};
-  adj_chain_quad(c, theta, vc.x, m.x, d.x, q.x, zx.x, hz.x, dl.x, inc.x, Qx, a);
-  adj_chain_quad(c, theta, vc.y, m.y, d.y, q.y, zx.y, hz.y, dl.y, inc.y, Qy, a);
+  const AdjPre Px{inc.x, dl.x, q.x,  zx.x,  hzc.x, hzcd.x,  tmv.x, vc.x, bz.x,
+                  bz2.x, cg.x, cz.x, am2.x, hrb.x, amr.x, ropb2.x, F.x,   m4r.x, tr.x};
+  const AdjPre Py{inc.y, dl.y, q.y,  zx.y,  hzc.y, hzcd.y,  tmv.y, vc.y, bz.y,
+                  bz2.y, cg.y, cz.y, am2.y, hrb.y, amr.y, ropb2.y, F.y,   m4r.y, tr.y};
+  adj_chain_quad(c.E, c1, Px, a);
+  adj_chain_quad(c.E, c1, Py, a);
 }
 
 // The draw the reverse step of state v needs: Z_V in the quadratic branch,
 // 1 - U_V otherwise (same branch test as the forward step).
-__device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float omu, float zv) {
+__device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float xv, float zv) {
   const float m = fmaf(v, c.E, c.thE);
-  const float s2 = fmaf(v, c.c1, c.c2);
-  return s2 < 1.5f * (m * m) ? zv : omu;
+  const float s2h = fmaf(v, c.h1, c.h2);
+  return qe_t(m * m, s2h) > kQuadT ? zv : one_minus_u(xv);
 }
 
 // The stored data of one step (recompute pass): (state, branch draw) as one
 // pair and Z_X, from the step's centred variance uniform and its two normals.
 __device__ __forceinline__ void keep_step(const ScenConst& c, float xv_v, float zv, float zx, float2* bvd, float* bz,
                                           float& v) {
-  const float omu = 0.5f * (1.0f - xv_v);
-  *bvd = make_float2(v, branch_draw(c, v, omu, zv));
+  *bvd = make_float2(v, branch_draw(c, v, xv_v, zv));
   *bz = zx;
-  v = qe_only(c, v, omu, zv);
+  v = qe_only(c, v, xv_v, zv);
 }
 
 // A thread's column of a segment buffer of `stride` columns (8-byte aligned):
@@ -247,11 +290,12 @@ __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a,
 // way; g = d x_T / d(v0, kappa, theta, sigma, rho).
 template <typename Seg, bool PAIRED>
 __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
-                                           const uint32_t (&rk)[10][2], uint32_t plo, uint32_t phi,
+                                           const uint32_t (&rk)[10][2], const PhiloxLane& pl,
                                            const float* ck, int cstride, float v_last, const Seg& S,
                                            float& x_out, float& comp_out, float (&g)[5]) {
   using I = decltype(S.stride());
   const float theta = A.theta;
+  const float c1 = c.h1 + c.h1;  // s^2 = v c1 + c2
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
   AdjSums as = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -263,67 +307,73 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
     const uint32_t n0 = (uint32_t)sgi * k, n1 = min(n0 + k, N);
     float vv = ck_next;
     if (sgi > 0) ck_next = ck[(sgi - 1) * cstride];
-    for (uint32_t p = n0 / 2; 2 * p < n1; ++p) {  // recompute v_n0 .. v_n1 and keep the draws
-      const I i = (I)(2 * p - n0) * bd;
-      const uint4 w = philox4x32_10(p, plo, phi, option, rk);
-      const float xa = centered_uniform(w.x), xb = centered_uniform(w.z);
-      const float2 zv = norminv_centered2(make_float2(xa, xb));  // the pair's normals two at a time
-      const float2 zx = norminv_centered2(make_float2(centered_uniform(w.y), centered_uniform(w.w)));
-      keep_step(c, xa, zv.x, zx.x, s01 + i, s2 + i, vv);
-      if (2 * p + 1 < n1) keep_step(c, xb, zv.y, zx.y, s01 + i + bd, s2 + i + bd, vv);
+    // recompute v_n0 .. v_n1 and keep the draws: rows 2 (p - n0/2) and the next of
+    // this thread's column, by pointers stepped two rows per pair (n0 is even)
+    float2* wp = s01;
+    float* wz = s2;
+    for (uint32_t p = n0 / 2; 2 * p < n1; ++p, wp += 2 * bd, wz += 2 * bd) {
+      const uint4 w = philox_draw(pl, philox_ctr(p, option, rk), rk);
+      const float2 xv = centered_uniform2(w.x, w.z);
+      const float2 zv = norminv_centered2(xv);  // the pair's normals two at a time
+      const float2 zx = norminv_centered2(centered_uniform2(w.y, w.w));
+      keep_step(c, xv.x, zv.x, zx.x, wp, wz, vv);
+      if (2 * p + 1 < n1) keep_step(c, xv.y, zv.y, zx.y, wp + bd, wz + bd, vv);
     }
     float vnext = vv;  // v_{n1}
+    // the reverse steps read row i by pointers rp, rz stepped down from the top row
+    int i = (int)(n1 - n0) - 1;
+    const float2* rp = s01 + (I)i * bd;
+    const float* rz = s2 + (I)i * bd;
     if constexpr (PAIRED) {
       if constexpr (Seg::kGlobal) {
         // global memory: the steps in pairs (n, n - 1) from the top, each pair's
         // data loaded one pair ahead into registers and asked into L2
         // kPrefetchSteps steps ahead
         constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
-        int i = (int)(n1 - n0) - 1;
-        float2 pa = s01[(I)i * bd], pb = make_float2(0.0f, 0.0f);
-        float za = s2[(I)i * bd], zb = 0.0f;
+        const I o2 = 2 * bd, o3 = 3 * bd, f2 = (2 + kPrefetchSteps) * bd, f3 = (3 + kPrefetchSteps) * bd;
+        float2 pa = rp[0], pb = make_float2(0.0f, 0.0f);
+        float za = rz[0], zb = 0.0f;
         if (i >= 1) {
-          pb = s01[(I)(i - 1) * bd];
-          zb = s2[(I)(i - 1) * bd];
+          pb = rp[-bd];
+          zb = rz[-bd];
         }
-        for (; i >= 1; i -= 2) {
+        for (; i >= 1; i -= 2, rp -= o2, rz -= o2) {
           const float2 ca = pa, cb = pb;
           const float cza = za, czb = zb;
           if (i - 2 - kPrefetchSteps >= 0) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - 2 - kPrefetchSteps) * bd));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - 2 - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rp - f2));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rz - f2));
           }
           if (i - 3 - kPrefetchSteps >= 0) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - 3 - kPrefetchSteps) * bd));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - 3 - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rp - f3));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rz - f3));
           }
           if (i >= 2) {
-            pa = s01[(I)(i - 2) * bd];
-            za = s2[(I)(i - 2) * bd];
+            pa = rp[-o2];
+            za = rz[-o2];
           }
           if (i >= 3) {
-            pb = s01[(I)(i - 3) * bd];
-            zb = s2[(I)(i - 3) * bd];
+            pb = rp[-o3];
+            zb = rz[-o3];
           }
-          adjoint_step2(c, theta, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
+          adjoint_step2(c, theta, c1, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
                         make_float2(cza, czb), as);
           vnext = cb.x;
         }
         if (i == 0) {  // an odd count: the last step alone (loaded as pa)
-          adjoint_step(c, theta, pa.x, vnext, pa.y, za, as);
+          adjoint_step(c, theta, c1, pa.x, vnext, pa.y, za, as);
           vnext = pa.x;
         }
       } else {
-        int i = (int)(n1 - n0) - 1;
-        for (; i >= 1; i -= 2) {
-          const float2 ca = s01[(I)i * bd], cb = s01[(I)(i - 1) * bd];
-          adjoint_step2(c, theta, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
-                        make_float2(s2[(I)i * bd], s2[(I)(i - 1) * bd]), as);
+        for (; i >= 1; i -= 2, rp -= 2 * bd, rz -= 2 * bd) {
+          const float2 ca = rp[0], cb = rp[-bd];
+          adjoint_step2(c, theta, c1, make_float2(ca.x, cb.x), make_float2(vnext, ca.x), make_float2(ca.y, cb.y),
+                        make_float2(rz[0], rz[-bd]), as);
           vnext = cb.x;
         }
         if (i == 0) {
           const float2 vd = s01[0];
-          adjoint_step(c, theta, vd.x, vnext, vd.y, s2[0], as);
+          adjoint_step(c, theta, c1, vd.x, vnext, vd.y, s2[0], as);
           vnext = vd.x;
         }
       }
@@ -332,27 +382,27 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
         // global memory: each step's data loaded one step ahead into registers,
         // and asked into L2 kPrefetchSteps steps ahead
         constexpr int kPrefetchSteps = SIMR_ADJ_PREFETCH;
-        int i = (int)(n1 - n0) - 1;
-        float2 vd_n = s01[(I)i * bd];
-        float zx_n = s2[(I)i * bd];
-        for (; i >= 0; --i) {
+        const I f = (I)kPrefetchSteps * bd;
+        float2 vd_n = rp[0];
+        float zx_n = rz[0];
+        for (; i >= 0; --i, rp -= bd, rz -= bd) {
           const float2 vd = vd_n;
           const float zx = zx_n;
           if (i >= kPrefetchSteps) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s01 + (I)(i - kPrefetchSteps) * bd));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(s2 + (I)(i - kPrefetchSteps) * bd));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rp - f));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rz - f));
           }
           if (i > 0) {
-            vd_n = s01[(I)(i - 1) * bd];
-            zx_n = s2[(I)(i - 1) * bd];
+            vd_n = rp[-bd];
+            zx_n = rz[-bd];
           }
-          adjoint_step(c, theta, vd.x, vnext, vd.y, zx, as);
+          adjoint_step(c, theta, c1, vd.x, vnext, vd.y, zx, as);
           vnext = vd.x;
         }
       } else {
-        for (int i = (int)(n1 - n0) - 1; i >= 0; --i) {
-          const float2 vd = s01[(I)i * bd];
-          adjoint_step(c, theta, vd.x, vnext, vd.y, s2[(I)i * bd], as);
+        for (; i >= 0; --i, rp -= bd, rz -= bd) {
+          const float2 vd = rp[0];
+          adjoint_step(c, theta, c1, vd.x, vnext, vd.y, rz[0], as);
           vnext = vd.x;
         }
       }
@@ -380,12 +430,9 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
   static_assert(PPT == 1 || PPT == 2, "one or two paths per thread");
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
-  uint32_t plo[PPT], phi[PPT];
+  PhiloxLane pl[PPT];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    plo[j] = (uint32_t)path[j];
-    phi[j] = (uint32_t)(path[j] >> 32);
-  }
+  for (int j = 0; j < PPT; ++j) pl[j] = philox_lane(path[j], rk);
   // forward pass: the variance recursion up to the last checkpoint, (n_seg - 1) k
   // < N; k is even, so every pair of steps below it is whole
   float v[PPT];
@@ -398,31 +445,28 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
     for (uint32_t p = p0; p < p0 + k / 2; ++p) {
       uint4 w[PPT];
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], option, rk);
+      for (int j = 0; j < PPT; ++j) w[j] = philox_draw(pl[j], philox_ctr(p, option, rk), rk);
       if constexpr (PPT == 2) {
-        const float xa0 = centered_uniform(w[0].x), xa1 = centered_uniform(w[1].x);
-        const float xb0 = centered_uniform(w[0].z), xb1 = centered_uniform(w[1].z);
-        const float2 za = norminv_centered2(make_float2(xa0, xa1));
-        const float2 zb = norminv_centered2(make_float2(xb0, xb1));
+        const float2 xa = centered_uniform2(w[0].x, w[1].x), xb = centered_uniform2(w[0].z, w[1].z);
+        const float2 za = norminv_centered2(xa);
+        const float2 zb = norminv_centered2(xb);
         float2 vv = make_float2(v[0], v[1]), vn, dl;
-        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.c1), p_bc(c.c2)),
-                         make_float2(0.5f * (1.0f - xa0), 0.5f * (1.0f - xa1)), za, vn, dl);
+        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.h1), p_bc(c.h2)), xa, za, vn, dl);
         vv = vn;
-        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.c1), p_bc(c.c2)),
-                         make_float2(0.5f * (1.0f - xb0), 0.5f * (1.0f - xb1)), zb, vn, dl);
+        qe_from_moments2(p_fma(vv, p_bc(c.E), p_bc(c.thE)), p_fma(vv, p_bc(c.h1), p_bc(c.h2)), xb, zb, vn, dl);
         v[0] = vn.x;
         v[1] = vn.y;
       } else {  // the pair's two variance normals together
-        const float xa = centered_uniform(w[0].x), xb = centered_uniform(w[0].z);
-        const float2 zv = norminv_centered2(make_float2(xa, xb));
-        v[0] = qe_only(c, v[0], 0.5f * (1.0f - xa), zv.x);
-        v[0] = qe_only(c, v[0], 0.5f * (1.0f - xb), zv.y);
+        const float2 xv = centered_uniform2(w[0].x, w[0].z);
+        const float2 zv = norminv_centered2(xv);
+        v[0] = qe_only(c, v[0], xv.x, zv.x);
+        v[0] = qe_only(c, v[0], xv.y, zv.y);
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
-    path_sweep<Seg, PAIRED>(c, A, N, option, rk, plo[j], phi[j], ck + j * ck_stride, PPT * ck_stride, v[j], S,
+    path_sweep<Seg, PAIRED>(c, A, N, option, rk, pl[j], ck + j * ck_stride, PPT * ck_stride, v[j], S,
                             x_out[j], comp_out[j], g[j]);
 }
 

@@ -185,8 +185,8 @@ ScenConst pack(const double c[9], double ratio, double v0) {
   ScenConst s;
   s.E = (float)c[0];
   s.thE = (float)c[1];
-  s.c1 = (float)c[2];
-  s.c2 = (float)c[3];
+  s.h1 = (float)(0.5 * c[2]);  // halves of c1, c2: the step carries s^2 / 2
+  s.h2 = (float)(0.5 * c[3]);
   s.C0 = (float)c[4];
   s.Cv = (float)c[5];
   s.Cd = (float)c[6];

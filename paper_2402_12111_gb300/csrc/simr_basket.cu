@@ -27,10 +27,10 @@ constexpr int kBasketTpb = 256;
 
 // step_base<false> of two assets at once in packed FP32, lane for lane the
 // scalar step's operations and rounding.
-__device__ __forceinline__ void step_pair(const ScenConst2& c, float2 omu, float2 zv, float2 zx, float2& v, float2& x,
+__device__ __forceinline__ void step_pair(const ScenConst2& c, float2 xv, float2 zv, float2 zx, float2& v, float2& x,
                                           float2& comp) {
   float2 vn, dl;
-  qe_from_moments2(p_fma(v, c.E, c.thE), p_fma(v, c.c1, c.c2), omu, zv, vn, dl);
+  qe_from_moments2(p_fma(v, c.E, c.thE), p_fma(v, c.h1, c.h2), xv, zv, vn, dl);
   const float2 s = p_add(v, vn);
   float2 inc = p_fma(c.Cv, s, c.C0);
   inc = p_fma(c.mCd, v, inc);
@@ -59,7 +59,7 @@ __device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const Sc
   }
   z.y = __fmaf_rn(rb[k + 1], eps[k + 1], z.y);
   const float2 zv = norminv_centered2(xv);
-  step_pair(c, make_float2(0.5f * (1.0f - xv.x), 0.5f * (1.0f - xv.y)), zv, z, v, x, comp);
+  step_pair(c, xv, zv, z, v, x, comp);
 }
 
 // One step of the lone last asset k of an odd count (k only known at run
@@ -74,7 +74,7 @@ __device__ __forceinline__ void basket_lone_step(const BasketLaunch& L, int k, f
   for (int j = 0; j < NA; ++j)
     if (j < k) z = __fmaf_rn(ra[j], eps[j], z);
   z = __fmaf_rn(ra[k], e, z);
-  step_base<false>(L.sc[k], 0.5f * (1.0f - xv), norminv_centered(xv), z, v, x, comp);
+  step_base<false>(L.sc[k], xv, norminv_centered(xv), z, v, x, comp);
 }
 
 template <int NA, int TILE>
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
   for (uint64_t bt = (uint64_t)blockIdx.x * warps + warp; bt < batches; bt += total_warps) {
     const uint64_t path = bt * kWarp + lane;
     const bool active = path < L.paths;
-    const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+    const PhiloxLane pl = philox_lane(path, L.rk);  // shared by the assets' counters
     float2 v[NA / 2], x[NA / 2], comp[NA / 2];  // the pairs
     float eps[NA];
     uint32_t wz[NA], ww[NA];  // the odd step's words of each asset
@@ -130,20 +130,19 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
       for (int q = 0; q < NA / 2; ++q) {
         const int k = 2 * q;
         if (k + 1 >= na) break;
-        const uint4 wa = philox4x32_10(p, plo, phi, (uint32_t)k, L.rk);
-        const uint4 wb = philox4x32_10(p, plo, phi, (uint32_t)(k + 1), L.rk);
+        const uint4 wa = philox_draw(pl, philox_ctr(p, (uint32_t)k, L.rk), L.rk);
+        const uint4 wb = philox_draw(pl, philox_ctr(p, (uint32_t)(k + 1), L.rk), L.rk);
         wz[k] = wa.z;
         ww[k] = wa.w;
         wz[k + 1] = wb.z;
         ww[k + 1] = wb.w;
-        const float2 e = norminv_centered2(make_float2(centered_uniform(wa.y), centered_uniform(wb.y)));
+        const float2 e = norminv_centered2(centered_uniform2(wa.y, wb.y));
         eps[k] = e.x;
         eps[k + 1] = e.y;
-        basket_pair_step<NA>(L, L.pk[q], k,
-                             make_float2(centered_uniform(wa.x), centered_uniform(wb.x)), eps, v[q], x[q], comp[q]);
+        basket_pair_step<NA>(L, L.pk[q], k, centered_uniform2(wa.x, wb.x), eps, v[q], x[q], comp[q]);
       }
       if (na & 1) {
-        const uint4 w = philox4x32_10(p, plo, phi, (uint32_t)kl, L.rk);
+        const uint4 w = philox_draw(pl, philox_ctr(p, (uint32_t)kl, L.rk), L.rk);
         wzl = w.z;
         wwl = w.w;
         basket_lone_step<NA>(L, kl, centered_uniform(w.x), eps, norminv_centered(centered_uniform(w.y)), vl, xl, cl);
@@ -153,12 +152,10 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
         for (int q = 0; q < NA / 2; ++q) {
           const int k = 2 * q;
           if (k + 1 >= na) break;
-          const float2 e = norminv_centered2(make_float2(centered_uniform(ww[k]), centered_uniform(ww[k + 1])));
+          const float2 e = norminv_centered2(centered_uniform2(ww[k], ww[k + 1]));
           eps[k] = e.x;
           eps[k + 1] = e.y;
-          basket_pair_step<NA>(L, L.pk[q], k,
-                               make_float2(centered_uniform(wz[k]), centered_uniform(wz[k + 1])), eps, v[q], x[q],
-                               comp[q]);
+          basket_pair_step<NA>(L, L.pk[q], k, centered_uniform2(wz[k], wz[k + 1]), eps, v[q], x[q], comp[q]);
         }
         if (na & 1)
           basket_lone_step<NA>(L, kl, centered_uniform(wzl), eps, norminv_centered(centered_uniform(wwl)), vl, xl,

@@ -16,8 +16,10 @@ constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
 // Per-scenario FP32 constants of the QE variance step and the log-spot step
 // (Andersen 2008 with gamma1 = gamma2 = 1/2, risk-neutral drift r), computed on
 // the host in FP64 and rounded once:
-//   m   = theta + (v - theta) E          = fma(v, E, thE)
-//   s^2 = v c1 + c2
+//   m     = theta + (v - theta) E        = fma(v, E, thE)
+//   s^2/2 = v h1 + h2                    (h1 = c1/2, h2 = c2/2 of s^2 = v c1 + c2:
+//           the step needs t = 2 m^2 / s^2 = m^2 / (s^2/2), so it carries half the
+//           conditional variance; the halving is exact)
 //   x' = x + K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X, rewritten without
 //   the large cancelling rho/sigma terms as
 //   x' = x + C0 + Cv (v + v') - Cd v + Cdl (v' - m) + sK3 sqrt(v + v') Z_X
@@ -36,7 +38,7 @@ constexpr int kMaxScen = 13;  // base + 6 re-simulated Greeks x (up, down)
 // the difference.  The initial variance is not a delta: each scenario starts
 // from its own FP32 v0, and the host divides by the realised FP32 bump.
 struct ScenConst {
-  float E, thE, c1, c2;
+  float E, thE, h1, h2;
   float C0, Cv, Cd, Cdl;
   float sK3;
   float ratio;  // base: 1; bumped: (discount of this scenario / base discount) - 1
@@ -48,15 +50,15 @@ struct ScenConst {
 // paired steps, read from the launch parameters as they are (the same values
 // in both lanes for two paths or the v0 bumps; a bumped pair's own deltas).
 struct ScenConst2 {
-  float2 E, thE, c1, c2, C0, Cv, mCd, Cdl, sK3;  // mCd = -Cd
+  float2 E, thE, h1, h2, C0, Cv, mCd, Cdl, sK3;  // mCd = -Cd
 };
 
 __host__ __device__ inline ScenConst2 pack_const(const ScenConst& a, const ScenConst& b) {
   ScenConst2 p;
   p.E = make_float2(a.E, b.E);
   p.thE = make_float2(a.thE, b.thE);
-  p.c1 = make_float2(a.c1, b.c1);
-  p.c2 = make_float2(a.c2, b.c2);
+  p.h1 = make_float2(a.h1, b.h1);
+  p.h2 = make_float2(a.h2, b.h2);
   p.C0 = make_float2(a.C0, b.C0);
   p.Cv = make_float2(a.Cv, b.Cv);
   p.mCd = make_float2(-a.Cd, -b.Cd);
@@ -167,15 +169,55 @@ __device__ __forceinline__ float2 p_sqrt(float2 a) { return make_float2(sqrt_app
 __device__ __forceinline__ float2 p_lg2(float2 a) { return make_float2(lg2_approx(a.x), lg2_approx(a.y)); }
 
 // ------------------------------------------------------------- Philox ----
-// Philox4x32-10 (Salmon et al., SC'11).  rk[i] = key + i * (0x9E3779B9, 0xBB67AE85)
-// is precomputed on the host (the key is uniform over the launch), so each round
-// is two 32x32->64 multiplies and two three-input XORs with a constant operand.
-__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                               const uint32_t (&rk)[10][2]) {
+// Philox4x32-10 (Salmon et al., SC'11) of the counter (p, plo, phi, option):
+// ten rounds (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+// lo(M0 c0)) under the round keys rk[i] = key + i * (0x9E3779B9, 0xBB67AE85),
+// precomputed on the host (the key is uniform over the launch).
+// The first two rounds are split by what their words depend on.  Round 0
+// multiplies phi (path) and p (step pair); round 1 multiplies round 0's
+// path-only word s0 and its step-only word s2.  So round 1's output is
+//   (a(p) ^ s1, b(p), h0 ^ c(p), l0)
+// with (s1, h0, l0) a function of the path alone (PhiloxLane, formed once per
+// path) and (a, b, c) of the step pair and option alone (PhiloxCtr, formed once
+// per step pair and shared by every path that draws it); rounds 2..9 run per
+// path: 16 of the 20 32x32 -> 64-bit products a path needs per draw.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+
+struct PhiloxLane {
+  uint32_t s1, h0, l0;  // lo(M1 phi); hi and lo of M0 s0, s0 = hi(M1 phi) ^ plo ^ rk[0][0]
+};
+struct PhiloxCtr {
+  uint32_t a, b, c;  // hi(M1 s2) ^ rk[1][0]; lo(M1 s2); lo(M0 p) ^ rk[1][1], s2 = hi(M0 p) ^ option ^ rk[0][1]
+};
+
+__device__ __forceinline__ PhiloxLane philox_lane(uint32_t plo, uint32_t phi, const uint32_t (&rk)[10][2]) {
+  const uint32_t s0 = __umulhi(kPhiloxM1, phi) ^ plo ^ rk[0][0];
+  PhiloxLane l;
+  l.s1 = kPhiloxM1 * phi;
+  l.h0 = __umulhi(kPhiloxM0, s0);
+  l.l0 = kPhiloxM0 * s0;
+  return l;
+}
+__device__ __forceinline__ PhiloxLane philox_lane(uint64_t path, const uint32_t (&rk)[10][2]) {
+  return philox_lane((uint32_t)path, (uint32_t)(path >> 32), rk);
+}
+
+__device__ __forceinline__ PhiloxCtr philox_ctr(uint32_t p, uint32_t option, const uint32_t (&rk)[10][2]) {
+  const uint32_t s2 = __umulhi(kPhiloxM0, p) ^ option ^ rk[0][1];
+  PhiloxCtr u;
+  u.a = __umulhi(kPhiloxM1, s2) ^ rk[1][0];
+  u.b = kPhiloxM1 * s2;
+  u.c = (kPhiloxM0 * p) ^ rk[1][1];
+  return u;
+}
+
+// Rounds 2..9 from the two halves of round 1's output.
+__device__ __forceinline__ uint4 philox_draw(const PhiloxLane& l, const PhiloxCtr& u, const uint32_t (&rk)[10][2]) {
+  uint32_t c0 = u.a ^ l.s1, c1 = u.b, c2 = l.h0 ^ u.c, c3 = l.l0;
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+  for (int i = 2; i < 10; ++i) {
+    const uint32_t lo0 = kPhiloxM0 * c0, hi0 = __umulhi(kPhiloxM0, c0);
+    const uint32_t lo1 = kPhiloxM1 * c2, hi1 = __umulhi(kPhiloxM1, c2);
     const uint32_t n0 = hi1 ^ c1 ^ rk[i][0];
     const uint32_t n2 = hi0 ^ c3 ^ rk[i][1];
     c0 = n0;
@@ -186,6 +228,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
   return make_uint4(c0, c1, c2, c3);
 }
 
+// The whole generator for one counter.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const uint32_t (&rk)[10][2]) {
+  return philox_draw(philox_lane(c1, c2, rk), philox_ctr(c0, c3, rk), rk);
+}
+
 // x = 2u - 1 for u = ((w >> 9) + 1/2) 2^-23, exact in FP32:
 // f = 1 + (w >> 9) 2^-23 from the bits, f - 1.5 is exact, and
 // 2 (f - 1.5) + 2^-23 = (2k + 1 - 2^23) 2^-23 needs at most 23 significant bits.
@@ -193,13 +241,19 @@ __device__ __forceinline__ float centered_uniform(uint32_t w) {
   const float f = __uint_as_float(0x3f800000u | (w >> 9));
   return fmaf(2.0f, f - 1.5f, 0x1p-23f);
 }
+// Two of them in packed FP32 (the same operations, lane for lane).
+__device__ __forceinline__ float2 centered_uniform2(uint32_t wa, uint32_t wb);
+// 1 - U_V from x = 2 U_V - 1 (exact): the exponential branch's uniform.
+__device__ __forceinline__ float one_minus_u(float x) { return 0.5f * (1.0f - x); }
 
 // Z = Phi^-1(u) = sqrt(2) erfinv(x), x = 2u - 1, by M. Giles' single-precision
 // erfinv approximation ("Approximating the erfinv function", GPU Computing Gems
 // Jade Edition, 2011): w = -ln(1 - x^2); a degree-8 polynomial in w - 2.5 for
 // w < 5, else in sqrt(w) - 3, times x.  The coefficients below are Giles'
 // multiplied by sqrt(2) (in double, rounded once), so no final scaling is needed.
-// 1 - x^2 is formed by one FMA (exact product, one rounding).
+// 1 - x^2 is formed by one FMA (exact product, one rounding) -- as x^2 - 1 with
+// the sign dropped at the logarithm, which rounds to the same magnitude -- and
+// w - 2.5 = -ln2 lg2(1 - x^2) - 2.5 by one more.
 #define SIMR_S2(c) ((float)((c) * 1.4142135623730951))
 // the tail branch (w >= 5, |x| > 0.9966: about 0.3% of the draws)
 __device__ __forceinline__ float norminv_tail(float w) {
@@ -215,29 +269,32 @@ __device__ __forceinline__ float norminv_tail(float w) {
   p = __fmaf_rn(p, w, SIMR_S2(2.83297682));
   return p;
 }
+// w - 2.5 from lg2(1 - x^2)
+__device__ __forceinline__ float norminv_wc(float x) {
+  return __fmaf_rn(lg2_approx(fabsf(__fmaf_rn(x, x, -1.0f))), -0.69314718055994531f, -2.5f);
+}
+__device__ __forceinline__ float norminv_central(float wc) {
+  float p = SIMR_S2(2.81022636e-08);
+  p = __fmaf_rn(p, wc, SIMR_S2(3.43273939e-07));
+  p = __fmaf_rn(p, wc, SIMR_S2(-3.5233877e-06));
+  p = __fmaf_rn(p, wc, SIMR_S2(-4.39150654e-06));
+  p = __fmaf_rn(p, wc, SIMR_S2(0.00021858087));
+  p = __fmaf_rn(p, wc, SIMR_S2(-0.00125372503));
+  p = __fmaf_rn(p, wc, SIMR_S2(-0.00417768164));
+  p = __fmaf_rn(p, wc, SIMR_S2(0.246640727));
+  p = __fmaf_rn(p, wc, SIMR_S2(1.50140941));
+  return p;
+}
 __device__ __forceinline__ float norminv_centered(float x) {
-  const float w = __fmul_rn(-0.69314718055994531f, lg2_approx(__fmaf_rn(-x, x, 1.0f)));
-  float p;
-  if (w < 5.0f) {
-    const float wc = __fsub_rn(w, 2.5f);
-    p = SIMR_S2(2.81022636e-08);
-    p = __fmaf_rn(p, wc, SIMR_S2(3.43273939e-07));
-    p = __fmaf_rn(p, wc, SIMR_S2(-3.5233877e-06));
-    p = __fmaf_rn(p, wc, SIMR_S2(-4.39150654e-06));
-    p = __fmaf_rn(p, wc, SIMR_S2(0.00021858087));
-    p = __fmaf_rn(p, wc, SIMR_S2(-0.00125372503));
-    p = __fmaf_rn(p, wc, SIMR_S2(-0.00417768164));
-    p = __fmaf_rn(p, wc, SIMR_S2(0.246640727));
-    p = __fmaf_rn(p, wc, SIMR_S2(1.50140941));
-  } else {
-    p = norminv_tail(w);
-  }
+  const float wc = norminv_wc(x);
+  const float p = wc < 2.5f ? norminv_central(wc) : norminv_tail(__fadd_rn(wc, 2.5f));
   return __fmul_rn(p, x);
 }
 // Two inverse normals at once (the central polynomial paired, the rare tail per lane).
 __device__ __forceinline__ float2 norminv_centered2(float2 x) {
-  const float2 w = p_mul(p_bc(-0.69314718055994531f), p_lg2(p_fma(p_mul(x, p_bc(-1.0f)), x, p_bc(1.0f))));
-  const float2 wc = p_sub(w, p_bc(2.5f));
+  const float2 t = p_fma(x, x, p_bc(-1.0f));
+  const float2 L = make_float2(lg2_approx(fabsf(t.x)), lg2_approx(fabsf(t.y)));
+  const float2 wc = p_fma(L, p_bc(-0.69314718055994531f), p_bc(-2.5f));
   float2 p = p_bc(SIMR_S2(2.81022636e-08));
   p = p_fma(p, wc, p_bc(SIMR_S2(3.43273939e-07)));
   p = p_fma(p, wc, p_bc(SIMR_S2(-3.5233877e-06)));
@@ -247,36 +304,46 @@ __device__ __forceinline__ float2 norminv_centered2(float2 x) {
   p = p_fma(p, wc, p_bc(SIMR_S2(-0.00417768164)));
   p = p_fma(p, wc, p_bc(SIMR_S2(0.246640727)));
   p = p_fma(p, wc, p_bc(SIMR_S2(1.50140941)));
-  if (!(w.x < 5.0f && w.y < 5.0f)) {  // one test on the common path
-    if (!(w.x < 5.0f)) p.x = norminv_tail(w.x);
-    if (!(w.y < 5.0f)) p.y = norminv_tail(w.y);
+  if (!(wc.x < 2.5f && wc.y < 2.5f)) {  // one test on the common path
+    if (!(wc.x < 2.5f)) p.x = norminv_tail(__fadd_rn(wc.x, 2.5f));
+    if (!(wc.y < 2.5f)) p.y = norminv_tail(__fadd_rn(wc.y, 2.5f));
   }
   return p_mul(p, x);
 }
 #undef SIMR_S2
 
+__device__ __forceinline__ float2 centered_uniform2(uint32_t wa, uint32_t wb) {
+  const float2 f = make_float2(__uint_as_float(0x3f800000u | (wa >> 9)), __uint_as_float(0x3f800000u | (wb >> 9)));
+  return p_fma(p_bc(2.0f), p_sub(f, p_bc(1.5f)), p_bc(0x1p-23f));
+}
+
 // ------------------------------------------------------------ QE step ----
 // VariancePathQE (paper Sec. 4) with Andersen's QE rule, psi_c = 1.5, given
-// m = E[v'|v] and s2 = Var[v'|v]:
+// m = E[v'|v] and s2h = Var[v'|v] / 2:
 //   psi = s^2/m^2 <= 1.5 : v' = a (b + Z_V)^2, b^2 = t - 1 + sqrt(t (t - 1)),
-//                          t = 2/psi, a = m / (1 + b^2)
+//                          t = 2/psi = m^2 / s2h, a = m / (1 + b^2)
 //   psi > 1.5            : p = (psi-1)/(psi+1); v' = 0 if U_V <= p,
 //                          else ((1-p)/m)^-1 ln((1-p)/(1-U_V))
-// The branch test needs no division: s^2 < 1.5 m^2 in FP32, strictly, so that
-// m = 0 (theta = 0 and v = 0: then s^2 = 0 as well) falls through to the
-// exponential branch's m > 0 test (v' = 0) with no test of its own in the
-// common path; an exact FP32 tie -- at FP32 distance from the threshold, where
-// the FP64 reading psi <= psi_c can go either way anyway -- takes the
-// exponential branch.  U_V <= p is tested as
-// (1 - U_V)(m^2 + s^2) >= 2 m^2.  Besides v' it returns dl = v' - m (the
-// innovation the log-spot step needs) without cancellation in the quadratic
-// branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1) since m = a (1 + b^2).
-// omu = 1 - U_V (exact), zv = Phi^-1(U_V).
+// The branch test is t > 4/3 in FP32, strictly: t is needed by the quadratic
+// branch anyway, and m = 0 (theta = 0 and v = 0, so s2h = 0 as well: t = NaN)
+// falls through to the exponential branch's m > 0 test (v' = 0) with no test of
+// its own in the common path; a decision at FP32 distance from the threshold,
+// where the FP64 reading psi <= psi_c can go either way anyway, may differ from
+// it.  t - 1 is exact for t in [1, 2^24], so t (t - 1) rounds as t^2 - t.
+// U_V <= p is tested as (1 - U_V)(m^2 + s^2) >= 2 m^2.  Besides v' the step
+// returns dl = v' - m (the innovation the log-spot step needs) without
+// cancellation in the quadratic branch: a (b + Z)^2 - m = a (Z (Z + 2b) - 1)
+// since m = a (1 + b^2).  xv = 2 U_V - 1 (1 - U_V is formed only where the
+// exponential branch needs it), zv = Phi^-1(U_V).
+constexpr float kQuadT = 1.33333333333333333f;  // t above it: the quadratic branch (psi < 1.5)
+
+__device__ __forceinline__ float qe_t(float m2, float s2h) { return __fmul_rn(m2, rcp_approx(s2h)); }
+
 // the exponential branch (and the zero-mean case) of qe_from_moments
-__device__ __forceinline__ void qe_exp_branch(float m, float s2, float m2, float omu, float& v_next, float& dl) {
+__device__ __forceinline__ void qe_exp_branch(float m, float s2h, float m2, float xv, float& v_next, float& dl) {
   if (m > 0.0f) {
-    const float ms = __fadd_rn(m2, s2);
-    const float W = __fmul_rn(omu, ms);
+    const float ms = __fadd_rn(m2, __fadd_rn(s2h, s2h));
+    const float W = __fmul_rn(one_minus_u(xv), ms);
     if (W >= __fmul_rn(2.0f, m2)) {
       v_next = 0.0f;
     } else {
@@ -290,41 +357,48 @@ __device__ __forceinline__ void qe_exp_branch(float m, float s2, float m2, float
   }
 }
 
-__device__ __forceinline__ void qe_from_moments(float m, float s2, float omu, float zv, float& v_next,
-                                                float& dl) {
+// the quadratic branch from t = m^2 / s2h
+__device__ __forceinline__ void qe_quad_branch(float m, float t, float zv, float& v_next, float& dl, float* b2_out = nullptr,
+                                               float* a_out = nullptr) {
+  const float tm1 = __fsub_rn(t, 1.0f);
+  const float root = sqrt_approx(__fmul_rn(t, tm1));
+  const float b2 = __fadd_rn(tm1, root);
+  const float b = sqrt_approx(b2);
+  const float a = __fmul_rn(m, rcp_approx(__fadd_rn(t, root)));
+  const float bz = __fadd_rn(b, zv);
+  v_next = __fmul_rn(__fmul_rn(a, bz), bz);
+  dl = __fmul_rn(a, __fmaf_rn(zv, __fadd_rn(bz, b), -1.0f));
+  if (b2_out) *b2_out = b2;
+  if (a_out) *a_out = a;
+}
+
+__device__ __forceinline__ void qe_from_moments(float m, float s2h, float xv, float zv, float& v_next, float& dl) {
   const float m2 = __fmul_rn(m, m);
-  if (s2 < __fmul_rn(1.5f, m2)) {
-    const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
-    const float root = sqrt_approx(__fmaf_rn(t, t, -t));
-    const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
-    const float b = sqrt_approx(b2);
-    const float a = __fmul_rn(m, rcp_approx(__fadd_rn(t, root)));
-    const float bz = __fadd_rn(b, zv);
-    v_next = __fmul_rn(__fmul_rn(a, bz), bz);
-    dl = __fmul_rn(a, __fmaf_rn(zv, __fadd_rn(zv, __fmul_rn(2.0f, b)), -1.0f));
-  } else {
-    qe_exp_branch(m, s2, m2, omu, v_next, dl);
-  }
+  const float t = qe_t(m2, s2h);
+  if (t > kQuadT)
+    qe_quad_branch(m, t, zv, v_next, dl);
+  else
+    qe_exp_branch(m, s2h, m2, xv, v_next, dl);
 }
 
 // Two QE variance steps: the quadratic branch paired for both lanes, then any
 // lane outside it redone by the scalar exponential branch.
-__device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2, float2 omu, float2 zv, float2& v_next,
+__device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2h, float2 xv, float2 zv, float2& v_next,
                                                  float2& dl) {
   const float2 m2 = p_mul(m, m);
-  const float2 lim = p_mul(p_bc(1.5f), m2);
-  const float2 t = p_mul(p_mul(p_bc(2.0f), m2), p_rcp(s2));
-  const float2 root = p_sqrt(p_fma(t, t, p_mul(t, p_bc(-1.0f))));
-  const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+  const float2 t = p_mul(m2, p_rcp(s2h));
+  const float2 tm1 = p_sub(t, p_bc(1.0f));
+  const float2 root = p_sqrt(p_mul(t, tm1));
+  const float2 b2 = p_add(tm1, root);
   const float2 b = p_sqrt(b2);
   const float2 a = p_mul(m, p_rcp(p_add(t, root)));
   const float2 bz = p_add(b, zv);
   v_next = p_mul(p_mul(a, bz), bz);
-  dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
-  const bool qx = s2.x < lim.x, qy = s2.y < lim.y;
+  dl = p_mul(a, p_fma(zv, p_add(bz, b), p_bc(-1.0f)));
+  const bool qx = t.x > kQuadT, qy = t.y > kQuadT;
   if (!(qx && qy)) {  // one test on the common path
-    if (!qx) qe_exp_branch(m.x, s2.x, m2.x, omu.x, v_next.x, dl.x);
-    if (!qy) qe_exp_branch(m.y, s2.y, m2.y, omu.y, v_next.y, dl.y);
+    if (!qx) qe_exp_branch(m.x, s2h.x, m2.x, xv.x, v_next.x, dl.x);
+    if (!qy) qe_exp_branch(m.y, s2h.y, m2.y, xv.y, v_next.y, dl.y);
   }
 }
 
@@ -333,14 +407,14 @@ __device__ __forceinline__ void qe_from_moments2(float2 m, float2 s2, float2 omu
 // moments are formed in the bumped scenarios' rounding order (product, then
 // the additive constant) so the two share their systematic rounding.
 template <bool CRN>
-__device__ __forceinline__ void step_base(const ScenConst& c, float omu, float zv, float zx, float& v, float& x,
+__device__ __forceinline__ void step_base(const ScenConst& c, float xv, float zv, float zx, float& v, float& x,
                                           float& comp) {
   float vn, dl;
   // CRN: round(round(v E) + thE), exactly the bumped scenarios' sequence with zero
   // deltas (__fmul_rn / __fadd_rn are never contracted into an FMA)
   const float m = CRN ? __fadd_rn(__fmul_rn(v, c.E), c.thE) : __fmaf_rn(v, c.E, c.thE);
-  const float s2 = CRN ? __fadd_rn(__fmul_rn(v, c.c1), c.c2) : __fmaf_rn(v, c.c1, c.c2);
-  qe_from_moments(m, s2, omu, zv, vn, dl);
+  const float s2h = CRN ? __fadd_rn(__fmul_rn(v, c.h1), c.h2) : __fmaf_rn(v, c.h1, c.h2);
+  qe_from_moments(m, s2h, xv, zv, vn, dl);
   const float s = __fadd_rn(v, vn);
   float inc = __fmaf_rn(c.Cv, s, c.C0);
   inc = __fmaf_rn(-c.Cd, v, inc);
@@ -356,12 +430,12 @@ __device__ __forceinline__ void step_base(const ScenConst& c, float omu, float z
 // step_base for two lanes sharing the constants (two paths, or two scenarios
 // that differ only in v0).
 template <bool CRN>
-__device__ __forceinline__ void step_base2(const ScenConst2& c, float2 omu, float2 zv, float2 zx, float2& v,
+__device__ __forceinline__ void step_base2(const ScenConst2& c, float2 xv, float2 zv, float2 zx, float2& v,
                                            float2& x, float2& comp) {
   float2 vn, dl;
   const float2 m = CRN ? p_add(p_mul(v, c.E), c.thE) : p_fma(v, c.E, c.thE);
-  const float2 s2 = CRN ? p_add(p_mul(v, c.c1), c.c2) : p_fma(v, c.c1, c.c2);
-  qe_from_moments2(m, s2, omu, zv, vn, dl);
+  const float2 s2h = CRN ? p_add(p_mul(v, c.h1), c.h2) : p_fma(v, c.h1, c.h2);
+  qe_from_moments2(m, s2h, xv, zv, vn, dl);
   const float2 s = p_add(v, vn);
   float2 inc = p_fma(c.Cv, s, c.C0);
   inc = p_fma(c.mCd, v, inc);
@@ -375,9 +449,9 @@ __device__ __forceinline__ void step_base2(const ScenConst2& c, float2 omu, floa
 }
 
 template <bool CRN>
-__device__ __forceinline__ void step_base2(const ScenConst& c, float2 omu, float2 zv, float2 zx, float2& v,
+__device__ __forceinline__ void step_base2(const ScenConst& c, float2 xv, float2 zv, float2 zx, float2& v,
                                            float2& x, float2& comp) {
-  step_base2<CRN>(pack_const(c, c), omu, zv, zx, v, x, comp);
+  step_base2<CRN>(pack_const(c, c), xv, zv, zx, v, x, comp);
 }
 
 // QE-M (Andersen 2008, martingale correction): the constant K0 - r dt of the
@@ -412,19 +486,14 @@ __device__ __forceinline__ float neg_log1m_tail(float u) {
 // A >= beta).  Quadratic: lam = 2 (A a)^2 b^2 / (1 - 2 A a) + g(2 A a)/2;
 // exponential: lam = ln(1 + (1 - p) w / (1 - w)) - (1 - p) w with w = A / beta,
 // 1 - p = 2 m^2 / (m^2 + s^2), beta = 2 m / (m^2 + s^2).
-__device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, float zv, float A, float& v_next,
+__device__ __forceinline__ bool qem_from_moments(float m, float s2h, float xv, float zv, float A, float& v_next,
                                                  float& dl, float& lam) {
   const float m2 = __fmul_rn(m, m);
+  const float t = qe_t(m2, s2h);
   lam = 0.0f;
-  if (s2 < __fmul_rn(1.5f, m2)) {
-    const float t = __fmul_rn(__fmul_rn(2.0f, m2), rcp_approx(s2));
-    const float root = sqrt_approx(__fmaf_rn(t, t, -t));
-    const float b2 = __fadd_rn(__fsub_rn(t, 1.0f), root);
-    const float b = sqrt_approx(b2);
-    const float a = __fmul_rn(m, rcp_approx(__fadd_rn(t, root)));
-    const float bz = __fadd_rn(b, zv);
-    v_next = __fmul_rn(__fmul_rn(a, bz), bz);
-    dl = __fmul_rn(a, __fmaf_rn(zv, __fadd_rn(zv, __fmul_rn(2.0f, b)), -1.0f));
+  if (t > kQuadT) {
+    float b2, a;
+    qe_quad_branch(m, t, zv, v_next, dl, &b2, &a);
     const float Aa = __fmul_rn(A, a);
     const float u = __fmul_rn(2.0f, Aa);
     if (!(u < 1.0f)) return false;
@@ -433,15 +502,8 @@ __device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, f
     return true;
   }
   if (m > 0.0f) {
-    const float ms = m2 + s2;
-    const float W = omu * ms;
-    if (W >= 2.0f * m2) {
-      v_next = 0.0f;
-    } else {
-      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
-      v_next = 0.5f * ms * rcp_approx(m) * L;
-    }
-    dl = v_next - m;
+    qe_exp_branch(m, s2h, m2, xv, v_next, dl);
+    const float ms = m2 + (s2h + s2h);
     const float onep = 2.0f * m2 * rcp_approx(ms);  // 1 - p
     const float w = 0.5f * A * ms * rcp_approx(m);  // A / beta
     if (!(w < 1.0f)) return false;
@@ -455,12 +517,12 @@ __device__ __forceinline__ bool qem_from_moments(float m, float s2, float omu, f
 
 // One QE-M step of the base scenario (variance step identical to step_base's);
 // where the correction does not exist the plain QE increment is taken.
-__device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, float omu, float zv, float zx,
+__device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, float xv, float zv, float zx,
                                          float& v, float& x, float& comp) {
   float vn, dl, lam;
   const float m = __fmaf_rn(v, c.E, c.thE);
-  const float s2 = __fmaf_rn(v, c.c1, c.c2);
-  const bool ok = qem_from_moments(m, s2, omu, zv, q.A, vn, dl, lam);
+  const float s2h = __fmaf_rn(v, c.h1, c.h2);
+  const bool ok = qem_from_moments(m, s2h, xv, zv, q.A, vn, dl, lam);
   const float s = __fadd_rn(v, vn);
   float inc;
   if (ok) {
@@ -482,23 +544,23 @@ __device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, 
 // Two QE-M steps (two paths on the same constants) in packed FP32, lane for
 // lane step_qem: the quadratic branch and the series part of lam paired when
 // both lanes take them, every other case per lane by the scalar functions.
-__device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q, float2 omu, float2 zv, float2 zx,
+__device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q, float2 xv, float2 zv, float2 zx,
                                           float2& v, float2& x, float2& comp) {
   const float2 m = p_fma(v, p_bc(c.E), p_bc(c.thE));
-  const float2 s2 = p_fma(v, p_bc(c.c1), p_bc(c.c2));
+  const float2 s2h = p_fma(v, p_bc(c.h1), p_bc(c.h2));
   const float2 m2 = p_mul(m, m);
-  const float2 lim = p_mul(p_bc(1.5f), m2);
+  const float2 t = p_mul(m2, p_rcp(s2h));
   float2 vn, dl, lam;
   bool okx, oky;
-  if (s2.x < lim.x && s2.y < lim.y) {
-    const float2 t = p_mul(p_mul(p_bc(2.0f), m2), p_rcp(s2));
-    const float2 root = p_sqrt(p_fma(t, t, p_mul(t, p_bc(-1.0f))));
-    const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+  if (t.x > kQuadT && t.y > kQuadT) {
+    const float2 tm1 = p_sub(t, p_bc(1.0f));
+    const float2 root = p_sqrt(p_mul(t, tm1));
+    const float2 b2 = p_add(tm1, root);
     const float2 b = p_sqrt(b2);
     const float2 a = p_mul(m, p_rcp(p_add(t, root)));
     const float2 bz = p_add(b, zv);
     vn = p_mul(p_mul(a, bz), bz);
-    dl = p_mul(a, p_fma(zv, p_add(zv, p_mul(p_bc(2.0f), b)), p_bc(-1.0f)));
+    dl = p_mul(a, p_fma(zv, p_add(bz, b), p_bc(-1.0f)));
     const float2 Aa = p_mul(p_bc(q.A), a);
     const float2 u = p_mul(p_bc(2.0f), Aa);
     okx = u.x < 1.0f;
@@ -519,8 +581,8 @@ __device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q,
     if (!okx) lam.x = 0.0f;
     if (!oky) lam.y = 0.0f;
   } else {
-    okx = qem_from_moments(m.x, s2.x, omu.x, zv.x, q.A, vn.x, dl.x, lam.x);
-    oky = qem_from_moments(m.y, s2.y, omu.y, zv.y, q.A, vn.y, dl.y, lam.y);
+    okx = qem_from_moments(m.x, s2h.x, xv.x, zv.x, q.A, vn.x, dl.x, lam.x);
+    oky = qem_from_moments(m.y, s2h.y, xv.y, zv.y, q.A, vn.y, dl.y, lam.y);
   }
   const float2 s = p_add(v, vn);
   float2 inc;
@@ -546,21 +608,21 @@ __device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q,
   }
   inc = p_fma(p_mul(p_bc(c.sK3), p_sqrt(s)), zx, inc);
   const float2 y = p_sub(inc, comp);
-  const float2 t = p_add(x, y);
-  comp = p_sub(p_sub(t, x), y);
-  x = t;
+  const float2 t2 = p_add(x, y);
+  comp = p_sub(p_sub(t2, x), y);
+  x = t2;
   v = vn;
 }
 
 // One step of the base scenario under scheme QEM (false: QE) with the CRN
 // rounding order of step_base<CRN> for the plain scheme.
 template <bool CRN, bool QEM>
-__device__ __forceinline__ void step_scheme(const ScenConst& c, const QemConst& q, float omu, float zv, float zx,
+__device__ __forceinline__ void step_scheme(const ScenConst& c, const QemConst& q, float xv, float zv, float zx,
                                             float& v, float& x, float& comp) {
   if constexpr (QEM)
-    step_qem(c, q, omu, zv, zx, v, x, comp);
+    step_qem(c, q, xv, zv, zx, v, x, comp);
   else
-    step_base<CRN>(c, omu, zv, zx, v, x, comp);
+    step_base<CRN>(c, xv, zv, zx, v, x, comp);
 }
 
 #ifndef SIMR_KAHAN_BUMPED
@@ -568,12 +630,12 @@ __device__ __forceinline__ void step_scheme(const ScenConst& c, const QemConst& 
 #endif
 
 // One step of a bumped scenario: base constants b plus deltas d.
-__device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float omu, float zv, float zx,
+__device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst& d, float xv, float zv, float zx,
                                             float& v, float& x, float& comp) {
   const float m = __fadd_rn(__fmaf_rn(v, b.E, __fmaf_rn(v, d.E, d.thE)), b.thE);
-  const float s2 = __fadd_rn(__fmaf_rn(v, b.c1, __fmaf_rn(v, d.c1, d.c2)), b.c2);
+  const float s2h = __fadd_rn(__fmaf_rn(v, b.h1, __fmaf_rn(v, d.h1, d.h2)), b.h2);
   float vn, dl;
-  qe_from_moments(m, s2, omu, zv, vn, dl);
+  qe_from_moments(m, s2h, xv, zv, vn, dl);
   const float s = __fadd_rn(v, vn);
   const float q = sqrt_approx(s);
   float inc = __fmaf_rn(b.Cv, s, b.C0);
@@ -598,12 +660,12 @@ __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst&
 
 // step_bumped for two scenarios: base constants b (both lanes), deltas d (lane
 // x the first scenario's, lane y the second's).
-__device__ __forceinline__ void step_bumped2(const ScenConst2& b, const ScenConst2& d, float2 omu, float2 zv,
+__device__ __forceinline__ void step_bumped2(const ScenConst2& b, const ScenConst2& d, float2 xv, float2 zv,
                                              float2 zx, float2& v, float2& x, float2& comp) {
   const float2 m = p_add(p_fma(v, b.E, p_fma(v, d.E, d.thE)), b.thE);
-  const float2 s2 = p_add(p_fma(v, b.c1, p_fma(v, d.c1, d.c2)), b.c2);
+  const float2 s2h = p_add(p_fma(v, b.h1, p_fma(v, d.h1, d.h2)), b.h2);
   float2 vn, dl;
-  qe_from_moments2(m, s2, omu, zv, vn, dl);
+  qe_from_moments2(m, s2h, xv, zv, vn, dl);
   const float2 s = p_add(v, vn);
   const float2 q = p_sqrt(s);
   float2 inc = p_fma(b.Cv, s, b.C0);
@@ -682,22 +744,20 @@ template <bool QEM = false, int U = 1>
 __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps, uint32_t option,
                                              const uint32_t (&rk)[10][2], uint64_t path, float& x, float& comp,
                                              const QemConst& q = QemConst{}) {
-  const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+  const PhiloxLane pl = philox_lane(path, rk);
   float v = c.v0;
   x = 0.0f;
   comp = 0.0f;
 #pragma unroll U
   for (uint32_t p = 0; 2 * p < steps; ++p) {
-    const uint4 w = philox4x32_10(p, plo, phi, option, rk);
+    const uint4 w = philox_draw(pl, philox_ctr(p, option, rk), rk);
     {
       const float xv = centered_uniform(w.x);
-      step_scheme<false, QEM>(c, q, 0.5f * (1.0f - xv), norminv_centered(xv),
-                              norminv_centered(centered_uniform(w.y)), v, x, comp);
+      step_scheme<false, QEM>(c, q, xv, norminv_centered(xv), norminv_centered(centered_uniform(w.y)), v, x, comp);
     }
     if (2 * p + 1 < steps) {
       const float xv = centered_uniform(w.z);
-      step_scheme<false, QEM>(c, q, 0.5f * (1.0f - xv), norminv_centered(xv),
-                              norminv_centered(centered_uniform(w.w)), v, x, comp);
+      step_scheme<false, QEM>(c, q, xv, norminv_centered(xv), norminv_centered(centered_uniform(w.w)), v, x, comp);
     }
   }
 }
@@ -709,26 +769,26 @@ template <int U = 1>
 __device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps, uint32_t option,
                                              const uint32_t (&rk)[10][2], uint64_t path0, uint64_t path1,
                                              float2& x, float2& comp) {
-  const uint32_t plo0 = (uint32_t)path0, phi0 = (uint32_t)(path0 >> 32);
-  const uint32_t plo1 = (uint32_t)path1, phi1 = (uint32_t)(path1 >> 32);
+  const PhiloxLane pl0 = philox_lane(path0, rk), pl1 = philox_lane(path1, rk);
   float2 v = make_float2(c.v0, c.v0);
   x = make_float2(0.0f, 0.0f);
   comp = make_float2(0.0f, 0.0f);
 #pragma unroll U
   for (uint32_t p = 0; 2 * p < steps; ++p) {
-    const uint4 w0 = philox4x32_10(p, plo0, phi0, option, rk);
-    const uint4 w1 = philox4x32_10(p, plo1, phi1, option, rk);
+    const PhiloxCtr u = philox_ctr(p, option, rk);
+    const uint4 w0 = philox_draw(pl0, u, rk);
+    const uint4 w1 = philox_draw(pl1, u, rk);
     {
-      const float xa = centered_uniform(w0.x), xb = centered_uniform(w1.x);
-      const float2 zv = norminv_centered2(make_float2(xa, xb));
-      const float2 zx = norminv_centered2(make_float2(centered_uniform(w0.y), centered_uniform(w1.y)));
-      step_base2<false>(c, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, v, x, comp);
+      const float2 xv = centered_uniform2(w0.x, w1.x);
+      const float2 zv = norminv_centered2(xv);
+      const float2 zx = norminv_centered2(centered_uniform2(w0.y, w1.y));
+      step_base2<false>(c, xv, zv, zx, v, x, comp);
     }
     if (2 * p + 1 < steps) {
-      const float xa = centered_uniform(w0.z), xb = centered_uniform(w1.z);
-      const float2 zv = norminv_centered2(make_float2(xa, xb));
-      const float2 zx = norminv_centered2(make_float2(centered_uniform(w0.w), centered_uniform(w1.w)));
-      step_base2<false>(c, make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb)), zv, zx, v, x, comp);
+      const float2 xv = centered_uniform2(w0.z, w1.z);
+      const float2 zv = norminv_centered2(xv);
+      const float2 zx = norminv_centered2(centered_uniform2(w0.w, w1.w));
+      step_base2<false>(c, xv, zv, zx, v, x, comp);
     }
   }
 }

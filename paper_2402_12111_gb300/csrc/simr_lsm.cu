@@ -77,15 +77,14 @@ template <bool QEM>
 __device__ __forceinline__ void step_two(const LsmLaunch& L, uint32_t wv0, uint32_t wx0, uint32_t wv1, uint32_t wx1,
                                          float (&v)[kLsmPpt], float (&x)[kLsmPpt], float (&comp)[kLsmPpt]) {
   static_assert(kLsmPpt == 2, "two paths per thread");
-  const float xa = centered_uniform(wv0), xb = centered_uniform(wv1);
-  const float2 zv = norminv_centered2(make_float2(xa, xb));
-  const float2 zx = norminv_centered2(make_float2(centered_uniform(wx0), centered_uniform(wx1)));
+  const float2 xv = centered_uniform2(wv0, wv1);
+  const float2 zv = norminv_centered2(xv);
+  const float2 zx = norminv_centered2(centered_uniform2(wx0, wx1));
   float2 vv = make_float2(v[0], v[1]), xx = make_float2(x[0], x[1]), cc = make_float2(comp[0], comp[1]);
-  const float2 omu = make_float2(0.5f * (1.0f - xa), 0.5f * (1.0f - xb));
   if constexpr (QEM)
-    step_qem2(L.sc, L.qm, omu, zv, zx, vv, xx, cc);
+    step_qem2(L.sc, L.qm, xv, zv, zx, vv, xx, cc);
   else
-    step_base2<false>(L.sc, omu, zv, zx, vv, xx, cc);
+    step_base2<false>(L.sc, xv, zv, zx, vv, xx, cc);
   v[0] = vv.x;
   v[1] = vv.y;
   x[0] = xx.x;
@@ -106,13 +105,12 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
   const bool put = L.is_put != 0;
   for (uint64_t bt = (uint64_t)blockIdx.x * kLsmWarps + (threadIdx.x >> 5); bt < batches; bt += n_warps) {
     uint64_t idx[kLsmPpt];
-    uint32_t plo[kLsmPpt], phi[kLsmPpt];
+    PhiloxLane pl[kLsmPpt];
     float v[kLsmPpt], x[kLsmPpt], comp[kLsmPpt];
 #pragma unroll
     for (int j = 0; j < kLsmPpt; ++j) {
       idx[j] = bt * per + (uint64_t)j * kWarp + lane;
-      plo[j] = (uint32_t)idx[j];
-      phi[j] = (uint32_t)(idx[j] >> 32);
+      pl[j] = philox_lane(idx[j], L.rk);
       v[j] = L.sc.v0;
       x[j] = 0.0f;
       comp[j] = 0.0f;
@@ -131,8 +129,9 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
     };
     for (uint32_t p = 0; 2 * p < L.steps; ++p) {
       uint4 w[kLsmPpt];
+      const PhiloxCtr u = philox_ctr(p, L.option_index, L.rk);
 #pragma unroll
-      for (int j = 0; j < kLsmPpt; ++j) w[j] = philox4x32_10(p, plo[j], phi[j], L.option_index, L.rk);
+      for (int j = 0; j < kLsmPpt; ++j) w[j] = philox_draw(pl[j], u, L.rk);
       step_two<QEM>(L, w[0].x, w[0].y, w[1].x, w[1].y, v, x, comp);
       if (++cnt == L.every) {
         cnt = 0;

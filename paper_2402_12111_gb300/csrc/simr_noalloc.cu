@@ -1,11 +1,10 @@
 // simr_noalloc.cu -- simr_price_noalloc: the European pricing call of simr_price
 // for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (cudaMalloc is not a stream operation and synchronises the
-// device), latency-bound serving loops that must never block on the
-// allocator, and host applications or plugins that hand out all device memory
-// themselves and forbid libraries from taking more.  This entry point takes
+// Some callers cannot call cudaMalloc: latency-bound serving loops that must
+// never block on the allocator (cudaMalloc can synchronise the device), and
+// host applications or plugins that hand out all device memory themselves and
+// forbid libraries from taking more.  This entry point takes
 // device pointers for its inputs and outputs, needs no context, and keeps its
 // reduction scratch (partial sums of each block, the finishing ticket and a
 // status word) in one file-scope __device__ array of fixed size, which every
@@ -60,6 +59,19 @@ int setup(int device, DeviceSlot** out) {
   return SIMR_OK;
 }
 
+// Device memory of `device` (or managed memory).  Device memory of another GPU
+// would pass a plain device-pointer test and then fault in the kernel.
+bool on_device(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 }  // namespace
 
 extern "C" SIMR_API int simr_price_noalloc(const simr_heston* model, const double* strikes, int n_strikes,
@@ -75,6 +87,8 @@ extern "C" SIMR_API int simr_price_noalloc(const simr_heston* model, const doubl
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return simr::internal_cuda_fail(e, "cudaGetDevice");
+  if (!on_device(strikes, device) || !on_device(price, device) || (stderr_out && !on_device(stderr_out, device)))
+    return simr::internal_fail(SIMR_EINVAL, "simr_price_noalloc takes device pointers only, of the current device");
   if (device < 0 || device >= kMaxDevices) return simr::internal_fail(SIMR_EUNSUPPORTED, "device ordinal too large");
   DeviceSlot* slot = nullptr;
   if ((rc = setup(device, &slot))) return rc;

@@ -94,21 +94,20 @@ __device__ __forceinline__ float resim_term(const PathLaunch& L, int up, int dn,
 template <int NS, int NV, bool DYN, bool QEM = false>
 __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                          float (&x)[NS], float (&c)[NS]) {
-  const float xv = centered_uniform(w_v);
-  const float omu = 0.5f * (1.0f - xv);  // 1 - U_V, exact
-  const float2 z = norminv_centered2(make_float2(xv, centered_uniform(w_x)));
-  const float zv = z.x, zx = z.y;
+  const float2 xu = centered_uniform2(w_v, w_x);  // (2 U_V - 1, 2 U_X - 1)
+  const float2 z = norminv_centered2(xu);
+  const float xv = xu.x, zv = z.x, zx = z.y;
   static_assert(!QEM || NS == 1, "QE-M runs the base scenario only");
   static_assert(NS % 2 == 1, "the base scenario plus up/down pairs");
-  step_scheme<(NS > 1), QEM>(L.sc[0], L.qm, omu, zv, zx, v[0], x[0], c[0]);
+  step_scheme<(NS > 1), QEM>(L.sc[0], L.qm, xv, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
   for (int s = 1; s + 1 < NS; s += 2) {
     if (DYN && s >= L.n_scen) break;
     float2 vv = make_float2(v[s], v[s + 1]), xx = make_float2(x[s], x[s + 1]), cc = make_float2(c[s], c[s + 1]);
     if (s + 1 <= NV)
-      step_base2<true>(L.sc[0], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
+      step_base2<true>(L.sc[0], p_bc(xv), p_bc(zv), p_bc(zx), vv, xx, cc);
     else
-      step_bumped2(pack_const(L.sc[0], L.sc[0]), L.pair2[(s - 1) / 2], p_bc(omu), p_bc(zv), p_bc(zx), vv, xx, cc);
+      step_bumped2(pack_const(L.sc[0], L.sc[0]), L.pair2[(s - 1) / 2], p_bc(xv), p_bc(zv), p_bc(zx), vv, xx, cc);
     v[s] = vv.x;
     v[s + 1] = vv.y;
     x[s] = xx.x;
@@ -125,15 +124,14 @@ template <int NS, int NV, bool DYN, int PPT, bool QEM>
 __device__ __forceinline__ void step_paths(const PathLaunch& L, const uint32_t (&wv)[PPT], const uint32_t (&wx)[PPT],
                                            float (&v)[PPT][NS], float (&x)[PPT][NS], float (&c)[PPT][NS]) {
   if constexpr (NS == 1 && PPT == 2) {
-    const float xv0 = centered_uniform(wv[0]), xv1 = centered_uniform(wv[1]);
-    const float2 zv = norminv_centered2(make_float2(xv0, xv1));
-    const float2 zx = norminv_centered2(make_float2(centered_uniform(wx[0]), centered_uniform(wx[1])));
-    const float2 omu = make_float2(0.5f * (1.0f - xv0), 0.5f * (1.0f - xv1));
+    const float2 xv = centered_uniform2(wv[0], wv[1]);
+    const float2 zv = norminv_centered2(xv);
+    const float2 zx = norminv_centered2(centered_uniform2(wx[0], wx[1]));
     float2 vv = make_float2(v[0][0], v[1][0]), xx = make_float2(x[0][0], x[1][0]), cc = make_float2(c[0][0], c[1][0]);
     if constexpr (QEM)
-      step_qem2(L.sc[0], L.qm, omu, zv, zx, vv, xx, cc);
+      step_qem2(L.sc[0], L.qm, xv, zv, zx, vv, xx, cc);
     else
-      step_base2<false>(L.sc[0], omu, zv, zx, vv, xx, cc);
+      step_base2<false>(L.sc[0], xv, zv, zx, vv, xx, cc);
     v[0][0] = vv.x;
     v[1][0] = vv.y;
     x[0][0] = xx.x;
@@ -151,7 +149,7 @@ template <int NS, bool DYN>
 __device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                           float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
-  const float omu = 0.5f * (1.0f - xv);
+  const float omu = one_minus_u(xv);
   const float zv = norminv_centered(xv);
   const float zx = norminv_centered(centered_uniform(w_x));
   const ScenConst zero{};
@@ -180,18 +178,16 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
       c[j][s] = 0.0f;
     }
   }
-  uint32_t plo[PPT], phi[PPT];
+  PhiloxLane pl[PPT];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    plo[j] = (uint32_t)path[j];
-    phi[j] = (uint32_t)(path[j] >> 32);
-  }
+  for (int j = 0; j < PPT; ++j) pl[j] = philox_lane(path[j], L.rk);
   const uint32_t pairs = L.steps >> 1;
   uint32_t i0 = 0;
   if (NS > 1 && L.first_split) {
     uint4 w[PPT];
+    const PhiloxCtr u = philox_ctr(0u, L.option_index, L.rk);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(0u, plo[j], phi[j], L.option_index, L.rk);
+    for (int j = 0; j < PPT; ++j) w[j] = philox_draw(pl[j], u, L.rk);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) step0_all<NS, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
     if (L.steps > 1) {
@@ -205,8 +201,9 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
   for (uint32_t i = i0; i < pairs; ++i) {
     uint4 w[PPT];
     uint32_t wv[PPT], wx[PPT];
+    const PhiloxCtr u = philox_ctr(i, L.option_index, L.rk);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) w[j] = philox4x32_10(i, plo[j], phi[j], L.option_index, L.rk);
+    for (int j = 0; j < PPT; ++j) w[j] = philox_draw(pl[j], u, L.rk);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) wv[j] = w[j].x, wx[j] = w[j].y;
     step_paths<NS, NV, DYN, PPT, QEM>(L, wv, wx, v, x, c);
@@ -216,9 +213,10 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
   }
   if ((L.steps & 1u) && pairs >= i0) {  // odd last step (step 0 itself when steps == 1 without the split)
     uint32_t wv[PPT], wx[PPT];
+    const PhiloxCtr u = philox_ctr(pairs, L.option_index, L.rk);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      const uint4 w = philox4x32_10(pairs, plo[j], phi[j], L.option_index, L.rk);
+      const uint4 w = philox_draw(pl[j], u, L.rk);
       wv[j] = w.x;
       wx[j] = w.y;
     }

@@ -80,13 +80,14 @@ def _bench():
 
 
 def test_algorithmic_flops_of_the_bench_step():
-    # 48 flops shared per step (two inverse normals, two uniforms) + 41 per simulated
-    # scenario; the bench step simulates base, v0 +- and T +- (delta, gamma and rho
-    # revalue the base path)
+    # 44 flops shared per step (two inverse normals) + 23 per simulated scenario (QE
+    # variance step 16, log-spot step 7); the bench step simulates base, v0 +- and
+    # T +- (delta, gamma and rho revalue the base path); pricing alone is 67
     b = _bench()
     g5 = ["delta", "gamma", "vega", "theta", "rho"]
     assert b.simulated_scenarios(g5) == 5
-    assert b.flops_per_path_step(g5) == 253
+    assert b.flops_per_path_step(g5) == 159
+    assert b.flops_per_path_step([]) == 67
     assert b.simulated_scenarios(["delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr"]) == 11
 
 

@@ -1,10 +1,10 @@
 """simr_price_noalloc: the pricing entry point for callers that cannot allocate.
 
-Code that runs while a CUDA graph is captured, serving loops that must never
-block on the allocator, and hosts that own all device memory cannot let a
-library call cudaMalloc.  simr_price_noalloc keeps its scratch in a static
-device array instead; called through the C ABI it must give what simr_price
-gives, call after call.  (Collected last: a failure here leaves every other
+Serving loops that must never block on the allocator, and hosts that own all
+device memory, cannot let a library call cudaMalloc.  simr_price_noalloc keeps
+its scratch in a static device array instead; called through the C ABI it must
+give what simr_price gives, bit for bit (the same kernel, constants and launch
+shape), call after call.  (Collected last: a failure here leaves every other
 test already run.)
 """
 import ctypes
@@ -50,9 +50,9 @@ def test_noalloc_matches_simr_price_on_two_calls(lib, K_np, is_put, steps, paths
         rc = _call(L, simr, model, K, is_put, steps, paths, seed, p, se)
         assert rc == 0, L.simr_last_error()
         torch.cuda.synchronize()
-        # same kernel and launch shape as simr_price: equal to the test suite's price tolerance (1e-5)
-        torch.testing.assert_close(p, p_ref, rtol=1e-5, atol=0)
-        torch.testing.assert_close(se, se_ref, rtol=1e-5, atol=0)
+        # the same kernel, constants and launch shape as simr_price: the same bits
+        torch.testing.assert_close(p, p_ref, rtol=0, atol=0)
+        torch.testing.assert_close(se, se_ref, rtol=0, atol=0)
 
 
 def test_noalloc_rejects_sizes_and_host_pointers(lib):
@@ -66,3 +66,16 @@ def test_noalloc_rejects_sizes_and_host_pointers(lib):
     ph = torch.empty(4, dtype=torch.float64)
     assert _call(L, simr, model, Kh, False, 8, 1000, 1, ph, None) == -1
     assert b"device pointers" in L.simr_last_error()
+
+
+def test_noalloc_rejects_another_gpus_memory(lib):
+    # host-side pointer check only: no kernel is launched for a refused call
+    simr, L = lib
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU: no other device's memory to pass")
+    model = dict(workloads.BASE_MODEL)
+    K = torch.full((4,), 100.0, dtype=torch.float64, device="cuda:1")
+    p = torch.empty(4, dtype=torch.float64, device="cuda:1")
+    with torch.cuda.device(0):
+        assert _call(L, simr, model, K, False, 8, 1000, 1, p, None) == -1
+    assert b"current device" in L.simr_last_error()
