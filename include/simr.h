@@ -348,6 +348,37 @@ SIMR_API int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, i
                             double* price, double* stderr_out, double* beta, int32_t* stop, void* stream);
 
 /*
+ * The random inputs the path kernels draw -- the paper's V and Z, which it
+ * streams from the host (Sec. 3 Table 1, Sec. 4) -- computed by the kernels' own
+ * device functions, for checking the generator word by word.
+ *
+ * simr_philox_words: Philox4x32-10 (Salmon et al., SC'11; 10 rounds, multipliers
+ * 0xD2511F53, 0xCD9E8D57, Weyl key increments 0x9E3779B9, 0xBB67AE85) of the
+ * counters the path kernels use, (pair, path mod 2^32, path >> 32, option_index)
+ * under the key (seed mod 2^32, seed >> 32): step pair `pair` of a path gives
+ * words 0, 1 (U_V, U_X of step 2 pair) and 2, 3 (those of step 2 pair + 1).
+ *   paths [path_begin, path_begin + n_paths), pairs [pair_begin, pair_begin +
+ *   n_pairs) (pair_begin + n_pairs <= 2^32); n_paths * n_pairs in [1, 2^28].
+ *   words   out   DEVICE pointer, uint32 [n_paths][n_pairs][4].
+ *
+ * simr_normals: the FP32 standard normal of each 32-bit word w, as the path
+ * kernels form it: x = 2u - 1 with u = ((w >> 9) + 1/2) 2^-23 (exact), then
+ * Z = Phi^-1(u) by M. Giles' single-precision erfinv approximation (GPU
+ * Computing Gems, 2011) with the special-function unit's logarithm and square
+ * root.
+ *   words[n] in (DEVICE), n in [1, 2^31]; z[n] out (DEVICE): one word at a time;
+ *   z_paired[n] out (DEVICE, nullable): words 2j, 2j + 1 through the packed
+ *   two-lane form (the same values, bit for bit, by construction).
+ * Both: SIMR_EINVAL for host pointers, NULLs or sizes out of range; asynchronous
+ * on `stream`.
+ */
+SIMR_API int simr_philox_words(simr_ctx* ctx, uint64_t seed, uint32_t option_index, uint64_t path_begin,
+                               uint64_t n_paths, uint32_t pair_begin, uint32_t n_pairs, uint32_t* words,
+                               void* stream);
+SIMR_API int simr_normals(simr_ctx* ctx, const uint32_t* words, uint64_t n, float* z, float* z_paired,
+                          void* stream);
+
+/*
  * Terminal state of paths [path_begin, path_begin + n_paths): x_T = ln(S_T/S0)
  * and v_T per path, FP32, the state the paper's writeLongstaffSchwartzPath stage
  * writes out (Sec. 5).  x_T[n_paths], v_T[n_paths] out; v_T may be NULL.

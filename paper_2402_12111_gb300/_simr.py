@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True):
         L.simr_basket_price.argtypes = [vp, H, c_int, dp, dp, dp, c_int, c_int, u32, u64, u64, dp, dp, vp]
         L.simr_sync.argtypes = [vp, vp]
         L.simr_price_noalloc.argtypes = [H, dp, c_int, c_int, u32, u64, u64, u32, dp, dp, vp]
+        L.simr_philox_words.argtypes = [vp, u64, u32, u64, u64, u32, u32, dp, vp]
+        L.simr_normals.argtypes = [vp, dp, u64, dp, dp, vp]
         _lib = L
         return L
 

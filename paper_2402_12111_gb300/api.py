@@ -288,3 +288,30 @@ def sync(device: int = 0, stream=None):
     L = S.load()
     st = stream if stream is not None else torch.cuda.current_stream(device)
     S.check(L.simr_sync(S.context(device), ctypes.c_void_p(st.cuda_stream)))
+
+
+def philox_words(seed: int, option_index: int, path_begin: int, n_paths: int, pair_begin: int, n_pairs: int,
+                 device="cuda", stream=None):
+    """simr_philox_words: int32 tensor [n_paths, n_pairs, 4] holding the uint32 words the path
+    kernels draw for those counters (view as uint32 on the host: ``.cpu().numpy().view(np.uint32)``)."""
+    dev = torch.device(device)
+    w = torch.empty((int(n_paths), int(n_pairs), 4), dtype=torch.int32, device=dev)
+    L = S.load()
+    ctx = S.context(_device_index(w, device))
+    S.check(L.simr_philox_words(ctx, int(seed), int(option_index), int(path_begin), int(n_paths), int(pair_begin),
+                                int(n_pairs), _ptr(w), _stream(w, stream)))
+    return w
+
+
+def normals(words: torch.Tensor, paired: bool = True, stream=None):
+    """simr_normals: (z, z_paired or None), FP32, the path kernels' standard normals of int32/uint32
+    words on a CUDA device (one at a time, and two at a time in the packed form)."""
+    w = words.contiguous().view(-1)
+    if w.dtype not in (torch.int32,):
+        w = w.to(torch.int32)
+    z = torch.empty(w.numel(), dtype=torch.float32, device=w.device)
+    zp = torch.empty_like(z) if paired else None
+    L = S.load()
+    ctx = S.context(_device_index(w, None))
+    S.check(L.simr_normals(ctx, _ptr(w), w.numel(), _ptr(z), _ptr(zp), _stream(w, stream)))
+    return z, zp

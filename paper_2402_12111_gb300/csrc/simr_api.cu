@@ -1311,6 +1311,45 @@ int simr_paths_terminal(simr_ctx* ctx, const simr_heston* model, uint32_t steps,
   return SIMR_OK;
 }
 
+int simr_philox_words(simr_ctx* ctx, uint64_t seed, uint32_t option_index, uint64_t path_begin, uint64_t n_paths,
+                      uint32_t pair_begin, uint32_t n_pairs, uint32_t* words, void* stream) {
+  const NvtxRange nvtx("simr_philox_words");
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (!words) return fail(SIMR_EINVAL, "words is NULL");
+  if (n_paths < 1 || n_pairs < 1 || n_paths * (uint64_t)n_pairs > (1ull << 28))
+    return fail(SIMR_EINVAL, "n_paths * n_pairs must lie in [1, 2^28]");
+  if ((uint64_t)pair_begin + n_pairs > (1ull << 32)) return fail(SIMR_EINVAL, "pair_begin + n_pairs exceeds 2^32");
+  if (!is_device_ptr(words)) return fail(SIMR_EINVAL, "words must be a device pointer");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  DrawLaunch D;
+  philox_round_keys(seed, D.rk);
+  D.path_begin = path_begin;
+  D.n_paths = n_paths;
+  D.pair_begin = pair_begin;
+  D.n_pairs = n_pairs;
+  D.option_index = option_index;
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources
+                                                : launch_philox_words(D, words, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the Philox kernel");
+  return SIMR_OK;
+}
+
+int simr_normals(simr_ctx* ctx, const uint32_t* words, uint64_t n, float* z, float* z_paired, void* stream) {
+  const NvtxRange nvtx("simr_normals");
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (!words || !z) return fail(SIMR_EINVAL, "words and z must be non-NULL");
+  if (n < 1 || n > (1ull << 31)) return fail(SIMR_EINVAL, "n must lie in [1, 2^31]");
+  if (!is_device_ptr(words) || !is_device_ptr(z) || (z_paired && !is_device_ptr(z_paired)))
+    return fail(SIMR_EINVAL, "words, z and z_paired must be device pointers");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources
+                                                : launch_normals(words, n, z, z_paired, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the normal kernel");
+  return SIMR_OK;
+}
+
 int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
                       const double* weights, const double* strikes, int n_strikes, int is_put, uint32_t steps,
                       uint64_t paths, uint64_t seed, double* price, double* stderr_out, void* stream) {

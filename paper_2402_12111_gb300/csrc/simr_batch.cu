@@ -31,8 +31,11 @@ namespace {
 // Adjoint books ask the register allocator for 768 resident threads per SM
 // (6 blocks of 128, 3 of 256: at most 85 registers), which it would otherwise
 // trade for registers it does not need.
+#ifndef SIMR_BOOK_ADJ_THREADS
+#define SIMR_BOOK_ADJ_THREADS 768
+#endif
 template <bool ADJ, bool GSEG, int TPB, int PPT, int U>
-__global__ void __launch_bounds__(TPB, ADJ ? 768 / TPB : 1) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
+__global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
                                                            const BatchOption* __restrict__ opts,
                                                            const BatchItem* __restrict__ items,
                                                            unsigned int* __restrict__ counter,

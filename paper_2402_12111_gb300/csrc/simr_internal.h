@@ -47,6 +47,14 @@ struct PathLaunch {
   QemConst qm;            // QE-M constants of the base scenario
 };
 
+// Counters of the generator's raw words: paths [path_begin, path_begin + n_paths)
+// x step pairs [pair_begin, pair_begin + n_pairs) of option option_index.
+struct DrawLaunch {
+  uint32_t rk[10][2];
+  uint64_t path_begin, n_paths;
+  uint32_t pair_begin, n_pairs, option_index;
+};
+
 struct PathOutputs {
   double* price;   // [n_strikes]
   double* stderr_; // [n_strikes] or null
@@ -181,6 +189,8 @@ void batch_variant(int v, bool adjoint, BatchLaunch* B);
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);
+cudaError_t launch_philox_words(const DrawLaunch& D, uint32_t* words, cudaStream_t stream);
+cudaError_t launch_normals(const uint32_t* words, uint64_t n, float* z, float* zp, cudaStream_t stream);
 
 // Longstaff-Schwartz (simr_lsm.cu).  Exercise dates t_j = (j + 1) every dt,
 // j = 0 .. n_ex - 1; per-path states at the dates in [date][path] arrays.
