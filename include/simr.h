@@ -328,9 +328,12 @@ SIMR_API int simr_set_scheme(simr_ctx* ctx, int scheme);
  *   backwards from t_{n_ex-2}: over the paths with a positive payoff h at t_j,
  *   least squares of the cash flow they realise later, discounted to t_j, on
  *   the basis (1, x, x^2, y, x y, y^2), x = S/K - 1, y = v/w - 1,
- *   w = (v0 + theta)/2 (1 if 0); normal equations by Cholesky in FP64 with a
- *   basis function left out when its pivot is not above 1e-12 of its diagonal
- *   entry; fewer than 12 such paths: no exercise at that date; a path
+ *   w = (v0 + theta)/2 (1 if 0), fitted in per-date standardised coordinates
+ *   (the same quadratics with order-one Gram entries): normal equations by FP32
+ *   Cholesky with one step of refinement against an FP64 residual, a basis
+ *   function left out when its pivot is not above 1e-5 of its diagonal entry
+ *   (FP32's resolution; non-degenerate fits have pivots near 0.05 or above);
+ *   fewer than 12 such paths: no exercise at that date; a path
  *   exercises where h > the fitted continuation value (FP32);
  *   price = mean of e^{-r t_stop} h(t_stop) (0 if never exercised).
  *   K, is_put         in   strike (finite, > 0), 0 = call

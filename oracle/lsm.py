@@ -22,9 +22,14 @@ Readings of what neither source fixes for this model (stated once here):
     E v and sd_v the CIR mean and standard deviation of v_t): the same
     quadratics as in x, y, with order-one Gram entries.  Cholesky in basis
     order, a basis function left out (coefficient 0) when its pivot is not
-    above 1e-5 of its diagonal entry (exact or near collinearity); with fewer
-    than 12 in-the-money paths there is no regression and no exercise at that
-    date (coefficients NaN).  Coefficients are reported in x, y;
+    above 1e-12 of its diagonal entry: least squares fixes the projection onto
+    the span of the basis, not the coefficients of dependent functions, and in
+    FP64 a Gram matrix of order-one entries summed over at most 2^31 paths
+    carries relative rounding far below 1e-12, so a pivot under that threshold
+    is a function in the span of the earlier ones (exact collinearity) and
+    leaving it out leaves the projection unchanged; with fewer than 12
+    in-the-money paths there is no regression and no exercise at that date
+    (coefficients NaN).  Coefficients are reported in x, y;
   * exercise when payoff > continuation (strict);
   * price = mean over paths of e^{-r t_stop} x cash flow (0 if never exercised),
     standard error as for the European estimator.
@@ -40,7 +45,7 @@ from . import states
 
 N_BASIS = 6
 MIN_ITM = 12
-PIVOT_TOL = 1e-5
+PIVOT_TOL = 1e-12
 
 
 def basis_scale(model) -> float:

@@ -20,9 +20,9 @@
 //     (1, xs, xs^2, ys, xs ys, ys^2), and the 6 products of the basis with the
 //     discounted cash flow -- FP32 per thread and across the warp, FP64 from the
 //     warp on; the last block sums the block rows in block order and solves the
-//     normal equations by Cholesky in FP64, leaving out a basis function whose
-//     pivot is not above 1e-12 of its diagonal entry.  The launch of date 0
-//     applies its rule and reduces the discounted cash flows to the price.
+//     normal equations (lsm_solve_warp: FP32 Cholesky, refined against an FP64
+//     residual).  The launch of date 0 applies its rule and reduces the
+//     discounted cash flows to the price.
 //
 // The coordinates xs = (S - F_j)/sd_j and ys = (v - E v_j)/sd(v_j) are x and y
 // of the basis (1, x, x^2, y, xy, y^2), x = S/K - 1, y = v/w - 1, shifted and
@@ -180,7 +180,10 @@ __constant__ int c_gram_index[kNB * kNB] = {0, 1, 3, 2,  4,  5,  1, 3,  6,  4,  
 // Cholesky factor L; every lane ends with all of beta).  In the standardised
 // coordinates G has order-one entries, so the factorisation runs in FP32:
 // Cholesky in basis order, basis function k left out (coefficient 0) when its
-// pivot is not above 1e-5 G[k][k]; then one step of iterative refinement with
+// pivot is not above 1e-5 G[k][k] -- the threshold at which FP32's own rounding
+// of the order-one Gram entries (~1e-7 each) can no longer tell a pivot from
+// zero; pivots of non-degenerate fits are near 0.05 or above; then one step of
+// iterative refinement with
 // the residual b - G x formed in FP64 (row r in lane r), which brings the
 // solution to about FP64 accuracy for condition numbers far below 1e7.
 __device__ void lsm_solve_warp(const double* tot, double* beta, int lane) {

@@ -148,3 +148,34 @@ def test_put_early_exercise_premium_is_positive():
     r = lsm.lsm(BASE, 100.0, True, 64, 4, 1 << 14, seed=2)
     p, _ = oracle.price(BASE, [100.0], True, 64, 1 << 14, 2)
     assert r.price > p[0] + 3 * r.stderr
+
+
+# The cases the GPU parity test (test_gpu_lsm.py) runs, and a bench-shaped sample.
+PIVOT_CASES = [
+    (BASE, 100.0, True, 64, 4, 1 << 14, 1), (BASE, 110.0, True, 50, 1, 8192, 2),
+    (BASE, 90.0, False, 32, 2, 8192, 3), (dict(BASE, sigma=0.9, rho=-0.3, kappa=0.5, v0=0.09), 100.0, True, 48, 3,
+                                         1 << 14, 4),
+    (BASE, 105.0, True, 33, 11, 5003, 5), (BASE, 130.0, True, 40, 2, 6000, 6), (BASE, 100.0, True, 252, 1, 1 << 13, 1),
+]
+
+
+@pytest.mark.parametrize("case", PIVOT_CASES)
+def test_gpu_pivot_threshold_never_binds_on_the_parity_cases(case, monkeypatch):
+    # The oracle leaves a basis function out below 1e-12 of its diagonal (FP64),
+    # the GPU's FP32 Cholesky below 1e-5.  On every regression of these cases the
+    # smallest pivot ratio is far above both, so both keep all six functions and
+    # the thresholds cannot make the two sides' fits differ.
+    pivots = []
+    orig = lsm.solve_normal
+
+    def recording(G, b, tol=lsm.PIVOT_TOL):
+        beta, keep = orig(G, b, tol)
+        n = len(b)
+        d = np.linalg.cholesky(G)  # all kept: the plain factor
+        pivots.append(min(d[k, k] ** 2 / G[k, k] for k in range(n)))
+        assert all(keep)
+        return beta, keep
+
+    monkeypatch.setattr(lsm, "solve_normal", recording)
+    lsm.lsm(*case)
+    assert pivots and min(pivots) > 1e-3, min(pivots)
