@@ -81,6 +81,11 @@ def lib():
             L.oracle_path_grad_reverse.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_path_grad_forward.argtypes = [H, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_adjoint.argtypes = [H, dp, c_int, c_int, u32, i64, u64, u32, dp, dp]
+            L.oracle_path_grad_flip.argtypes = [H, u32, u64, u32, u64, i64, ctypes.c_double, dp, dp,
+                                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_terminal_forced.argtypes = [H, u32, u64, u32, u64, ctypes.c_int64, c_int, c_int]
+            L.oracle_terminal_forced.restype = ctypes.c_double
             L.oracle_states.argtypes = [H, u32, u32, u64, u32, u64, i64, dp, dp]
             L.oracle_basket_terminal.argtypes = [H, c_int, dp, u32, u64, u64, i64, dp, dp]
             L.oracle_set_scheme.argtypes = [c_int]
@@ -293,6 +298,37 @@ def path_grad(model, steps: int, seed: int, path_begin: int, n_paths: int, mode:
     if rc != 0:
         raise ValueError(f"oracle path gradient failed ({rc})")
     return x, g.reshape(n_paths, 5)
+
+
+def path_grad_flip(model, steps: int, seed: int, path_begin: int, n_paths: int, margin_below: float,
+                   option_index: int = 0):
+    """Per path, (x_T, dx_T/d(v0, kappa, theta, sigma, rho), flip_step, flip_kind, flip_value) of the path with
+    its branch decision closest to its threshold taken the other way, where that decision's margin
+    is below margin_below (flip_step -1 and the plain reverse-mode result elsewhere): the pathwise
+    derivative a lower-precision evaluation computes when it decides that step the other way.
+    flip_kind 1: the QE branch (psi against psi_c; value 1 quadratic); 2: the exponential branch's atom
+    (U_V against p; value 1 the logarithm's side)."""
+    x = np.empty(n_paths)
+    g = np.empty(n_paths * 5)
+    st = np.empty(n_paths, dtype=np.int64)
+    kd = np.empty(n_paths, dtype=np.int32)
+    fv = np.empty(n_paths, dtype=np.int32)
+    rc = lib().oracle_path_grad_flip(ctypes.byref(_model(model)), steps, seed, option_index, path_begin, n_paths,
+                                     float(margin_below), _dp(x), _dp(g),
+                                     st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     kd.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     fv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError(f"oracle_path_grad_flip failed ({rc})")
+    return x, g.reshape(n_paths, 5), st, kd, fv
+
+
+def terminal_forced(model, steps: int, seed: int, path: int, f_step: int, f_kind: int, f_value: int,
+                    option_index: int = 0) -> float:
+    """x_T of one path with the decision of kind f_kind at step f_step imposed as f_value
+    (f_step -1: none)."""
+    return float(lib().oracle_terminal_forced(ctypes.byref(_model(model)), steps, seed, option_index, path,
+                                              int(f_step), int(f_kind), int(f_value)))
 
 
 def adjoint(model, strikes, is_put: bool, steps: int, paths: int, seed: int, option_index: int = 0):

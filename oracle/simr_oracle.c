@@ -669,16 +669,19 @@ int oracle_greeks_fd(const oracle_heston* m, const double* strikes, int n_strike
  * K0..K4 and theta as it enters m), then maps those onto the parameters.
  * grad5 = {dx/dv0, dx/dkappa, dx/dtheta, dx/dsigma, dx/drho}; dx/dr = T exactly.
  */
-static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
-                         uint32_t option_index, uint64_t path, double* v_hist, double* x_out,
-                         double grad5[5]) {
+static double qe_step_forced(double v, double u_v, const double* k, int f_kind, int f_value);
+
+static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
+                                uint32_t option_index, uint64_t path, double* v_hist, double* x_out,
+                                double grad5[5], int64_t f_step, int f_kind, int f_value) {
   double v = m->v0, x = 0.0;
   v_hist[0] = v;
   for (uint32_t n = 0; n < steps; ++n) {
     double u_v, u_x, mg;
     int br;
     oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
-    double vn = oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
+    double vn = ((int64_t)n == f_step) ? qe_step_forced(v, u_v, k, f_kind, f_value)
+                                       : oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
     x += k[4] + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
     v = vn;
     v_hist[n + 1] = v;
@@ -711,7 +714,9 @@ static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps
     double bar_m = 0.0, bar_s2 = 0.0;
     if (mm > 0.0) {
       double psi = s2 / (mm * mm);
-      if (psi <= PSI_C) {
+      int quad = psi <= PSI_C;
+      if (n == f_step && f_kind == 1) quad = f_value;
+      if (quad) {
         double t = 2.0 / psi; /* = 2 m^2 / s^2 */
         double root = sqrt(t) * sqrt(t - 1.0);
         double b2 = t - 1.0 + root;
@@ -726,7 +731,9 @@ static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps
         bar_s2 = -bar_t * t / s2;
       } else {
         double p = (psi - 1.0) / (psi + 1.0);
-        if (u_v > p) {
+        int pos = u_v > p;
+        if (n == f_step && f_kind == 2) pos = f_value;
+        if (pos) {
           double q = 2.0 * mm * mm / (mm * mm + s2); /* 1 - p */
           double L = log(q / (1.0 - u_v));
           double dv_dm = L / q;
@@ -765,6 +772,149 @@ static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps
   grad5[4] = bar_K0 * (-kap * th * dt / sig) + bar_K1 * (GAMMA1 * dt * kap / sig - 1.0 / sig) +
              bar_K2 * (GAMMA2 * dt * kap / sig + 1.0 / sig) + bar_K3 * (-2.0 * GAMMA1 * dt * rho) +
              bar_K4 * (-2.0 * GAMMA2 * dt * rho);
+}
+
+static void path_adjoint(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
+                         uint32_t option_index, uint64_t path, double* v_hist, double* x_out,
+                         double grad5[5]) {
+  path_adjoint_forced(m, k, steps, seed, option_index, path, v_hist, x_out, grad5, -1, 0, 0);
+}
+
+/*
+ * The other side of a branch decision.  A pathwise derivative holds every
+ * branch decision of the path fixed; where a lower-precision evaluation of the
+ * same path can take the other side of a decision that sits close to its
+ * threshold, the derivative it computes is that of the path with the decision
+ * taken the other way.  qe_step_forced is the QE variance step of
+ * oracle_qe_variance_step with one decision imposed: f_kind 1 the branch
+ * (f_value 1 quadratic, 0 exponential; the quadratic formulas need psi <= 2,
+ * the exponential ones psi > -1 -- both hold near psi_c), f_kind 2 the
+ * exponential branch's atom (f_value 1: v' = ln((1-p)/(1-U_V))/beta, its
+ * continuation below U_V = p held at 0 -- the value and one-sided derivative
+ * at the boundary; 0: v' = 0).
+ */
+static double qe_step_forced(double v, double u_v, const double* k, int f_kind, int f_value) {
+  const double theta_ = k[9], E = k[1], c1 = k[2], c2 = k[3];
+  const double mean = theta_ + (v - theta_) * E;
+  const double var = v * c1 + c2;
+  if (mean <= 0.0) return 0.0;
+  const double ps = var / (mean * mean);
+  int quad = ps <= PSI_C;
+  if (f_kind == 1) quad = f_value;
+  if (quad) { /* v' = a (b + Z_V)^2 */
+    const double t2 = 2.0 / ps;
+    const double bb = t2 - 1.0 + sqrt(t2) * sqrt(t2 - 1.0);
+    const double aa = mean / (1.0 + bb);
+    const double bz = sqrt(bb) + oracle_norminv(u_v);
+    return aa * bz * bz;
+  }
+  const double pp = (ps - 1.0) / (ps + 1.0); /* atom probability */
+  int pos = u_v > pp;
+  if (f_kind == 2) pos = f_value;
+  if (!pos) return 0.0;
+  const double vn = log((1.0 - pp) / (1.0 - u_v)) * mean / (1.0 - pp);
+  return vn > 0.0 ? vn : 0.0;
+}
+
+/* The decision of a path closest to its threshold: its step, kind (1 the
+ * branch, 2 the atom) and margin (|psi - psi_c| / psi_c, or |U_V - p|), and the
+ * value the decision takes there. */
+static void closest_decision(const oracle_heston* m, const double* k, uint32_t steps, uint64_t seed,
+                             uint32_t option_index, uint64_t path, int64_t* step, int* kind, int* value,
+                             double* margin) {
+  double v = m->v0;
+  *step = -1;
+  *kind = 0;
+  *value = 0;
+  *margin = INFINITY;
+  const double theta_ = k[9], E = k[1], c1 = k[2], c2 = k[3];
+  for (uint32_t n = 0; n < steps; ++n) {
+    double u_v, u_x, mg;
+    int br;
+    oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
+    double mm = theta_ + (v - theta_) * E;
+    double s2 = v * c1 + c2;
+    if (mm > 0.0) {
+      double psi = s2 / (mm * mm);
+      double mpsi = fabs(psi - PSI_C) / PSI_C;
+      if (mpsi < *margin) {
+        *margin = mpsi;
+        *step = n;
+        *kind = 1;
+        *value = psi <= PSI_C;
+      }
+      if (psi > PSI_C) {
+        double p = (psi - 1.0) / (psi + 1.0);
+        if (fabs(u_v - p) < *margin) {
+          *margin = fabs(u_v - p);
+          *step = n;
+          *kind = 2;
+          *value = u_v > p;
+        }
+      }
+    }
+    v = oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
+  }
+}
+
+/*
+ * Per path: the reverse-mode gradient with the path's closest decision taken
+ * the other way where its margin is below margin_below (flip_step[i] = its
+ * step, flip_kind[i] its kind, flip_value[i] the value imposed), else the plain
+ * gradient (flip_step[i] = -1); x_T and grad[i*5 + j] as
+ * oracle_path_grad_reverse.
+ */
+int oracle_path_grad_flip(const oracle_heston* m, uint32_t steps, uint64_t seed, uint32_t option_index,
+                          uint64_t path_begin, int64_t n_paths, double margin_below, double* x_T, double* grad,
+                          int64_t* flip_step, int32_t* flip_kind, int32_t* flip_value) {
+  if (steps == 0 || n_paths < 0) return -1;
+  double k[10];
+  step_constants(m, steps, k);
+  int rc = 0;
+#pragma omp parallel
+  {
+    double* hist = (double*)malloc(sizeof(double) * ((size_t)steps + 1));
+    if (!hist) {
+#pragma omp atomic write
+      rc = -2;
+    } else {
+#pragma omp for schedule(static)
+      for (int64_t i = 0; i < n_paths; ++i) {
+        const uint64_t path = path_begin + (uint64_t)i;
+        int64_t st;
+        int kind, value;
+        double mg;
+        closest_decision(m, k, steps, seed, option_index, path, &st, &kind, &value, &mg);
+        if (!(mg < margin_below)) st = -1;
+        flip_step[i] = st;
+        flip_kind[i] = st >= 0 ? kind : 0;
+        flip_value[i] = st >= 0 ? !value : 0;
+        path_adjoint_forced(m, k, steps, seed, option_index, path, hist, &x_T[i], &grad[i * 5], st, kind,
+                            !value);
+      }
+    }
+    free(hist);
+  }
+  return rc;
+}
+
+/* x_T of one path with one decision imposed (f_step < 0: none) -- the forward
+ * simulation of path_adjoint_forced, for finite-difference checks of it. */
+double oracle_terminal_forced(const oracle_heston* m, uint32_t steps, uint64_t seed, uint32_t option_index,
+                              uint64_t path, int64_t f_step, int f_kind, int f_value) {
+  double k[10];
+  step_constants(m, steps, k);
+  double v = m->v0, x = 0.0;
+  for (uint32_t n = 0; n < steps; ++n) {
+    double u_v, u_x, mg;
+    int br;
+    oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
+    double vn = ((int64_t)n == f_step) ? qe_step_forced(v, u_v, k, f_kind, f_value)
+                                       : oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
+    x += k[4] + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
+    v = vn;
+  }
+  return x;
 }
 
 /* One QE variance step for a model and step count (the step function above with

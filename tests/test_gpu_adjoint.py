@@ -1,23 +1,40 @@
 """GPU pathwise adjoint vs the FP64 oracle's reverse-mode adjoint on the same Philox counters.
 
-Both differentiate the same discretised path with branches held fixed, so on
-every path where both take the same QE branches they agree up to FP32 rounding.
-Tolerance per Greek: relative 1e-4 (the target for Greeks), an absolute floor of
-1e-4 x the column's largest magnitude (columns that pass through zero across the
-strike grid), plus the exact effect of the paths whose oracle branch decisions
-sit within 1e-3 of a threshold or whose payoff indicator differs: for those the
-GPU's own per-path terms (simr_paths_adjoint, the same device code as the
-reduction) are compared with the oracle's, and their difference / paths is
-allowed -- on such a path FP32 may take the other branch of the QE map, whose
-derivative belongs to the other branch, and near the exponential branch's
-U_V = p boundary v' = (m/q) ln(q/(1 - U_V)) is a small logarithm that FP32
-resolves with relative error ~1e-7 / |U_V - p|.  The same accounting covers paths
-that pass a quadratic step with |b + Z_V| < 1e-2 (1 + b): there v' = a (b + Z_V)^2
-is a cancellation that FP32 resolves to a few digits only.  Both are common only
-far outside the Feller condition (vol-of-vol 0.9: 9% of the paths; none of the
-64-step single-option model's).
+Both differentiate the same discretised path with the branches held fixed, so on
+every path where both take the same branches and the same side of the payoff
+kink they agree up to FP32 rounding.  Every flag and allowance below comes from
+the oracle alone (its states, decision margins and derivatives); the GPU is only
+ever the quantity under test.
+
+  * Kink flags: (strike k, path p) with |x_T,p - ln(K_k/S0)| < DX, where the FP32
+    path can end on the other side of the strike (DX is 3 times the per-path
+    x_T bound of the parity tests, 1.5e-7 sqrt(N) + 1e-6, which the measured
+    largest errors -- 0.9e-6 at 64 steps, 3.1e-6 at 252 -- stay within; for
+    vol-of-vol far outside the Feller condition, where paths restart from v = 0,
+    1e-4).  If the indicator flips, the path's term jumps by its whole value, so
+    the allowance is e^{-rT} sum |f'(S_T) S_T dx_T/dq| / P over the flagged
+    pairs.  The test also checks that no unflagged pair's GPU indicator differs.
+  * Decision flags: paths whose branch decision closest to its threshold (the QE
+    branch, or the exponential branch's atom) has a margin below 1e-3.  FP32 can
+    take the other side there, and short of that it resolves the step poorly (a
+    small logarithm just above the atom, whose inputs an FP32 state knows to
+    ~1e-6); the oracle computes the derivative of the path with that decision
+    taken the other way (oracle.path_grad_flip, pinned by finite differences in
+    the CPU suite), and the allowance is e^{-rT} sum |term(flipped) - term| / P
+    over those paths.  No decision of the standard model comes within 1e-2 of
+    its threshold.
+  * Greeks: |GPU - oracle| <= 1e-4 |oracle| + 1e-4 max|column| (columns that
+    change sign across the strikes) + the two allowances; the flagged fractions
+    and the allowances themselves are bounded per case.
+  * The unflagged bulk, strictly: the GPU's per-path terms (simr_paths_adjoint,
+    the same device code as the reduction) summed over the paths no flag
+    touches equal the oracle's to 1e-4 (standard model; 1e-3 in the stress case
+    with vol-of-vol 0.9, whose FP32 state resolves its many near-zero variances
+    to ~1e-6 relative), plus 1e-5 of the column's largest sum.
+  * Per path: 99.9% of the unflagged paths' derivatives agree to pq relative.
 """
 import math
+
 import numpy as np
 import pytest
 import torch
@@ -29,6 +46,7 @@ pytestmark = pytest.mark.gpu
 
 CFG = dict(workloads.BASE_MODEL)
 HARD = dict(S0=100.0, r=0.05, T=1.0, v0=0.09, kappa=1.0, theta=0.04, sigma=0.9, rho=-0.3)
+DECISION_MARGIN = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -45,56 +63,114 @@ def _dev(x):
     return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
 
 
-# pq: bound on the 99.9% quantile of per-path relative derivative errors.  With
-# vol-of-vol 0.9 many steps end near v = 0 through v' = a (b + Z_V)^2 with
-# Z_V close to -b, where FP32 keeps few digits of v' and of its derivatives.
-CASES = [
-    ("single", CFG, [100.0], False, 64, 65536, 1, 16, 1e-3),
-    ("grid", CFG, workloads.strike_grid(), False, 252, 16384, 1, 16, 1e-3),
-    ("grid_put", CFG, workloads.strike_grid(n=8), True, 252, 16384, 2, 0, 1e-3),
-    ("odd_steps_small_ckpt", CFG, [90.0, 110.0], False, 33, 8192, 3, 2, 1e-3),
-    ("ckpt_beyond_steps", CFG, [100.0], True, 10, 4097, 4, 64, 1e-3),
-    ("hard_exp_branch", HARD, [90.0, 100.0, 110.0], False, 64, 16384, 5, 8, 5e-3),
-    ("one_step", CFG, [100.0], False, 1, 2048, 6, 2, 1e-3),
-]
+def _kink_dx(model, steps):
+    feller = 2.0 * model["kappa"] * model["theta"] >= model["sigma"] ** 2
+    return 3.0 * (1.5e-7 * math.sqrt(steps) + 1e-6) if feller else 1e-4
 
 
-def _terms(model, K, is_put, S, g):
-    """Per-path, per-strike adjoint terms [n_K, n_paths, 7] (before the discount and the -T P of r)."""
-    fp = np.where(S[None, :] < K[:, None], -1.0, 0.0) if is_put else np.where(S[None, :] > K[:, None], 1.0, 0.0)
-    w = fp * S[None, :]
-    cols = [w / model["S0"]] + [w * g[None, :, j] for j in range(5)] + [w * model["T"]]
-    return np.stack(cols, axis=2)
+def _strike_terms(model, K, is_put, x, g):
+    """Per-path adjoint terms of one strike, [n_paths, 7] (before the discount and the -T P of r)."""
+    S = model["S0"] * np.exp(x)
+    fp = np.where(S < K, -1.0, 0.0) if is_put else np.where(S > K, 1.0, 0.0)
+    w = fp * S
+    return np.concatenate([(w / model["S0"])[:, None], w[:, None] * g, (w * model["T"])[:, None]], axis=1)
 
 
-@pytest.mark.parametrize("name,model,K,is_put,steps,paths,seed,ckpt,pq", CASES, ids=[c[0] for c in CASES])
-def test_adjoint_matches_oracle(simr, name, model, K, is_put, steps, paths, seed, ckpt, pq):
+def oracle_allowances(model, K, is_put, steps, paths, seed):
+    """Oracle-only flags and allowances (see the module docstring): per strike the
+    kink and decision allowances [n_K, 7], the kink flags [n_K, paths] and the
+    decision flags [paths], plus the oracle's per-path (x_T, gradient)."""
+    disc = math.exp(-model["r"] * model["T"])
+    xo, go = oracle.path_grad(model, steps, seed, 0, paths)
+    xf, gf, st, _, _ = oracle.path_grad_flip(model, steps, seed, 0, paths, DECISION_MARGIN)
+    dec = st >= 0
+    dx = _kink_dx(model, steps)
+    kink = np.abs(xo[None, :] - np.log(np.asarray(K)[:, None] / model["S0"])) < dx
+    a_kink = np.zeros((len(K), 7))
+    a_dec = np.zeros((len(K), 7))
+    for k, Kk in enumerate(K):
+        to = _strike_terms(model, Kk, is_put, xo, go)
+        a_kink[k] = disc * np.abs(to[kink[k]]).sum(axis=0) / paths
+        if dec.any():
+            tf = _strike_terms(model, Kk, is_put, xf[dec], gf[dec])
+            a_dec[k] = disc * np.abs(tf - to[dec]).sum(axis=0) / paths
+    return a_kink, a_dec, kink, dec, xo, go
+
+
+def check_adjoint(simr, model, K, is_put, steps, paths, seed, ckpt, pq, dec_frac_max, allow_max, bulk_tol=1e-4):
     K = np.asarray(K, dtype=np.float64)
     p, se, g = simr.greeks_adjoint(model, _dev(K), is_put, steps, paths, seed, ckpt_every=ckpt)
     p, g = p.cpu().numpy(), g.cpu().numpy()
     po, go = oracle.adjoint(model, K, is_put, steps, paths, seed)
-    # per path: GPU and oracle
+    a_kink, a_dec, kink, dec, xo, gro = oracle_allowances(model, K, is_put, steps, paths, seed)
+    colmax = np.abs(go).max(axis=0, keepdims=True)
+    # the flags and allowances stay small
+    assert dec.mean() <= dec_frac_max, dec.mean()
+    assert kink.mean() <= 1e-3, kink.mean()
+    assert np.all(a_kink + a_dec <= allow_max * colmax), (a_kink + a_dec) / colmax
+    # prices: 1e-5
+    assert np.all(np.abs(p - po) <= 1e-5 * np.abs(po) + 1e-9), (p, po)
+    # Greeks, with the oracle's allowances
+    err = np.abs(g - go)
+    tol = 1e-4 * np.abs(go) + 1e-4 * colmax + a_kink + a_dec
+    bad = err > tol
+    assert not bad.any(), (np.argwhere(bad), (err / colmax)[bad], ((a_kink + a_dec) / colmax)[bad])
+    # the unflagged bulk, strictly, and per path
     xg, gg = simr.paths_adjoint(model, steps, 0, paths, seed, ckpt_every=ckpt)
     xg, gg = xg.cpu().double().numpy(), gg.cpu().double().numpy()
-    xo, gro = oracle.path_grad(model, steps, seed, 0, paths)
-    _, _, mg, cond = oracle.terminal_diag(model, steps, seed, 0, paths)
-    Sg, So = model["S0"] * np.exp(xg), model["S0"] * np.exp(xo)
-    ind_g = (Sg < K[:, None]) if is_put else (Sg > K[:, None])
-    ind_o = (So < K[:, None]) if is_put else (So > K[:, None])
-    ill = (mg < 1e-3) | (cond < 1e-2)
-    flagged = ill[None, :] | (ind_g != ind_o)                               # [n_K, n_paths]
-    ok = ~ill
-    # paths with the same branches: per-path derivatives agree to FP32 accuracy
-    scale = np.abs(gro[ok]).max(axis=0, keepdims=True)
-    assert np.quantile(np.abs(gg[ok] - gro[ok]) / (np.abs(gro[ok]) + 1e-3 * scale), 0.999) < pq
-    diff = np.abs(_terms(model, K, is_put, Sg, gg) - _terms(model, K, is_put, So, gro))
-    allowance = math.exp(-model["r"] * model["T"]) * (diff * flagged[:, :, None]).sum(axis=1) / paths
-    assert np.all(np.abs(p - po) <= 1e-5 * np.abs(po) + 1e-9), (p, po)
-    floor = 1e-4 * np.max(np.abs(go), axis=0, keepdims=True)
-    err = np.abs(g - go)
-    tol = 1e-4 * np.abs(go) + floor + allowance
-    bad = err > tol
-    assert not bad.any(), (np.argwhere(bad), (err / np.maximum(np.abs(go), 1e-300))[bad])
+    # the kink band covers every side the GPU took differently
+    lnk = np.log(K[:, None] / model["S0"])
+    assert not np.any(((xg[None, :] > lnk) != (xo[None, :] > lnk)) & ~kink), "an unflagged strike side differs"
+    clean = ~dec & ~kink.any(axis=0)
+    scale = np.abs(gro[clean]).max(axis=0, keepdims=True)
+    assert np.quantile(np.abs(gg[clean] - gro[clean]) / (np.abs(gro[clean]) + 1e-3 * scale), 0.999) < pq
+    sg = np.array([_strike_terms(model, Kk, is_put, xg[clean], gg[clean]).sum(axis=0) for Kk in K])
+    so = np.array([_strike_terms(model, Kk, is_put, xo[clean], gro[clean]).sum(axis=0) for Kk in K])
+    tol_c = bulk_tol * np.abs(so).max(axis=0, keepdims=True) if bulk_tol > 1e-4 else \
+        1e-4 * np.abs(so) + 1e-5 * np.abs(so).max(axis=0, keepdims=True)
+    bad_c = np.abs(sg - so) > tol_c
+    assert not bad_c.any(), (np.argwhere(bad_c), (np.abs(sg - so) / np.abs(so).max(axis=0))[bad_c])
+    return err / colmax, (a_kink + a_dec) / colmax
+
+
+# pq: bound on the 99.9% quantile of unflagged paths' relative derivative errors.
+# With vol-of-vol 0.9 many steps end near v = 0 through v' = a (b + Z_V)^2 with
+# Z_V close to -b, or through a small logarithm just above the exponential
+# branch's atom, where FP32 keeps few digits of v' and of its derivatives.
+# dec_frac_max, allow_max: bounds on the decision-flagged fraction of the paths
+# and on the allowances (x the column's largest magnitude).  The standard model's
+# decisions all sit far from their thresholds (no flags) and its allowances are
+# the kink terms alone, at most 1.05e-3 of a column (the rho column, whose
+# per-path derivatives largely cancel in the mean).  With vol-of-vol 0.9 (Feller
+# ratio 0.1) 6.9% of the paths have a decision within 1e-3 of its threshold,
+# mostly the exponential branch's atom, and the other side's derivative moves
+# dP/dkappa (a column near zero across these strikes), dP/dtheta and dP/dsigma by
+# up to 2.2, 0.35 and 0.74 of their largest values: that case's Greek-level
+# check is loose on those three columns, and its strict check is the bulk's
+# (the other 93% of the paths).
+CASES = [
+    ("single", CFG, [100.0], False, 64, 65536, 1, 16, 1e-3, 0.0, 2e-3),
+    ("grid", CFG, workloads.strike_grid(), False, 252, 16384, 1, 16, 1e-3, 0.0, 2e-3),
+    ("grid_put", CFG, workloads.strike_grid(n=8), True, 252, 16384, 2, 0, 1e-3, 0.0, 2e-3),
+    ("odd_steps_small_ckpt", CFG, [90.0, 110.0], False, 33, 8192, 3, 2, 1e-3, 0.0, 2e-3),
+    ("ckpt_beyond_steps", CFG, [100.0], True, 10, 4097, 4, 64, 1e-3, 0.0, 2e-3),
+    ("hard_exp_branch", HARD, [90.0, 100.0, 110.0], False, 64, 16384, 5, 8, 5e-3, 0.08, 2.5, 1e-3),
+    ("one_step", CFG, [100.0], False, 1, 2048, 6, 2, 1e-3, 0.0, 2e-3),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_matches_oracle(simr, case):
+    check_adjoint(simr, *case[1:])
+
+
+def test_adjoint_full_size_grid_checkpoint_every_16(simr):
+    # the adjoint workload at full size: 252 steps x 2^20 paths x 32 strikes, a
+    # checkpoint every 16 steps; every column against the oracle's FP64 reverse
+    # mode, with the oracle-only kink allowance (no decision of this model comes
+    # within 1e-3 of its threshold; the allowance is at most 3.9e-4 of a column,
+    # the rho column's)
+    check_adjoint(simr, CFG, workloads.strike_grid(), False, 252, 1 << 20, 1, 16, 1e-3, 0.0, 1e-3)
 
 
 def test_adjoint_price_equals_price_kernel(simr):

@@ -119,6 +119,11 @@ C_MISTAKES = [
      pins.test_reverse_mode_matches_forward_mode_duals),
     ("dual_sqrt_rule", "a.d[i] / (2.0 * r.v)", "a.d[i] / r.v", pins.test_reverse_mode_matches_forward_mode_duals),
     ("adjoint_delta_weight", "s[0] += w / m->S0;", "s[0] += w;", pins.test_adjoint_matches_fd_and_closed_form_delta),
+    # the decision taken the other way: the reverse sweep must impose it where the forward did
+    ("flip_reverse_keeps_natural_branch", "if (n == f_step && f_kind == 1) quad = f_value;", "",
+     pins.test_flipped_decision_gradient_matches_finite_differences),
+    ("flip_forward_exponential_drops_log", "const double vn = log((1.0 - pp) / (1.0 - u_v)) * mean / (1.0 - pp);",
+     "const double vn = 0.0;", pins.test_flipped_decision_gradient_matches_finite_differences),
     ("adjoint_drops_rate_discount", "grad[j * 7 + 6] -= m->T * price[j];", "",
      pins.test_adjoint_matches_fd_and_closed_form_delta),
     # QE-M martingale correction

@@ -398,3 +398,54 @@ def test_paper_table2_ops_per_cycle():
     for _, _, cycles, opc, eff in _read_golden("paper_table2_ops.txt"):
         assert round(ops / int(cycles), 2) == float(opc)
         assert abs(100 * ops / int(cycles) / 8 - float(eff)) < 0.06
+
+
+# ------------------------------------------------ branch decision taken the other way ----
+HARD_FLIP = dict(S0=100.0, r=0.05, T=1.0, v0=0.09, kappa=1.0, theta=0.04, sigma=0.9, rho=-0.3)
+
+
+def test_flipped_decision_gradient_matches_finite_differences():
+    # oracle.path_grad_flip: the reverse-mode gradient of the path whose decision
+    # closest to its threshold is taken the other way.  Central differences of that
+    # forced path's x_T (oracle.terminal_forced, the decision imposed at the same
+    # step, every other decision left to the path) must agree with it, and paths
+    # without a flip must equal the plain reverse mode bit for bit.  A path whose
+    # atom (v' = 0) is forced to the logarithm's side keeps v' = 0 there (the
+    # continuation below the boundary is negative) and takes that side's
+    # one-sided derivative, which no difference of the held value can show: those
+    # flips are left out of the check.
+    steps, seed, n = 64, 5, 4096
+    x, g, st, kd, fv = oracle.path_grad_flip(HARD_FLIP, steps, seed, 0, n, 1e-3)
+    x0, g0 = oracle.path_grad(HARD_FLIP, steps, seed, 0, n)
+    nf = st < 0
+    assert 0.01 < (~nf).mean() < 0.2 and set(np.unique(kd[~nf])) <= {1, 2}
+    np.testing.assert_array_equal(g[nf], g0[nf])
+    np.testing.assert_array_equal(x[nf], x0[nf])
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(x))
+    fields = ("v0", "kappa", "theta", "sigma", "rho")
+    checked = {1: 0, 2: 0}
+    for i in np.flatnonzero(~nf)[:120]:
+        i = int(i)
+        value = int(fv[i])
+        assert oracle.terminal_forced(HARD_FLIP, steps, seed, i, int(st[i]), int(kd[i]), value) == x[i]
+        if kd[i] == 2 and value == 1:
+            continue  # the atom forced to the logarithm's side: held at v' = 0
+        fd, clean = np.empty(5), True
+        for j, f in enumerate(fields):
+            vals = []
+            for h in (1e-6, 5e-7):
+                hh = h * max(abs(HARD_FLIP[f]), 1.0)
+                up, dn = dict(HARD_FLIP), dict(HARD_FLIP)
+                up[f] += hh
+                dn[f] -= hh
+                xu = oracle.terminal_forced(up, steps, seed, i, int(st[i]), int(kd[i]), value)
+                xd = oracle.terminal_forced(dn, steps, seed, i, int(st[i]), int(kd[i]), value)
+                vals.append((xu - xd) / (2 * hh))
+            # another decision of the path within the bump makes the difference meaningless
+            clean = clean and abs(vals[0] - vals[1]) <= 1e-4 * max(abs(vals[0]), 1e-2)
+            fd[j] = vals[0]
+        if not clean:
+            continue
+        np.testing.assert_allclose(g[i], fd, rtol=1e-4, atol=1e-6 * np.abs(g[i]).max(), err_msg=f"path {i}")
+        checked[int(kd[i])] += 1
+    assert checked[1] >= 3 and checked[2] >= 5, checked
