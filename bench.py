@@ -46,6 +46,12 @@ FP32_LANES_PER_SM = 128
 # the Kahan compensation of x, the CRN scenarios' constant deltas, Philox.
 FLOPS_SHARED = 44
 FLOPS_PER_SCENARIO = 23
+# The reverse step of the pathwise adjoint, in the same count (the oracle's
+# reverse-mode step, reusing the forward step's quantities): the log-spot step's
+# adjoint 14 (d sqrt(w) Z / dw, the adjoints of v_n, v_n+1 and K0..K4), the QE
+# map's 24 (abar, bbar, b2bar, tbar, mbar, s2bar), the moments' 13 (through E,
+# theta, c1, c2 and v_n) = 51; price + adjoint Greeks = 44 + 23 + 51 = 118.
+FLOPS_ADJOINT_REVERSE = 51
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -228,29 +234,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_run(w, paths_sample: int):
-    """One oracle pass (price + the same FD Greeks) on paths [0, paths_sample) of the workload."""
+def cpu_oracle_run(w, paths_sample: int, with_result: bool = False):
+    """One oracle pass (price + the same FD Greeks) on paths [0, paths_sample) of the workload:
+    its wall time (and its (price, greeks) with with_result)."""
     import oracle
 
     bits = {"delta": oracle.G_DELTA, "gamma": oracle.G_GAMMA, "vega": oracle.G_VEGA, "theta": oracle.G_THETA,
             "rho": oracle.G_RHO}
     mask = sum(bits[g] for g in w.greeks)
     t0 = time.perf_counter()
-    oracle.greeks_fd(w.model, w.strikes, w.is_put, w.steps, paths_sample, w.seed, w.rel_bump, mask)
-    return time.perf_counter() - t0
+    res = oracle.greeks_fd(w.model, w.strikes, w.is_put, w.steps, paths_sample, w.seed, w.rel_bump, mask)
+    dt = time.perf_counter() - t0
+    return (dt, res) if with_result else dt
 
 
 def cpu_baseline(w, paths_sample: int = 1 << 20):
-    """The oracle on the host cores; by default the whole workload (2^20 paths, ~12 s on 16 cores)."""
+    """The oracle on the host cores; by default the whole workload (2^20 paths, ~12 s on 16 cores).
+    Returns the baseline record and, for a whole-workload run, the oracle's (price, greeks)."""
     import oracle
 
     oracle.build()
     cores = oracle.max_threads()
     paths_sample = min(paths_sample, w.paths)
-    dt = cpu_oracle_run(w, paths_sample)
-    return {"value": paths_sample * w.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{w.name}: paths [0, {paths_sample}) of {w.paths}, all {w.steps} steps, all "
-                      f"{len(w.strikes)} strikes and the same Greeks; {dt:.2f} s wall on {cores} threads"}
+    dt, res = cpu_oracle_run(w, paths_sample, with_result=True)
+    rec = {"value": paths_sample * w.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{w.name}: paths [0, {paths_sample}) of {w.paths}, all {w.steps} steps, all "
+                     f"{len(w.strikes)} strikes and the same Greeks; {dt:.2f} s wall on {cores} threads"}
+    return rec, (res if paths_sample == w.paths else None)
+
+
+def result_errors(gpu, ref):
+    """Per column: "rel", the largest |GPU - oracle| / |oracle| over the strikes whose oracle value
+    is at least 1e-3 of the column's largest, and "rel_col", the largest |GPU - oracle| over the
+    column's largest |oracle|."""
+    gpu, ref = np.asarray(gpu, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref).max()
+    keep = np.abs(ref) >= 1e-3 * scale
+    err = np.abs(gpu - ref)
+    return {"rel": float(np.max(err[keep] / np.abs(ref[keep]))), "rel_col": float(err.max() / scale)}
 
 
 def run_reference(args):
@@ -320,6 +341,103 @@ def run_profile_leg(args):
         fn()
     torch.cuda.synchronize()
     return 0
+
+
+def run_headline(args, simr, dev, stream):
+    """The 8-underlying headline workload: price + adjoint Greeks at a checkpoint every 32 steps."""
+    import torch
+
+    hw = workloads.headline()
+    fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
+    ps_head = sum(u.steps * u.paths for u in hw)
+    k_cfg = 32
+    head = {"metric": "Heston path-steps/s (price + adjoint Greeks, checkpoint every 32 steps) on 1 GB300",
+            "unit": UNIT, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "heston_book8_1024x67108864_adjoint_k32", "underlyings": len(hw),
+                       "time_steps": hw[0].steps, "paths": hw[0].paths, "strikes": len(hw[0].strikes),
+                       "ckpt_every": k_cfg, "sensitivities": ["S0", "v0", "kappa", "theta", "sigma", "rho", "r"],
+                       "path_steps": ps_head,
+                       "l2": "inputs (model, strikes) negligible; each pass reads and writes far more than L2"},
+            "library_ckpt_every": simr.adjoint_interval(len(hw[0].strikes), hw[0].steps, dev.index or 0)}
+    Kh = [torch.as_tensor(u.strikes, dtype=torch.float64, device=dev) for u in hw]
+    legs = {
+        "price": lambda u, k: simr.price(u.model, k, u.is_put, u.steps, u.paths, u.seed),
+        "adjoint_k32": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
+                                                        ckpt_every=k_cfg),
+        # the library's interval (one segment of the whole path in global memory, no forward pass)
+        "adjoint_lib": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed),
+        "fd7": lambda u, k: simr.greeks_fd(u.model, k, u.is_put, u.steps, u.paths, u.seed, greeks=fd7,
+                                           rel_bump=u.rel_bump),
+    }
+    clk_k32 = None
+    for name, fn in legs.items():
+        u0 = hw[0]
+        small = workloads.Workload(u0.name, u0.model, u0.strikes, u0.steps, 1 << 16, ckpt_every=u0.ckpt_every)
+        fn(small, Kh[0])  # warm-up (context scratch, module load)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index or 0) as clk:
+            a.record(stream)
+            for u, k in zip(hw, Kh):
+                fn(u, k)
+            b.record(stream)
+            torch.cuda.synchronize()
+        if name == "adjoint_k32":
+            clk_k32 = clk.summary()
+        sec = a.elapsed_time(b) * 1e-3
+        head[f"{name}_s"] = sec
+        head[f"{name}_path_steps_per_s"] = ps_head / sec
+    head["value"] = head["adjoint_k32_path_steps_per_s"]
+    head["ms_per_step"] = head["adjoint_k32_s"] * 1e3 / len(hw)  # one underlying = one launch
+    head["adjoint_k32_cost_vs_price"] = head["adjoint_k32_s"] / head["price_s"]
+    head["adjoint_lib_cost_vs_price"] = head["adjoint_lib_s"] / head["price_s"]
+    head["adjoint_k32_speedup_vs_fd"] = head["fd7_s"] / head["adjoint_k32_s"]
+    head["clocks"] = clk_k32
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clk_k32.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    flops = FLOPS_SHARED + FLOPS_PER_SCENARIO + FLOPS_ADJOINT_REVERSE
+    achieved = flops * ps_head / head["adjoint_k32_s"] / 1e12
+    head["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_kind": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                                     f"x 2 x {sm_mhz:.0f} MHz (the median SM clock sampled during the pass)",
+                        "flops_per_path_step": flops,
+                        "kernel": "heston_adjoint_kernel (shared-memory segments of 32 steps)"}
+    # end to end through the public API with host buffers: strikes in, prices and 7 Greeks out
+    if not args.no_e2e:
+        K_host = [torch.as_tensor(u.strikes, dtype=torch.float64).pin_memory() for u in hw]
+        simr.greeks_adjoint(hw[0].model, K_host[0], hw[0].is_put, hw[0].steps, 1 << 16, hw[0].seed,
+                            ckpt_every=k_cfg, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out_b = 0
+        for u, k in zip(hw, K_host):
+            p_h, se_h, g_h = simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed, ckpt_every=k_cfg,
+                                                 device=dev)
+            out_b += (p_h.numel() + se_h.numel() + g_h.numel()) * 8
+        e2e_s = time.perf_counter() - t0
+        head["e2e"] = {"value": ps_head / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": sum(k.numel() for k in K_host) * 8 // len(hw),
+                       "d2h_bytes_per_step": out_b // len(hw), "steps": len(hw),
+                       "note": "one step = one underlying's call with host strike and result buffers"}
+    # the FP64 oracle's reverse mode on the host cores, on a path sample of every underlying
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        n_s = 1 << 10
+        t0 = time.perf_counter()
+        for u in hw:
+            oracle.adjoint(u.model, u.strikes, u.is_put, u.steps, n_s, u.seed)
+        dt = time.perf_counter() - t0
+        cores = oracle.max_threads()
+        head["cpu_baseline"] = {"value": len(hw) * n_s * hw[0].steps / dt, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"paths [0, {n_s}) of each of the {len(hw)} underlyings, all "
+                                          f"{hw[0].steps} steps and {len(hw[0].strikes)} strikes, price + the 7 "
+                                          f"pathwise sensitivities; {dt:.2f} s wall on {cores} threads"}
+    return head
 
 
 def run_native(args):
@@ -527,46 +645,13 @@ def run_native(args):
                   "asset_path_steps_per_s": 8 * 252 * (1 << 20) / (ms_b * 1e-3)}
 
     # large-scale headline: 8 underlyings (book-style parameters), 32 strikes each,
-    # 1,024 steps, 2^26 paths; price, adjoint Greeks (the library's checkpoint interval) and
-    # CRN bump-and-revalue of the same 7 sensitivities, one timed pass each
+    # 1,024 steps, 2^26 paths; price plus adjoint Greeks with a checkpoint every 32
+    # steps -- a record of its own (metric, value, roofline, e2e, cpu_baseline) --
+    # beside the library's interval, a pricing pass and CRN bump-and-revalue of the
+    # same 7 sensitivities, one timed pass each
     head = None
     if not args.no_headline:
-        hw = workloads.headline()
-        fd7 = ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")
-        ps_head = sum(u.steps * u.paths for u in hw)
-        head = {"underlyings": len(hw), "time_steps": hw[0].steps, "paths": hw[0].paths,
-                "strikes": len(hw[0].strikes),
-                "ckpt_every": hw[0].ckpt_every or simr.adjoint_interval(len(hw[0].strikes), hw[0].steps, dev.index or 0),
-                "path_steps": ps_head,
-                "sensitivities": list(fd7)}
-        Kh = [torch.as_tensor(u.strikes, dtype=torch.float64, device=dev) for u in hw]
-        legs = {
-            "price": lambda u, k: simr.price(u.model, k, u.is_put, u.steps, u.paths, u.seed),
-            "adjoint": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
-                                                        ckpt_every=u.ckpt_every),
-            # the same with a checkpoint every 32 steps (shared-memory segments, forward pass)
-            "adjoint_k32": lambda u, k: simr.greeks_adjoint(u.model, k, u.is_put, u.steps, u.paths, u.seed,
-                                                            ckpt_every=32),
-            "fd7": lambda u, k: simr.greeks_fd(u.model, k, u.is_put, u.steps, u.paths, u.seed, greeks=fd7,
-                                               rel_bump=u.rel_bump),
-        }
-        for name, fn in legs.items():
-            u0 = hw[0]
-            small = workloads.Workload(u0.name, u0.model, u0.strikes, u0.steps, 1 << 16, ckpt_every=u0.ckpt_every)
-            fn(small, Kh[0])  # warm-up (context scratch, module load)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for u, k in zip(hw, Kh):
-                fn(u, k)
-            b.record(stream)
-            torch.cuda.synchronize()
-            sec = a.elapsed_time(b) * 1e-3
-            head[f"{name}_s"] = sec
-            head[f"{name}_path_steps_per_s"] = ps_head / sec
-        head["adjoint_speedup_vs_fd"] = head["fd7_s"] / head["adjoint_s"]
-        head["adjoint_cost_vs_price"] = head["adjoint_s"] / head["price_s"]
-        head["adjoint_k32_cost_vs_price"] = head["adjoint_k32_s"] / head["price_s"]
+        head = run_headline(args, simr, dev, stream)
 
     # Longstaff-Schwartz Bermudan put (252 steps, exercisable after every step, 2^20
     # paths): the path kernel, then the backward induction (one cooperative sweep
@@ -650,7 +735,27 @@ def run_native(args):
         "wall_s_timed_region": t_wall,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"], ref = cpu_baseline(w)
+        # the stated error of every result against the FP64 oracle on the same draws:
+        # the bench step's price and Greeks (the baseline's oracle run is the same
+        # workload), and the 7 adjoint sensitivities of the grid at 2^18 paths
+        if ref is not None and world == 1:
+            p_g, g_g = (t.cpu().numpy() for t in out)
+            errs = {"price": result_errors(p_g, ref[0])}
+            for j, n in enumerate(greeks):
+                errs[n] = result_errors(g_g[:, j], ref[1][:, j])
+            import oracle
+
+            n_adj = 1 << 18
+            pa, _, ga = simr.greeks_adjoint(w.model, K, w.is_put, w.steps, n_adj, w.seed, ckpt_every=16)
+            pao, gao = oracle.adjoint(w.model, w.strikes, w.is_put, w.steps, n_adj, w.seed)
+            aerr = {"price": result_errors(pa.cpu().numpy(), pao)}
+            for j, n in enumerate(simr.ADJOINT_COLUMNS):
+                aerr["d/d" + n] = result_errors(ga.cpu().numpy()[:, j], gao[:, j])
+            line["errors"] = {
+                "note": "rel: max over strikes of |GPU - oracle| / |oracle| (strikes with |oracle| >= 1e-3 of "
+                        "the column's largest); rel_col: max |GPU - oracle| / max |oracle column|",
+                f"{w.name}_fd": errs, f"heston_grid32_252x{n_adj}_adjoint_k16": aerr}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -122,6 +122,45 @@ __device__ __forceinline__ void adj_common_pre(const ScenConst& c, float theta, 
   P.vc = vc;
 }
 
+// The exponential branch's innovation dl = v' - m of a reverse step (m <= 0:
+// v' = 0 and dl = 0), with d = 1 - U_V its stored draw; *atom: v' = 0 by the
+// atom (W >= 2 m^2, the forward step's test).
+__device__ __forceinline__ float adj_exp_dl(float m, float m2, float s2h, float vn, float d, bool* atom) {
+  *atom = true;
+  if (!(m > 0.0f)) return 0.0f;
+  const float ms = m2 + (s2h + s2h);
+  *atom = d * ms >= 2.0f * m2;
+  return *atom ? -m : vn - m;
+}
+
+// The adjoint chain of an exponential-branch reverse step, then adj_tail (P.dl
+// and P.inc already set by adj_exp_dl and adj_inc).
+__device__ __forceinline__ void adj_chain_exp(float E, float c1, float Cdl, float m, float m2, float s2h, float d,
+                                              bool atom, const AdjPre& P, AdjSums& a) {
+  const float vnbar = a.vbar + P.hzc;  // total adjoint of v_{n+1}
+  const float dlbar = Cdl;
+  float mbar = 0.0f, s2bar = 0.0f;
+  if (m > 0.0f) {
+    if (atom) {
+      mbar = -dlbar;
+    } else {
+      const float s2 = s2h + s2h;
+      const float ms = m2 + s2;
+      const float W = d * ms;
+      const float rm = rcp_approx(m), rms = rcp_approx(ms);
+      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
+      const float A = 0.5f * ms * rm;
+      const float dA_dm = 0.5f * (m2 - s2) * rm * rm;
+      const float dL_dm = 2.0f * rm - 2.0f * m * rms;
+      const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
+      const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
+      mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
+      s2bar = (vnbar + dlbar) * dv_ds;
+    }
+  }
+  adj_tail(E, c1, P, mbar, s2bar, a);
+}
+
 // Reverse step n: state vc -> vn (both known), the step's stored draw d (Z_V in
 // the quadratic branch, 1 - U_V in the exponential one; the branch follows from
 // vc) and Z_X; vbar holds the adjoint of v_{n+1} on entry and of v_n on exit.
@@ -141,54 +180,18 @@ __device__ __forceinline__ void adjoint_step(const ScenConst& c, float theta, fl
     adj_chain_quad(c.E, c1, P, a);
     return;
   }
-  const float vnbar = a.vbar + P.hzc;  // total adjoint of v_{n+1}
-  const float dlbar = c.Cdl;
-  float mbar = 0.0f, s2bar = 0.0f;
-  P.dl = 0.0f;
-  if (m > 0.0f) {
-    const float omu = d;
-    const float s2 = s2h + s2h;
-    const float ms = m2 + s2;
-    const float W = omu * ms;
-    if (W >= 2.0f * m2) {
-      P.dl = -m;
-      mbar = -dlbar;
-    } else {
-      const float rm = rcp_approx(m), rms = rcp_approx(ms);
-      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
-      const float A = 0.5f * ms * rm;
-      const float dA_dm = 0.5f * (m2 - s2) * rm * rm;
-      const float dL_dm = 2.0f * rm - 2.0f * m * rms;
-      const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
-      const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
-      P.dl = vn - m;
-      mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
-      s2bar = (vnbar + dlbar) * dv_ds;
-    }
-  }
+  bool atom;
+  P.dl = adj_exp_dl(m, m2, s2h, vn, d, &atom);
   P.inc = adj_inc(c, vc + vn, vc, P.dl, P.q, zx);
-  adj_tail(c.E, c1, P, mbar, s2bar, a);
+  adj_chain_exp(c.E, c1, c.Cdl, m, m2, s2h, d, atom, P, a);
 }
 
-// Two consecutive reverse steps, n (lane x) then n - 1 (lane y): when both
-// take the quadratic branch, their quantities that do not depend on the
-// carried adjoint (adj_common_pre, adj_quad_pre, the log-spot increment) in
-// packed FP32, then the two adjoint chains in order; else two adjoint_step
-// calls.  Lane for lane adjoint_step's operations, so the same sums bit for bit
-// however the steps are paired.
-__device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, float c1, float2 vc, float2 vn,
-                                              float2 d, float2 zx, AdjSums& a) {
-  const float2 m = p_fma(vc, p_bc(c.E), p_bc(c.thE));
-  const float2 s2h = p_fma(vc, p_bc(c.h1), p_bc(c.h2));
-  const float2 m2 = p_mul(m, m);
-  const float2 rs2h = p_rcp(s2h);
-  const float2 t = p_mul(m2, rs2h);  // qe_t, lane for lane
-  if (!(t.x > kQuadT && t.y > kQuadT)) {
-    adjoint_step(c, theta, c1, vc.x, vn.x, d.x, zx.x, a);
-    adjoint_step(c, theta, c1, vc.y, vn.y, d.y, zx.y, a);
-    return;
-  }
-  // adj_common_pre, paired
+// adjoint_step2 for a warp whose every lane takes the quadratic branch in both
+// steps (the same operations as its general form, without the exponential
+// branch's code and registers).
+__device__ __forceinline__ void adjoint_step2_quad(const ScenConst& c, float theta, float c1, float2 vc, float2 vn,
+                                                   float2 d, float2 zx, float2 m, float2 m2, float2 rs2h, float2 t,
+                                                   AdjSums& a) {
   const float2 s = p_add(vc, vn);
   const float2 rq = make_float2(rsqrt_approx(s.x), rsqrt_approx(s.y));
   const float2 sq = p_mul(s, rq);
@@ -197,7 +200,6 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
   const float2 hzc = p_add(make_float2(s.x > 0.0f ? hq.x : 0.0f, s.y > 0.0f ? hq.y : 0.0f), p_bc(c.Cv));
   const float2 hzcd = p_sub(hzc, p_bc(c.Cd));
   const float2 tmv = p_sub(p_bc(theta), vc);
-  // adj_quad_pre, paired
   const float2 tt = p_fma(t, t, p_mul(t, p_bc(-1.0f)));
   const float2 rroot = make_float2(rsqrt_approx(tt.x), rsqrt_approx(tt.y));
   const float2 root = p_mul(tt, rroot);
@@ -209,6 +211,10 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
   const float2 bz = p_add(b, d);
   const float2 g = p_fma(d, p_add(d, p_mul(p_bc(2.0f), b)), p_bc(-1.0f));
   const float2 dl = p_mul(am, g);
+  float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
+  inc = p_fma(p_bc(-c.Cd), vc, inc);
+  inc = p_fma(p_bc(c.Cdl), dl, inc);
+  inc = p_fma(p_mul(p_bc(c.sK3), q), zx, inc);
   const float2 bz2 = p_mul(bz, bz);
   const float2 cg = p_mul(p_bc(c.Cdl), g);
   const float2 cz = p_mul(p_bc(c.Cdl), d);
@@ -218,6 +224,68 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
   const float2 F = p_fma(p_fma(p_bc(2.0f), t, p_bc(-1.0f)), p_mul(p_bc(0.5f), rroot), p_bc(1.0f));
   const float2 m4r = p_mul(p_add(m, m), rs2h);
   const float2 tr = p_mul(t, p_mul(p_bc(0.5f), rs2h));
+  const AdjPre Px{inc.x, dl.x, q.x,  zx.x,  hzc.x, hzcd.x,  tmv.x, vc.x, bz.x,
+                  bz2.x, cg.x, cz.x, am2.x, hrb.x, amr.x, ropb2.x, F.x,   m4r.x, tr.x};
+  const AdjPre Py{inc.y, dl.y, q.y,  zx.y,  hzc.y, hzcd.y,  tmv.y, vc.y, bz.y,
+                  bz2.y, cg.y, cz.y, am2.y, hrb.y, amr.y, ropb2.y, F.y,   m4r.y, tr.y};
+  adj_chain_quad(c.E, c1, Px, a);
+  adj_chain_quad(c.E, c1, Py, a);
+}
+
+// Two consecutive reverse steps, n (lane x) then n - 1 (lane y): their
+// quantities that do not depend on the carried adjoint (adj_common_pre,
+// adj_quad_pre -- used only by a lane in the quadratic branch -- and the
+// log-spot increment, with each lane's innovation from its own branch) in packed
+// FP32, then the two adjoint chains in order, each by its lane's branch.  Lane
+// for lane adjoint_step's operations, so the same sums bit for bit however the
+// steps are paired; lanes of a warp in different branches diverge only in the
+// chains.
+__device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, float c1, float2 vc, float2 vn,
+                                              float2 d, float2 zx, AdjSums& a) {
+  const float2 m = p_fma(vc, p_bc(c.E), p_bc(c.thE));
+  const float2 s2h = p_fma(vc, p_bc(c.h1), p_bc(c.h2));
+  const float2 m2 = p_mul(m, m);
+  const float2 rs2h = p_rcp(s2h);
+  const float2 t = p_mul(m2, rs2h);  // qe_t, lane for lane
+  const bool qx = t.x > kQuadT, qy = t.y > kQuadT;
+  if (__all_sync(0xffffffffu, qx && qy)) {  // the whole warp in the quadratic branch
+    adjoint_step2_quad(c, theta, c1, vc, vn, d, zx, m, m2, rs2h, t, a);
+    return;
+  }
+  // adj_common_pre, paired
+  const float2 s = p_add(vc, vn);
+  const float2 rq = make_float2(rsqrt_approx(s.x), rsqrt_approx(s.y));
+  const float2 sq = p_mul(s, rq);
+  const float2 hq = p_mul(p_mul(p_bc(0.5f * c.sK3), zx), rq);
+  const float2 q = make_float2(s.x > 0.0f ? sq.x : 0.0f, s.y > 0.0f ? sq.y : 0.0f);
+  const float2 hzc = p_add(make_float2(s.x > 0.0f ? hq.x : 0.0f, s.y > 0.0f ? hq.y : 0.0f), p_bc(c.Cv));
+  const float2 hzcd = p_sub(hzc, p_bc(c.Cd));
+  const float2 tmv = p_sub(p_bc(theta), vc);
+  // adj_quad_pre, paired (its values are used by quadratic-branch lanes only)
+  const float2 tt = p_fma(t, t, p_mul(t, p_bc(-1.0f)));
+  const float2 rroot = make_float2(rsqrt_approx(tt.x), rsqrt_approx(tt.y));
+  const float2 root = p_mul(tt, rroot);
+  const float2 b2 = p_add(p_sub(t, p_bc(1.0f)), root);
+  const float2 rb = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
+  const float2 b = p_mul(b2, rb);
+  const float2 ropb2 = p_rcp(p_add(t, root));
+  const float2 am = p_mul(m, ropb2);
+  const float2 bz = p_add(b, d);
+  const float2 g = p_fma(d, p_add(d, p_mul(p_bc(2.0f), b)), p_bc(-1.0f));
+  float2 dl = p_mul(am, g);
+  const float2 bz2 = p_mul(bz, bz);
+  const float2 cg = p_mul(p_bc(c.Cdl), g);
+  const float2 cz = p_mul(p_bc(c.Cdl), d);
+  const float2 am2 = p_add(am, am);
+  const float2 hrb = p_mul(p_bc(0.5f), rb);
+  const float2 amr = p_mul(am, ropb2);
+  const float2 F = p_fma(p_fma(p_bc(2.0f), t, p_bc(-1.0f)), p_mul(p_bc(0.5f), rroot), p_bc(1.0f));
+  const float2 m4r = p_mul(p_add(m, m), rs2h);
+  const float2 tr = p_mul(t, p_mul(p_bc(0.5f), rs2h));
+  // each lane's innovation from its own branch
+  bool ax = false, ay = false;
+  if (!qx) dl.x = adj_exp_dl(m.x, m2.x, s2h.x, vn.x, d.x, &ax);
+  if (!qy) dl.y = adj_exp_dl(m.y, m2.y, s2h.y, vn.y, d.y, &ay);
   // adj_inc, paired
   float2 inc = p_fma(p_bc(c.Cv), s, p_bc(c.C0));
   inc = p_fma(p_bc(-c.Cd), vc, inc);
@@ -227,8 +295,14 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
                   bz2.x, cg.x, cz.x, am2.x, hrb.x, amr.x, ropb2.x, F.x,   m4r.x, tr.x};
   const AdjPre Py{inc.y, dl.y, q.y,  zx.y,  hzc.y, hzcd.y,  tmv.y, vc.y, bz.y,
                   bz2.y, cg.y, cz.y, am2.y, hrb.y, amr.y, ropb2.y, F.y,   m4r.y, tr.y};
-  adj_chain_quad(c.E, c1, Px, a);
-  adj_chain_quad(c.E, c1, Py, a);
+  if (qx)
+    adj_chain_quad(c.E, c1, Px, a);
+  else
+    adj_chain_exp(c.E, c1, c.Cdl, m.x, m2.x, s2h.x, d.x, ax, Px, a);
+  if (qy)
+    adj_chain_quad(c.E, c1, Py, a);
+  else
+    adj_chain_exp(c.E, c1, c.Cdl, m.y, m2.y, s2h.y, d.y, ay, Py, a);
 }
 
 // The draw the reverse step of state v needs: Z_V in the quadratic branch,
