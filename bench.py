@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=0, help="override the time-step count of --profile-leg")
     ap.add_argument("--ckpt-every", type=int, default=0,
                     help="checkpoint interval of --profile-leg adjoint (0: the library's choice)")
-    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "lsm", "basket"],
+    ap.add_argument("--profile-leg", default="", choices=["", "fd", "price", "adjoint", "book", "book_price", "lsm",
+                                                          "basket"],
                     help="only run one call W + K times on the workload (for profilers); prints no JSON")
     return ap.parse_args()
 
@@ -172,8 +173,8 @@ def profiled_traffic(sha: str):
 def profiled_pipes(sha: str):
     """The path kernel's ncu pipe utilisation from the committed summary (or None)."""
     kv = _profile_values(sha)
-    keys = ("fma_pipe_cycles_active_pct_of_active", "xu_pipe_cycles_active_pct_of_elapsed",
-            "issue_active_pct_of_active")
+    keys = ("fmaheavy_pipe_cycles_active_pct_of_active", "fmalite_pipe_cycles_active_pct_of_active",
+            "xu_pipe_cycles_active_pct_of_active", "issue_active_pct_of_active")
     try:
         out = {k: float(kv[k]) for k in keys}
     except (KeyError, ValueError):
@@ -323,9 +324,10 @@ def run_profile_leg(args):
         "adjoint": lambda: simr.greeks_adjoint(w.model, K, w.is_put, w.steps, w.paths, w.seed,
                                                ckpt_every=args.ckpt_every),
     }
-    if args.profile_leg == "book":
+    if args.profile_leg in ("book", "book_price"):
         opts = workloads.book(n_options=128, paths_range=(16384, args.paths or 1 << 18))
-        fn = lambda: simr.batch(opts, seed=1, adjoint=True, autotune=False)  # noqa: E731
+        adj = args.profile_leg == "book"
+        fn = lambda: simr.batch(opts, seed=1, adjoint=adj, autotune=False)  # noqa: E731
     elif args.profile_leg == "basket":
         bm, C, wts, kb, bsteps, bpaths = workloads.basket()
         Kb = torch.as_tensor(kb, dtype=torch.float64, device="cuda")

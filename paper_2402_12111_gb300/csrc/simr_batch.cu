@@ -28,11 +28,15 @@ namespace {
 // together in packed FP32, or 1 at a time -- each lane then adds its two paths'
 // terms in the same order, so both give the same sums bit for bit); U, the
 // unrolling of the step-pair loop.
-// Adjoint books ask the register allocator for 768 resident threads per SM
-// (6 blocks of 128, 3 of 256: at most 85 registers), which it would otherwise
-// trade for registers it does not need.
+// Adjoint books ask the register allocator for 640 resident threads per SM (5
+// blocks of 128: at most 102 registers), which it would otherwise trade for
+// registers it does not need (measured on the 1,024-option book with paired
+// reverse steps: 311 ms, against 317 at 768 threads and 393 with no bound).
+#ifndef SIMR_BOOK_PAIRED
+#define SIMR_BOOK_PAIRED true  // reverse steps in pairs (one at a time: 351 ms against 311 for the book)
+#endif
 #ifndef SIMR_BOOK_ADJ_THREADS
-#define SIMR_BOOK_ADJ_THREADS 768
+#define SIMR_BOOK_ADJ_THREADS 640
 #endif
 template <bool ADJ, bool GSEG, int TPB, int PPT, int U>
 __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
@@ -71,12 +75,12 @@ __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) he
         // arrays of seg_rows rows (the largest over the book), so threads on
         // options with different checkpoint intervals never overlap
         if constexpr (GSEG)  // one segment: no checkpoints are read or written
-          path_adjoint_ppt<1, SegGlobal, false>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
+          path_adjoint_ppt<1, SegGlobal, SIMR_BOOK_PAIRED>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
                               SegGlobal{B.gseg, (long long)blockIdx.x * bd + tid, B.seg_rows,
                                         (long long)gridDim.x * bd},
                               x, comp, g);
         else
-          path_adjoint_ppt<1, SegShared, false>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
+          path_adjoint_ppt<1, SegShared, SIMR_BOOK_PAIRED>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
                               SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll

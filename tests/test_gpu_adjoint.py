@@ -76,13 +76,14 @@ def _strike_terms(model, K, is_put, x, g):
     return np.concatenate([(w / model["S0"])[:, None], w[:, None] * g, (w * model["T"])[:, None]], axis=1)
 
 
-def oracle_allowances(model, K, is_put, steps, paths, seed):
+def oracle_allowances(model, K, is_put, steps, paths, seed, option_index=0):
     """Oracle-only flags and allowances (see the module docstring): per strike the
     kink and decision allowances [n_K, 7], the kink flags [n_K, paths] and the
     decision flags [paths], plus the oracle's per-path (x_T, gradient)."""
     disc = math.exp(-model["r"] * model["T"])
-    xo, go = oracle.path_grad(model, steps, seed, 0, paths)
-    xf, gf, st, _, _ = oracle.path_grad_flip(model, steps, seed, 0, paths, DECISION_MARGIN)
+    xo, go = oracle.path_grad(model, steps, seed, 0, paths, option_index=option_index)
+    xf, gf, st, _, _ = oracle.path_grad_flip(model, steps, seed, 0, paths, DECISION_MARGIN,
+                                             option_index=option_index)
     dec = st >= 0
     dx = _kink_dx(model, steps)
     kink = np.abs(xo[None, :] - np.log(np.asarray(K)[:, None] / model["S0"])) < dx

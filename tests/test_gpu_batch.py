@@ -156,3 +156,41 @@ def test_batch_host_outputs_and_errors(simr, small_book):
     bad = [dict(small_book[0], K=-1.0)]
     with pytest.raises(simr.SimrError):
         simr.batch(bad)
+
+
+def test_book_at_full_size_matches_oracle_price_and_adjoint(simr):
+    # The 1,024-option heterogeneous book at its full sizes (steps log-uniform in
+    # [16, 512], paths in [16,384, 2^20]), prices and adjoint Greeks in one
+    # submission; options sampled across the book -- the most steps, the most
+    # paths, the most path-steps and nine more -- checked directly against the
+    # oracle's FP64 price and reverse-mode adjoint of the same counters
+    # (option_index = the option's position).  Tolerances: prices 1e-5 relative
+    # plus the oracle's flip allowance; each Greek 1e-4 relative plus 1e-4 of the
+    # price per unit of its parameter's own size (a floor for sensitivities near
+    # zero) plus the oracle-only kink and decision allowances of
+    # test_gpu_adjoint (many of the book's models violate the Feller condition).
+    from test_gpu_adjoint import oracle_allowances
+
+    book = workloads.book()
+    p, _, g = simr.batch(book, seed=1, adjoint=True)
+    p, g = p.cpu().numpy(), g.cpu().numpy()
+    sizes = np.array([o["steps"] * o["paths"] for o in book])
+    rng = np.random.default_rng(17)
+    pick = {int(np.argmax([o["steps"] for o in book])), int(np.argmax([o["paths"] for o in book])),
+            int(np.argmax(sizes))} | set(int(i) for i in rng.choice(len(book), 9, replace=False))
+    cols = ("S0", "v0", "kappa", "theta", "sigma", "rho", "r")
+    for i in sorted(pick):
+        o = book[i]
+        m, K = o["model"], np.array([o["K"]])
+        po, go = oracle.adjoint(m, K, o["is_put"], o["steps"], o["paths"], 1, option_index=i)
+        x, _, mg = oracle.terminal(m, o["steps"], 1, 0, o["paths"], option_index=i)
+        close = mg < 1e-4
+        Sx = m["S0"] * np.exp(x[close])
+        allow_p = math.exp(-m["r"] * m["T"]) * close.sum() * \
+            (o["K"] if o["is_put"] else max(Sx.max(initial=o["K"]) * 1.5, o["K"])) / o["paths"]
+        assert abs(p[i] - po[0]) <= 1e-5 * abs(po[0]) + allow_p + 1e-12, (i, p[i], po[0])
+        a_kink, a_dec, _, _, _, _ = oracle_allowances(m, K, o["is_put"], o["steps"], o["paths"], 1, option_index=i)
+        floor = 1e-4 * abs(po[0]) / np.array([max(abs(m[c]), 0.01) for c in cols])
+        tol = 1e-4 * np.abs(go[0]) + floor + a_kink[0] + a_dec[0]
+        assert np.all(np.abs(g[i] - go[0]) <= tol), (i, o["steps"], o["paths"], g[i], go[0], tol)
+
