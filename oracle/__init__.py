@@ -307,7 +307,8 @@ def path_grad_flip(model, steps: int, seed: int, path_begin: int, n_paths: int, 
     is below margin_below (flip_step -1 and the plain reverse-mode result elsewhere): the pathwise
     derivative a lower-precision evaluation computes when it decides that step the other way.
     flip_kind 1: the QE branch (psi against psi_c; value 1 quadratic); 2: the exponential branch's atom
-    (U_V against p; value 1 the logarithm's side)."""
+    (U_V against p; value 1 the logarithm's side).  Under QE-M an imposed branch is also the branch whose
+    ln M the step's martingale correction takes."""
     x = np.empty(n_paths)
     g = np.empty(n_paths * 5)
     st = np.empty(n_paths, dtype=np.int64)

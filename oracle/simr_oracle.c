@@ -257,7 +257,7 @@ void oracle_set_scheme(int scheme) { g_scheme = scheme; }
 
 /* ln M of the QE-M correction at state v (k: the 9 constants + theta); *ok = 0
  * where the correction does not exist.  m = 0 gives v' = 0, M = 1. */
-static double qem_log_m(double v, const double* k, int* ok) {
+static double qem_log_m_branch(double v, const double* k, int quad_forced, int* ok) {
   const double theta_ = k[9], E = k[1], c1 = k[2], c2 = k[3];
   const double A = k[6] + 0.5 * k[8];
   const double m = theta_ + (v - theta_) * E;
@@ -265,7 +265,7 @@ static double qem_log_m(double v, const double* k, int* ok) {
   *ok = 1;
   if (m <= 0.0) return 0.0;
   const double psi = s2 / (m * m);
-  if (psi <= PSI_C) {
+  if (quad_forced >= 0 ? quad_forced : psi <= PSI_C) {
     const double two_over_psi = 2.0 / psi;
     const double b2 = two_over_psi - 1.0 + sqrt(two_over_psi) * sqrt(two_over_psi - 1.0);
     const double a = m / (1.0 + b2);
@@ -282,6 +282,66 @@ static double qem_log_m(double v, const double* k, int* ok) {
     return 0.0;
   }
   return log(p + beta * (1.0 - p) / (beta - A));
+}
+
+/* ln M in the branch the variance step takes. */
+static double qem_log_m(double v, const double* k, int* ok) { return qem_log_m_branch(v, k, -1, ok); }
+
+/*
+ * The constant term of a log-spot step from state v (r dt included): K0 (k[4])
+ * under QE; under QE-M, where M exists, K0* + r dt = r dt - ln M - (K1 + K3/2) v
+ * with ln M in the branch quad_forced imposes (-1: the step's own).
+ */
+static double step_k0(const oracle_heston* m, const double* k, double v, int quad_forced) {
+  if (g_scheme != 1) return k[4];
+  int ok;
+  const double lnM = qem_log_m_branch(v, k, quad_forced, &ok);
+  if (!ok) return k[4];
+  return m->r * k[0] - lnM - (k[5] + 0.5 * k[7]) * v;
+}
+
+/*
+ * The adjoint of -ln M at the state with mean m and variance s2 (A = K2 + K4/2),
+ * where the correction exists: adds to *bar_A, *bar_m, *bar_s2 the derivatives of
+ * -ln M in the branch the variance step takes (quad_forced 1 or 0: the quadratic
+ * or the exponential branch imposed; -1: the step's own).
+
+ *   quadratic: ln M = A b^2 a / D - ln(D)/2, D = 1 - 2 A a, a = m / (1 + b^2),
+ *              b^2 = t - 1 + sqrt(t (t - 1)), t = 2 m^2 / s2;
+ *   exponential: ln M = ln((1 - q) + beta q / (beta - A)), q = 1 - p = 2 m^2 / (m^2 + s2),
+ *              beta = q / m.
+ */
+static void qem_log_m_adjoint(double m, double s2, double A, int quad_forced, double* bar_A, double* bar_m,
+                              double* bar_s2) {
+  if (m <= 0.0) return;
+  const double psi = s2 / (m * m);
+  if (quad_forced >= 0 ? quad_forced : psi <= PSI_C) {
+    const double t = 2.0 / psi;
+    const double root = sqrt(t) * sqrt(t - 1.0);
+    const double b2 = t - 1.0 + root;
+    const double a = m / (1.0 + b2);
+    const double D = 1.0 - 2.0 * A * a;
+    const double dA = b2 * a / D + A * b2 * a * 2.0 * a / (D * D) + a / D;
+    const double da = A * b2 / D + A * b2 * a * 2.0 * A / (D * D) + A / D;
+    const double db2 = A * a / D;
+    const double ba = -da;                                  /* bar a of -ln M */
+    const double bb2 = -db2 + ba * (-m / ((1.0 + b2) * (1.0 + b2)));
+    const double bt = bb2 * (1.0 + (2.0 * t - 1.0) / (2.0 * root));
+    *bar_A += -dA;
+    *bar_m += ba / (1.0 + b2) + bt * 4.0 * m / s2;
+    *bar_s2 += -bt * t / s2;
+    return;
+  }
+  const double den = m * m + s2;
+  const double q = 2.0 * m * m / den;
+  const double beta = q / m;
+  const double M = (1.0 - q) + beta * q / (beta - A);
+  const double bM = -1.0 / M;
+  const double bbeta = bM * (-A * q / ((beta - A) * (beta - A)));
+  const double bq = bM * (-1.0 + beta / (beta - A)) + bbeta / m;
+  *bar_A += bM * beta * q / ((beta - A) * (beta - A));
+  *bar_m += bbeta * (-q / (m * m)) + bq * 4.0 * m * s2 / (den * den);
+  *bar_s2 += bq * (-2.0 * m * m / (den * den));
 }
 
 /* Constants array used by the step: the 9 QE constants followed by theta. */
@@ -311,12 +371,7 @@ static void simulate_path_rec(const oracle_heston* m, const double* k, uint32_t 
     if (cd < min_cond) min_cond = cd;
     /* LogPricePathQE: x += K0 + K1 v + K2 v' + sqrt(K3 v + K4 v') Z_X */
     double z_x = oracle_norminv(u_x);
-    double k0 = k[4];
-    if (g_scheme == 1) { /* QE-M: r dt + K0* in place of K0 */
-      int ok;
-      const double lnM = qem_log_m(v, k, &ok);
-      if (ok) k0 = m->r * k[0] - lnM - (k[5] + 0.5 * k[7]) * v;
-    }
+    const double k0 = step_k0(m, k, v, -1);
     x += k0 + k[5] * v + k[6] * v_next + sqrt(k[7] * v + k[8] * v_next) * z_x;
     v = v_next;
     if (every && (n + 1) % every == 0) {
@@ -488,12 +543,7 @@ int oracle_basket_terminal(const oracle_heston* models, int n_assets, const doub
 double oracle_step_exp_mean(const oracle_heston* m, uint32_t steps, double v) {
   double k[10];
   step_constants(m, steps, k);
-  double k0 = k[4] - m->r * k[0];
-  if (g_scheme == 1) {
-    int ok;
-    const double lnM = qem_log_m(v, k, &ok);
-    if (ok) k0 = -lnM - (k[5] + 0.5 * k[7]) * v;
-  }
+  const double k0 = step_k0(m, k, v, -1) - m->r * k[0];
   const int64_t n = (int64_t)1 << 23;
   double sum = 0.0;
   for (int64_t j = 0; j < n; ++j) {
@@ -682,7 +732,8 @@ static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_
     oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
     double vn = ((int64_t)n == f_step) ? qe_step_forced(v, u_v, k, f_kind, f_value)
                                        : oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
-    x += k[4] + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
+    const double k0 = step_k0(m, k, v, ((int64_t)n == f_step && f_kind == 1) ? f_value : -1);
+    x += k0 + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
     v = vn;
     v_hist[n + 1] = v;
   }
@@ -703,8 +754,6 @@ static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_
     double dsq = (w > 0.0) ? z_x / (2.0 * sqrt(w)) : 0.0; /* d sqrt(w) z / dw */
     double bar_vcur = K1 + K3 * dsq;
     bar_vnext += K2 + K4 * dsq;
-    bar_K0 += 1.0;
-    bar_K1 += vc;
     bar_K2 += vn;
     bar_K3 += vc * dsq;
     bar_K4 += vn * dsq;
@@ -712,6 +761,23 @@ static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_
     double mm = th + (vc - th) * E;
     double s2 = vc * c1 + c2;
     double bar_m = 0.0, bar_s2 = 0.0;
+    int qem_ok = 0;
+    const int quad_forced = (n == f_step && f_kind == 1) ? f_value : -1;
+    if (g_scheme == 1) (void)qem_log_m_branch(vc, k, quad_forced, &qem_ok);
+    if (qem_ok) {
+      /* QE-M: K0 + K1 v is replaced by r dt - ln M(v) - (K1 + K3/2) v + K1 v, so K0 and
+       * K1 drop out, K3 gains -v/2 and v gains -(K1 + K3/2); ln M adds its own adjoint
+       * (bar ln M = -1) to A = K2 + K4/2 and to m and s^2 (qem_log_m_adjoint). */
+      bar_vcur -= K1 + 0.5 * K3;
+      bar_K3 -= 0.5 * vc;
+      double bar_A = 0.0;
+      qem_log_m_adjoint(mm, s2, K2 + 0.5 * K4, quad_forced, &bar_A, &bar_m, &bar_s2);
+      bar_K2 += bar_A;
+      bar_K4 += 0.5 * bar_A;
+    } else {
+      bar_K0 += 1.0;
+      bar_K1 += vc;
+    }
     if (mm > 0.0) {
       double psi = s2 / (mm * mm);
       int quad = psi <= PSI_C;
@@ -727,8 +793,8 @@ static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_
         double bar_b = bar_vnext * 2.0 * a * (b + zv);
         double bar_b2 = bar_b / (2.0 * b) - bar_a * mm / ((1.0 + b2) * (1.0 + b2));
         double bar_t = bar_b2 * (1.0 + (2.0 * t - 1.0) / (2.0 * root));
-        bar_m = bar_a / (1.0 + b2) + bar_t * 4.0 * mm / s2;
-        bar_s2 = -bar_t * t / s2;
+        bar_m += bar_a / (1.0 + b2) + bar_t * 4.0 * mm / s2;
+        bar_s2 += -bar_t * t / s2;
       } else {
         double p = (psi - 1.0) / (psi + 1.0);
         int pos = u_v > p;
@@ -741,8 +807,8 @@ static void path_adjoint_forced(const oracle_heston* m, const double* k, uint32_
           double den = (mm * mm + s2) * (mm * mm + s2);
           double dq_dm = 4.0 * mm * s2 / den;
           double dq_ds2 = -2.0 * mm * mm / den;
-          bar_m = bar_vnext * (dv_dm + dv_dq * dq_dm);
-          bar_s2 = bar_vnext * dv_dq * dq_ds2;
+          bar_m += bar_vnext * (dv_dm + dv_dq * dq_dm);
+          bar_s2 += bar_vnext * dv_dq * dq_ds2;
         }
       }
     }
@@ -911,7 +977,8 @@ double oracle_terminal_forced(const oracle_heston* m, uint32_t steps, uint64_t s
     oracle_step_uniforms(seed, option_index, path, n, &u_v, &u_x);
     double vn = ((int64_t)n == f_step) ? qe_step_forced(v, u_v, k, f_kind, f_value)
                                        : oracle_qe_variance_step(v, u_v, k, &br, &mg, NULL);
-    x += k[4] + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
+    const double k0 = step_k0(m, k, v, ((int64_t)n == f_step && f_kind == 1) ? f_value : -1);
+    x += k0 + k[5] * v + k[6] * vn + sqrt(k[7] * v + k[8] * vn) * oracle_norminv(u_x);
     v = vn;
   }
   return x;
@@ -1064,6 +1131,10 @@ int oracle_path_grad_forward(const oracle_heston* m, uint32_t steps, uint64_t se
       dual5 mm = dadd(th, dmul(dsub(v, th), E));
       dual5 s2 = dadd(dmul(v, c1), c2);
       dual5 vn;
+      /* QE-M: ln M of this step's branch (Andersen's martingale correction), where it exists */
+      const dual5 Aq = dadd(K2, dscale(K4, 0.5));
+      dual5 lnM = dconst(0.0);
+      int ok = 1;
       if (mm.v <= 0.0) {
         vn = dconst(0.0);
       } else {
@@ -1074,18 +1145,26 @@ int oracle_path_grad_forward(const oracle_heston* m, uint32_t steps, uint64_t se
           dual5 a = ddiv(mm, dadd(one, b2));
           dual5 bz = dadd(dsqrt(b2), dconst(oracle_norminv(u_v)));
           vn = dmul(a, dmul(bz, bz));
+          dual5 D = dsub(one, dscale(dmul(Aq, a), 2.0));
+          ok = D.v > 0.0;
+          if (ok) lnM = dsub(ddiv(dmul(dmul(Aq, b2), a), D), dscale(dlog(D), 0.5));
         } else {
           dual5 p = ddiv(dsub(psi, one), dadd(psi, one));
+          dual5 beta = ddiv(dsub(one, p), mm);
           if (u_v <= p.v) {
             vn = dconst(0.0);
           } else {
-            dual5 beta = ddiv(dsub(one, p), mm);
             vn = ddiv(dlog(ddiv(dsub(one, p), dconst(1.0 - u_v))), beta);
           }
+          ok = Aq.v < beta.v;
+          if (ok) lnM = dlog(dadd(p, ddiv(dmul(beta, dsub(one, p)), dsub(beta, Aq))));
         }
       }
+      dual5 k0 = K0;
+      if (g_scheme == 1 && ok)
+        k0 = dsub(dsub(dconst(m->r * dt), lnM), dmul(dadd(K1, dscale(K3, 0.5)), v));
       dual5 w = dadd(dmul(K3, v), dmul(K4, vn));
-      dual5 inc = dadd(dadd(K0, dmul(K1, v)), dmul(K2, vn));
+      dual5 inc = dadd(dadd(k0, dmul(K1, v)), dmul(K2, vn));
       inc = dadd(inc, dscale(dsqrt(w), oracle_norminv(u_x)));
       x = dadd(x, inc);
       v = vn;

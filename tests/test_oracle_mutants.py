@@ -85,8 +85,8 @@ C_MISTAKES = [
      _log_spot_pin()),
     ("log_spot_variance_drops_vnext", "sqrt(k[7] * v + k[8] * v_next) * z_x", "sqrt(k[7] * v) * z_x",
      _log_spot_pin()),
-    ("log_spot_normal_from_variance_uniform", "double z_x = oracle_norminv(u_x);\n    double k0",
-     "double z_x = oracle_norminv(u_v);\n    double k0", _price_pin(False)),
+    ("log_spot_normal_from_variance_uniform", "double z_x = oracle_norminv(u_x);\n    const double k0",
+     "double z_x = oracle_norminv(u_v);\n    const double k0", _price_pin(False)),
     # payoff, discounting, standard error
     ("payoff_call_put_swapped", "double d = is_put ? (K - s_T) : (s_T - K);",
      "double d = is_put ? (s_T - K) : (K - s_T);", pins.test_put_call_parity_on_common_paths),
@@ -121,19 +121,33 @@ C_MISTAKES = [
     ("adjoint_delta_weight", "s[0] += w / m->S0;", "s[0] += w;", pins.test_adjoint_matches_fd_and_closed_form_delta),
     # the decision taken the other way: the reverse sweep must impose it where the forward did
     ("flip_reverse_keeps_natural_branch", "if (n == f_step && f_kind == 1) quad = f_value;", "",
-     pins.test_flipped_decision_gradient_matches_finite_differences),
+     lambda: pins.test_flipped_decision_gradient_matches_finite_differences("qe")),
     ("flip_forward_exponential_drops_log", "const double vn = log((1.0 - pp) / (1.0 - u_v)) * mean / (1.0 - pp);",
-     "const double vn = 0.0;", pins.test_flipped_decision_gradient_matches_finite_differences),
+     "const double vn = 0.0;", lambda: pins.test_flipped_decision_gradient_matches_finite_differences("qe")),
+    # QE-M reverse mode: ln M's adjoint in the quadratic branch (b^2 term), in the
+    # exponential branch (its A term's sign), and K3's share of the corrected K0*
+    ("qem_adjoint_quadratic_b2", "const double db2 = A * a / D;", "const double db2 = A / D;",
+     lambda: qem_pins.test_qem_reverse_mode_matches_forward_mode_duals(qem_pins.BASE)),
+    ("qem_adjoint_exponential_A_sign", "*bar_A += bM * beta * q / ((beta - A) * (beta - A));",
+     "*bar_A -= bM * beta * q / ((beta - A) * (beta - A));",
+     lambda: qem_pins.test_qem_reverse_mode_matches_forward_mode_duals(qem_pins.HARD_Q)),
+    ("qem_adjoint_drops_K3_share", "bar_K3 -= 0.5 * vc;", "",
+     lambda: qem_pins.test_qem_reverse_mode_matches_forward_mode_duals(qem_pins.BASE)),
+    # QE-M: the flipped step's reverse mode takes ln M's adjoint in the natural branch
+    ("flip_qem_reverse_natural_log_m_branch", "qem_log_m_adjoint(mm, s2, K2 + 0.5 * K4, quad_forced,",
+     "qem_log_m_adjoint(mm, s2, K2 + 0.5 * K4, -1,",
+     lambda: pins.test_flipped_decision_gradient_matches_finite_differences("qem")),
     ("adjoint_drops_rate_discount", "grad[j * 7 + 6] -= m->T * price[j];", "",
      pins.test_adjoint_matches_fd_and_closed_form_delta),
     # QE-M martingale correction
     ("qem_quadratic_log_sign", "- 0.5 * log(1.0 - 2.0 * A * a);", "+ 0.5 * log(1.0 - 2.0 * A * a);",
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.BASE)),
-    ("qem_exponential_branch", "(beta - A));", "(beta + A));",  # psi > 1.5 occurs on the coarse model
+    ("qem_exponential_branch", "return log(p + beta * (1.0 - p) / (beta - A));",
+     "return log(p + beta * (1.0 - p) / (beta + A));",  # psi > 1.5 occurs on the coarse model
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.WILD)),
     ("qem_A_definition", "const double A = k[6] + 0.5 * k[8];", "const double A = k[6] + k[8];",
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.BASE)),
-    ("qem_drops_rate", "if (ok) k0 = m->r * k[0] - lnM", "if (ok) k0 = -lnM",
+    ("qem_drops_rate", "return m->r * k[0] - lnM", "return -lnM",
      qem_pins.test_multi_step_martingale_within_monte_carlo_error),
     # correlated baskets
     ("basket_cholesky_transposed", "z += Lc[a * A + j] * eps[j];", "z += Lc[j * A + a] * eps[j];",

@@ -404,7 +404,15 @@ def test_paper_table2_ops_per_cycle():
 HARD_FLIP = dict(S0=100.0, r=0.05, T=1.0, v0=0.09, kappa=1.0, theta=0.04, sigma=0.9, rho=-0.3)
 
 
-def test_flipped_decision_gradient_matches_finite_differences():
+# Under QE-M the two branches' ln M agree to second order in A (both match the
+# step's mean and variance), so the branch ln M takes shows in the gradient only
+# with a large |A| and coarse steps: rho = -0.9 over 8 steps (up to 2.4e-3 of a
+# path's largest derivative there, against 6e-5 at rho = -0.3).
+FLIP_CASES = {"qe": (HARD_FLIP, 64, 4096), "qem": (dict(HARD_FLIP, rho=-0.9), 8, 16384)}
+
+
+@pytest.mark.parametrize("scheme", ["qe", "qem"])
+def test_flipped_decision_gradient_matches_finite_differences(scheme):
     # oracle.path_grad_flip: the reverse-mode gradient of the path whose decision
     # closest to its threshold is taken the other way.  Central differences of that
     # forced path's x_T (oracle.terminal_forced, the decision imposed at the same
@@ -413,10 +421,16 @@ def test_flipped_decision_gradient_matches_finite_differences():
     # atom (v' = 0) is forced to the logarithm's side keeps v' = 0 there (the
     # continuation below the boundary is negative) and takes that side's
     # one-sided derivative, which no difference of the held value can show: those
-    # flips are left out of the check.
-    steps, seed, n = 64, 5, 4096
-    x, g, st, kd, fv = oracle.path_grad_flip(HARD_FLIP, steps, seed, 0, n, 1e-3)
-    x0, g0 = oracle.path_grad(HARD_FLIP, steps, seed, 0, n)
+    # flips are left out of the check.  Under QE-M a flipped branch also takes the
+    # other branch's ln M in the step's correction, on both sides of the check.
+    with oracle.scheme(scheme):
+        _check_flipped_decision_gradient(*FLIP_CASES[scheme])
+
+
+def _check_flipped_decision_gradient(model, steps, n):
+    seed = 5
+    x, g, st, kd, fv = oracle.path_grad_flip(model, steps, seed, 0, n, 1e-3)
+    x0, g0 = oracle.path_grad(model, steps, seed, 0, n)
     nf = st < 0
     assert 0.01 < (~nf).mean() < 0.2 and set(np.unique(kd[~nf])) <= {1, 2}
     np.testing.assert_array_equal(g[nf], g0[nf])
@@ -424,18 +438,20 @@ def test_flipped_decision_gradient_matches_finite_differences():
     assert np.all(np.isfinite(g)) and np.all(np.isfinite(x))
     fields = ("v0", "kappa", "theta", "sigma", "rho")
     checked = {1: 0, 2: 0}
-    for i in np.flatnonzero(~nf)[:120]:
+    # every branch flip (up to 40) and the first 80 atom flips
+    pick = np.concatenate([np.flatnonzero(~nf & (kd == 1))[:40], np.flatnonzero(~nf & (kd == 2))[:80]])
+    for i in pick:
         i = int(i)
         value = int(fv[i])
-        assert oracle.terminal_forced(HARD_FLIP, steps, seed, i, int(st[i]), int(kd[i]), value) == x[i]
+        assert oracle.terminal_forced(model, steps, seed, i, int(st[i]), int(kd[i]), value) == x[i]
         if kd[i] == 2 and value == 1:
             continue  # the atom forced to the logarithm's side: held at v' = 0
         fd, clean = np.empty(5), True
         for j, f in enumerate(fields):
             vals = []
             for h in (1e-6, 5e-7):
-                hh = h * max(abs(HARD_FLIP[f]), 1.0)
-                up, dn = dict(HARD_FLIP), dict(HARD_FLIP)
+                hh = h * max(abs(model[f]), 1.0)
+                up, dn = dict(model), dict(model)
                 up[f] += hh
                 dn[f] -= hh
                 xu = oracle.terminal_forced(up, steps, seed, i, int(st[i]), int(kd[i]), value)

@@ -65,3 +65,41 @@ def test_multi_step_martingale_within_monte_carlo_error():
     disc = np.exp(-WILD["r"] * WILD["T"]) * WILD["S0"] * np.exp(x)
     se = disc.std(ddof=1) / math.sqrt(n)
     assert abs(disc.mean() - WILD["S0"]) < 3 * se
+
+
+HARD_Q = dict(S0=100.0, r=0.05, T=1.0, v0=0.09, kappa=1.0, theta=0.04, sigma=0.9, rho=-0.3)
+
+
+@pytest.mark.parametrize("model", [BASE, WILD, HARD_Q], ids=["base", "wild", "hard"])
+def test_qem_reverse_mode_matches_forward_mode_duals(model):
+    # the reverse mode's adjoint of ln M (oracle C: qem_log_m_adjoint) against the
+    # dual-number forward mode, which differentiates ln M's formula as written --
+    # independent code; and the reverse sweep's x_T is the QE-M simulation's
+    with oracle.scheme("qem"):
+        xr, gr = oracle.path_grad(model, 48, 5, 0, 4096, mode="reverse")
+        xf, gf = oracle.path_grad(model, 48, 5, 0, 4096, mode="forward")
+        xs, _, _ = oracle.terminal(model, 48, 5, 0, 4096)
+    np.testing.assert_allclose(xr, xf, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(xr, xs, rtol=0, atol=1e-12)
+    scale = np.maximum(np.abs(gf), 1e-3)
+    assert np.max(np.abs(gr - gf) / scale) < 1e-9
+    # and the correction is in there: the QE-M gradient differs from QE's
+    xq, gq = oracle.path_grad(model, 48, 5, 0, 4096, mode="reverse")
+    assert np.max(np.abs(gq - gr)) > 1e-6
+
+
+def test_qem_adjoint_matches_its_finite_differences():
+    # pathwise Greeks of the QE-M estimator against central differences of the same
+    # estimator (common draws, relative bump 1e-5): only the QE map's rare branch
+    # switches separate them, as for plain QE
+    P = 1 << 17
+    K = np.array([90.0, 100.0, 110.0])
+    mask = oracle.G_DELTA | oracle.G_VEGA | oracle.G_RHO | oracle.G_KAPPA | oracle.G_LRVAR | oracle.G_VOLVOL | \
+        oracle.G_CORR
+    with oracle.scheme("qem"):
+        pa, ga = oracle.adjoint(BASE, K, False, 64, P, 13)
+        pf, gf = oracle.greeks_fd(BASE, K, False, 64, P, 13, 1e-5, mask)
+    np.testing.assert_allclose(pa, pf, rtol=1e-13)
+    for ca, cf in [(0, 0), (1, 1), (6, 2), (2, 3), (3, 4), (4, 5), (5, 6)]:
+        tol = 2e-3 * max(abs(gf[:, cf]).max(), 1.0)
+        np.testing.assert_allclose(ga[:, ca], gf[:, cf], rtol=2e-2, atol=tol)
