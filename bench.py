@@ -558,25 +558,28 @@ def run_native(args):
                 times.append((a, b))
             torch.cuda.synchronize()
             adj[name] = sum(x.elapsed_time(y) for x, y in times) / reps
-        # the same pricing pass under QE-M (Andersen's martingale correction)
+        # the pricing pass, the adjoint and the 7-Greek bump-and-revalue under QE-M
+        # (Andersen's martingale correction)
         simr.set_scheme("qem", dev.index or 0)
         try:
-            for _ in range(3):
-                legs["price_ms"]()
-                flush.zero_()
-            times = []
-            for _ in range(reps):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                legs["price_ms"]()
-                b.record(stream)
-                flush.zero_()
-                times.append((a, b))
-            torch.cuda.synchronize()
-            adj["price_qem_ms"] = sum(x.elapsed_time(y) for x, y in times) / reps
+            for name in ("price_ms", "adjoint_ms", "fd7_ms"):
+                for _ in range(3):
+                    legs[name]()
+                    flush.zero_()
+                times = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    legs[name]()
+                    b.record(stream)
+                    flush.zero_()
+                    times.append((a, b))
+                torch.cuda.synchronize()
+                adj[name.replace("_ms", "_qem_ms")] = sum(x.elapsed_time(y) for x, y in times) / reps
         finally:
             simr.set_scheme("qe", dev.index or 0)
         adj["qem_cost_vs_qe"] = adj["price_qem_ms"] / adj["price_ms"]
+        adj["qem_adjoint_cost_vs_price"] = adj["adjoint_qem_ms"] / adj["price_qem_ms"]
         adj["speedup_vs_fd"] = adj["fd7_ms"] / adj["adjoint_ms"]
         adj["cost_vs_price"] = adj["adjoint_ms"] / adj["price_ms"]
         adj["k16_cost_vs_price"] = adj["adjoint_k16_ms"] / adj["price_ms"]

@@ -308,11 +308,16 @@ SIMR_API int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_a
  *                    K0* = -ln M - (K1 + K3/2) v, M = E[exp(A v(t+dt)) | v(t)],
  *                    A = K2 + K4/2 (the plain step where M does not exist), so
  *                    that the discounted spot is an exact martingale of the scheme.
- * QE-M applies to simr_price, simr_paths_terminal, simr_lsm_price and to
- * simr_greeks_fd / simr_path_sums with Greeks read off the base path (delta,
- * gamma, rho); the re-simulated Greeks, the adjoint kernels and the batched book
- * return SIMR_EUNSUPPORTED under it.  simr_price_noalloc is always QE.
- * SIMR_EINVAL for an unknown scheme.
+ * QE-M applies to simr_price, simr_paths_terminal, simr_lsm_price,
+ * simr_greeks_fd / simr_path_sums (every Greek: each re-simulated scenario takes
+ * the QE-M step on its own moments and A, the deltas of its constants to the base
+ * scenario's entering as separate sums as under QE, step 0 on FP64 first-step
+ * constants r dt - qa (v0 + m0) - lam(v0)), simr_greeks_adjoint /
+ * simr_paths_adjoint (the reverse step also differentiates lam = ln M - A m and
+ * the constants qa = dt (1 - rho^2)/4, K2 and A) and simr_batch_submit (price
+ * books then have two kernel shapes, SIMR_BATCH_VARIANT 0 and 1: two paths per
+ * thread, no unrolling).  simr_basket_price returns SIMR_EUNSUPPORTED under it;
+ * simr_price_noalloc is always QE.  SIMR_EINVAL for an unknown scheme.
  */
 SIMR_API int simr_set_scheme(simr_ctx* ctx, int scheme);
 

@@ -100,7 +100,9 @@ __device__ __forceinline__ void strike_tile_terms(bool put, float K, const float
 // GSEG: the segment buffers in global memory, [3 k][grid threads] (for a
 // segment too long for shared memory, in particular one segment of the whole
 // path: no forward pass).
-template <int TILE, int PPT, bool RACC, bool GSEG>
+// QEM: the QE-M log-spot step (the launch's scheme 1), differentiated one step
+// at a time.
+template <int TILE, int PPT, bool RACC, bool GSEG, bool QEM>
 __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB_SMEM) heston_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                              const __grid_constant__ AdjConst A,
                                                              const double* __restrict__ strikes, AdjOutputs out,
@@ -154,12 +156,12 @@ __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB
     }
     float x[PPT], comp[PPT], g[PPT][5], S[PPT];
     if constexpr (GSEG)
-      path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
-                            SegGlobal{gseg, (long long)blockIdx.x * bd + tid, A.ckpt_every, (long long)ck_stride},
-                            x, comp, g);
+      path_adjoint_ppt<PPT, SegGlobal, true, QEM>(
+          L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
+          SegGlobal{gseg, (long long)blockIdx.x * bd + tid, A.ckpt_every, (long long)ck_stride}, x, comp, g, L.qm);
     else
-      path_adjoint_ppt<PPT>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
-                            SegShared{sbuf, A.ckpt_every}, x, comp, g);
+      path_adjoint_ppt<PPT, SegShared, true, QEM>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ck, ck_stride,
+                                                  SegShared{sbuf, A.ckpt_every}, x, comp, g, L.qm);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) S[j] = terminal_spot(L.S0, x[j], comp[j]);
 
@@ -244,6 +246,7 @@ __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB
 }
 
 // Per-path output: x_T and g = d x_T / d(v0, kappa, theta, sigma, rho).
+template <bool QEM>
 __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_constant__ PathLaunch L,
                                                                    const __grid_constant__ AdjConst A,
                                                                    float* __restrict__ x_T, float* __restrict__ grad) {
@@ -254,8 +257,8 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
   if (i >= L.path_count) return;  // no block-wide synchronisation below
   float x[1], comp[1], g[1][5];
   const uint64_t pth[1] = {L.path_begin + i};
-  path_adjoint_ppt<1>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt + tid, bd,
-                      SegShared{ckpt + (A.n_seg - 1) * bd, A.ckpt_every}, x, comp, g);
+  path_adjoint_ppt<1, SegShared, true, QEM>(L.sc[0], A, L.steps, L.option_index, L.rk, pth, ckpt + tid, bd,
+                                            SegShared{ckpt + (A.n_seg - 1) * bd, A.ckpt_every}, x, comp, g, L.qm);
   x_T[i] = x[0] - comp[0];
 #pragma unroll
   for (int j = 0; j < 5; ++j) grad[i * 5 + j] = g[0][j];
@@ -263,12 +266,12 @@ __global__ void __launch_bounds__(128) heston_paths_adjoint_kernel(const __grid_
 
 // The grid of the per-strike kernel variant (resident blocks, at most what the
 // paths need) and its dynamic shared memory.
-template <int TILE, bool RACC, bool GSEG>
+template <int TILE, bool RACC, bool GSEG, bool QEM>
 cudaError_t adjoint_grid_t(const PathLaunch& L, const AdjConst& A, int num_sms, uint64_t* grid, size_t* smem) {
   constexpr int PPT = SIMR_ADJ_PPT;
   const int tpb = 128, warps = tpb / kWarp;
   *smem = adjoint_smem_bytes_t(L, A, tpb, PPT, RACC, GSEG);
-  auto kern = heston_adjoint_kernel<TILE, PPT, RACC, GSEG>;
+  auto kern = heston_adjoint_kernel<TILE, PPT, RACC, GSEG, QEM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -283,7 +286,7 @@ cudaError_t adjoint_grid_t(const PathLaunch& L, const AdjConst& A, int num_sms, 
   return cudaSuccess;
 }
 
-template <int TILE, bool RACC, bool GSEG>
+template <int TILE, bool RACC, bool GSEG, bool QEM>
 cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                              const Scratch& s, int num_sms, cudaStream_t stream) {
   constexpr int PPT = SIMR_ADJ_PPT;
@@ -291,12 +294,12 @@ cudaError_t launch_adjoint_t(const PathLaunch& L, const AdjConst& A, const doubl
   const size_t row = (size_t)kAdjAcc * L.nk_pad;
   uint64_t grid = 0;
   size_t smem = 0;
-  cudaError_t e = adjoint_grid_t<TILE, RACC, GSEG>(L, A, num_sms, &grid, &smem);
+  cudaError_t e = adjoint_grid_t<TILE, RACC, GSEG, QEM>(L, A, num_sms, &grid, &smem);
   if (e != cudaSuccess) return e;
   if ((size_t)grid * row > s.partial_doubles) return cudaErrorMemoryAllocation;
   if ((size_t)grid * tpb * adjoint_ckpt_floats(A, PPT) > s.ckpt_floats) return cudaErrorMemoryAllocation;
   if (GSEG && (size_t)grid * tpb * adjoint_seg_floats(A, PPT) > s.gseg_floats) return cudaErrorMemoryAllocation;
-  heston_adjoint_kernel<TILE, PPT, RACC, GSEG>
+  heston_adjoint_kernel<TILE, PPT, RACC, GSEG, QEM>
       <<<(unsigned)grid, tpb, smem, stream>>>(L, A, strikes, out, s.partials, s.ticket, s.ckpt, s.gseg);
   return cudaGetLastError();
 }
@@ -309,6 +312,19 @@ bool adjoint_gseg(const PathLaunch& L, const AdjConst& A) {
   return adjoint_smem_bytes_t(L, A, 128, SIMR_ADJ_PPT, L.nk_pad == 32) > kAdjMaxSmem;
 }
 
+template <bool QEM>
+cudaError_t launch_adjoint_s(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
+                             const Scratch& s, int num_sms, cudaStream_t stream) {
+  if (adjoint_gseg(L, A)) {
+    if (L.nk_pad == 1) return launch_adjoint_t<1, false, true, QEM>(L, A, strikes, out, s, num_sms, stream);
+    if (L.nk_pad == 32) return launch_adjoint_t<32, true, true, QEM>(L, A, strikes, out, s, num_sms, stream);
+    return launch_adjoint_t<32, false, true, QEM>(L, A, strikes, out, s, num_sms, stream);
+  }
+  if (L.nk_pad == 1) return launch_adjoint_t<1, false, false, QEM>(L, A, strikes, out, s, num_sms, stream);
+  if (L.nk_pad == 32) return launch_adjoint_t<32, true, false, QEM>(L, A, strikes, out, s, num_sms, stream);
+  return launch_adjoint_t<32, false, false, QEM>(L, A, strikes, out, s, num_sms, stream);
+}
+
 }  // namespace
 
 size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
@@ -318,9 +334,9 @@ size_t adjoint_scratch_doubles(const PathLaunch& L, int num_sms) {
 cudaError_t adjoint_max_ckpt_every(const PathLaunch& L, int steps_cap, int* k_max) {
   // the kernel variant launch_adjoint picks for this strike count
   const bool racc = L.nk_pad == 32;
-  const void* kern = L.nk_pad == 1 ? (const void*)heston_adjoint_kernel<1, SIMR_ADJ_PPT, false, false>
-                     : racc      ? (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, true, false>
-                                 : (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, false, false>;
+  const void* kern = L.nk_pad == 1 ? (const void*)heston_adjoint_kernel<1, SIMR_ADJ_PPT, false, false, false>
+                     : racc      ? (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, true, false, false>
+                                 : (const void*)heston_adjoint_kernel<32, SIMR_ADJ_PPT, false, false, false>;
   auto blocks = [&](int k, int* n) -> cudaError_t {
     AdjConst A{};
     A.ckpt_every = k;
@@ -356,9 +372,16 @@ cudaError_t adjoint_gseg_floats(const PathLaunch& L, const AdjConst& A, int num_
   if (!adjoint_gseg(L, A)) return cudaSuccess;
   uint64_t grid = 0;
   size_t smem = 0;
-  cudaError_t e = L.nk_pad == 1    ? adjoint_grid_t<1, false, true>(L, A, num_sms, &grid, &smem)
-                  : L.nk_pad == 32 ? adjoint_grid_t<32, true, true>(L, A, num_sms, &grid, &smem)
-                                   : adjoint_grid_t<32, false, true>(L, A, num_sms, &grid, &smem);
+  cudaError_t e = L.nk_pad == 1    ? adjoint_grid_t<1, false, true, false>(L, A, num_sms, &grid, &smem)
+                  : L.nk_pad == 32 ? adjoint_grid_t<32, true, true, false>(L, A, num_sms, &grid, &smem)
+                                   : adjoint_grid_t<32, false, true, false>(L, A, num_sms, &grid, &smem);
+  if (e == cudaSuccess && L.scheme == 1) {  // the QE-M kernel's occupancy may differ: take the larger grid
+    uint64_t grid_q = 0;
+    e = L.nk_pad == 1    ? adjoint_grid_t<1, false, true, true>(L, A, num_sms, &grid_q, &smem)
+        : L.nk_pad == 32 ? adjoint_grid_t<32, true, true, true>(L, A, num_sms, &grid_q, &smem)
+                         : adjoint_grid_t<32, false, true, true>(L, A, num_sms, &grid_q, &smem);
+    if (grid_q > grid) grid = grid_q;
+  }
   if (e == cudaSuccess) *floats = (size_t)grid * 128 * adjoint_seg_floats(A, SIMR_ADJ_PPT);
   return e;
 }
@@ -371,24 +394,18 @@ size_t adjoint_ckpt_scratch_floats(const AdjConst& A, int num_sms) {
 cudaError_t launch_paths_adjoint(const PathLaunch& L, const AdjConst& A, float* x_T, float* grad, cudaStream_t stream) {
   const int tpb = 128;
   const size_t smem = (size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * tpb * sizeof(float);
-  cudaError_t e =
-      cudaFuncSetAttribute(heston_paths_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = L.scheme == 1 ? heston_paths_adjoint_kernel<true> : heston_paths_adjoint_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t grid = (L.path_count + tpb - 1) / tpb;
-  heston_paths_adjoint_kernel<<<(unsigned)grid, tpb, smem, stream>>>(L, A, x_T, grad);
+  kern<<<(unsigned)grid, tpb, smem, stream>>>(L, A, x_T, grad);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const PathLaunch& L, const AdjConst& A, const double* strikes, const AdjOutputs& out,
                            const Scratch& s, int num_sms, cudaStream_t stream) {
-  if (adjoint_gseg(L, A)) {
-    if (L.nk_pad == 1) return launch_adjoint_t<1, false, true>(L, A, strikes, out, s, num_sms, stream);
-    if (L.nk_pad == 32) return launch_adjoint_t<32, true, true>(L, A, strikes, out, s, num_sms, stream);
-    return launch_adjoint_t<32, false, true>(L, A, strikes, out, s, num_sms, stream);
-  }
-  if (L.nk_pad == 1) return launch_adjoint_t<1, false, false>(L, A, strikes, out, s, num_sms, stream);
-  if (L.nk_pad == 32) return launch_adjoint_t<32, true, false>(L, A, strikes, out, s, num_sms, stream);
-  return launch_adjoint_t<32, false, false>(L, A, strikes, out, s, num_sms, stream);
+  if (L.scheme == 1) return launch_adjoint_s<true>(L, A, strikes, out, s, num_sms, stream);
+  return launch_adjoint_s<false>(L, A, strikes, out, s, num_sms, stream);
 }
 
 }  // namespace simr

@@ -25,6 +25,9 @@ __device__ __forceinline__ float qe_only(const ScenConst& c, float v, float xv, 
 struct AdjSums {
   float vbar, Am, Amv, As, Asv, Ad, Adl, Ak3;
   float x, comp;  // x_T accumulated over the reverse sweep (Kahan-compensated)
+  // QE-M only: sum (v + m), sum (v' - m) and sum lam's A-adjoint over the corrected
+  // steps, and the count of steps that took the plain log-spot step
+  float Aqa, AK2, AA, Np;
 };
 
 // What a reverse step needs besides the adjoint carried in from the later steps.
@@ -42,30 +45,46 @@ struct AdjSums {
 struct AdjPre {
   float inc, dl, q, zx, hzc, hzcd, tmv, vc;
   float bz, bz2, cg, cz, am2, hrb, amr, ropb2, F, m4r, tr;
+  float am, b2, g;  // a, b^2 and g themselves (the QE-M step's correction needs them)
 };
 
-// The quadratic branch's factors from m, t = m^2/(s^2/2), rs2h = 1/(s^2/2), Z_V.
+// a * b, rounded on its own when RN (no FMA formed by the compiler from it and a
+// later sum), else left to the compiler.
+template <bool RN>
+__device__ __forceinline__ float mul_rn(float a, float b) {
+  if constexpr (RN)
+    return __fmul_rn(a, b);
+  else
+    return a * b;
+}
+
+// The quadratic branch's factors from m, t = m^2/(s^2/2), rs2h = 1/(s^2/2), Z_V
+// (RN: for adjoint_step_qem, every product rounded on its own).
+template <bool RN = false>
 __device__ __forceinline__ void adj_quad_pre(const ScenConst& c, float m, float t, float rs2h, float zv, AdjPre& P) {
   const float tt = fmaf(t, t, -t);
   const float rroot = rsqrt_approx(tt);
-  const float root = tt * rroot;
+  const float root = mul_rn<RN>(tt, rroot);
   const float b2 = (t - 1.0f) + root;
   const float rb = rsqrt_approx(b2);
-  const float b = b2 * rb;
+  const float b = mul_rn<RN>(b2, rb);
   P.ropb2 = rcp_approx(t + root);  // 1 / (1 + b^2)
-  const float am = m * P.ropb2;
+  const float am = mul_rn<RN>(m, P.ropb2);
   P.bz = b + zv;
   const float g = fmaf(zv, zv + 2.0f * b, -1.0f);
-  P.dl = am * g;
-  P.bz2 = P.bz * P.bz;
-  P.cg = c.Cdl * g;
-  P.cz = c.Cdl * zv;
+  P.am = am;
+  P.b2 = b2;
+  P.g = g;
+  P.dl = mul_rn<RN>(am, g);
+  P.bz2 = mul_rn<RN>(P.bz, P.bz);
+  P.cg = mul_rn<RN>(c.Cdl, g);
+  P.cz = mul_rn<RN>(c.Cdl, zv);
   P.am2 = am + am;
   P.hrb = 0.5f * rb;
-  P.amr = am * P.ropb2;
+  P.amr = mul_rn<RN>(am, P.ropb2);
   P.F = fmaf(fmaf(2.0f, t, -1.0f), 0.5f * rroot, 1.0f);
-  P.m4r = (m + m) * rs2h;  // 4 m / s^2
-  P.tr = t * (0.5f * rs2h);  // t / s^2
+  P.m4r = mul_rn<RN>(m + m, rs2h);      // 4 m / s^2
+  P.tr = mul_rn<RN>(t, 0.5f * rs2h);  // t / s^2
 }
 
 // The step's log-spot increment (LogPricePathQE), summed into x_T in the
@@ -305,6 +324,141 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
     adj_chain_exp(c.E, c1, c.Cdl, m.y, m2.y, s2h.y, d.y, ay, Py, a);
 }
 
+// Reverse step n under QE-M (Andersen's martingale correction, QemConst q): where
+// the correction exists the step's increment is
+//   r dt - qa (v + m) - lam + K2 (v' - m) + sK3 sqrt(v + v') Z_X,
+// lam = ln M - A m formed as the forward step forms it (qem_from_moments), and
+// the plain increment elsewhere.  lam's adjoint (bar lam = -1):
+//   quadratic: lam = u^2 b^2 / (2 (1 - u)) + g(u)/2, u = 2 A a, g(u) = -u - ln(1 - u):
+//     dlam/du = b^2 u (2 - u) / (2 (1 - u)^2) + u / (2 (1 - u)), dlam/db^2 = u^2 / (2 (1 - u)),
+//     into a (du/da = 2A), b^2 and A (du/dA = 2a);
+//   exponential: lam = ln(1 + q w / (1 - w)) - q w, q = 2 m^2 / (m^2 + s^2), w = A (m^2 + s^2) / (2 m):
+//     dlam/dq = w / (1 - w + q w) - w, dlam/dw = q / ((1 - w)(1 - w + q w)) - q,
+//     into m, s^2 and A.
+// The sums Aqa, AK2, AA carry the dependence on qa, K2 and A; Np counts the plain
+// steps (their C0 = r dt + Cd theta).  One step at a time (no packed pairs).
+__device__ __forceinline__ void adjoint_step_qem(const ScenConst& c, const QemConst& q, float theta, float c1,
+                                                 float vc, float vn, float d, float zx, AdjSums& a) {
+  // every product is rounded on its own (__fmul_rn) or fused explicitly (fmaf), so
+  // the compiler forms no FMA of its own: the same values in every kernel
+  const float m = fmaf(vc, c.E, c.thE);
+  const float s2h = fmaf(vc, c.h1, c.h2);
+  const float m2 = __fmul_rn(m, m);
+  const float rs2h = rcp_approx(s2h);
+  const float t = __fmul_rn(m2, rs2h);  // qe_t
+  const float s = vc + vn;
+  const float rq = rsqrt_approx(s);
+  const float qs = s > 0.0f ? __fmul_rn(s, rq) : 0.0f;
+  const float hz = s > 0.0f ? __fmul_rn(__fmul_rn(0.5f * c.sK3, zx), rq) : 0.0f;  // d(sK3 sqrt(s) Z)/ds
+  float mbar = 0.0f, s2bar = 0.0f, Abar = 0.0f, dl, lam = 0.0f;
+  bool ok = true;
+  if (t > kQuadT) {
+    AdjPre P;
+    adj_quad_pre<true>(c, m, t, rs2h, d, P);
+    dl = P.dl;
+    const float am = P.am, bb2 = P.b2;
+    const float Aa = __fmul_rn(q.A, am);
+    const float u = 2.0f * Aa;
+    ok = u < 1.0f;
+    float lu = 0.0f, lb2 = 0.0f;
+    if (ok) {
+      const float r1u = rcp_approx(1.0f - u);
+      const float ur = __fmul_rn(u, r1u);
+      lam = fmaf(0.5f, neg_log1m_tail(u), __fmul_rn(__fmul_rn(__fmul_rn(2.0f * Aa, Aa), bb2), r1u));
+      lu = fmaf(__fmul_rn(__fmul_rn(bb2, ur), 2.0f - u), 0.5f * r1u, 0.5f * ur);
+      lb2 = __fmul_rn(0.5f * u, ur);
+    }
+    const float vnbar = a.vbar + hz + (ok ? 0.0f : c.Cv);  // adjoint of v_{n+1}
+    const float dlbar = ok ? q.K2 : c.Cdl;
+    float abar = fmaf(vnbar, P.bz2, __fmul_rn(dlbar, P.g));
+    if (ok) {
+      const float lu2 = 2.0f * lu;
+      abar = fmaf(-lu2, q.A, abar);
+      Abar = __fmul_rn(-lu2, am);
+    }
+    const float bbar = __fmul_rn(P.am2, fmaf(vnbar, P.bz, __fmul_rn(dlbar, d)));
+    const float b2bar = fmaf(bbar, P.hrb, -__fmul_rn(abar, P.amr)) - (ok ? lb2 : 0.0f);
+    const float tbar = __fmul_rn(b2bar, P.F);
+    mbar = fmaf(tbar, P.m4r, __fmul_rn(abar, P.ropb2));
+    s2bar = -__fmul_rn(tbar, P.tr);
+  } else {
+    bool atom;
+    dl = adj_exp_dl(m, m2, s2h, vn, d, &atom);
+    float qq = 0.0f, w = 0.0f, ms = 0.0f;
+    if (m > 0.0f) {
+      ms = m2 + (s2h + s2h);
+      qq = __fmul_rn(2.0f * m2, rcp_approx(ms));             // 1 - p
+      w = __fmul_rn(__fmul_rn(0.5f * q.A, ms), rcp_approx(m));  // A / beta
+      ok = w < 1.0f;
+      if (ok) {
+        const float qw = __fmul_rn(qq, w);
+        lam = log1pf(__fmul_rn(qw, rcp_approx(1.0f - w))) - qw;
+      }
+    }
+    const float vnbar = a.vbar + hz + (ok ? 0.0f : c.Cv);
+    const float dlbar = ok ? q.K2 : c.Cdl;
+    if (m > 0.0f) {
+      const float rm = rcp_approx(m), rms = rcp_approx(ms);
+      const float s2 = s2h + s2h;
+      if (atom) {
+        mbar = -dlbar;
+      } else {
+        const float W = __fmul_rn(d, ms);
+        const float L = 0.69314718055994531f * lg2_approx(__fmul_rn(2.0f * m2, rcp_approx(W)));
+        const float Av = __fmul_rn(0.5f * ms, rm);
+        const float dA_dm = __fmul_rn(__fmul_rn(0.5f * (m2 - s2), rm), rm);
+        const float dL_dm = 2.0f * rm - __fmul_rn(2.0f * m, rms);
+        const float dv_dm = fmaf(dA_dm, L, __fmul_rn(Av, dL_dm));
+        const float dv_ds = fmaf(0.5f * rm, L, -__fmul_rn(Av, rms));
+        mbar = fmaf(vnbar, dv_dm, __fmul_rn(dlbar, dv_dm - 1.0f));
+        s2bar = __fmul_rn(vnbar + dlbar, dv_ds);
+      }
+      if (ok) {
+        const float den = (1.0f - w) + __fmul_rn(qq, w);
+        const float lq = __fmul_rn(w, rcp_approx(den)) - w;
+        const float lw = __fmul_rn(qq, rcp_approx(__fmul_rn(1.0f - w, den))) - qq;
+        const float rms2 = __fmul_rn(rms, rms), rm2 = __fmul_rn(rm, rm);
+        const float dq_dm = __fmul_rn(__fmul_rn(4.0f * m, s2), rms2), dq_ds = __fmul_rn(-2.0f * m2, rms2);
+        const float dw_dm = __fmul_rn(q.A, 0.5f - __fmul_rn(0.5f * s2, rm2)), dw_ds = __fmul_rn(0.5f * q.A, rm);
+        mbar -= fmaf(lq, dq_dm, __fmul_rn(lw, dw_dm));
+        s2bar -= fmaf(lq, dq_ds, __fmul_rn(lw, dw_ds));
+        Abar = __fmul_rn(__fmul_rn(-0.5f * lw, ms), rm);
+      }
+    }
+  }
+  // the increment, x_T (Kahan), the adjoint of v_n, the sums
+  float inc;
+  if (ok) {
+    inc = fmaf(-q.qa, vc + m, q.rdt) - lam;
+    inc = fmaf(q.K2, dl, inc);
+    mbar -= q.qa;
+  } else {
+    inc = fmaf(c.Cv, s, c.C0);
+    inc = fmaf(-c.Cd, vc, inc);
+    inc = fmaf(c.Cdl, dl, inc);
+  }
+  inc = fmaf(__fmul_rn(c.sK3, qs), zx, inc);
+  const float y = inc - a.comp;
+  const float tx = a.x + y;
+  a.comp = (tx - a.x) - y;
+  a.x = tx;
+  a.vbar = fmaf(mbar, c.E, fmaf(s2bar, c1, ok ? hz - q.qa : (c.Cv - c.Cd) + hz));
+  a.Am += mbar;
+  a.Amv = fmaf(mbar, vc - theta, a.Amv);
+  a.As += s2bar;
+  a.Asv = fmaf(s2bar, vc, a.Asv);
+  a.Ak3 = fmaf(qs, zx, a.Ak3);
+  if (ok) {
+    a.Aqa += vc + m;
+    a.AK2 += dl;
+    a.AA += Abar;
+  } else {
+    a.Ad += theta - vc;
+    a.Adl += dl;
+    a.Np += 1.0f;
+  }
+}
+
 // The draw the reverse step of state v needs: Z_V in the quadratic branch,
 // 1 - U_V otherwise (same branch test as the forward step).
 __device__ __forceinline__ float branch_draw(const ScenConst& c, float v, float xv, float zv) {
@@ -346,13 +500,26 @@ struct SegGlobal {
 };
 
 // The FP64 map of the sweep's sums onto d x_T / d(v0, kappa, theta, sigma, rho).
+// Under QE-M the plain steps' C0 contributes Cd theta per plain step (Np of them)
+// instead of every step's, and qa, K2 and A add their sums.
+template <bool QEM = false>
 __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a, float (&g)[5]) {
   const double Amv = a.Amv, Asv = a.Asv, As = a.As, Ad = a.Ad, Adl = a.Adl, Am = a.Am, Ak3 = a.Ak3;
   g[0] = a.vbar;
-  g[1] = (float)(A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl);
-  g[2] = (float)(A.omE * Am + A.dc2_dth * As + A.N_Cd);
-  g[3] = (float)(A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl);
-  g[4] = (float)(A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3);
+  double gk = A.dE_dk * Amv + A.dc1_dk * Asv + A.dc2_dk * As + A.dCd_dk * Ad + A.dCdl_dk * Adl;
+  double gt = A.omE * Am + A.dc2_dth * As + (QEM ? A.Cd * (double)a.Np : A.N_Cd);
+  double gs = A.two_over_sigma * (A.c1 * Asv + A.c2 * As) - A.Cd_over_sigma * Ad - A.Cdl_over_sigma * Adl;
+  double gr = A.D_over_sigma * Ad + A.B_over_sigma * Adl + A.dsK3_drho * Ak3;
+  if (QEM) {
+    const double Aqa = a.Aqa, AK2 = a.AK2, AA = a.AA;
+    gk += A.dK2_dk * AK2 + A.dA_dk * AA;
+    gs += A.dK2_ds * AK2 + A.dA_ds * AA;
+    gr += -A.dqa_drho * Aqa + A.dK2_dr * AK2 + A.dA_dr * AA;
+  }
+  g[1] = (float)gk;
+  g[2] = (float)gt;
+  g[3] = (float)gs;
+  g[4] = (float)gr;
 }
 
 // Reverse sweep of one path, segment by segment, last first: each segment's
@@ -362,17 +529,17 @@ __device__ __forceinline__ void adjoint_map(const AdjConst& A, const AdjSums& a,
 // thread's segment column S (at least k rows) -- then the steps are
 // differentiated backwards.  x_T (with its Kahan remainder) is summed on the
 // way; g = d x_T / d(v0, kappa, theta, sigma, rho).
-template <typename Seg, bool PAIRED>
+template <typename Seg, bool PAIRED, bool QEM = false>
 __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                            const uint32_t (&rk)[10][2], const PhiloxLane& pl,
                                            const float* ck, int cstride, float v_last, const Seg& S,
-                                           float& x_out, float& comp_out, float (&g)[5]) {
+                                           float& x_out, float& comp_out, float (&g)[5], const QemConst& qm) {
   using I = decltype(S.stride());
   const float theta = A.theta;
   const float c1 = c.h1 + c.h1;  // s^2 = v c1 + c2
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
-  AdjSums as = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  AdjSums as = AdjSums{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   float2* s01 = S.pairs();
   float* s2 = S.zx();
   const I bd = S.stride();
@@ -398,7 +565,13 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
     int i = (int)(n1 - n0) - 1;
     const float2* rp = s01 + (I)i * bd;
     const float* rz = s2 + (I)i * bd;
-    if constexpr (PAIRED) {
+    if constexpr (QEM) {
+      for (; i >= 0; --i, rp -= bd, rz -= bd) {
+        const float2 vd = rp[0];
+        adjoint_step_qem(c, qm, theta, c1, vd.x, vnext, vd.y, rz[0], as);
+        vnext = vd.x;
+      }
+    } else if constexpr (PAIRED) {
       if constexpr (Seg::kGlobal) {
         // global memory: the steps in pairs (n, n - 1) from the top, each pair's
         // data loaded one pair ahead into registers and asked into L2
@@ -484,7 +657,7 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
   }
   x_out = as.x;
   comp_out = as.comp;
-  adjoint_map(A, as, g);
+  adjoint_map<QEM>(A, as, g);
 }
 
 // Forward pass with checkpoints, then the reverse sweeps, for PPT paths: the
@@ -496,11 +669,12 @@ __device__ __forceinline__ void path_sweep(const ScenConst& c, const AdjConst& A
 // Checkpoint (slot, path j) of this thread at ck[(slot * PPT + j) * ck_stride]
 // (n_seg - 1 slots; shared or global memory); S is this thread's segment column
 // (shared or global memory, at least k rows).
-template <int PPT, typename Seg, bool PAIRED = true>
+template <int PPT, typename Seg, bool PAIRED = true, bool QEM = false>
 __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjConst& A, uint32_t N, uint32_t option,
                                                  const uint32_t (&rk)[10][2], const uint64_t (&path)[PPT], float* ck,
                                                  int ck_stride, const Seg& S, float (&x_out)[PPT],
-                                                 float (&comp_out)[PPT], float (&g)[PPT][5]) {
+                                                 float (&comp_out)[PPT], float (&g)[PPT][5],
+                                                 const QemConst& qm = QemConst{}) {
   static_assert(PPT == 1 || PPT == 2, "one or two paths per thread");
   const uint32_t k = (uint32_t)A.ckpt_every;
   const int n_seg = A.n_seg;
@@ -540,8 +714,8 @@ __device__ __forceinline__ void path_adjoint_ppt(const ScenConst& c, const AdjCo
   }
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
-    path_sweep<Seg, PAIRED>(c, A, N, option, rk, pl[j], ck + j * ck_stride, PPT * ck_stride, v[j], S,
-                            x_out[j], comp_out[j], g[j]);
+    path_sweep<Seg, PAIRED, QEM>(c, A, N, option, rk, pl[j], ck + j * ck_stride, PPT * ck_stride, v[j], S,
+                                 x_out[j], comp_out[j], g[j], qm);
 }
 
 // Floats per thread of path_adjoint_ppt: checkpoints and the segment buffer.

@@ -264,7 +264,7 @@ int popcount9(uint32_t m) {
 // analytic bumps and the FP64 normalisation constants.
 int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps, uint64_t path_begin,
                  uint64_t path_count, uint64_t paths_total, uint64_t seed, uint32_t option_index,
-                 double rel_bump, uint32_t mask, PathLaunch* L) {
+                 double rel_bump, uint32_t mask, PathLaunch* L, simr_heston* scen_out = nullptr) {
   std::memset(L, 0, sizeof(*L));
   philox_round_keys(seed, L->rk);
   L->path_begin = path_begin;
@@ -383,6 +383,8 @@ int build_launch(const simr_heston* m, int n_strikes, int is_put, uint32_t steps
     fc.K0p = (float)f[6];
     fc.branch = br;
   }
+  if (scen_out)
+    for (int s = 0; s < ns; ++s) scen_out[s] = scen_model[s];
   return SIMR_OK;
 }
 
@@ -423,6 +425,8 @@ int build_adjoint(const simr_heston& m, uint32_t steps, uint32_t ckpt_every, Adj
   A->D_over_sigma = D / m.sigma;
   A->B_over_sigma = B / m.sigma;
   A->dsK3_drho = sK3 > 0.0 ? -m.rho * dt / (2.0 * sK3) : __builtin_nan("");
+  A->qem = 0;  // plain QE unless adjoint_scheme sets QE-M
+  A->Cd = A->dqa_drho = A->dK2_dk = A->dK2_ds = A->dK2_dr = A->dA_dk = A->dA_ds = A->dA_dr = 0.0;
   return SIMR_OK;
 }
 
@@ -524,24 +528,115 @@ int with_device(simr_ctx* ctx) {
   return SIMR_OK;
 }
 
-// QE-M constants (FP64 -> FP32): r dt, qa = dt (1 - rho^2)/4 (= K3/2 = K4/2),
+// QE-M constants in FP64: r dt, qa = dt (1 - rho^2)/4 (= K3/2 = K4/2),
 // K2 = dt/2 (kappa rho/sigma - 1/2) + rho/sigma, A = K2 + K4/2 = K2 + qa.
-QemConst qem_const(const simr_heston& m, uint32_t steps) {
+void qem_const64(const simr_heston& m, uint32_t steps, double q[4]) {
   const double dt = m.T / (double)steps;
   const double K2 = 0.5 * dt * (m.kappa * m.rho / m.sigma - 0.5) + m.rho / m.sigma;
   const double qa = 0.25 * dt * (1.0 - m.rho * m.rho);
-  return QemConst{(float)(m.r * dt), (float)qa, (float)K2, (float)(K2 + qa)};
+  q[0] = m.r * dt;
+  q[1] = qa;
+  q[2] = K2;
+  q[3] = K2 + qa;
 }
 
-// The context's scheme on a path launch: QE-M runs the base scenario only (price,
-// and the Greeks read off the base path: delta, gamma, rho).
-int apply_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, PathLaunch* L) {
+QemConst qem_const(const simr_heston& m, uint32_t steps) {
+  double q[4];
+  qem_const64(m, steps, q);
+  return QemConst{(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+}
+
+// The QE-M first-step constant of a scenario starting from v0, in FP64:
+// r dt - qa (v0 + m0) - lam(v0), lam = ln M - A m0 in the branch of step 0
+// (quadratic: 2 (A a)^2 b^2 / (1 - u) + g(u)/2 with u = 2 A a and
+// g(u) = -u - ln(1 - u); exponential: ln(1 + q w / (1 - w)) - q w with
+// q = 1 - p, w = A / beta; zero mean: lam = 0).  False where M does not exist.
+bool qem_first64(const simr_heston& m, uint32_t steps, double v0, double* K0q) {
+  double c[9], q[4];
+  scen_const64(m, steps, c);
+  qem_const64(m, steps, q);
+  const double m0 = c[1] + v0 * c[0], s20 = v0 * c[2] + c[3], A = q[3];
+  double lam = 0.0;
+  if (m0 > 0.0) {
+    const double psi = s20 / (m0 * m0);
+    if (psi <= 1.5) {
+      const double t = 2.0 / psi;
+      const double b2 = t - 1.0 + std::sqrt(t) * std::sqrt(t - 1.0);
+      const double a = m0 / (1.0 + b2);
+      const double u = 2.0 * A * a;
+      if (!(u < 1.0)) return false;
+      lam = 0.5 * u * u * b2 / (1.0 - u) + 0.5 * (-u - std::log1p(-u));
+    } else {
+      const double qq = 2.0 / (psi + 1.0);  // 1 - p
+      const double w = A * m0 / qq;         // A / beta, beta = (1 - p) / m0
+      if (!(w < 1.0)) return false;
+      lam = std::log1p(qq * w / (1.0 - w)) - qq * w;
+    }
+  }
+  *K0q = q[0] - q[1] * (v0 + m0) - lam;
+  return true;
+}
+
+// The context's scheme on a path launch.  QE-M with bumped scenarios (scen: the
+// launch's scenario models, base first) adds each scenario's QE-M constant
+// deltas to the base's, in FP64; step 0's split (the CRN first step) takes the
+// QE-M first-step constants where M exists at every scenario's v0, and is
+// dropped otherwise.
+int apply_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, PathLaunch* L,
+                 const simr_heston* scen = nullptr) {
   if (ctx->scheme == SIMR_SCHEME_QE) return SIMR_OK;
-  if (L->n_scen != 1)
-    return fail(SIMR_EUNSUPPORTED, "scheme QE-M supports prices and the delta, gamma and rho of the base path only");
   L->scheme = 1;
   L->qm = qem_const(m, steps);
+  if (L->n_scen == 1) return SIMR_OK;
+  if (!scen) return fail(SIMR_EUNSUPPORTED, "internal: QE-M bumped scenarios without their models");
+  double qb[4];
+  qem_const64(m, steps, qb);
+  L->qmd[0] = QemConst{0.0f, 0.0f, 0.0f, 0.0f};
+  for (int s = 1; s < L->n_scen; ++s) {
+    double qs[4];
+    qem_const64(scen[s], steps, qs);
+    L->qmd[s] = QemConst{(float)(qs[0] - qb[0]), (float)(qs[1] - qb[1]), (float)(qs[2] - qb[2]),
+                         (float)(qs[3] - qb[3])};
+  }
+  if (L->first_split) {
+    double k0b = 0.0;
+    bool ok = qem_first64(m, steps, (double)L->sc[0].v0, &k0b);
+    double k0s[kMaxScen];
+    for (int s = 1; s < L->n_scen && ok; ++s) ok = qem_first64(scen[s], steps, (double)L->sc[s].v0, &k0s[s]);
+    if (!ok) {
+      L->first_split = 0;
+    } else {
+      L->f0[0].K0p = (float)k0b;
+      for (int s = 1; s < L->n_scen; ++s) L->f0[s].K0p = (float)(k0s[s] - k0b);
+    }
+  }
   return SIMR_OK;
+}
+
+// The FP64 derivatives of the QE-M constants in the adjoint's map (qa, K2 and
+// A = K2 + qa in kappa, sigma and rho; Cd theta's coefficient per plain step).
+void adjoint_qem_fields(const simr_heston& m, uint32_t steps, AdjConst* A) {
+  const double dt = m.T / (double)steps, kdt = m.kappa * dt, E = std::exp(-kdt), omE = -std::expm1(-kdt);
+  const double sg = m.sigma, r = m.rho;
+  A->qem = 1;
+  A->Cd = (r / sg) * (omE - 0.5 * kdt * (1.0 + E));
+  A->dqa_drho = -0.5 * dt * r;
+  A->dK2_dk = 0.5 * dt * r / sg;
+  A->dK2_ds = -0.5 * dt * m.kappa * r / (sg * sg) - r / (sg * sg);
+  A->dK2_dr = 0.5 * dt * m.kappa / sg + 1.0 / sg;
+  A->dA_dk = A->dK2_dk;
+  A->dA_ds = A->dK2_ds;
+  A->dA_dr = A->dK2_dr + A->dqa_drho;
+}
+
+// The context's scheme on an adjoint launch: under QE-M the launch's scheme and
+// QemConst, and the adjoint map's QE-M fields.
+void adjoint_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, PathLaunch* L, AdjConst* A) {
+  A->qem = 0;
+  if (ctx->scheme != SIMR_SCHEME_QEM) return;
+  L->scheme = 1;
+  L->qm = qem_const(m, steps);
+  adjoint_qem_fields(m, steps, A);
 }
 
 int require_plain_qe(const simr_ctx* ctx, const char* what) {
@@ -579,7 +674,7 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
 }
 
 // Per-option device records (caller's order) and the longest-first order.
-int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vector<BatchOption>* out,
+int build_batch_options(const simr_option* opts, int n, bool adjoint, bool qem, std::vector<BatchOption>* out,
                         bool one_segment, std::vector<uint32_t>* order, int* ckpt_rows, int* seg_rows) {
   out->resize(n);
   std::vector<double> cost(n);
@@ -605,7 +700,9 @@ int build_batch_options(const simr_option* opts, int n, bool adjoint, std::vecto
       if ((rc = build_adjoint(o.m, o.steps, one_segment ? o.steps + (o.steps & 1u) : 0u, &b.A))) return rc;
       crows = std::max(crows, b.A.n_seg - 1);
       srows = std::max(srows, b.A.ckpt_every);
+      if (qem) adjoint_qem_fields(o.m, o.steps, &b.A);
     }
+    if (qem) b.qm = qem_const(o.m, o.steps);
     b.S0 = (float)o.m.S0;
     b.K = (float)o.K;
     b.invS0 = (float)(1.0 / o.m.S0);
@@ -818,10 +915,11 @@ int simr_greeks_fd(simr_ctx* ctx, const simr_heston* model, const double* strike
   if ((rc = with_device(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   PathLaunch L;
+  simr_heston scen[kMaxScen];
   if ((rc = build_launch(model, n_strikes, is_put, steps, 0, paths, paths, seed, option_index, rel_bump,
-                         greek_mask, &L)))
+                         greek_mask, &L, scen)))
     return rc;
-  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L, scen))) return rc;
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
   OutStage o;
@@ -901,7 +999,6 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   int rc = check_common(ctx, model, strikes, n_strikes, 256, steps, paths);
   if (rc) return rc;
   if (!price || !grad) return fail(SIMR_EINVAL, "price and grad must be non-NULL");
-  if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
   if ((rc = with_device(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   PathLaunch L;
@@ -912,6 +1009,7 @@ int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const double* s
   if (k == 0 && (rc = fast_ckpt_every(ctx, L, steps, &k))) return rc;
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, k, &A))) return rc;
+  adjoint_scheme(ctx, *model, steps, &L, &A);
   if (adjoint_smem_bytes(L, A) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "ckpt_every %d with %u steps needs more shared memory than a block has",
                 A.ckpt_every, steps);
@@ -959,7 +1057,6 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   if (n_paths < 1 || n_paths > (1ull << 31)) return fail(SIMR_EINVAL, "n_paths must lie in [1, 2^31]");
   if (!x_T || !grad) return fail(SIMR_EINVAL, "x_T and grad must be non-NULL");
   if (!is_device_ptr(x_T) || !is_device_ptr(grad)) return fail(SIMR_EINVAL, "x_T and grad must be device pointers");
-  if ((rc = require_plain_qe(ctx, "the adjoint kernel"))) return rc;
   AdjConst A;
   if ((rc = build_adjoint(*model, steps, ckpt_every, &A))) return rc;
   if ((size_t)adjoint_thread_floats(A.n_seg, A.ckpt_every, 1) * 128 * sizeof(float) > kAdjMaxSmem)
@@ -969,6 +1066,7 @@ int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_t steps, 
   PathLaunch L;
   if ((rc = build_launch(model, 1, 0, steps, path_begin, n_paths, n_paths, seed, option_index, 1e-4, 0u, &L)))
     return rc;
+  adjoint_scheme(ctx, *model, steps, &L, &A);
   cudaError_t e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_paths_adjoint(L, A, x_T, grad, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching the per-path adjoint kernel");
   return SIMR_OK;
@@ -987,10 +1085,11 @@ int simr_path_sums(simr_ctx* ctx, const simr_heston* model, const double* strike
   if ((rc = with_device(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   PathLaunch L;
+  simr_heston scen[kMaxScen];
   if ((rc = build_launch(model, n_strikes, is_put, steps, path_begin, path_count, path_count, seed, option_index,
-                         greek_mask ? rel_bump : 1e-4, greek_mask, &L)))
+                         greek_mask ? rel_bump : 1e-4, greek_mask, &L, scen)))
     return rc;
-  if ((rc = apply_scheme(ctx, *model, steps, &L))) return rc;
+  if ((rc = apply_scheme(ctx, *model, steps, &L, scen))) return rc;
   L.raw_sums = 1;
   const double* ks = nullptr;
   if ((rc = stage_strikes(ctx, strikes, n_strikes, st, &ks))) return rc;
@@ -1098,8 +1197,9 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   if (is_device_ptr(opts)) return fail(SIMR_EINVAL, "the option table must be in host memory");
   const bool adjoint = (flags & SIMR_BATCH_ADJOINT) != 0;
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
-  int rc0 = require_plain_qe(ctx, "the batched book");
-  if (rc0) return rc0;
+  const bool qem = ctx->scheme == SIMR_SCHEME_QEM;
+  if (qem && forced > 1 && !adjoint)
+    return fail(SIMR_EINVAL, "price books under QE-M have two kernel shapes (SIMR_BATCH_VARIANT 0 or 1)");
   if (adjoint && !grad) return fail(SIMR_EINVAL, "adjoint books need grad");
   int rc = with_device(ctx);
   if (rc) return rc;
@@ -1123,7 +1223,8 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     }
   }
   int ckpt_rows = 0, seg_rows = 0;
-  if ((rc = build_batch_options(opts, n_opts, adjoint, &bo, one_segment, &order, &ckpt_rows, &seg_rows))) return rc;
+  if ((rc = build_batch_options(opts, n_opts, adjoint, qem, &bo, one_segment, &order, &ckpt_rows, &seg_rows)))
+    return rc;
   if (!one_segment && (size_t)(ckpt_rows + 3 * seg_rows) * 128 * sizeof(float) > kAdjMaxSmem)
     return fail(SIMR_EUNSUPPORTED, "the book's checkpoints need more shared memory than a block has");
   if (one_segment && (rc = ensure(&ctx->gseg, &ctx->gseg_floats, gseg_floats, "segment buffers"))) return rc;
@@ -1135,6 +1236,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   B.ckpt_rows = ckpt_rows;
   B.seg_rows = seg_rows;
   B.gseg = one_segment ? ctx->gseg : nullptr;
+  B.qem = qem ? 1 : 0;
   const int nacc = adjoint ? 9 : 2;
   OutStage o;
   o.user[0] = price;
@@ -1153,7 +1255,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
   double total = 0.0;
   for (const BatchOption& b : bo) total += (double)b.steps * (double)b.paths;
   const uint64_t tkey = (adjoint ? 1ull : 0ull) | ((uint64_t)std::max(0.0, std::log2(total + 1.0)) << 1) |
-                        ((uint64_t)std::log2((double)n_opts) << 16);
+                        ((uint64_t)std::log2((double)n_opts) << 16) | ((qem ? 1ull : 0ull) << 40);
   // a chunk that fills the GPU: about two items per resident warp (the kernel
   // runs ~40 warps per SM), a multiple of the paths a warp takes per pass
   double total_paths = 0.0;
@@ -1197,7 +1299,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
       return SIMR_OK;
     };
     float best = 0.0f;
-    const int n_var = adjoint ? 2 : kBatchVariants;
+    const int n_var = (adjoint || qem) ? 2 : kBatchVariants;
     for (int v = 0; v < n_var && e == cudaSuccess && !rc; ++v) {  // the kernel shape at the default chunk
       float ms = 0.0f;
       rc = time_one(chunk, v, &ms);
@@ -1245,6 +1347,7 @@ int simr_batch_submit(simr_ctx* ctx, const simr_option* opts, int n_opts, uint64
     key = fnv1a(&flags, sizeof(flags), key);
     key = fnv1a(&chunk, sizeof(chunk), key);
     key = fnv1a(&variant, sizeof(variant), key);
+    key = fnv1a(&B.qem, sizeof(B.qem), key);
     key = fnv1a(&out, sizeof(out), key);
     // the captured launches hold the context's device buffers: a reallocation
     // since the capture makes a new graph

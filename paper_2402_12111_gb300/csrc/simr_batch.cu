@@ -38,7 +38,9 @@ namespace {
 #ifndef SIMR_BOOK_ADJ_THREADS
 #define SIMR_BOOK_ADJ_THREADS 640
 #endif
-template <bool ADJ, bool GSEG, int TPB, int PPT, int U>
+// QEM: the options' log-spot steps under QE-M (their QemConst); price books
+// then run two paths per thread, unrolled once (two shapes: the block size).
+template <bool ADJ, bool GSEG, int TPB, int PPT, int U, bool QEM>
 __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) heston_batch_kernel(const __grid_constant__ BatchLaunch B,
                                                            const BatchOption* __restrict__ opts,
                                                            const BatchItem* __restrict__ items,
@@ -75,13 +77,14 @@ __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) he
         // arrays of seg_rows rows (the largest over the book), so threads on
         // options with different checkpoint intervals never overlap
         if constexpr (GSEG)  // one segment: no checkpoints are read or written
-          path_adjoint_ppt<1, SegGlobal, SIMR_BOOK_PAIRED>(c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
-                              SegGlobal{B.gseg, (long long)blockIdx.x * bd + tid, B.seg_rows,
-                                        (long long)gridDim.x * bd},
-                              x, comp, g);
+          path_adjoint_ppt<1, SegGlobal, SIMR_BOOK_PAIRED, QEM>(
+              c, O.A, steps, oidx, B.rk, pth, B.gseg, 0,
+              SegGlobal{B.gseg, (long long)blockIdx.x * bd + tid, B.seg_rows, (long long)gridDim.x * bd}, x, comp,
+              g, O.qm);
         else
-          path_adjoint_ppt<1, SegShared, SIMR_BOOK_PAIRED>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
-                              SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows}, x, comp, g);
+          path_adjoint_ppt<1, SegShared, SIMR_BOOK_PAIRED, QEM>(c, O.A, steps, oidx, B.rk, pth, smem_f + tid, bd,
+                                                                SegShared{smem_f + B.ckpt_rows * bd, B.seg_rows},
+                                                                x, comp, g, O.qm);
         const float S = terminal_spot(S0, x[0], comp[0]);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) terms[a] = active ? adj_term(a, put, S, K, g[0], O.invS0, O.T) : 0.0f;
@@ -90,7 +93,8 @@ __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) he
         float xs[2], cs[2];
         if constexpr (PPT == 2) {
           float2 x2, comp2;
-          simulate_two<U>(c, steps, oidx, B.rk, I.path_begin + b + lane, I.path_begin + b + 32 + lane, x2, comp2);
+          simulate_two<U, QEM>(c, steps, oidx, B.rk, I.path_begin + b + lane, I.path_begin + b + 32 + lane, x2,
+                               comp2, O.qm);
           xs[0] = x2.x;
           xs[1] = x2.y;
           cs[0] = comp2.x;
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(TPB, ADJ ? SIMR_BOOK_ADJ_THREADS / TPB : 1) he
         } else {
 #pragma unroll 1
           for (int j = 0; j < 2; ++j)
-            simulate_one<false, U>(c, steps, oidx, B.rk, I.path_begin + b + 32 * j + lane, xs[j], cs[j]);
+            simulate_one<QEM, U>(c, steps, oidx, B.rk, I.path_begin + b + 32 * j + lane, xs[j], cs[j], O.qm);
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -152,22 +156,30 @@ using BatchKernel = void (*)(BatchLaunch, const BatchOption*, const BatchItem*, 
 // The kernel of a book's mode and shape: price books any of the kBatchVariants
 // (threads per block 128 / 256, paths per thread 2 / 1, unroll 1 / 2); adjoint
 // books the thread count only.
-BatchKernel batch_kernel(bool adjoint, bool gseg, int tpb, int ppt, int unroll) {
+BatchKernel batch_kernel(bool adjoint, bool gseg, int tpb, int ppt, int unroll, bool qem) {
   const bool t256 = tpb == 256;
+  if (qem) {
+    if (adjoint) {
+      if (gseg)
+        return t256 ? heston_batch_kernel<true, true, 256, 1, 1, true> : heston_batch_kernel<true, true, 128, 1, 1, true>;
+      return t256 ? heston_batch_kernel<true, false, 256, 1, 1, true> : heston_batch_kernel<true, false, 128, 1, 1, true>;
+    }
+    return t256 ? heston_batch_kernel<false, false, 256, 2, 1, true> : heston_batch_kernel<false, false, 128, 2, 1, true>;
+  }
   if (adjoint) {
-    if (gseg) return t256 ? heston_batch_kernel<true, true, 256, 1, 1> : heston_batch_kernel<true, true, 128, 1, 1>;
-    return t256 ? heston_batch_kernel<true, false, 256, 1, 1> : heston_batch_kernel<true, false, 128, 1, 1>;
+    if (gseg) return t256 ? heston_batch_kernel<true, true, 256, 1, 1, false> : heston_batch_kernel<true, true, 128, 1, 1, false>;
+    return t256 ? heston_batch_kernel<true, false, 256, 1, 1, false> : heston_batch_kernel<true, false, 128, 1, 1, false>;
   }
   const bool p1 = ppt == 1, u2 = unroll == 2;
   if (t256)
-    return p1 ? (u2 ? heston_batch_kernel<false, false, 256, 1, 2> : heston_batch_kernel<false, false, 256, 1, 1>)
-              : (u2 ? heston_batch_kernel<false, false, 256, 2, 2> : heston_batch_kernel<false, false, 256, 2, 1>);
-  return p1 ? (u2 ? heston_batch_kernel<false, false, 128, 1, 2> : heston_batch_kernel<false, false, 128, 1, 1>)
-            : (u2 ? heston_batch_kernel<false, false, 128, 2, 2> : heston_batch_kernel<false, false, 128, 2, 1>);
+    return p1 ? (u2 ? heston_batch_kernel<false, false, 256, 1, 2, false> : heston_batch_kernel<false, false, 256, 1, 1, false>)
+              : (u2 ? heston_batch_kernel<false, false, 256, 2, 2, false> : heston_batch_kernel<false, false, 256, 2, 1, false>);
+  return p1 ? (u2 ? heston_batch_kernel<false, false, 128, 1, 2, false> : heston_batch_kernel<false, false, 128, 1, 1, false>)
+            : (u2 ? heston_batch_kernel<false, false, 128, 2, 2, false> : heston_batch_kernel<false, false, 128, 2, 1, false>);
 }
 
 BatchKernel batch_kernel(const BatchLaunch& B) {
-  return batch_kernel(B.adjoint != 0, B.gseg != nullptr, B.tpb, B.ppt, B.unroll);
+  return batch_kernel(B.adjoint != 0, B.gseg != nullptr, B.tpb, B.ppt, B.unroll, B.qem != 0);
 }
 
 size_t batch_smem(const BatchLaunch& B) {
@@ -178,8 +190,8 @@ size_t batch_smem(const BatchLaunch& B) {
 
 void batch_variant(int v, bool adjoint, BatchLaunch* B) {
   B->tpb = (v & 1) ? 256 : 128;
-  B->ppt = adjoint ? 1 : ((v >> 1) & 1) ? 1 : 2;
-  B->unroll = adjoint ? 1 : ((v >> 2) & 1) ? 2 : 1;
+  B->ppt = adjoint ? 1 : (((v >> 1) & 1) && !B->qem) ? 1 : 2;
+  B->unroll = adjoint ? 1 : (((v >> 2) & 1) && !B->qem) ? 2 : 1;
 }
 
 cudaError_t prepare_batch(const BatchLaunch& B) {
@@ -190,12 +202,14 @@ cudaError_t prepare_batch(const BatchLaunch& B) {
 cudaError_t batch_gseg_threads(int num_sms, size_t* threads) {
   // the largest grid any adjoint variant runs
   *threads = 0;
-  for (int tpb = 128; tpb <= 256; tpb *= 2) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(true, true, tpb, 1, 1), tpb, 0);
-    if (e != cudaSuccess) return e;
-    *threads = std::max(*threads, (size_t)num_sms * (size_t)per_sm * tpb);
-  }
+  for (int q = 0; q < 2; ++q)
+    for (int tpb = 128; tpb <= 256; tpb *= 2) {
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(true, true, tpb, 1, 1, q),
+                                                                    tpb, 0);
+      if (e != cudaSuccess) return e;
+      *threads = std::max(*threads, (size_t)num_sms * (size_t)per_sm * tpb);
+    }
   return cudaSuccess;
 }
 

@@ -658,6 +658,49 @@ __device__ __forceinline__ void step_bumped(const ScenConst& b, const ScenConst&
   v = vn;
 }
 
+// One QE-M step of a scenario in a common-random-number launch: base constants
+// b, q plus deltas d, qd (zero for the base scenario itself).  The variance step
+// is step_bumped's; the correction lam comes from the scenario's own moments
+// and A; the deltas of r dt, qa, K2 and sK3 enter as a separate sum, so the bump
+// is not lost to the base terms' rounding.  Where M does not exist the plain
+// bumped increment is taken.
+__device__ __forceinline__ void step_qem_bumped(const ScenConst& b, const ScenConst& d, const QemConst& q,
+                                                const QemConst& qd, float xv, float zv, float zx, float& v,
+                                                float& x, float& comp) {
+  const float m = __fadd_rn(__fmaf_rn(v, b.E, __fmaf_rn(v, d.E, d.thE)), b.thE);
+  const float s2h = __fadd_rn(__fmaf_rn(v, b.h1, __fmaf_rn(v, d.h1, d.h2)), b.h2);
+  float vn, dl, lam;
+  const bool ok = qem_from_moments(m, s2h, xv, zv, __fadd_rn(q.A, qd.A), vn, dl, lam);
+  const float s = __fadd_rn(v, vn);
+  const float r = sqrt_approx(s);
+  float inc, sm;
+  if (ok) {
+    const float vm = __fadd_rn(v, m);
+    inc = __fmaf_rn(-q.qa, vm, q.rdt);
+    inc = __fmaf_rn(q.K2, dl, inc);
+    inc = __fmaf_rn(__fmul_rn(b.sK3, r), zx, inc);
+    sm = __fmaf_rn(-qd.qa, vm, qd.rdt);
+    sm = __fmaf_rn(qd.K2, dl, sm);
+    sm = __fmaf_rn(__fmul_rn(d.sK3, r), zx, sm);
+    sm = __fsub_rn(sm, lam);
+  } else {
+    inc = __fmaf_rn(b.Cv, s, b.C0);
+    inc = __fmaf_rn(-b.Cd, v, inc);
+    inc = __fmaf_rn(b.Cdl, dl, inc);
+    inc = __fmaf_rn(__fmul_rn(b.sK3, r), zx, inc);
+    sm = __fmaf_rn(d.Cv, s, d.C0);
+    sm = __fmaf_rn(-d.Cd, v, sm);
+    sm = __fmaf_rn(d.Cdl, dl, sm);
+    sm = __fmaf_rn(__fmul_rn(d.sK3, r), zx, sm);
+  }
+  inc = __fadd_rn(inc, sm);
+  const float y = __fsub_rn(inc, comp);
+  const float t = __fadd_rn(x, y);
+  comp = __fsub_rn(__fsub_rn(t, x), y);
+  x = t;
+  v = vn;
+}
+
 // step_bumped for two scenarios: base constants b (both lanes), deltas d (lane
 // x the first scenario's, lane y the second's).
 __device__ __forceinline__ void step_bumped2(const ScenConst2& b, const ScenConst2& d, float2 xv, float2 zv,
@@ -762,13 +805,13 @@ __device__ __forceinline__ void simulate_one(const ScenConst& c, uint32_t steps,
   }
 }
 
-// Two paths of one scenario in lockstep (plain QE): simulate_one's arithmetic,
-// paired lane for lane, so each path's x_T and remainder equal simulate_one's
-// (U: the step-pair loop unrolled U times).
-template <int U = 1>
+// Two paths of one scenario in lockstep: simulate_one's arithmetic, paired lane
+// for lane (QE, or QE-M through step_qem2), so each path's x_T and remainder
+// equal simulate_one's (U: the step-pair loop unrolled U times).
+template <int U = 1, bool QEM = false>
 __device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps, uint32_t option,
                                              const uint32_t (&rk)[10][2], uint64_t path0, uint64_t path1,
-                                             float2& x, float2& comp) {
+                                             float2& x, float2& comp, const QemConst& q = QemConst{}) {
   const PhiloxLane pl0 = philox_lane(path0, rk), pl1 = philox_lane(path1, rk);
   float2 v = make_float2(c.v0, c.v0);
   x = make_float2(0.0f, 0.0f);
@@ -782,13 +825,19 @@ __device__ __forceinline__ void simulate_two(const ScenConst& c, uint32_t steps,
       const float2 xv = centered_uniform2(w0.x, w1.x);
       const float2 zv = norminv_centered2(xv);
       const float2 zx = norminv_centered2(centered_uniform2(w0.y, w1.y));
-      step_base2<false>(c, xv, zv, zx, v, x, comp);
+      if constexpr (QEM)
+        step_qem2(c, q, xv, zv, zx, v, x, comp);
+      else
+        step_base2<false>(c, xv, zv, zx, v, x, comp);
     }
     if (2 * p + 1 < steps) {
       const float2 xv = centered_uniform2(w0.z, w1.z);
       const float2 zv = norminv_centered2(xv);
       const float2 zx = norminv_centered2(centered_uniform2(w0.w, w1.w));
-      step_base2<false>(c, xv, zv, zx, v, x, comp);
+      if constexpr (QEM)
+        step_qem2(c, q, xv, zv, zx, v, x, comp);
+      else
+        step_base2<false>(c, xv, zv, zx, v, x, comp);
     }
   }
 }

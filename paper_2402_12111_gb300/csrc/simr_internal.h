@@ -43,8 +43,9 @@ struct PathLaunch {
   double paths_total;     // denominator of the mean
   double denom[kMaxGreeks];  // per Greek: bump denominator (sign folded in)
   int32_t raw_sums;       // 1: write raw sums instead of normalised results
-  int32_t scheme;         // 0: QE; 1: QE-M (base scenario only, n_scen == 1)
+  int32_t scheme;         // 0: QE; 1: QE-M
   QemConst qm;            // QE-M constants of the base scenario
+  QemConst qmd[kMaxScen]; // QE-M: the bumped scenarios' constant deltas to qm (qmd[0] zero)
 };
 
 // Counters of the generator's raw words: paths [path_begin, path_begin + n_paths)
@@ -75,6 +76,12 @@ struct AdjConst {
   double dCd_dk, dCdl_dk, N_Cd;
   double two_over_sigma, c1, c2, Cd_over_sigma, Cdl_over_sigma;
   double D_over_sigma, B_over_sigma, dsK3_drho;
+  // QE-M (scheme 1): the log-spot step r dt - qa (v + m) - lam(A) + K2 (v' - m) + sK3 sqrt(v + v') Z_X
+  // on the steps where the correction exists, the plain step on the others; derivatives of
+  // qa = dt (1 - rho^2)/4, K2 and A = K2 + qa with respect to kappa, sigma, rho, and Cd for the
+  // plain steps' C0 = r dt + Cd theta
+  int32_t qem;
+  double Cd, dqa_drho, dK2_dk, dK2_ds, dK2_dr, dA_dk, dA_ds, dA_dr;
 };
 
 // Shared floats per thread of the per-path adjoint with checkpoints in shared
@@ -93,6 +100,7 @@ struct AdjOutputs {
 struct BatchOption {
   ScenConst sc;             // base scenario constants
   AdjConst A;               // adjoint constants (adjoint books)
+  QemConst qm;              // QE-M constants (books under scheme QE-M)
   float S0, K, invS0, T;
   int32_t is_put;
   uint32_t steps;
@@ -119,6 +127,7 @@ struct BatchLaunch {
   float* gseg;        // adjoint with one segment per path: [3 seg_rows][grid threads] in global memory, else null
   size_t gseg_floats;  // its capacity
   int32_t tpb, ppt, unroll;  // the kernel's shape (batch_variant)
+  int32_t qem;               // 1: the options' log-spot steps under QE-M
 };
 
 struct BatchOutputs {
@@ -185,7 +194,7 @@ cudaError_t batch_gseg_threads(int num_sms, size_t* threads);
 // 256 (bit 0); price books: paths per thread 2 / 1 (bit 1), step-pair loop
 // unrolled 1 / 2 times (bit 2); adjoint books use bit 0 only.
 constexpr int kBatchVariants = 8;
-void batch_variant(int v, bool adjoint, BatchLaunch* B);
+void batch_variant(int v, bool adjoint, BatchLaunch* B);  // reads B->qem
 
 // Terminal (x_T, v_T) per path of scenario 0.
 cudaError_t launch_terminal(const PathLaunch& L, float* x_T, float* v_T, cudaStream_t stream);

@@ -97,8 +97,18 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
   const float2 xu = centered_uniform2(w_v, w_x);  // (2 U_V - 1, 2 U_X - 1)
   const float2 z = norminv_centered2(xu);
   const float xv = xu.x, zv = z.x, zx = z.y;
-  static_assert(!QEM || NS == 1, "QE-M runs the base scenario only");
   static_assert(NS % 2 == 1, "the base scenario plus up/down pairs");
+  if constexpr (QEM && NS > 1) {  // QE-M with bumped scenarios: one scenario at a time
+    const ScenConst zero{};
+    const QemConst zq{};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (DYN && s >= L.n_scen) break;
+      step_qem_bumped(L.sc[0], s == 0 ? zero : L.sc[s], L.qm, s == 0 ? zq : L.qmd[s], xv, zv, zx, v[s], x[s],
+                      c[s]);
+    }
+    return;
+  }
   step_scheme<(NS > 1), QEM>(L.sc[0], L.qm, xv, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
   for (int s = 1; s + 1 < NS; s += 2) {
@@ -145,7 +155,10 @@ __device__ __forceinline__ void step_paths(const PathLaunch& L, const uint32_t (
 }
 
 // Step 0 of every scenario of a common-random-number launch (see step0_crn).
-template <int NS, bool DYN>
+// Under QE-M the first-step constant K0p is r dt - qa (v0 + m0) - lam(v0) (set
+// on the host in FP64, where M exists at every scenario's v0), v' has no term of
+// its own and dl the coefficient K2.
+template <int NS, bool DYN, bool QEM = false>
 __device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uint32_t w_x, float (&v)[NS],
                                           float (&x)[NS], float (&c)[NS]) {
   const float xv = centered_uniform(w_v);
@@ -155,11 +168,20 @@ __device__ __forceinline__ void step0_all(const PathLaunch& L, uint32_t w_v, uin
   const ScenConst zero{};
   FirstConst fz = L.f0[0];
   fz.a = fz.b = fz.C = fz.L = fz.m0 = fz.K0p = 0.0f;  // base: zero deltas, its own threshold
+  ScenConst b0 = L.sc[0];
+  if (QEM) {
+    b0.Cv = 0.0f;
+    b0.Cdl = L.qm.K2;
+  }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     if (DYN && s >= L.n_scen) break;
-    step0_crn(L.f0[0], s == 0 ? fz : L.f0[s], L.sc[0], s == 0 ? zero : L.sc[s], L.sc[s].v0, omu, zv, zx, v[s],
-              x[s], c[s]);
+    ScenConst d0 = s == 0 ? zero : L.sc[s];
+    if (QEM) {
+      d0.Cv = 0.0f;
+      d0.Cdl = s == 0 ? 0.0f : L.qmd[s].K2;
+    }
+    step0_crn(L.f0[0], s == 0 ? fz : L.f0[s], b0, d0, L.sc[s].v0, omu, zv, zx, v[s], x[s], c[s]);
   }
 }
 
@@ -189,7 +211,7 @@ __device__ __forceinline__ void simulate_ppt(const PathLaunch& L, const uint64_t
 #pragma unroll
     for (int j = 0; j < PPT; ++j) w[j] = philox_draw(pl[j], u, L.rk);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) step0_all<NS, DYN>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
+    for (int j = 0; j < PPT; ++j) step0_all<NS, DYN, QEM>(L, w[j].x, w[j].y, v[j], x[j], c[j]);
     if (L.steps > 1) {
       uint32_t wv[PPT], wx[PPT];
 #pragma unroll
@@ -432,8 +454,11 @@ cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathO
 #define SIMR_LAUNCH(NS_, NV_, DYN_)                                                                \
   (one ? launch_t<NS_, NV_, 1, DYN_>(L, strikes, out, s, num_sms, stream, grid_used)               \
        : launch_t<NS_, NV_, 32, DYN_>(L, strikes, out, s, num_sms, stream, grid_used))
-  if (L.scheme == 1) {  // QE-M: the base scenario alone
-    if (L.n_scen != 1) return cudaErrorInvalidValue;
+  if (L.scheme == 1) {  // QE-M: the base scenario alone, or any scenario count
+    if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
+    if (L.n_scen > 1)
+      return one ? launch_t<kMaxScen, 0, 1, true, true>(L, strikes, out, s, num_sms, stream, grid_used)
+                 : launch_t<kMaxScen, 0, 32, true, true>(L, strikes, out, s, num_sms, stream, grid_used);
     return one ? launch_t<1, 0, 1, false, true>(L, strikes, out, s, num_sms, stream, grid_used)
                : launch_t<1, 0, 32, false, true>(L, strikes, out, s, num_sms, stream, grid_used);
   }
