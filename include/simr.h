@@ -433,7 +433,9 @@ SIMR_API int simr_finalize_sums(simr_ctx* ctx, const simr_heston* model, const d
  *   those of simr_price with the same seed, option_index and sizes.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Calls on one device share the array, which keeps the last call's
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset on a device it no longer names the array, so a process that
+ * resets a device must not call simr_price_noalloc on it again.  Calls on one device share the array, which keeps the last call's
  * contents (each call clears the words that must start at zero): calls that
  * overlap on the GPU -- on different streams, or from several host threads --
  * race and must be serialised by the caller.  A device strike that is not

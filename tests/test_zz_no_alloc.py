@@ -55,6 +55,26 @@ def test_noalloc_matches_simr_price_on_two_calls(lib, K_np, is_put, steps, paths
         torch.testing.assert_close(se, se_ref, rtol=0, atol=0)
 
 
+def test_noalloc_leaves_device_memory_unchanged(lib):
+    # after a first call (the symbol lookup), a call takes no device memory: the
+    # device's free memory and torch's allocator are the same before and after
+    simr, L = lib
+    model = dict(workloads.BASE_MODEL)
+    K = torch.as_tensor(workloads.strike_grid(), dtype=torch.float64, device="cuda")
+    p = torch.empty_like(K)
+    se = torch.empty_like(K)
+    assert _call(L, simr, model, K, False, 16, 50_000, 3, p, se) == 0, L.simr_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for seed in (4, 5):
+        assert _call(L, simr, model, K, False, 16, 50_000, seed, p, se) == 0, L.simr_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.isfinite(p).all() and torch.isfinite(se).all()
+
+
 def test_noalloc_rejects_sizes_and_host_pointers(lib):
     simr, L = lib
     model = dict(workloads.BASE_MODEL)
