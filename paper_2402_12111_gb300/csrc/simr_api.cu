@@ -598,6 +598,12 @@ int apply_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, Path
     L->qmd[s] = QemConst{(float)(qs[0] - qb[0]), (float)(qs[1] - qb[1]), (float)(qs[2] - qb[2]),
                          (float)(qs[3] - qb[3])};
   }
+  for (int k = 0; 2 * k + 1 < L->n_scen; ++k) {  // the paired steps' operands (as pair2)
+    const QemConst& a = L->qmd[2 * k + 1];
+    const QemConst& b = L->qmd[2 * k + 2 < L->n_scen ? 2 * k + 2 : 2 * k + 1];
+    L->qmd2[k] = QemConst2{make_float2(a.rdt, b.rdt), make_float2(a.qa, b.qa), make_float2(a.K2, b.K2),
+                           make_float2(a.A, b.A)};
+  }
   if (L->first_split) {
     double k0b = 0.0;
     bool ok = qem_first64(m, steps, (double)L->sc[0].v0, &k0b);

@@ -464,6 +464,9 @@ __device__ __forceinline__ void step_base2(const ScenConst& c, float2 xv, float2
 struct QemConst {
   float rdt, qa, K2, A;  // r dt, dt (1 - rho^2)/4, K2, K2 + K4/2
 };
+struct QemConst2 {  // two scenarios' QemConst (their deltas), lane by lane
+  float2 rdt, qa, K2, A;
+};
 
 // g(u) = -u - ln(1 - u) = sum_{k >= 2} u^k / k, u < 1: the series to u^8 for
 // |u| < 1/8 (remainder below 6e-8 relative), else the logarithm.
@@ -541,17 +544,13 @@ __device__ __forceinline__ void step_qem(const ScenConst& c, const QemConst& q, 
   v = vn;
 }
 
-// Two QE-M steps (two paths on the same constants) in packed FP32, lane for
-// lane step_qem: the quadratic branch and the series part of lam paired when
-// both lanes take them, every other case per lane by the scalar functions.
-__device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q, float2 xv, float2 zv, float2 zx,
-                                          float2& v, float2& x, float2& comp) {
-  const float2 m = p_fma(v, p_bc(c.E), p_bc(c.thE));
-  const float2 s2h = p_fma(v, p_bc(c.h1), p_bc(c.h2));
+// The QE-M variance step of two lanes with their own A (qem_from_moments lane
+// for lane): the quadratic branch and the series part of lam paired when both
+// lanes take them, every other case per lane by the scalar function.
+__device__ __forceinline__ void qem_from_moments2(float2 m, float2 s2h, float2 xv, float2 zv, float2 A, float2& vn,
+                                                  float2& dl, float2& lam, bool& okx, bool& oky) {
   const float2 m2 = p_mul(m, m);
   const float2 t = p_mul(m2, p_rcp(s2h));
-  float2 vn, dl, lam;
-  bool okx, oky;
   if (t.x > kQuadT && t.y > kQuadT) {
     const float2 tm1 = p_sub(t, p_bc(1.0f));
     const float2 root = p_sqrt(p_mul(t, tm1));
@@ -561,7 +560,7 @@ __device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q,
     const float2 bz = p_add(b, zv);
     vn = p_mul(p_mul(a, bz), bz);
     dl = p_mul(a, p_fma(zv, p_add(bz, b), p_bc(-1.0f)));
-    const float2 Aa = p_mul(p_bc(q.A), a);
+    const float2 Aa = p_mul(A, a);
     const float2 u = p_mul(p_bc(2.0f), Aa);
     okx = u.x < 1.0f;
     oky = u.y < 1.0f;
@@ -581,9 +580,20 @@ __device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q,
     if (!okx) lam.x = 0.0f;
     if (!oky) lam.y = 0.0f;
   } else {
-    okx = qem_from_moments(m.x, s2h.x, xv.x, zv.x, q.A, vn.x, dl.x, lam.x);
-    oky = qem_from_moments(m.y, s2h.y, xv.y, zv.y, q.A, vn.y, dl.y, lam.y);
+    okx = qem_from_moments(m.x, s2h.x, xv.x, zv.x, A.x, vn.x, dl.x, lam.x);
+    oky = qem_from_moments(m.y, s2h.y, xv.y, zv.y, A.y, vn.y, dl.y, lam.y);
   }
+}
+
+// Two QE-M steps (two paths on the same constants) in packed FP32, lane for
+// lane step_qem.
+__device__ __forceinline__ void step_qem2(const ScenConst& c, const QemConst& q, float2 xv, float2 zv, float2 zx,
+                                          float2& v, float2& x, float2& comp) {
+  const float2 m = p_fma(v, p_bc(c.E), p_bc(c.thE));
+  const float2 s2h = p_fma(v, p_bc(c.h1), p_bc(c.h2));
+  float2 vn, dl, lam;
+  bool okx, oky;
+  qem_from_moments2(m, s2h, xv, zv, p_bc(q.A), vn, dl, lam, okx, oky);
   const float2 s = p_add(v, vn);
   float2 inc;
   if (okx && oky) {
@@ -697,6 +707,77 @@ __device__ __forceinline__ void step_qem_bumped(const ScenConst& b, const ScenCo
   const float y = __fsub_rn(inc, comp);
   const float t = __fadd_rn(x, y);
   comp = __fsub_rn(__fsub_rn(t, x), y);
+  x = t;
+  v = vn;
+}
+
+// step_qem_bumped for two scenarios (lane for lane its operations): base
+// constants b, q (both lanes), deltas d, qd (lane x the first scenario's, lane y
+// the second's).
+__device__ __forceinline__ void step_qem_bumped2(const ScenConst2& b, const ScenConst2& d, const QemConst& q,
+                                                 const QemConst2& qd, float2 xv, float2 zv, float2 zx, float2& v,
+                                                 float2& x, float2& comp) {
+  const float2 m = p_add(p_fma(v, b.E, p_fma(v, d.E, d.thE)), b.thE);
+  const float2 s2h = p_add(p_fma(v, b.h1, p_fma(v, d.h1, d.h2)), b.h2);
+  float2 vn, dl, lam;
+  bool okx, oky;
+  qem_from_moments2(m, s2h, xv, zv, p_add(p_bc(q.A), qd.A), vn, dl, lam, okx, oky);
+  const float2 s = p_add(v, vn);
+  const float2 r = p_sqrt(s);
+  float2 inc, sm;
+  if (okx && oky) {
+    const float2 vm = p_add(v, m);
+    inc = p_fma(p_bc(-q.qa), vm, p_bc(q.rdt));
+    inc = p_fma(p_bc(q.K2), dl, inc);
+    inc = p_fma(p_mul(b.sK3, r), zx, inc);
+    sm = p_fma(p_mul(p_bc(-1.0f), qd.qa), vm, qd.rdt);
+    sm = p_fma(qd.K2, dl, sm);
+    sm = p_fma(p_mul(d.sK3, r), zx, sm);
+    sm = p_sub(sm, lam);
+  } else {  // per lane, step_qem_bumped's increment of that lane's branch
+    const float vv[2] = {v.x, v.y}, mm[2] = {m.x, m.y}, ss[2] = {s.x, s.y}, dd[2] = {dl.x, dl.y},
+                ll[2] = {lam.x, lam.y}, rr[2] = {r.x, r.y};
+    const float bsk[2] = {b.sK3.x, b.sK3.y}, dsk[2] = {d.sK3.x, d.sK3.y};
+    const float bC0[2] = {b.C0.x, b.C0.y}, bCv[2] = {b.Cv.x, b.Cv.y}, bmCd[2] = {b.mCd.x, b.mCd.y},
+                bCdl[2] = {b.Cdl.x, b.Cdl.y};
+    const float dC0[2] = {d.C0.x, d.C0.y}, dCv[2] = {d.Cv.x, d.Cv.y}, dmCd[2] = {d.mCd.x, d.mCd.y},
+                dCdl[2] = {d.Cdl.x, d.Cdl.y};
+    const float qrdt[2] = {qd.rdt.x, qd.rdt.y}, qqa[2] = {qd.qa.x, qd.qa.y}, qK2[2] = {qd.K2.x, qd.K2.y};
+    const float zz[2] = {zx.x, zx.y};
+    const bool ok[2] = {okx, oky};
+    float ri[2], rs[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float a, c;
+      if (ok[j]) {
+        const float vm = __fadd_rn(vv[j], mm[j]);
+        a = __fmaf_rn(-q.qa, vm, q.rdt);
+        a = __fmaf_rn(q.K2, dd[j], a);
+        a = __fmaf_rn(__fmul_rn(bsk[j], rr[j]), zz[j], a);
+        c = __fmaf_rn(-qqa[j], vm, qrdt[j]);
+        c = __fmaf_rn(qK2[j], dd[j], c);
+        c = __fmaf_rn(__fmul_rn(dsk[j], rr[j]), zz[j], c);
+        c = __fsub_rn(c, ll[j]);
+      } else {
+        a = __fmaf_rn(bCv[j], ss[j], bC0[j]);
+        a = __fmaf_rn(bmCd[j], vv[j], a);
+        a = __fmaf_rn(bCdl[j], dd[j], a);
+        a = __fmaf_rn(__fmul_rn(bsk[j], rr[j]), zz[j], a);
+        c = __fmaf_rn(dCv[j], ss[j], dC0[j]);
+        c = __fmaf_rn(dmCd[j], vv[j], c);
+        c = __fmaf_rn(dCdl[j], dd[j], c);
+        c = __fmaf_rn(__fmul_rn(dsk[j], rr[j]), zz[j], c);
+      }
+      ri[j] = a;
+      rs[j] = c;
+    }
+    inc = make_float2(ri[0], ri[1]);
+    sm = make_float2(rs[0], rs[1]);
+  }
+  inc = p_add(inc, sm);
+  const float2 y = p_sub(inc, comp);
+  const float2 t = p_add(x, y);
+  comp = p_sub(p_sub(t, x), y);
   x = t;
   v = vn;
 }

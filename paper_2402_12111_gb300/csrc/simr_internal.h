@@ -46,6 +46,7 @@ struct PathLaunch {
   int32_t scheme;         // 0: QE; 1: QE-M
   QemConst qm;            // QE-M constants of the base scenario
   QemConst qmd[kMaxScen]; // QE-M: the bumped scenarios' constant deltas to qm (qmd[0] zero)
+  QemConst2 qmd2[kMaxScen / 2];  // QE-M: scenarios (2k + 1, 2k + 2): their deltas lane by lane
 };
 
 // Counters of the generator's raw words: paths [path_begin, path_begin + n_paths)

@@ -98,14 +98,27 @@ __device__ __forceinline__ void step_all(const PathLaunch& L, uint32_t w_v, uint
   const float2 z = norminv_centered2(xu);
   const float xv = xu.x, zv = z.x, zx = z.y;
   static_assert(NS % 2 == 1, "the base scenario plus up/down pairs");
-  if constexpr (QEM && NS > 1) {  // QE-M with bumped scenarios: one scenario at a time
+  if constexpr (QEM && NS > 1) {  // QE-M with bumped scenarios: the base, then the pairs (DYN: one at a time)
     const ScenConst zero{};
     const QemConst zq{};
+    step_qem_bumped(L.sc[0], zero, L.qm, zq, xv, zv, zx, v[0], x[0], c[0]);
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      if (DYN && s >= L.n_scen) break;
-      step_qem_bumped(L.sc[0], s == 0 ? zero : L.sc[s], L.qm, s == 0 ? zq : L.qmd[s], xv, zv, zx, v[s], x[s],
-                      c[s]);
+    for (int s = 1; s < NS; ++s) {
+      if constexpr (DYN) {
+        if (s >= L.n_scen) break;
+        step_qem_bumped(L.sc[0], L.sc[s], L.qm, L.qmd[s], xv, zv, zx, v[s], x[s], c[s]);
+      } else if (s % 2 == 1) {
+        float2 vv = make_float2(v[s], v[s + 1]), xx = make_float2(x[s], x[s + 1]),
+               cc = make_float2(c[s], c[s + 1]);
+        step_qem_bumped2(pack_const(L.sc[0], L.sc[0]), L.pair2[(s - 1) / 2], L.qm, L.qmd2[(s - 1) / 2], p_bc(xv),
+                         p_bc(zv), p_bc(zx), vv, xx, cc);
+        v[s] = vv.x;
+        v[s + 1] = vv.y;
+        x[s] = xx.x;
+        x[s + 1] = xx.y;
+        c[s] = cc.x;
+        c[s + 1] = cc.y;
+      }
     }
     return;
   }
@@ -454,13 +467,22 @@ cudaError_t launch_paths(const PathLaunch& L, const double* strikes, const PathO
 #define SIMR_LAUNCH(NS_, NV_, DYN_)                                                                \
   (one ? launch_t<NS_, NV_, 1, DYN_>(L, strikes, out, s, num_sms, stream, grid_used)               \
        : launch_t<NS_, NV_, 32, DYN_>(L, strikes, out, s, num_sms, stream, grid_used))
-  if (L.scheme == 1) {  // QE-M: the base scenario alone, or any scenario count
-    if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
-    if (L.n_scen > 1)
-      return one ? launch_t<kMaxScen, 0, 1, true, true>(L, strikes, out, s, num_sms, stream, grid_used)
-                 : launch_t<kMaxScen, 0, 32, true, true>(L, strikes, out, s, num_sms, stream, grid_used);
-    return one ? launch_t<1, 0, 1, false, true>(L, strikes, out, s, num_sms, stream, grid_used)
-               : launch_t<1, 0, 32, false, true>(L, strikes, out, s, num_sms, stream, grid_used);
+  if (L.scheme == 1) {  // QE-M: the base scenario alone, 5 or 11 scenarios in pairs, any other count dynamic
+#define SIMR_LAUNCH_QEM(NS_, DYN_)                                                                     \
+  (one ? launch_t<NS_, 0, 1, DYN_, true>(L, strikes, out, s, num_sms, stream, grid_used)               \
+       : launch_t<NS_, 0, 32, DYN_, true>(L, strikes, out, s, num_sms, stream, grid_used))
+    switch (L.n_scen) {
+      case 1:
+        return SIMR_LAUNCH_QEM(1, false);
+      case 5:
+        return SIMR_LAUNCH_QEM(5, false);
+      case 11:
+        return SIMR_LAUNCH_QEM(11, false);
+      default:
+        if (L.n_scen < 1 || L.n_scen > kMaxScen) return cudaErrorInvalidValue;
+        return SIMR_LAUNCH_QEM(kMaxScen, true);
+    }
+#undef SIMR_LAUNCH_QEM
   }
   switch (L.n_scen) {
     case 1:

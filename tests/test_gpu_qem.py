@@ -166,6 +166,10 @@ QEM_FD_CASES = [
     ("positive_rho_grid", POS_RHO, workloads.strike_grid(), False, 64, 1 << 15, 5,
      ("vega", "theta", "kappa", "lrvar", "volvol", "corr")),
     ("one_sided_v0_zero", dict(CFG, v0=0.0), [100.0], False, 16, 1 << 14, 5, ("vega", "corr")),
+    ("seven_in_pairs", COARSE, [90.0, 100.0, 110.0], True, 16, 1 << 15, 6,
+     ("delta", "vega", "rho", "kappa", "lrvar", "volvol", "corr")),
+    ("one_step_ragged_all_nine", CFG, [95.0, 100.5, 105.0], True, 1, 999, 7, ALL_NINE),
+    ("one_step_in_pairs", CFG, [100.0], False, 1, 4097, 8, ("delta", "gamma", "vega", "theta", "rho")),
 ]
 
 
@@ -189,6 +193,22 @@ def test_fd_greeks_match_qem_oracle(simr, name, model, K, is_put, steps, paths, 
         tol = _greek_tol(gname, go[:, j], h, steps, paths, model)
         err = np.abs(g[:, j] - go[:, j])
         assert np.all(err <= tol), (gname, err.max(), (err / np.maximum(np.abs(go[:, j]), 1e-300)).max())
+
+
+def test_qem_scenario_pairs_equal_single_scenarios(simr):
+    # 5 and 11 scenarios run in packed pairs, other counts one scenario at a time
+    # (the dynamic kernel): lane for lane the same operations, so the Greeks both
+    # kernels compute are equal bit for bit
+    K = _dev([90.0, 100.0, 110.0])
+    with simr.scheme("qem"):
+        _, g5 = simr.greeks_fd(COARSE, K, False, 16, 20000, 3, greeks=("vega", "theta"))        # 5: pairs
+        _, g7 = simr.greeks_fd(COARSE, K, False, 16, 20000, 3, greeks=("vega", "theta", "corr"))  # 7: dynamic
+        _, g11 = simr.greeks_fd(COARSE, K, False, 16, 20000, 3,
+                                greeks=("vega", "theta", "kappa", "lrvar", "volvol"))             # 11: pairs
+        _, g13 = simr.greeks_fd(COARSE, K, False, 16, 20000, 3,
+                                greeks=("vega", "theta", "kappa", "lrvar", "volvol", "corr"))     # 13: dynamic
+    torch.testing.assert_close(g5, g7[:, :2], rtol=0, atol=0)
+    torch.testing.assert_close(g11, g13[:, :5], rtol=0, atol=0)
 
 
 def test_qem_fd_differs_from_qe_fd(simr):
@@ -250,6 +270,9 @@ QEM_ADJ_CASES = [
     ("wild_coarse", WILD, [90.0, 100.0, 110.0], False, 8, 65536, 4, 2, 1e-3, 0.03, 0.5),
     ("hard_exp_branch", HARD, [90.0, 100.0, 110.0], False, 64, 16384, 5, 8, 5e-3, 0.08, 2.5, 1e-3),
     ("odd_steps_one_segment", CFG, [95.0, 105.0], True, 33, 4097, 6, 34, 1e-3, 0.0, 2e-3),
+    # 40 strikes (a ragged second 32-strike tile), 7 steps, 1,000 paths (a ragged last warp)
+    ("ragged_40_strikes", CFG, workloads.strike_grid(n=40), True, 7, 1000, 9, 2, 1e-3, 0.0, 2e-2),
+    ("one_step", COARSE, [100.0], False, 1, 2048, 10, 2, 1e-3, 0.0, 2e-3),
 ]
 
 
