@@ -292,7 +292,8 @@ SIMR_API int simr_paths_adjoint(simr_ctx* ctx, const simr_heston* model, uint32_
  *   weights[n_assets]       in  host, finite (negative allowed: spreads, exchange)
  *   strikes[n_strikes]      in  host or device, finite and >= 0; n_strikes <= 1024
  *   price, stderr_out (nullable)  out  [n_strikes], host or device
- * Plain QE only (SIMR_EUNSUPPORTED under SIMR_SCHEME_QEM).
+ * Under SIMR_SCHEME_QEM each asset takes the QE-M log-spot step with its own
+ * martingale correction.
  */
 SIMR_API int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
                                const double* weights, const double* strikes, int n_strikes, int is_put,
@@ -316,7 +317,8 @@ SIMR_API int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_a
  * simr_paths_adjoint (the reverse step also differentiates lam = ln M - A m and
  * the constants qa = dt (1 - rho^2)/4, K2 and A) and simr_batch_submit (price
  * books then have two kernel shapes, SIMR_BATCH_VARIANT 0 and 1: two paths per
- * thread, no unrolling).  simr_basket_price returns SIMR_EUNSUPPORTED under it;
+ * thread, no unrolling) and simr_basket_price (each asset its own correction:
+ * its log-spot normal is independent of its own variance path).
  * simr_price_noalloc is always QE.  SIMR_EINVAL for an unknown scheme.
  */
 SIMR_API int simr_set_scheme(simr_ctx* ctx, int scheme);

@@ -472,7 +472,9 @@ int oracle_states(const oracle_heston* m, uint32_t steps, uint32_t every, uint64
  * index k, except that its log-spot normal is z_k = sum_{j <= k} Lc[k][j] eps_j,
  * where eps_j = Phi^-1(U_X) of asset j and Lc is the lower Cholesky factor of
  * the correlation of the spot drivers (row-major A x A; computed by the caller).
- * The variance drivers stay independent across assets.  x[i * A + k] =
+ * The variance drivers stay independent across assets.  Under QE-M each asset
+ * takes its own martingale correction: z_k is a standard normal independent of
+ * the asset's own variance path, so M is the single-asset one.  x[i * A + k] =
  * ln(S_T / S0) of asset k on path path_begin + i; margin[i] (may be NULL) the
  * smallest branch-decision margin over the path's assets and steps.
  */
@@ -516,7 +518,7 @@ int oracle_basket_terminal(const oracle_heston* models, int n_assets, const doub
             double mg;
             const double vn = oracle_qe_variance_step(v[a], uv[a], ka, &br, &mg, NULL);
             if (mg < min_mg) min_mg = mg;
-            x[a] += ka[4] + ka[5] * v[a] + ka[6] * vn + sqrt(ka[7] * v[a] + ka[8] * vn) * z;
+            x[a] += step_k0(&models[a], ka, v[a], -1) + ka[5] * v[a] + ka[6] * vn + sqrt(ka[7] * v[a] + ka[8] * vn) * z;
             v[a] = vn;
           }
         }

@@ -645,11 +645,6 @@ void adjoint_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, P
   adjoint_qem_fields(m, steps, A);
 }
 
-int require_plain_qe(const simr_ctx* ctx, const char* what) {
-  if (ctx->scheme == SIMR_SCHEME_QE) return SIMR_OK;
-  return fail(SIMR_EUNSUPPORTED, "%s runs the plain QE scheme only (simr_set_scheme)", what);
-}
-
 int ensure_scratch(simr_ctx* ctx, const PathLaunch& L) {
   return ensure(&ctx->partials, &ctx->partial_doubles, paths_scratch_doubles(L, ctx->num_sms), "reduction scratch");
 }
@@ -1473,8 +1468,7 @@ int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, co
   if (steps < 1) return fail(SIMR_EINVAL, "steps must be >= 1");
   if (paths < 1 || paths > (1ull << 40)) return fail(SIMR_EINVAL, "paths must lie in [1, 2^40]");
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
-  int rc = require_plain_qe(ctx, "the basket kernel");
-  if (rc) return rc;
+  int rc = SIMR_OK;
   for (int k = 0; k < n_assets; ++k) {
     if ((rc = check_model(&assets[k]))) {
       char msg[sizeof(g_err)];
@@ -1520,6 +1514,15 @@ int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, co
     for (int j = 0; j <= k; ++j) L.Lc[k * (k + 1) / 2 + j] = (float)Lc[k * A + j];
   }
   for (int q = 0; 2 * q + 1 < A; ++q) L.pk[q] = pack_const(L.sc[2 * q], L.sc[2 * q + 1]);
+  if (ctx->scheme == SIMR_SCHEME_QEM) {  // each asset its own martingale correction
+    L.scheme = 1;
+    for (int k = 0; k < A; ++k) L.qm[k] = qem_const(assets[k], steps);
+    for (int q = 0; 2 * q + 1 < A; ++q) {
+      const QemConst &a = L.qm[2 * q], &b = L.qm[2 * q + 1];
+      L.qk[q] = QemConst2{make_float2(a.rdt, b.rdt), make_float2(a.qa, b.qa), make_float2(a.K2, b.K2),
+                          make_float2(a.A, b.A)};
+    }
+  }
   L.n_assets = A;
   L.n_strikes = n_strikes;
   L.nk_pad = n_strikes == 1 ? 1 : ((n_strikes + 31) / 32) * 32;

@@ -43,10 +43,54 @@ __device__ __forceinline__ void step_pair(const ScenConst2& c, float2 xv, float2
   v = vn;
 }
 
+// step_qem of two assets at once (their own constants and A lane by lane), lane
+// for lane the scalar step's operations and rounding.  An asset's log-spot
+// normal z_k is standard normal and independent of its own variance path, so
+// its martingale correction is the single-asset one.
+__device__ __forceinline__ void step_pair_qem(const ScenConst2& c, const QemConst2& q, float2 xv, float2 zv,
+                                              float2 zx, float2& v, float2& x, float2& comp) {
+  const float2 m = p_fma(v, c.E, c.thE);
+  const float2 s2h = p_fma(v, c.h1, c.h2);
+  float2 vn, dl, lam;
+  bool okx, oky;
+  qem_from_moments2(m, s2h, xv, zv, q.A, vn, dl, lam, okx, oky);
+  const float2 s = p_add(v, vn);
+  float2 inc;
+  if (okx && oky) {
+    inc = p_sub(p_fma(p_mul(p_bc(-1.0f), q.qa), p_add(v, m), q.rdt), lam);
+    inc = p_fma(q.K2, dl, inc);
+  } else {
+    const float vv[2] = {v.x, v.y}, mm[2] = {m.x, m.y}, ss[2] = {s.x, s.y}, dd[2] = {dl.x, dl.y},
+                ll[2] = {lam.x, lam.y};
+    const float qa[2] = {q.qa.x, q.qa.y}, rdt[2] = {q.rdt.x, q.rdt.y}, K2[2] = {q.K2.x, q.K2.y};
+    const float C0[2] = {c.C0.x, c.C0.y}, Cv[2] = {c.Cv.x, c.Cv.y}, mCd[2] = {c.mCd.x, c.mCd.y},
+                Cdl[2] = {c.Cdl.x, c.Cdl.y};
+    const bool ok[2] = {okx, oky};
+    float r[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (ok[j]) {
+        r[j] = __fmaf_rn(K2[j], dd[j], __fsub_rn(__fmaf_rn(-qa[j], __fadd_rn(vv[j], mm[j]), rdt[j]), ll[j]));
+      } else {
+        float t = __fmaf_rn(Cv[j], ss[j], C0[j]);
+        t = __fmaf_rn(mCd[j], vv[j], t);
+        r[j] = __fmaf_rn(Cdl[j], dd[j], t);
+      }
+    }
+    inc = make_float2(r[0], r[1]);
+  }
+  inc = p_fma(p_mul(c.sK3, p_sqrt(s)), zx, inc);
+  const float2 y = p_sub(inc, comp);
+  const float2 t2 = p_add(x, y);
+  comp = p_sub(p_sub(t2, x), y);
+  x = t2;
+  v = vn;
+}
+
 // One step of the asset pair (k, k + 1) from their variance uniforms (centred)
 // and spot uniforms' normals eps[0 .. k + 1]: z = Lc eps over the rows k, k + 1,
 // summed in column order as for one asset at a time.
-template <int NA>
+template <int NA, bool QEM>
 __device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const ScenConst2& c, int k, float2 xv,
                                                  const float (&eps)[NA], float2& v, float2& x, float2& comp) {
   const float* ra = L.Lc + k * (k + 1) / 2;
@@ -59,13 +103,16 @@ __device__ __forceinline__ void basket_pair_step(const BasketLaunch& L, const Sc
   }
   z.y = __fmaf_rn(rb[k + 1], eps[k + 1], z.y);
   const float2 zv = norminv_centered2(xv);
-  step_pair(c, xv, zv, z, v, x, comp);
+  if constexpr (QEM)
+    step_pair_qem(c, L.qk[k / 2], xv, zv, z, v, x, comp);
+  else
+    step_pair(c, xv, zv, z, v, x, comp);
 }
 
 // One step of the lone last asset k of an odd count (k only known at run
 // time, its state in plain registers) from its variance uniform (centred), the
 // pairs' eps[0 .. k - 1] and its own e, as one lane of basket_pair_step.
-template <int NA>
+template <int NA, bool QEM>
 __device__ __forceinline__ void basket_lone_step(const BasketLaunch& L, int k, float xv, const float (&eps)[NA],
                                                  float e, float& v, float& x, float& comp) {
   const float* ra = L.Lc + k * (k + 1) / 2;
@@ -74,10 +121,10 @@ __device__ __forceinline__ void basket_lone_step(const BasketLaunch& L, int k, f
   for (int j = 0; j < NA; ++j)
     if (j < k) z = __fmaf_rn(ra[j], eps[j], z);
   z = __fmaf_rn(ra[k], e, z);
-  step_base<false>(L.sc[k], xv, norminv_centered(xv), z, v, x, comp);
+  step_scheme<false, QEM>(L.sc[k], L.qm[k], xv, norminv_centered(xv), z, v, x, comp);
 }
 
-template <int NA, int TILE>
+template <int NA, int TILE, bool QEM>
 __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_constant__ BasketLaunch L,
                                                                    const double* __restrict__ strikes,
                                                                    BasketOutputs out, double* __restrict__ partials,
@@ -139,13 +186,13 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
         const float2 e = norminv_centered2(centered_uniform2(wa.y, wb.y));
         eps[k] = e.x;
         eps[k + 1] = e.y;
-        basket_pair_step<NA>(L, L.pk[q], k, centered_uniform2(wa.x, wb.x), eps, v[q], x[q], comp[q]);
+        basket_pair_step<NA, QEM>(L, L.pk[q], k, centered_uniform2(wa.x, wb.x), eps, v[q], x[q], comp[q]);
       }
       if (na & 1) {
         const uint4 w = philox_draw(pl, philox_ctr(p, (uint32_t)kl, L.rk), L.rk);
         wzl = w.z;
         wwl = w.w;
-        basket_lone_step<NA>(L, kl, centered_uniform(w.x), eps, norminv_centered(centered_uniform(w.y)), vl, xl, cl);
+        basket_lone_step<NA, QEM>(L, kl, centered_uniform(w.x), eps, norminv_centered(centered_uniform(w.y)), vl, xl, cl);
       }
       if (2 * p + 1 < L.steps) {
 #pragma unroll
@@ -155,10 +202,10 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
           const float2 e = norminv_centered2(centered_uniform2(ww[k], ww[k + 1]));
           eps[k] = e.x;
           eps[k + 1] = e.y;
-          basket_pair_step<NA>(L, L.pk[q], k, centered_uniform2(wz[k], wz[k + 1]), eps, v[q], x[q], comp[q]);
+          basket_pair_step<NA, QEM>(L, L.pk[q], k, centered_uniform2(wz[k], wz[k + 1]), eps, v[q], x[q], comp[q]);
         }
         if (na & 1)
-          basket_lone_step<NA>(L, kl, centered_uniform(wzl), eps, norminv_centered(centered_uniform(wwl)), vl, xl,
+          basket_lone_step<NA, QEM>(L, kl, centered_uniform(wzl), eps, norminv_centered(centered_uniform(wwl)), vl, xl,
                                cl);
       }
     }
@@ -231,14 +278,14 @@ __global__ void __launch_bounds__(kBasketTpb) heston_basket_kernel(const __grid_
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-template <int NA, int TILE>
+template <int NA, int TILE, bool QEM>
 cudaError_t launch_basket_t(const BasketLaunch& L, const double* strikes, const BasketOutputs& out,
                             double* partials, size_t partial_doubles, unsigned int* ticket, int num_sms,
                             cudaStream_t stream) {
   const int warps = kBasketTpb / kWarp;
   const size_t row = 2 * (size_t)L.nk_pad;
   const size_t smem = warps * row * sizeof(double) + L.nk_pad * sizeof(float) + 16;
-  auto kern = heston_basket_kernel<NA, TILE>;
+  auto kern = heston_basket_kernel<NA, TILE, QEM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -259,9 +306,13 @@ template <int NA>
 cudaError_t launch_basket_na(const BasketLaunch& L, const double* strikes, const BasketOutputs& out,
                              double* partials, size_t partial_doubles, unsigned int* ticket, int num_sms,
                              cudaStream_t stream) {
+  if (L.scheme == 1)
+    return L.nk_pad == 1
+               ? launch_basket_t<NA, 1, true>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream)
+               : launch_basket_t<NA, 32, true>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
   return L.nk_pad == 1
-             ? launch_basket_t<NA, 1>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream)
-             : launch_basket_t<NA, 32>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
+             ? launch_basket_t<NA, 1, false>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream)
+             : launch_basket_t<NA, 32, false>(L, strikes, out, partials, partial_doubles, ticket, num_sms, stream);
 }
 
 }  // namespace

@@ -249,9 +249,12 @@ struct BasketLaunch {
   float Lc[kMaxAssets * (kMaxAssets + 1) / 2];       // lower Cholesky factor, rows packed
   float S0w[kMaxAssets];                             // S0_k w_k
   int32_t n_assets, n_strikes, nk_pad, is_put;
-  uint32_t steps, pad;
+  uint32_t steps;
+  int32_t scheme;                                    // 0: QE; 1: QE-M
   uint64_t paths;
   double disc, paths_total;
+  QemConst qm[kMaxAssets];                           // QE-M constants per asset
+  QemConst2 qk[kMaxAssets / 2];                      // the same, assets (2q, 2q + 1) packed lane by lane
 };
 
 struct BasketOutputs {

@@ -119,6 +119,43 @@ def test_basket_rejects_bad_inputs(simr):
         simr.basket_price([BASE, dict(BASE, T=2.0)], np.eye(2), [1, 1], [100.0])  # T differs
     with pytest.raises(simr.SimrError):
         simr.basket_price([BASE] * 17, np.eye(17), np.ones(17), [100.0])       # too many assets
+
+
+# QE-M: each asset takes its own martingale correction (its log-spot normal is
+# independent of its own variance path); both sides under QE-M, the same
+# tolerances.  Odd counts run their last asset alone (the scalar QE-M step).
+QEM_CASES = [
+    ("two_assets", 2, [100.0, 160.0], False, 32, 65536, 1),
+    ("five_call", 5, [400.0, 450.0, 500.0], False, 48, 32768, 3),
+    ("eight_ragged_put_grid", 8, list(np.linspace(500.0, 800.0, 40)), True, 33, 5003, 4),
+]
+
+
+@pytest.mark.parametrize("name,n,K,is_put,steps,paths,seed", QEM_CASES, ids=[c[0] for c in QEM_CASES])
+def test_basket_price_parity_under_qem(simr, name, n, K, is_put, steps, paths, seed):
+    models = _models(n, 10 + seed)
+    corr = _corr(n, seed)
+    w = np.linspace(1.0, 0.5, n)
+    K = np.asarray(K)
     with simr.scheme("qem"):
-        with pytest.raises(simr.SimrError):
-            simr.basket_price(m, np.eye(2), [1, 1], [100.0])
+        p, se = simr.basket_price(models, corr, w, torch.as_tensor(K, device="cuda"), is_put, steps, paths, seed)
+    p0, _ = simr.basket_price(models, corr, w, torch.as_tensor(K, device="cuda"), is_put, steps, paths, seed)
+    with oracle.scheme("qem"):
+        po, seo = oracle.basket_price(models, corr, w, K, is_put, steps, paths, seed)
+        tol = 1e-5 * np.abs(po) + _allowance(models, corr, w, K, is_put, steps, paths, seed) + 1e-12
+    p, se = p.cpu().numpy(), se.cpu().numpy()
+    assert np.all(np.abs(p - po) <= tol), (p - po, tol)
+    assert np.all(np.abs(se - seo) <= 1e-4 * seo + 1e-9)
+    assert np.abs(p0.cpu().numpy() - p).max() > 0.0  # the correction reached the kernel
+
+
+def test_identity_correlation_reproduces_single_asset_qem_prices(simr):
+    models = _models(3, 21)
+    K = np.array([70.0, 90.0, 110.0])
+    with simr.scheme("qem"):
+        for k in range(3):
+            w = np.eye(3)[k]
+            p, se = simr.basket_price(models, np.eye(3), w, K, False, 40, 30000, 6)
+            pk, sek = simr.price(models[k], K, False, 40, 30000, 6, option_index=k)
+            np.testing.assert_allclose(p.numpy(), pk.numpy(), rtol=1e-8, atol=1e-10)
+            np.testing.assert_allclose(se.numpy(), sek.numpy(), rtol=1e-6, atol=1e-10)

@@ -130,15 +130,14 @@ def test_lsm_under_qem_matches_oracle(simr):
         assert p.item() == pytest.approx(ref.price, rel=1e-5)
 
 
-def test_basket_refuses_qem(simr):
-    # correlated baskets run the plain scheme only
-    assets = [CFG, dict(CFG, S0=90.0)]
-    corr = np.eye(2)
-    args = (assets, corr, [0.5, 0.5], _dev([95.0]), False, 16, 1024, 1)
+def test_scheme_context_restores_qe(simr):
+    # every entry point runs QE-M inside the context and QE again after it
+    K = _dev([100.0])
+    p_qe, _ = simr.price(CFG, K, False, 16, 4096, 1)
     with simr.scheme("qem"):
-        with pytest.raises(simr.SimrError):
-            simr.basket_price(*args)
-    simr.basket_price(*args)  # the scheme is back to QE afterwards
+        p_qem, _ = simr.price(CFG, K, False, 16, 4096, 1)
+    p_after, _ = simr.price(CFG, K, False, 16, 4096, 1)
+    assert torch.equal(p_after, p_qe) and not torch.equal(p_qem, p_qe)
 
 
 # ---------------------------------------------------------------------------

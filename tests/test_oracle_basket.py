@@ -64,3 +64,41 @@ def test_discounted_basket_is_a_martingale():
     fwd = sum(wk * m["S0"] for wk, m in zip(w, models))
     # QE without the martingale correction: a small drift bias on top of 3 SE
     assert abs(p[0] - fwd) < 3 * se[0] + 2e-3 * fwd
+
+
+# QE-M: each asset's log-spot normal z_k is standard normal and independent of
+# its own variance path, so each asset takes its single-asset correction.
+def test_one_asset_is_the_single_asset_scheme_under_qem():
+    with oracle.scheme("qem"):
+        x = oracle.basket_terminal([BASE], [[1.0]], 24, 5, 0, 3000)
+        xo, _, _ = oracle.terminal(BASE, 24, 5, 0, 3000)
+    np.testing.assert_array_equal(x[:, 0], xo)
+    x_qe = oracle.basket_terminal([BASE], [[1.0]], 24, 5, 0, 3000)
+    assert np.abs(x_qe[:, 0] - xo).max() > 1e-7  # the correction is in there
+
+
+def test_identity_correlation_gives_each_asset_its_qem_paths():
+    models = workloads.random_models(3, 12)
+    for m in models:
+        m["T"] = 1.0
+        m["r"] = 0.03
+    with oracle.scheme("qem"):
+        x = oracle.basket_terminal(models, np.eye(3), 16, 9, 100, 2000)
+        for k, m in enumerate(models):
+            xo, _, _ = oracle.terminal(m, 16, 9, 100, 2000, option_index=k)
+            np.testing.assert_array_equal(x[:, k], xo)
+
+
+def test_each_discounted_asset_is_a_martingale_under_qem():
+    # a coarse, strongly correlated book: every asset's discounted spot within 3 SE
+    # of its S0 (the scheme's exact one-step martingale is pinned in
+    # test_oracle_qem.py; this checks that the correlated normals leave it intact)
+    models = [dict(BASE, sigma=1.0, rho=-0.9, kappa=0.5, T=2.0), dict(BASE, S0=80.0, sigma=0.8, rho=-0.8, T=2.0)]
+    corr = np.array([[1.0, 0.7], [0.7, 1.0]])
+    n = 1 << 18
+    with oracle.scheme("qem"):
+        x = oracle.basket_terminal(models, corr, 8, 6, 0, n)
+    for k, m in enumerate(models):
+        d = math.exp(-m["r"] * m["T"]) * m["S0"] * np.exp(x[:, k])
+        se = d.std(ddof=1) / math.sqrt(n)
+        assert abs(d.mean() - m["S0"]) < 3 * se, (k, d.mean(), se)

@@ -150,6 +150,8 @@ C_MISTAKES = [
     ("qem_drops_rate", "return m->r * k[0] - lnM", "return -lnM",
      qem_pins.test_multi_step_martingale_within_monte_carlo_error),
     # correlated baskets
+    ("basket_qem_plain_constant", "x[a] += step_k0(&models[a], ka, v[a], -1)", "x[a] += ka[4]",
+     basket_pins.test_one_asset_is_the_single_asset_scheme_under_qem),
     ("basket_cholesky_transposed", "z += Lc[a * A + j] * eps[j];", "z += Lc[j * A + a] * eps[j];",
      lambda: basket_pins.test_exchange_option_in_the_black_scholes_limit_is_margrabe(0.6)),
     ("basket_shared_draws", "oracle_step_uniforms(seed, (uint32_t)a, path, n, &uv[a], &u_x);",
