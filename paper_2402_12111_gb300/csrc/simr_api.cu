@@ -540,6 +540,12 @@ void qem_const64(const simr_heston& m, uint32_t steps, double q[4]) {
   q[3] = K2 + qa;
 }
 
+// Two scenarios' (or assets') QE-M constants lane by lane.
+QemConst2 pack_qem(const QemConst& a, const QemConst& b) {
+  return QemConst2{make_float2(a.rdt, b.rdt), make_float2(a.qa, b.qa), make_float2(a.K2, b.K2),
+                   make_float2(a.A, b.A)};
+}
+
 QemConst qem_const(const simr_heston& m, uint32_t steps) {
   double q[4];
   qem_const64(m, steps, q);
@@ -598,12 +604,8 @@ int apply_scheme(const simr_ctx* ctx, const simr_heston& m, uint32_t steps, Path
     L->qmd[s] = QemConst{(float)(qs[0] - qb[0]), (float)(qs[1] - qb[1]), (float)(qs[2] - qb[2]),
                          (float)(qs[3] - qb[3])};
   }
-  for (int k = 0; 2 * k + 1 < L->n_scen; ++k) {  // the paired steps' operands (as pair2)
-    const QemConst& a = L->qmd[2 * k + 1];
-    const QemConst& b = L->qmd[2 * k + 2 < L->n_scen ? 2 * k + 2 : 2 * k + 1];
-    L->qmd2[k] = QemConst2{make_float2(a.rdt, b.rdt), make_float2(a.qa, b.qa), make_float2(a.K2, b.K2),
-                           make_float2(a.A, b.A)};
-  }
+  for (int k = 0; 2 * k + 1 < L->n_scen; ++k)  // the paired steps' operands (as pair2)
+    L->qmd2[k] = pack_qem(L->qmd[2 * k + 1], L->qmd[2 * k + 2 < L->n_scen ? 2 * k + 2 : 2 * k + 1]);
   if (L->first_split) {
     double k0b = 0.0;
     bool ok = qem_first64(m, steps, (double)L->sc[0].v0, &k0b);
@@ -1517,11 +1519,7 @@ int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, co
   if (ctx->scheme == SIMR_SCHEME_QEM) {  // each asset its own martingale correction
     L.scheme = 1;
     for (int k = 0; k < A; ++k) L.qm[k] = qem_const(assets[k], steps);
-    for (int q = 0; 2 * q + 1 < A; ++q) {
-      const QemConst &a = L.qm[2 * q], &b = L.qm[2 * q + 1];
-      L.qk[q] = QemConst2{make_float2(a.rdt, b.rdt), make_float2(a.qa, b.qa), make_float2(a.K2, b.K2),
-                          make_float2(a.A, b.A)};
-    }
+    for (int q = 0; 2 * q + 1 < A; ++q) L.qk[q] = pack_qem(L.qm[2 * q], L.qm[2 * q + 1]);
   }
   L.n_assets = A;
   L.n_strikes = n_strikes;

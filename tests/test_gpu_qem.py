@@ -396,3 +396,25 @@ def test_qem_book_sample_matches_oracle(simr, small_book):
         # or a branch threshold can move a few paths' terms: the full parity is the
         # adjoint tests' above)
         assert np.all(np.abs(g[i] - go[0]) <= 1e-3 * np.abs(go[0]).max() + 1e-4 * np.abs(go[0])), (i, g[i], go[0])
+
+
+def test_full_size_grid_price_parity_under_qem(simr):
+    # the bench workload's size (252 steps x 2^20 paths x 32 strikes) under QE-M
+    w = workloads.grid()
+    with simr.scheme("qem"):
+        p, se = simr.price(w.model, _dev(w.strikes), False, w.steps, w.paths, w.seed)
+    with oracle.scheme("qem"):
+        po, seo = oracle.price(w.model, w.strikes, False, w.steps, w.paths, w.seed)
+    p, se = p.cpu().numpy(), se.cpu().numpy()
+    tol = 1e-5 * np.abs(po) + _flip_allowance(w.model, w.strikes, False, w.steps, w.paths, w.seed) + 1e-12
+    assert np.all(np.abs(p - po) <= tol), (np.abs(p - po) / np.abs(po)).max()
+    assert np.all(np.abs(se - seo) <= 1e-4 * seo + 1e-9)
+
+
+def test_full_size_adjoint_under_qem_checkpoint_every_16(simr):
+    # config 2's adjoint workload (252 x 2^20 x 32 strikes, a checkpoint every 16
+    # steps) under QE-M, every column against the QE-M oracle's reverse mode
+    from test_gpu_adjoint import check_adjoint
+
+    with simr.scheme("qem"), oracle.scheme("qem"):
+        check_adjoint(simr, CFG, workloads.strike_grid(), False, 252, 1 << 20, 1, 16, 1e-3, 0.0, 1e-3)
