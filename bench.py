@@ -145,13 +145,25 @@ def kernel_source_sha() -> str:
 
 
 PATH_KERNEL_PROFILE = os.path.join("profiles", "heston_paths_grid32_252x1048576.txt")
+ADJOINT_KERNEL_SOURCES = ("paper_2402_12111_gb300/csrc/simr_adjoint.cu",
+                          "paper_2402_12111_gb300/csrc/simr_adjoint_path.cuh") + PATH_KERNEL_SOURCES[1:]
+ADJOINT_KERNEL_PROFILE = os.path.join("profiles", "heston_adjoint_grid32_252x1048576.txt")
 
 
-def _profile_values(sha: str) -> dict:
-    """The key: value lines of the committed ncu summary of the path kernel, if it was taken on
-    the current kernel sources (else {})."""
+def adjoint_source_sha() -> str:
+    """Hash of the code (comments aside) the adjoint kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in ADJOINT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
+    return h.hexdigest()[:16]
+
+
+def _profile_values(sha: str, profile: str = PATH_KERNEL_PROFILE) -> dict:
+    """The key: value lines of a committed ncu summary, if it was taken on the current kernel
+    sources (else {})."""
     try:
-        lines = open(os.path.join(ROOT, PATH_KERNEL_PROFILE)).read().splitlines()
+        lines = open(os.path.join(ROOT, profile)).read().splitlines()
     except OSError:
         return {}
     kv = {}
@@ -160,6 +172,16 @@ def _profile_values(sha: str) -> dict:
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
     return kv if kv.get("kernel_source_sha") == sha else {}
+
+
+def profiled_adjoint_k32_traffic(sha: str):
+    """DRAM bytes per launch of the adjoint kernel at a checkpoint every 32 steps from the committed
+    ncu summary (or None).  Captured at 2^22 paths: the kernel's only DRAM traffic is its partial rows,
+    one per block of the persistent grid, which does not grow with the paths."""
+    try:
+        return float(_profile_values(sha, ADJOINT_KERNEL_PROFILE)["traffic_bytes_per_launch_k32"])
+    except (KeyError, ValueError):
+        return None
 
 
 def profiled_traffic(sha: str):
@@ -401,7 +423,8 @@ def run_headline(args, simr, dev, stream):
     flops = FLOPS_SHARED + FLOPS_PER_SCENARIO + FLOPS_ADJOINT_REVERSE
     achieved = flops * ps_head / head["adjoint_k32_s"] / 1e12
     head["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": profiled_adjoint_k32_traffic(adjoint_source_sha()),
+                        "traffic_source": ADJOINT_KERNEL_PROFILE,
                         "peak_kind": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                                      f"x 2 x {sm_mhz:.0f} MHz (the median SM clock sampled during the pass)",
                         "flops_per_path_step": flops,

@@ -103,3 +103,15 @@ def test_clock_summary_reads_clocks_and_throttle_reasons():
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
     s.out = []
     assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_profile_provenance_is_parsed_by_source_hash():
+    # roofline.traffic comes from a committed ncu summary only when the summary names
+    # the hash of the sources the kernel is compiled from; any other hash gives None
+    import bench
+
+    assert len(bench.kernel_source_sha()) == 16 and len(bench.adjoint_source_sha()) == 16
+    assert bench.profiled_traffic("0" * 16) is None
+    assert bench.profiled_adjoint_k32_traffic("0" * 16) is None
+    t = bench.profiled_traffic(bench.kernel_source_sha())
+    assert t is None or t > 0
