@@ -283,3 +283,25 @@ def test_injected_faults_are_reported_and_the_context_survives(simr):
             call()
         call()
     simr.inject_fault("off")
+
+
+def test_tiny_paths_reproduce_the_oracle_fixture(simr):
+    # the oracle's stored terminal states at 1 and 2 steps, 8 paths
+    # (tests/golden/tiny_paths.txt): the GPU's per-path states within FP32 rounding
+    import os
+
+    models = {"standard": CFG, "vol_of_vol_0.9": HARD}
+    bound = {"standard": 2e-6, "vol_of_vol_0.9": 8e-6}  # xf x (1.5e-7 sqrt(N) + 1e-6) of the per-path test
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "tiny_paths.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, steps, p, x, v = line.split()
+                rows.setdefault((name, int(steps)), []).append((int(p), float(x), float(v)))
+    assert len(rows) == 4
+    for (name, steps), vals in rows.items():
+        x, v = simr.paths_terminal(models[name], steps, 0, 8, seed=7)
+        x, v = x.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+        for p, xe, ve in vals:
+            assert abs(x[p] - xe) <= bound[name], (name, steps, p, x[p], xe)
+            assert abs(v[p] - ve) <= 1e-6 * max(ve, 0.01), (name, steps, p, v[p], ve)

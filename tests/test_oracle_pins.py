@@ -465,3 +465,26 @@ def _check_flipped_decision_gradient(model, steps, n):
         np.testing.assert_allclose(g[i], fd, rtol=1e-4, atol=1e-6 * np.abs(g[i]).max(), err_msg=f"path {i}")
         checked[int(kd[i])] += 1
     assert checked[1] >= 3 and checked[2] >= 5, checked
+
+
+def _tiny_paths():
+    rows = {}
+    for name, steps, p, x, v in _read_golden("tiny_paths.txt"):
+        rows.setdefault((name, int(steps)), []).append((int(p), float(x), float(v)))
+    return rows
+
+
+TINY_MODELS = {"standard": dict(workloads.BASE_MODEL),
+               "vol_of_vol_0.9": dict(S0=100.0, r=0.05, T=1.0, v0=0.09, kappa=1.0, theta=0.04, sigma=0.9, rho=-0.3)}
+
+
+def test_oracle_reproduces_its_tiny_path_fixture():
+    # a regression fixture (tests/golden/make_tiny_paths.py): the oracle's terminal
+    # states at 1 and 2 steps, 8 paths; a change of the oracle's path arithmetic
+    # shows here and must come with a regenerated fixture
+    rows = _tiny_paths()
+    assert len(rows) == 4
+    for (name, steps), vals in rows.items():
+        x, v, _ = oracle.terminal(TINY_MODELS[name], steps, 7, 0, 8)
+        for p, xe, ve in vals:
+            assert x[p] == pytest.approx(xe, rel=1e-15, abs=1e-17) and v[p] == pytest.approx(ve, rel=1e-15, abs=1e-17)
