@@ -56,13 +56,14 @@ inline size_t adjoint_smem_bytes_t(const PathLaunch& L, const AdjConst& A, int t
 // spot and d x_T / d(v0, kappa, theta, sigma, rho) -- and each lane adds its
 // strike's payoff f, f^2, and the in-the-money weight w (S_T for a call above
 // its strike, -S_T for a put below) alone and times each derivative; FP32 over
-// the warp's paths.  out[0..7]: f, f^2, w, w dx/dv0 .. w dx/drho (the S0 and r
-// columns are w / S0 and w T: scaled when added to the FP64 sums).
+// the warp's paths.  out[0..8]: f, f^2, w, w dx/dv0 .. w dx/drho, the signed
+// in-the-money indicator (the S0 column is w / S0, scaled when added to the FP64
+// sums; the r column e^{-rT} T K times the indicator's mean, see adj_term).
 template <int PPT>
 __device__ __forceinline__ void strike_tile_terms(bool put, float K, const float (&S)[PPT], const bool (&act)[PPT],
-                                                  const float (&g)[PPT][5], float (&out)[8]) {
+                                                  const float (&g)[PPT][5], float (&out)[kAdjAcc]) {
 #pragma unroll
-  for (int a = 0; a < 8; ++a) out[a] = 0.0f;
+  for (int a = 0; a < kAdjAcc; ++a) out[a] = 0.0f;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     const unsigned live = __ballot_sync(kFull, act[j]);
@@ -80,6 +81,7 @@ __device__ __forceinline__ void strike_tile_terms(bool put, float K, const float
         out[2] += w;
 #pragma unroll
         for (int k = 0; k < 5; ++k) out[3 + k] = fmaf(w, gp[k], out[3 + k]);
+        out[8] += put ? (Sp < K ? -1.0f : 0.0f) : (Sp > K ? 1.0f : 0.0f);
       }
     }
   }
@@ -167,10 +169,10 @@ __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB
 
     // per-strike terms, summed over the warp's paths
     if (RACC) {
-      float t[8];
+      float t[kAdjAcc];
       strike_tile_terms<PPT>(put, ks[lane].K, S, act, g, t);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) racc[a] += (double)t[a];
+      for (int a = 0; a < kAdjAcc; ++a) racc[a] += (double)t[a];
     } else if (TILE == 1) {
       for (int a = 0; a < kAdjAcc; ++a) {
         float t = 0.0f;
@@ -181,27 +183,25 @@ __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB
       }
     } else {
       for (int t0 = 0; t0 < L.nk_pad; t0 += 32) {
-        float t[8];
+        float t[kAdjAcc];
         strike_tile_terms<PPT>(put, ks[t0 + lane].K, S, act, g, t);
         double* row = my_acc + t0 + lane;
         row[0] += (double)t[0];
         row[(size_t)L.nk_pad] += (double)t[1];
         row[(size_t)2 * L.nk_pad] += (double)t[2] * (double)A.invS0;
 #pragma unroll
-        for (int a = 3; a < 8; ++a) row[(size_t)a * L.nk_pad] += (double)t[a];
-        row[(size_t)8 * L.nk_pad] += (double)t[2] * (double)A.T;
+        for (int a = 3; a < kAdjAcc; ++a) row[(size_t)a * L.nk_pad] += (double)t[a];
       }
     }
   }
   __syncthreads();
   if (RACC) {  // the segment buffers are free now: spill the lanes' sums into the rows
-    // racc[2] holds the weights w: the S0 column is w / S0, the r column w T
+    // racc[2] holds the weights w: the S0 column is w / S0
     my_acc[lane] = racc[0];
     my_acc[(size_t)L.nk_pad + lane] = racc[1];
     my_acc[(size_t)2 * L.nk_pad + lane] = racc[2] * (double)A.invS0;
 #pragma unroll
-    for (int a = 3; a < 8; ++a) my_acc[(size_t)a * L.nk_pad + lane] = racc[a];
-    my_acc[(size_t)8 * L.nk_pad + lane] = racc[2] * (double)A.T;
+    for (int a = 3; a < kAdjAcc; ++a) my_acc[(size_t)a * L.nk_pad + lane] = racc[a];
     __syncthreads();
   }
 
@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(128, GSEG ? SIMR_ADJ_MINB_GSEG : SIMR_ADJ_MINB
     }
     for (int c7 = 0; c7 < 7; ++c7) {
       double gsum = L.disc * acc[(size_t)(2 + c7) * L.nk_pad + kk] * inv_n;
-      if (c7 == 6) gsum -= (double)A.T * price;
+      // e^{-rT} T K E[indicator] with the FP32 T and K the paths use (as the book does)
+      if (c7 == 6) gsum *= (double)A.T * (double)(float)K;
       out.grad[(size_t)kk * 7 + c7] = bad ? nan : gsum;
     }
   }

@@ -724,17 +724,21 @@ __host__ __device__ inline size_t adjoint_seg_floats(const AdjConst& A, int /*pp
   return (size_t)3 * A.ckpt_every;
 }
 
-// Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho, 8 r (before -T P).
+// Terms per strike: 0 f, 1 f^2, 2 S0, 3 v0, 4 kappa, 5 theta, 6 sigma, 7 rho,
+// 8 r: the signed in-the-money indicator.  d/dr of e^{-rT} E[f] with dx_T/dr = T
+// is e^{-rT} T E[w - f], and w - f = K 1{S_T > K} for a call, -K 1{S_T < K} for
+// a put: the column is e^{-rT} T K E[indicator], with no cancellation of
+// E[w T] against T P (which loses the column when S_T >> K).
 constexpr int kAdjAcc = 9;
 
 __device__ __forceinline__ float adj_term(int a, bool put, float S, float K, const float (&g)[5], float invS0,
-                                          float T) {
+                                          float /*T: applied in the normalisation*/) {
   const float f = put ? fmaxf(K - S, 0.0f) : fmaxf(S - K, 0.0f);
   if (a == 0) return f;
   if (a == 1) return f * f;
+  if (a == 8) return put ? (S < K ? -1.0f : 0.0f) : (S > K ? 1.0f : 0.0f);
   const float w = put ? (S < K ? -S : 0.0f) : (S > K ? S : 0.0f);
   if (a == 2) return w * invS0;
-  if (a == 8) return w * T;
   return w * g[a - 3];
 }
 

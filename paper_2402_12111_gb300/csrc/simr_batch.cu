@@ -145,7 +145,7 @@ __global__ void batch_reduce_kernel(const BatchOption* __restrict__ opts, uint32
   if (out.grad && nacc == kAdjAcc) {
     for (int c7 = 0; c7 < 7; ++c7) {
       double g = O.disc * s[2 + c7] * inv_n;
-      if (c7 == 6) g -= (double)O.T * price;
+      if (c7 == 6) g *= (double)O.T * (double)O.K;  // e^{-rT} T K E[indicator] (adj_term)
       out.grad[(size_t)u * 7 + c7] = g;
     }
   }

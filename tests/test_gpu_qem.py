@@ -418,3 +418,37 @@ def test_full_size_adjoint_under_qem_checkpoint_every_16(simr):
 
     with simr.scheme("qem"), oracle.scheme("qem"):
         check_adjoint(simr, CFG, workloads.strike_grid(), False, 252, 1 << 20, 1, 16, 1e-3, 0.0, 1e-3)
+
+
+# Where the correction does not exist (2 A a >= 1 in the quadratic branch, A >= beta
+# in the exponential one) the QE-M step takes the plain increment.  One long step
+# from a large v0 reaches it on every path: NOEXIST_QUAD in the quadratic branch
+# (psi = 0.47, 2 A a = 1.30), NOEXIST_EXP in the exponential branch (the oracle's
+# fallback pin).
+NOEXIST_QUAD = dict(S0=100.0, r=0.03, T=7.6, v0=1.85, kappa=3.8, theta=0.75, sigma=1.64, rho=0.89)
+NOEXIST_EXP = dict(S0=100.0, r=0.05, T=4.0, v0=2.0, kappa=5.0, theta=0.04, sigma=3.0, rho=0.99)
+
+
+@pytest.mark.parametrize("model", [NOEXIST_QUAD, NOEXIST_EXP], ids=["quadratic", "exponential"])
+def test_absent_correction_takes_the_plain_step(simr, model):
+    K = _dev([60.0, 100.0, 160.0])
+    p0, se0 = simr.price(model, K, False, 1, 40000, 5)
+    _, _, g0 = simr.greeks_adjoint(model, K, False, 1, 40000, 5)
+    with simr.scheme("qem"):
+        p1, se1 = simr.price(model, K, False, 1, 40000, 5)
+        _, _, g1 = simr.greeks_adjoint(model, K, False, 1, 40000, 5)
+    # the plain step's arithmetic on every path: the same prices bit for bit; the
+    # reverse steps differ from the plain ones only in the order of their roundings
+    assert torch.equal(p1, p0) and torch.equal(se1, se0)
+    torch.testing.assert_close(g1, g0, rtol=1e-6, atol=0.0)
+    with oracle.scheme("qem"):
+        po, _ = oracle.price(model, K.cpu().numpy(), False, 1, 40000, 5)
+    np.testing.assert_allclose(p1.cpu().numpy(), po, rtol=1e-5)
+
+
+@pytest.mark.parametrize("model", [NOEXIST_QUAD, NOEXIST_EXP], ids=["quadratic", "exponential"])
+def test_absent_correction_adjoint_matches_qem_oracle(simr, model):
+    from test_gpu_adjoint import check_adjoint
+
+    with simr.scheme("qem"), oracle.scheme("qem"):
+        check_adjoint(simr, model, [60.0, 100.0, 160.0], False, 1, 40000, 5, 2, 1e-3, 0.05, 2.5, 1e-3)

@@ -103,3 +103,22 @@ def test_qem_adjoint_matches_its_finite_differences():
     for ca, cf in [(0, 0), (1, 1), (6, 2), (2, 3), (3, 4), (4, 5), (5, 6)]:
         tol = 2e-3 * max(abs(gf[:, cf]).max(), 1.0)
         np.testing.assert_allclose(ga[:, ca], gf[:, cf], rtol=2e-2, atol=tol)
+
+
+@pytest.mark.parametrize("model", [
+    dict(S0=100.0, r=0.03, T=7.6, v0=1.85, kappa=3.8, theta=0.75, sigma=1.64, rho=0.89),  # quadratic, 2Aa = 1.30
+    dict(S0=100.0, r=0.05, T=4.0, v0=2.0, kappa=5.0, theta=0.04, sigma=3.0, rho=0.99),    # exponential, A > beta
+], ids=["quadratic", "exponential"])
+def test_qem_reverse_mode_where_the_correction_does_not_exist(model):
+    # one long step from a large v0: M does not exist on any path, so QE-M takes the
+    # plain step -- its reverse mode (the plain derivatives) against the dual
+    # numbers' fallback branch, and both equal plain QE's
+    with oracle.scheme("qem"):
+        xr, gr = oracle.path_grad(model, 1, 5, 0, 2048, mode="reverse")
+        xf, gf = oracle.path_grad(model, 1, 5, 0, 2048, mode="forward")
+    xq, gq = oracle.path_grad(model, 1, 5, 0, 2048, mode="reverse")
+    np.testing.assert_allclose(xr, xf, rtol=0, atol=1e-12)
+    scale = np.maximum(np.abs(gf), 1e-3)
+    assert np.max(np.abs(gr - gf) / scale) < 1e-9
+    np.testing.assert_array_equal(xr, xq)
+    np.testing.assert_allclose(gr, gq, rtol=1e-13, atol=1e-14)
