@@ -159,23 +159,21 @@ __device__ __forceinline__ void adj_chain_exp(float E, float c1, float Cdl, floa
   const float vnbar = a.vbar + P.hzc;  // total adjoint of v_{n+1}
   const float dlbar = Cdl;
   float mbar = 0.0f, s2bar = 0.0f;
-  if (m > 0.0f) {
-    if (atom) {
-      mbar = -dlbar;
-    } else {
-      const float s2 = s2h + s2h;
-      const float ms = m2 + s2;
-      const float W = d * ms;
-      const float rm = rcp_approx(m), rms = rcp_approx(ms);
-      const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
-      const float A = 0.5f * ms * rm;
-      const float dA_dm = 0.5f * (m2 - s2) * rm * rm;
-      const float dL_dm = 2.0f * rm - 2.0f * m * rms;
-      const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
-      const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
-      mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
-      s2bar = (vnbar + dlbar) * dv_ds;
-    }
+  if (atom) {  // v' = 0 (the atom, or a zero mean): dl = -m
+    mbar = -dlbar;
+  } else {  // m > 0
+    const float s2 = s2h + s2h;
+    const float ms = m2 + s2;
+    const float W = d * ms;
+    const float rm = rcp_approx(m), rms = rcp_approx(ms);
+    const float L = 0.69314718055994531f * lg2_approx(2.0f * m2 * rcp_approx(W));
+    const float A = 0.5f * ms * rm;
+    const float dA_dm = 0.5f * (m2 - s2) * rm * rm;
+    const float dL_dm = 2.0f * rm - 2.0f * m * rms;
+    const float dv_dm = fmaf(dA_dm, L, A * dL_dm);
+    const float dv_ds = fmaf(0.5f * rm, L, -A * rms);
+    mbar = fmaf(vnbar, dv_dm, dlbar * (dv_dm - 1.0f));
+    s2bar = (vnbar + dlbar) * dv_ds;
   }
   adj_tail(E, c1, P, mbar, s2bar, a);
 }
@@ -334,7 +332,9 @@ __device__ __forceinline__ void adjoint_step2(const ScenConst& c, float theta, f
 //     into a (du/da = 2A), b^2 and A (du/dA = 2a);
 //   exponential: lam = ln(1 + q w / (1 - w)) - q w, q = 2 m^2 / (m^2 + s^2), w = A (m^2 + s^2) / (2 m):
 //     dlam/dq = w / (1 - w + q w) - w, dlam/dw = q / ((1 - w)(1 - w + q w)) - q,
-//     into m, s^2 and A.
+//     into m, s^2 and A;
+//   a zero mean (v = theta = 0): v' = 0 and M = 1 with no derivative, so lam = -A m
+//     and the increment r dt - qa v does not depend on m.
 // The sums Aqa, AK2, AA carry the dependence on qa, K2 and A; Np counts the plain
 // steps (their C0 = r dt + Cd theta).  One step at a time (no packed pairs).
 __device__ __forceinline__ void adjoint_step_qem(const ScenConst& c, const QemConst& q, float theta, float c1,
@@ -397,12 +397,14 @@ __device__ __forceinline__ void adjoint_step_qem(const ScenConst& c, const QemCo
     }
     const float vnbar = a.vbar + hz + (ok ? 0.0f : c.Cv);
     const float dlbar = ok ? q.K2 : c.Cdl;
+    // a zero mean: v' = 0 (dl = -m) and M = 1 with no derivative (lam = -A m), so
+    // -K2 + A = qa, and with the -qa below m drops out exactly
+    if (!(m > 0.0f)) mbar = q.qa;
     if (m > 0.0f) {
+      if (atom) mbar = -dlbar;  // v' = 0 by the atom: dl = -m
       const float rm = rcp_approx(m), rms = rcp_approx(ms);
       const float s2 = s2h + s2h;
-      if (atom) {
-        mbar = -dlbar;
-      } else {
+      if (!atom) {
         const float W = __fmul_rn(d, ms);
         const float L = 0.69314718055994531f * lg2_approx(__fmul_rn(2.0f * m2, rcp_approx(W)));
         const float Av = __fmul_rn(0.5f * ms, rm);

@@ -181,6 +181,11 @@ GREEK_CASES = [
                                                                            "kappa", "lrvar", "volvol", "corr"))),
     ("one_sided_v0_zero", dict(CFG, v0=0.0), [100.0], False, 16, 1 << 14, 5, ("vega",)),
     ("one_sided_rho_edge", dict(CFG, rho=-1.0), [100.0], False, 16, 1 << 14, 5, ("corr", "delta")),
+    # parameter edges: vol-of-vol near the Black-Scholes limit, mean reversion near zero
+    ("small_vol_of_vol", dict(CFG, sigma=0.01), [90.0, 100.0, 110.0], False, 32, 1 << 15, 7,
+     ("delta", "gamma", "vega", "theta", "rho", "corr")),
+    ("small_kappa", dict(CFG, kappa=1e-3), [90.0, 100.0, 110.0], True, 32, 1 << 15, 8,
+     ("delta", "gamma", "vega", "theta", "rho", "lrvar")),
 ]
 
 ORACLE_BITS = {"delta": oracle.G_DELTA, "gamma": oracle.G_GAMMA, "vega": oracle.G_VEGA, "theta": oracle.G_THETA,

@@ -283,6 +283,17 @@ def test_adjoint_matches_qem_oracle(simr, case):
         check_adjoint(simr, *case[1:])
 
 
+@pytest.mark.parametrize("case_id", ["small_vol_of_vol", "small_kappa", "zero_variance"])
+def test_adjoint_at_parameter_edges_under_qem(simr, case_id):
+    # the plain scheme's parameter edges (tests/test_gpu_adjoint.py) under QE-M; at
+    # v0 = theta = 0 every step has a zero mean, where M = 1 and only -A m of lam moves
+    from test_gpu_adjoint import EDGE_CASES, check_adjoint
+
+    case = next(c for c in EDGE_CASES if c[0] == case_id)
+    with simr.scheme("qem"), oracle.scheme("qem"):
+        check_adjoint(simr, *case[1:])
+
+
 def test_adjoint_price_is_the_qem_price(simr):
     K = _dev(workloads.strike_grid())
     with simr.scheme("qem"):
