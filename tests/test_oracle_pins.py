@@ -488,3 +488,36 @@ def test_oracle_reproduces_its_tiny_path_fixture():
         x, v, _ = oracle.terminal(TINY_MODELS[name], steps, 7, 0, 8)
         for p, xe, ve in vals:
             assert x[p] == pytest.approx(xe, rel=1e-15, abs=1e-17) and v[p] == pytest.approx(ve, rel=1e-15, abs=1e-17)
+
+
+@pytest.mark.parametrize("scheme", ["qe", "qem"])
+def test_adjoint_at_zero_variance_in_closed_form(scheme):
+    # v0 = theta = 0: m = s^2 = 0 at every step, every v' = 0 and x_T = r T on
+    # every path, so S_T = S0 e^{rT} and e^{-rT} S_T = S0.  With v' held at 0 the
+    # only dependence on v0 is the first step's v0 term of the log-spot step
+    # (the sqrt term's derivative at zero variance taken as 0): under QE
+    # K1 = dt (kappa rho / sigma - 1/2) / 2 - rho / sigma (Andersen's gamma1 = 1/2), so
+    # dP/dv0 = S0 K1 for a strike below S_T; under QE-M the step is
+    # r dt - ln M - (K1 + K3/2) v + K1 v + K2 v' with M = 1 at a zero mean, so
+    # dP/dv0 = -S0 K3 / 2, K3 = dt (1 - rho^2) / 2.  dP/dtheta: theta enters QE's
+    # K0 = -rho kappa theta dt / sigma + r dt at every step (S0 (-rho kappa T / sigma));
+    # QE-M replaces K0 by r dt - ln M, so 0.  kappa, sigma, rho: every term they
+    # enter multiplies theta or a variance, so 0.  dP/dS0 = 1, dP/dr = e^{-rT} T K.
+    # A strike above S_T: every column 0.
+    model = dict(CFG, v0=0.0, theta=0.0)
+    steps, S0, T, r = 16, model["S0"], model["T"], model["r"]
+    dt = T / steps
+    kap, sig, rho = model["kappa"], model["sigma"], model["rho"]
+    K = np.array([90.0, 110.0])
+    with oracle.scheme(scheme):
+        p, g = oracle.adjoint(model, K, False, steps, 64, 9)
+    K1 = 0.5 * dt * (kap * rho / sig - 0.5) - rho / sig
+    K3 = 0.5 * dt * (1.0 - rho * rho)
+    if scheme == "qe":
+        v0_col, theta_col = S0 * K1, -S0 * rho * kap * T / sig
+    else:
+        v0_col, theta_col = -0.5 * S0 * K3, 0.0
+    np.testing.assert_allclose(p, [S0 - math.exp(-r * T) * 90.0, 0.0], rtol=1e-13, atol=1e-13)
+    want = [1.0, v0_col, 0.0, theta_col, 0.0, 0.0, math.exp(-r * T) * T * 90.0]
+    np.testing.assert_allclose(g[0], want, rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(g[1], np.zeros(7))
