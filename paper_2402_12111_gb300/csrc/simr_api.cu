@@ -475,7 +475,7 @@ int take_status(simr_ctx* ctx, cudaStream_t st) {
   if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
   if (h & 1) return fail(SIMR_EINVAL, "a device-resident strike was not finite and > 0 (results are NaN)");
-  if (h & 2) return fail(SIMR_ETIMEOUT, "a grid barrier of the Longstaff-Schwartz sweep timed out (results invalid)");
+  if (h & 2) return fail(SIMR_ETIMEOUT, "a wait of the Longstaff-Schwartz sweep (grid barrier or state copy) timed out (results invalid)");
   return SIMR_OK;
 }
 

@@ -529,22 +529,60 @@ __device__ void lsm_solve_df(const DF* tot, float* x_out, float* dx_out, int lan
 // ---------------------------------------------------------------------------
 // Persistent sweep: the whole backward induction in one cooperative launch (all
 // blocks resident, one per SM).  Each date: apply the date's rule to the
-// thread's paths (states kept in registers from the previous date's
+// thread's paths (states kept in shared memory from the previous date's
 // regression), load the states of the date before, accumulate its regression
 // sums, write the block's row, one grid barrier, then EVERY block sums all
-// rows in block order and solves the same normal equations (identical
-// arithmetic, so identical coefficients everywhere and no second barrier).
-// Rows alternate between two buffers: a block writes a buffer again only after
-// the next barrier, which every block reaches after reading it.
+// rows (one warp per quantity, in a fixed order) and solves the same normal
+// equations (identical arithmetic, so identical coefficients everywhere and no
+// second barrier).  Rows alternate between two buffers: a block writes a buffer
+// again only after the next barrier, which every block reaches after reading it.
 constexpr int kSweepTpb = 1024;
 constexpr int kSweepWarps = kSweepTpb / kWarp;
-constexpr int kSweepParts = 48;             // threads per quantity in the cross-block sum (a multiple of 8)
+static_assert(kNReg <= kSweepWarps, "one warp per regression quantity in the cross-block sum");
 constexpr unsigned kSpinLimit = 1u << 23;   // barrier polls (>= 32 ns apart after 2048): ~0.3 s, then the wait gives up
+constexpr unsigned kCopySpinLimit = 1u << 22;  // mbarrier polls for a bulk copy (>= 32 ns apart after 2048): ~0.2 s
+
+// Bulk copies global -> shared memory by the TMA engine (cp.async.bulk, no
+// tensor map: contiguous 16-byte-aligned ranges), each completing its bytes on
+// an mbarrier in shared memory.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// The one arrival of a phase, announcing the bytes its copies will complete.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Waits for the phase of the given parity to complete (non-blocking polls,
+// backing off like the grid barrier); false after kCopySpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (unsigned it = 0; it < kCopySpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 2048) __nanosleep(32);
+  }
+  return false;
+}
 
 struct LsmSweep {
   unsigned int* count;  // arrivals at all barriers so far (zeroed before the launch)
   int* status;          // bit 1: a barrier wait timed out (results invalid)
-  float2* rows;         // [2][grid][kNReg]
+  float2* rows;         // [2][kNReg][grid]: two buffers, quantity-major
 };
 
 // Grid-wide barrier number `nb` (0, 1, ...) of the cooperative sweep: every block
@@ -553,9 +591,12 @@ struct LsmSweep {
 // to do, so the barrier costs one atomic and the polls.  Bounded: a wait that
 // exceeds kSpinLimit polls sets status bit 1 and returns false, and every later
 // barrier returns false at once, so all blocks leave within one time-out.
-__device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, int* s_flag) {
+// `idle()` runs in every thread once the block has arrived, while thread 0 waits.
+template <class Idle>
+__device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, int* s_flag, Idle&& idle) {
   __threadfence();
   __syncthreads();
+  idle();
   if (threadIdx.x == 0) {
     int ok = (*(volatile int*)Y.status & 2) == 0;
     if (ok) {
@@ -579,8 +620,10 @@ __device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, int* s_flag) {
 }
 
 // Block's FP32 warp sums (s_w[warp][q], q < nv) -> one double-float row: four
-// threads per quantity sum 8 warps each, then one sums the four in order.
-__device__ __forceinline__ void sweep_block_row(const float (*s_w)[kNReg], int nv, DF* s_quad, float2* row) {
+// threads per quantity sum 8 warps each, then one sums the four in order.  The
+// rows are stored quantity-major, [q][block], so that a warp reads one
+// quantity of 32 blocks as one contiguous line.
+__device__ __forceinline__ void sweep_block_row(const float (*s_w)[kNReg], int nv, DF* s_quad, float2* rows) {
   if (threadIdx.x < 4 * nv) {
     const int q = threadIdx.x % nv, g = threadIdx.x / nv;
     DF t{0.0f, 0.0f};
@@ -593,52 +636,57 @@ __device__ __forceinline__ void sweep_block_row(const float (*s_w)[kNReg], int n
     DF t{0.0f, 0.0f};
 #pragma unroll
     for (int g = 0; g < 4; ++g) t = df_add(t, s_quad[g * nv + threadIdx.x]);
-    row[threadIdx.x] = make_float2(t.hi, t.lo);
+    rows[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = make_float2(t.hi, t.lo);
   }
 }
 
-// Sum of all blocks' rows in block order into s_tot (double-float): thread
-// (part, q), part < kSweepParts, takes blocks part, part + kSweepParts, ...;
-// then groups of 8 parts, then the groups, each in order.
-__device__ __forceinline__ void sweep_total(const float2* rows, int nv, DF* s_part, DF* s_tot) {
-  if (threadIdx.x < kSweepParts * nv) {
-    const int q = threadIdx.x % nv, part = threadIdx.x / nv;
+// Sum of all blocks' rows into s_tot (double-float): warp q sums quantity q,
+// lane l taking blocks l, l + 32, ... in order (its loads issued together), then
+// a butterfly over the lanes; lane 0's total is the same in every block (the same
+// operations on the same rows).
+__device__ __forceinline__ void sweep_total(const float2* rows, int nv, DF* s_tot) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q < nv) {
+    constexpr int kAhead = 8;  // loads in flight per lane
     DF t{0.0f, 0.0f};
-#pragma unroll 4
-    for (unsigned b = part; b < gridDim.x; b += kSweepParts) {
-      const float2 r = __ldcg(rows + (size_t)b * kNReg + q);
-      t = df_add(t, DF{r.x, r.y});
+    for (unsigned b0 = 0; b0 < gridDim.x; b0 += kAhead * kWarp) {
+      float2 r[kAhead];
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) {
+        const unsigned b = b0 + k * kWarp + lane;
+        r[k] = b < gridDim.x ? __ldcg(rows + (size_t)q * gridDim.x + b) : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k)
+        if (b0 + k * kWarp + lane < gridDim.x) t = df_add(t, DF{r[k].x, r[k].y});
     }
-    s_part[threadIdx.x] = t;
-  }
-  __syncthreads();
-  constexpr int kGroups = kSweepParts / 8;
-  DF t{0.0f, 0.0f};
-  if (threadIdx.x < kGroups * nv) {
-    const int q = threadIdx.x % nv, grp = threadIdx.x / nv;
 #pragma unroll
-    for (int part = 8 * grp; part < 8 * grp + 8; ++part) t = df_add(t, s_part[part * nv + q]);
-  }
-  __syncthreads();
-  if (threadIdx.x < kGroups * nv) s_part[threadIdx.x] = t;
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    DF u{0.0f, 0.0f};
-#pragma unroll
-    for (int grp = 0; grp < kGroups; ++grp) u = df_add(u, s_part[grp * nv + threadIdx.x]);
-    s_tot[threadIdx.x] = u;
+    for (int o = 16; o > 0; o >>= 1)
+      t = df_add(t, DF{__shfl_xor_sync(kFull, t.hi, o), __shfl_xor_sync(kFull, t.lo, o)});
+    if (lane == 0) s_tot[q] = t;
   }
   __syncthreads();
 }
 
-template <int M>
+// BULK (paths a multiple of 4, so that every block's range of a date starts on
+// 16 bytes): each date's states come into shared memory by bulk copies issued a
+// date ahead, into two buffers used in turn; otherwise by loads from L2 after a
+// prefetch a date ahead.
+template <int M, bool BULK>
 __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_constant__ LsmLaunch L,
                                                                  const LsmBuffers B, const LsmSweep Y) {
-  // the states the regression of a date loads, kept for the next date's rule:
-  // [M][thread] S, then [M][thread] v (dynamic shared memory)
-  extern __shared__ float s_keep[];
+  // dynamic shared memory, [M][thread] each: the states of a date (S, then v;
+  // BULK: two such buffers, date j in buffer j & 1) -- the regression of date j
+  // reads them, the rule of date j reads them again -- then the thread's paths'
+  // cash flows and exercise dates for the whole sweep (each thread its own slots)
+  extern __shared__ __align__(16) float s_keep[];
+  constexpr int kBufs = BULK ? 2 : 1;
+  float* s_c = s_keep + kBufs * 2 * M * kSweepTpb;
+  int* s_st = reinterpret_cast<int*>(s_c + M * kSweepTpb);
+  auto states = [&](int j) { return s_keep + (BULK ? (j & 1) * 2 * M * kSweepTpb : 0); };
+  __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ float s_w[kSweepWarps][kNReg];
-  __shared__ DF s_part[kSweepParts * kNReg];
+  __shared__ DF s_quad[4 * kNReg];
   __shared__ DF s_tot[kNReg];
   __shared__ float s_beta[kNB];
   __shared__ int s_has, s_flag;
@@ -649,40 +697,84 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
   const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool put = L.is_put != 0;
   const float K = L.K;
-  // this thread's paths g0 + m gt: cash flow and exercise date in registers for
-  // the whole sweep (the states are read per date, from L2 after a prefetch)
-  float c[M];
-  int st[M];
+  // this thread's paths g0 + m gt
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const uint64_t i = g0 + (uint64_t)m * gt;
-    c[m] = i < P ? B.cash[i] : 0.0f;
-    st[m] = i < P ? B.stop[i] : -1;
+    s_c[m * kSweepTpb + threadIdx.x] = i < P ? B.cash[i] : 0.0f;
+    s_st[m * kSweepTpb + threadIdx.x] = i < P ? B.stop[i] : -1;
   }
-  if (threadIdx.x == 0) s_has = 0;
-  __syncthreads();
+  // BULK: block's share of date j: for each m the paths m gt + blockIdx.x 1024 +
+  // [0, 1024), cut at P (a multiple of 4 floats since P is); the block's last
+  // thread issues the copies (thread 0 runs the grid barrier meanwhile)
+  // per buffer b (bit b, the same in every thread): the parity of its next phase,
+  // and whether a copy into it is in flight
+  uint32_t parity = 0u, pending = 0u;
+  auto issue = [&](int j) {
+    if (threadIdx.x == kSweepTpb - 1) {
+      float* dst = states(j);
+      const float* Sg = B.S + (size_t)j * P;
+      const float* Vg = B.V + (size_t)j * P;
+      uint32_t total = 0;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const uint64_t a = (uint64_t)m * gt + (uint64_t)blockIdx.x * kSweepTpb;
+        total += a < P ? 8u * (uint32_t)(P - a < kSweepTpb ? P - a : kSweepTpb) : 0u;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer before the copies
+      mbar_arrive_expect(&s_bar[j & 1], total);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const uint64_t a = (uint64_t)m * gt + (uint64_t)blockIdx.x * kSweepTpb;
+        if (a < P) {
+          const uint32_t bytes = 4u * (uint32_t)(P - a < kSweepTpb ? P - a : kSweepTpb);
+          bulk_copy_g2s(dst + m * kSweepTpb, Sg + a, bytes, &s_bar[j & 1]);
+          bulk_copy_g2s(dst + (M + m) * kSweepTpb, Vg + a, bytes, &s_bar[j & 1]);
+        }
+      }
+    }
+    pending |= 1u << (j & 1);
+  };
+  // before an early return: the copies still in flight land first (bounded)
+  auto drain = [&]() {
+    if (BULK)
+      for (int b = 0; b < 2; ++b)
+        if ((pending >> b) & 1u) (void)mbar_wait(&s_bar[b], (parity >> b) & 1u);
+  };
+  if (threadIdx.x == 0) {
+    s_has = 0;
+    if (BULK) {
+      mbar_init(&s_bar[0]);
+      mbar_init(&s_bar[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();  // (the barriers' initialisation before the last thread's first copies)
+  if (BULK && L.n_ex >= 2) issue(L.n_ex - 2);
+  float4 tj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // date d's basis scaling (loaded a date ahead)
   for (int d = L.n_ex - 1; d >= 0; --d) {
     const bool regress = d >= 1;
     const int nv = regress ? kNReg : 2;
+    const float4 tr = regress ? __ldg(B.xform + (d - 1)) : tj;  // date d - 1's, requested early
     // date d's rule (no coefficients at the maturity)
-    if (s_has) {  // (a rule exists only below the last date: date d's states are in s_keep)
+    if (s_has) {  // (a rule exists only below the last date: date d's states are in shared memory)
       float bj[kNB];
 #pragma unroll
       for (int k = 0; k < kNB; ++k) bj[k] = s_beta[k];
-      const float4 tj = B.xform[d];
+      const float* sd = states(d);
       float Su[M], Vu[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        Su[m] = s_keep[m * kSweepTpb + threadIdx.x];
-        Vu[m] = s_keep[(M + m) * kSweepTpb + threadIdx.x];
+        Su[m] = sd[m * kSweepTpb + threadIdx.x];
+        Vu[m] = sd[(M + m) * kSweepTpb + threadIdx.x];
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const float h = lsm_payoff(put, Su[m], K);
         if (g0 + (uint64_t)m * gt < P && h > 0.0f &&
             h > lsm_continuation(bj, fmaf(Su[m], tj.x, tj.y), fmaf(Vu[m], tj.z, tj.w))) {
-          c[m] = h;
-          st[m] = d;
+          s_c[m * kSweepTpb + threadIdx.x] = h;
+          s_st[m * kSweepTpb + threadIdx.x] = d;
         }
       }
     }
@@ -690,21 +782,39 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
 #pragma unroll
     for (int k = 0; k < kNReg; ++k) acc[k] = 0.0f;
     if (regress) {
-      const float* Sr = B.S + (size_t)(d - 1) * P;
-      const float* Vr = B.V + (size_t)(d - 1) * P;
       float Sn[M], Vn[M];
+      if constexpr (BULK) {  // date d - 1's copies, issued a date ago
+        const int b = (d - 1) & 1;
+        const bool late = !mbar_wait(&s_bar[b], (parity >> b) & 1u);
+        if (__syncthreads_or(late)) {  // the whole block leaves
+          if (threadIdx.x == 0) atomicOr(Y.status, 2);
+          drain();
+          return;
+        }
+        parity ^= 1u << b;
+        pending &= ~(1u << b);
+        const float* sr = states(d - 1);
 #pragma unroll
-      for (int m = 0; m < M; ++m) {  // all loads first
-        const uint64_t i = g0 + (uint64_t)m * gt;
-        Sn[m] = i < P ? __ldcg(Sr + i) : 0.0f;
-        Vn[m] = i < P ? __ldcg(Vr + i) : 0.0f;
-      }
+        for (int m = 0; m < M; ++m) {
+          Sn[m] = sr[m * kSweepTpb + threadIdx.x];
+          Vn[m] = sr[(M + m) * kSweepTpb + threadIdx.x];
+        }
+      } else {
+        const float* Sr = B.S + (size_t)(d - 1) * P;
+        const float* Vr = B.V + (size_t)(d - 1) * P;
 #pragma unroll
-      for (int m = 0; m < M; ++m) {  // this thread's own slots: no barrier needed before the next date reads them
-        s_keep[m * kSweepTpb + threadIdx.x] = Sn[m];
-        s_keep[(M + m) * kSweepTpb + threadIdx.x] = Vn[m];
+        for (int m = 0; m < M; ++m) {  // all loads first
+          const uint64_t i = g0 + (uint64_t)m * gt;
+          Sn[m] = i < P ? __ldcg(Sr + i) : 0.0f;
+          Vn[m] = i < P ? __ldcg(Vr + i) : 0.0f;
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {  // this thread's own slots: no barrier needed before the next date reads them
+          s_keep[m * kSweepTpb + threadIdx.x] = Sn[m];
+          s_keep[(M + m) * kSweepTpb + threadIdx.x] = Vn[m];
+        }
       }
-      if (d >= 2) {  // the date after next into L2 while this one is reduced and solved
+      if (!BULK && d >= 2) {  // the date after next into L2 while this one is reduced and solved
         const float* Sp = B.S + (size_t)(d - 2) * P;
         const float* Vp = B.V + (size_t)(d - 2) * P;
 #pragma unroll
@@ -716,19 +826,20 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
           }
         }
       }
-      const float4 tr = B.xform[d - 1];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const float h = lsm_payoff(put, Sn[m], K);
         if (g0 + (uint64_t)m * gt < P && h > 0.0f) {
-          const float Yv = st[m] >= 0 ? c[m] * __ldg(B.dpow + (st[m] - (d - 1))) : 0.0f;
+          const int st = s_st[m * kSweepTpb + threadIdx.x];
+          const float Yv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * __ldg(B.dpow + (st - (d - 1))) : 0.0f;
           lsm_accumulate(acc, fmaf(Sn[m], tr.x, tr.y), fmaf(Vn[m], tr.z, tr.w), Yv);
         }
       }
     } else {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        const float dv = st[m] >= 0 ? c[m] * __ldg(B.dpow + st[m]) : 0.0f;  // discounted to t_0
+        const int st = s_st[m * kSweepTpb + threadIdx.x];
+        const float dv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * __ldg(B.dpow + st) : 0.0f;  // discounted to t_0
         acc[0] += dv;
         acc[1] = fmaf(dv, dv, acc[1]);
       }
@@ -743,9 +854,15 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     }
     __syncthreads();
     float2* rows = Y.rows + (size_t)(d & 1) * gridDim.x * kNReg;
-    sweep_block_row(s_w, nv, s_part, rows + (size_t)blockIdx.x * kNReg);
-    if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), &s_flag)) return;
-    sweep_total(rows, nv, s_part, s_tot);
+    sweep_block_row(s_w, nv, s_quad, rows);
+    // once every thread is past date d's rule, its buffer takes date d - 2
+    if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), &s_flag, [&] {
+          if (BULK && d >= 2) issue(d - 2);
+        })) {
+      drain();
+      return;
+    }
+    sweep_total(rows, nv, s_tot);
     if (regress) {
       // every block: the same solve; block 0 records the coefficients
       if (warp == 0) {
@@ -773,11 +890,12 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
         B.stderr_[0] = L.disc0 * sqrt(var > 0.0 ? var : 0.0);
       }
     }
+    tj = tr;  // date d - 1's rule comes next
   }
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const uint64_t i = g0 + (uint64_t)m * gt;
-    if (i < P) B.stop[i] = st[m];
+    if (i < P) B.stop[i] = s_st[m * kSweepTpb + threadIdx.x];
   }
   // the coefficients in x, y: one date per block (block 0's rows are visible
   // after the last barrier)
@@ -814,14 +932,16 @@ size_t lsm_partial_doubles(int num_sms) { return (size_t)num_sms * kLsmMaxBlocks
 
 namespace {
 
-template <int M>
-cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
-                        bool* used) {
-  const size_t smem = (size_t)2 * M * kSweepTpb * sizeof(float);  // s_keep
-  cudaError_t e = cudaFuncSetAttribute(lsm_sweep_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int M, bool BULK>
+cudaError_t try_sweep_mb(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
+                         bool* used) {
+  // S and v (two buffers with BULK), cash flow, exercise date
+  const size_t smem = (size_t)(BULK ? 6 : 4) * M * kSweepTpb * sizeof(float);
+  auto kern = lsm_sweep_kernel<M, BULK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsm_sweep_kernel<M>, kSweepTpb, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepTpb, smem);
   if (e != cudaSuccess || per_sm < 1) return e;
   const uint64_t resident = (uint64_t)num_sms * per_sm;
   const uint64_t per_block = (uint64_t)M * kSweepTpb;
@@ -834,9 +954,17 @@ cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep&
   LsmBuffers Bc = B;
   LsmSweep Yc = Y;
   void* args[] = {&Lc, &Bc, &Yc};
-  e = cudaLaunchCooperativeKernel((const void*)lsm_sweep_kernel<M>, dim3(grid), dim3(kSweepTpb), args, smem, st);
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kSweepTpb), args, smem, st);
   if (e == cudaSuccess) *used = true;
   return e;
+}
+
+template <int M>
+cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
+                        bool* used) {
+  // bulk copies need every block's range of a date on 16 bytes: P a multiple of 4
+  if (L.paths % 4 == 0) return try_sweep_mb<M, true>(L, B, Y, num_sms, st, used);
+  return try_sweep_mb<M, false>(L, B, Y, num_sms, st, used);
 }
 
 // The backward induction as one cooperative launch when the device supports it
