@@ -678,11 +678,13 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
   // dynamic shared memory, [M][thread] each: the states of a date (S, then v;
   // BULK: two such buffers, date j in buffer j & 1) -- the regression of date j
   // reads them, the rule of date j reads them again -- then the thread's paths'
-  // cash flows and exercise dates for the whole sweep (each thread its own slots)
+  // cash flows and exercise dates for the whole sweep (each thread its own
+  // slots), then the discount table (n_ex floats)
   extern __shared__ __align__(16) float s_keep[];
   constexpr int kBufs = BULK ? 2 : 1;
   float* s_c = s_keep + kBufs * 2 * M * kSweepTpb;
   int* s_st = reinterpret_cast<int*>(s_c + M * kSweepTpb);
+  float* s_dpow = s_c + 2 * M * kSweepTpb;
   auto states = [&](int j) { return s_keep + (BULK ? (j & 1) * 2 * M * kSweepTpb : 0); };
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ float s_w[kSweepWarps][kNReg];
@@ -697,6 +699,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
   const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool put = L.is_put != 0;
   const float K = L.K;
+  for (int k = threadIdx.x; k < L.n_ex; k += kSweepTpb) s_dpow[k] = B.dpow[k];
   // this thread's paths g0 + m gt
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -831,7 +834,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
         const float h = lsm_payoff(put, Sn[m], K);
         if (g0 + (uint64_t)m * gt < P && h > 0.0f) {
           const int st = s_st[m * kSweepTpb + threadIdx.x];
-          const float Yv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * __ldg(B.dpow + (st - (d - 1))) : 0.0f;
+          const float Yv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * s_dpow[st - (d - 1)] : 0.0f;
           lsm_accumulate(acc, fmaf(Sn[m], tr.x, tr.y), fmaf(Vn[m], tr.z, tr.w), Yv);
         }
       }
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const int st = s_st[m * kSweepTpb + threadIdx.x];
-        const float dv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * __ldg(B.dpow + st) : 0.0f;  // discounted to t_0
+        const float dv = st >= 0 ? s_c[m * kSweepTpb + threadIdx.x] * s_dpow[st] : 0.0f;  // discounted to t_0
         acc[0] += dv;
         acc[1] = fmaf(dv, dv, acc[1]);
       }
@@ -935,8 +938,8 @@ namespace {
 template <int M, bool BULK>
 cudaError_t try_sweep_mb(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
                          bool* used) {
-  // S and v (two buffers with BULK), cash flow, exercise date
-  const size_t smem = (size_t)(BULK ? 6 : 4) * M * kSweepTpb * sizeof(float);
+  // S and v (two buffers with BULK), cash flow, exercise date; the discount table
+  const size_t smem = ((size_t)(BULK ? 6 : 4) * M * kSweepTpb + (size_t)L.n_ex) * sizeof(float);
   auto kern = lsm_sweep_kernel<M, BULK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -205,7 +205,7 @@ def test_lsm_large_matches_oracle_within_its_own_sensitivity(simr):
     assert np.mean(stop.cpu().numpy() != ref.stop) <= 4 * ds + 1e-4
 
 
-@pytest.mark.parametrize("paths", [5003, 1 << 18, 1 << 20])
+@pytest.mark.parametrize("paths", [5003, 1 << 18, 400_000, 1 << 20])
 def test_cooperative_sweep_and_per_date_launches_agree(simr, paths, monkeypatch):
     # the backward induction runs as one cooperative launch or as one kernel per
     # date; they group the FP32 partial sums differently, so their fits differ at
