@@ -23,6 +23,12 @@
 //     normal equations (lsm_solve_warp: FP32 Cholesky, refined against an FP64
 //     residual).  The launch of date 0 applies its rule and reduces the
 //     discounted cash flows to the price.
+// (2') In place of (2), when the GPU can keep one 1024-thread block per SM
+//     resident for up to 7 paths per thread: the whole backward induction as
+//     one cooperative launch (lsm_sweep_kernel) -- per date a block row, one
+//     grid barrier, and in every block the same cross-block sum and solve; each
+//     date's states come into shared memory by TMA bulk copies issued a date
+//     ahead.
 //
 // The coordinates xs = (S - F_j)/sd_j and ys = (v - E v_j)/sd(v_j) are x and y
 // of the basis (1, x, x^2, y, xy, y^2), x = S/K - 1, y = v/w - 1, shifted and
