@@ -56,6 +56,8 @@ struct simr_ctx {
   size_t strikes_cap = 0;
   double* dev_out = nullptr;
   size_t out_cap = 0;
+  double* host_out = nullptr;  // pinned: the staged results and the status word on their way back
+  size_t host_out_cap = 0;
   float* dev_f32 = nullptr;
   size_t f32_cap = 0;
   // batched book: device tables, per-item partial rows, pinned upload staging
@@ -467,16 +469,22 @@ int stage_strikes(simr_ctx* ctx, const double* strikes, int n, cudaStream_t st, 
   return SIMR_OK;
 }
 
+// The device status word h as read from the device: clear it there, report it.
+int decode_status(simr_ctx* ctx, int h, cudaStream_t st) {
+  cudaError_t e = h ? cudaMemsetAsync(ctx->status, 0, sizeof(int), st) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the device status");
+  if (h & 1) return fail(SIMR_EINVAL, "a device-resident strike was not finite and > 0 (results are NaN)");
+  if (h & 2) return fail(SIMR_ETIMEOUT, "a wait of the Longstaff-Schwartz sweep (grid barrier or state copy) timed out (results invalid)");
+  return SIMR_OK;
+}
+
 // Read and clear the device status word (the stream must be idle).
 int take_status(simr_ctx* ctx, cudaStream_t st) {
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
-  if (h & 1) return fail(SIMR_EINVAL, "a device-resident strike was not finite and > 0 (results are NaN)");
-  if (h & 2) return fail(SIMR_ETIMEOUT, "a wait of the Longstaff-Schwartz sweep (grid barrier or state copy) timed out (results invalid)");
-  return SIMR_OK;
+  return decode_status(ctx, h, st);
 }
 
 struct OutStage {
@@ -509,17 +517,42 @@ int stage_outputs(simr_ctx* ctx, OutStage* o) {
   return SIMR_OK;
 }
 
+// Results for host buffers: the staged block (dev_out, the host outputs in
+// order) and the status word come back by two copies into pinned host memory and
+// one synchronisation, then go to the caller's buffers on the host.
 int finish_outputs(simr_ctx* ctx, const OutStage& o, cudaStream_t st) {
   if (!o.any_host) return SIMR_OK;
+  size_t total = 0;
+  for (int i = 0; i < 3; ++i)
+    if (o.user[i] && o.dev[i] != o.user[i]) total += o.n[i];
+  if (ctx->host_out_cap < total + 1) {  // + one double's room for the status word
+    cudaError_t e = cudaStreamSynchronize(st);  // (nothing in flight may still target the old buffer)
+    if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
+    if (ctx->host_out) cudaFreeHost(ctx->host_out);
+    ctx->host_out = nullptr;
+    ctx->host_out_cap = 0;
+    e = cudaHostAlloc((void**)&ctx->host_out, (total + 1) * sizeof(double), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SIMR_ENOMEM, "pinned result staging of %zu bytes: %s", (total + 1) * sizeof(double),
+                  cudaGetErrorString(e));
+    }
+    ctx->host_out_cap = total + 1;
+  }
+  int* h_status = reinterpret_cast<int*>(ctx->host_out + total);
+  cudaError_t e = cudaMemcpyAsync(ctx->host_out, ctx->dev_out, total * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copying results to the host");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
+  size_t off = 0;
   for (int i = 0; i < 3; ++i) {
     if (o.user[i] && o.dev[i] != o.user[i]) {
-      cudaError_t e = cudaMemcpyAsync(o.user[i], o.dev[i], o.n[i] * sizeof(double), cudaMemcpyDeviceToHost, st);
-      if (e != cudaSuccess) return cuda_fail(e, "copying results to the host");
+      std::memcpy(o.user[i], ctx->host_out + off, o.n[i] * sizeof(double));
+      off += o.n[i];
     }
   }
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
-  return take_status(ctx, st);
+  return decode_status(ctx, *h_status, st);
 }
 
 int with_device(simr_ctx* ctx) {
@@ -862,6 +895,7 @@ void simr_destroy(simr_ctx* ctx) {
   cudaFree(ctx->b_items);
   cudaFree(ctx->b_partials);
   if (ctx->b_host) cudaFreeHost(ctx->b_host);
+  if (ctx->host_out) cudaFreeHost(ctx->host_out);
   if (ctx->b_uploaded) cudaEventDestroy(ctx->b_uploaded);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->g_in) cudaEventDestroy(ctx->g_in);
