@@ -213,15 +213,22 @@ SIMR_API int simr_greeks_adjoint(simr_ctx* ctx, const simr_heston* model, const 
                                  double* grad, void* stream);
 
 /*
- * Host-side fault injection, for tests of the error paths (nothing reaches the
- * GPU): the after-th next request of this process for context scratch memory
+ * Fault injection, for tests of the error paths.  On the host (nothing reaches
+ * the GPU): the after-th next request of this process for context scratch memory
  * (what = SIMR_FAULT_ALLOC; allocated or reused) or for a kernel launch (what =
  * SIMR_FAULT_LAUNCH) fails as if the CUDA call had failed -- the entry point that
  * meets it returns SIMR_ENOMEM or SIMR_ECUDA and leaves the context usable.
+ * what = SIMR_FAULT_BARRIER: the after-th next cooperative Longstaff-Schwartz
+ * sweep waits at its first grid barrier for one block more than its grid holds,
+ * so that bounded wait runs out (0.25 s); the sweep's blocks leave, the device
+ * status reports SIMR_ETIMEOUT (simr_sync, or the call itself with host outputs)
+ * and the context stays usable.  No memory access changes; a valuation that runs
+ * per-date launches instead of the sweep consumes the injection unaffected.
  * what = 0 disarms.  after in [1, 2^30].  SIMR_EINVAL otherwise.
  */
 #define SIMR_FAULT_ALLOC 1
 #define SIMR_FAULT_LAUNCH 2
+#define SIMR_FAULT_BARRIER 3
 SIMR_API int simr_inject_fault(int what, int after);
 
 /*

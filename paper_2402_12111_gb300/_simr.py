@@ -46,7 +46,7 @@ class Option(ctypes.Structure):
 
 
 BATCH_ADJOINT, BATCH_GRAPH, BATCH_NO_AUTOTUNE = 1, 2, 4
-FAULT_ALLOC, FAULT_LAUNCH = 1, 2
+FAULT_ALLOC, FAULT_LAUNCH, FAULT_BARRIER = 1, 2, 3
 
 
 def batch_variant_flag(v: int) -> int:

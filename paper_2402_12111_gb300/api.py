@@ -99,8 +99,10 @@ def adjoint_interval(n_strikes: int, steps: int, device: int = 0) -> int:
 
 def inject_fault(what: str, after: int = 1) -> None:
     """simr_inject_fault: the after-th next scratch request ("alloc") or kernel launch
-    ("launch") of this process fails on the host; "off" disarms."""
-    kinds = {"off": 0, "alloc": S.FAULT_ALLOC, "launch": S.FAULT_LAUNCH}
+    ("launch") of this process fails on the host; "barrier": the after-th next
+    Longstaff-Schwartz sweep's first grid barrier waits until its bounded wait runs
+    out (SIMR_ETIMEOUT, the context stays usable); "off" disarms."""
+    kinds = {"off": 0, "alloc": S.FAULT_ALLOC, "launch": S.FAULT_LAUNCH, "barrier": S.FAULT_BARRIER}
     S.check(S.load().simr_inject_fault(kinds[what], int(after)))
 
 

@@ -827,8 +827,10 @@ int simr_inject_fault(int what, int after) {
     g_fault_what.store(0);
     return SIMR_OK;
   }
-  if ((what != SIMR_FAULT_ALLOC && what != SIMR_FAULT_LAUNCH) || after < 1 || after > (1 << 30))
-    return fail(SIMR_EINVAL, "simr_inject_fault: what must be 0, SIMR_FAULT_ALLOC or SIMR_FAULT_LAUNCH, after >= 1");
+  if ((what != SIMR_FAULT_ALLOC && what != SIMR_FAULT_LAUNCH && what != SIMR_FAULT_BARRIER) || after < 1 ||
+      after > (1 << 30))
+    return fail(SIMR_EINVAL,
+                "simr_inject_fault: what must be 0, SIMR_FAULT_ALLOC, SIMR_FAULT_LAUNCH or SIMR_FAULT_BARRIER, after >= 1");
   g_fault_what.store(0);
   g_fault_left.store(after);
   g_fault_what.store(what);
@@ -1693,6 +1695,7 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
                o.dev[0],
                o.dev[1]};
   if (o.dev[2]) e = cudaMemsetAsync(o.dev[2], 0xff, (size_t)n_ex * 6 * sizeof(double), st);
+  L.barrier_extra = take_fault(SIMR_FAULT_BARRIER) ? 1 : 0;
   if (e == cudaSuccess) e = take_fault(SIMR_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : launch_lsm(L, B, ctx->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "launching the Longstaff-Schwartz kernels");
   if (stop) {

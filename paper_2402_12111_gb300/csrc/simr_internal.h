@@ -215,6 +215,7 @@ struct LsmLaunch {
   double Kd, wd;       // strike and basis scale w in FP64 (coefficient conversion)
   int32_t scheme;      // 0: QE; 1: QE-M
   QemConst qm;
+  int32_t barrier_extra;  // 0; 1 (fault injection): the sweep's first grid barrier waits for a block too many
 };
 
 struct LsmBuffers {

@@ -545,8 +545,23 @@ __device__ void lsm_solve_df(const DF* tot, float* x_out, float* dx_out, int lan
 constexpr int kSweepTpb = 1024;
 constexpr int kSweepWarps = kSweepTpb / kWarp;
 static_assert(kNReg <= kSweepWarps, "one warp per regression quantity in the cross-block sum");
-constexpr unsigned kSpinLimit = 1u << 23;   // barrier polls (>= 32 ns apart after 2048): ~0.3 s, then the wait gives up
-constexpr unsigned kCopySpinLimit = 1u << 22;  // mbarrier polls for a bulk copy (>= 32 ns apart after 2048): ~0.2 s
+// Every wait of the sweep (grid barrier, bulk copy) gives up after kWaitLimitNs
+// of the GPU's global timer -- 25,000 times a date's whole time -- or, as a
+// backstop, after kSpinLimit polls.
+constexpr unsigned long long kWaitLimitNs = 250000000ull;
+constexpr unsigned kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Whether a wait that began at t0 and has polled `it` times should give up
+// (the timer read every 256 polls).
+__device__ __forceinline__ bool wait_expired(unsigned it, unsigned long long t0) {
+  return it > kSpinLimit || ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs);
+}
 
 // Bulk copies global -> shared memory by the TMA engine (cp.async.bulk, no
 // tensor map: contiguous 16-byte-aligned ranges), each completing its bytes on
@@ -570,9 +585,10 @@ __device__ __forceinline__ void bulk_copy_g2s(float* dst, const float* src, uint
 }
 
 // Waits for the phase of the given parity to complete (non-blocking polls,
-// backing off like the grid barrier); false after kCopySpinLimit polls.
+// backing off like the grid barrier); false once the wait has expired.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned it = 0; it < kCopySpinLimit; ++it) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -580,9 +596,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (done) return true;
+    if (wait_expired(it, t0)) return false;
     if (it > 2048) __nanosleep(32);
   }
-  return false;
 }
 
 struct LsmSweep {
@@ -593,24 +609,26 @@ struct LsmSweep {
 
 // Grid-wide barrier number `nb` (0, 1, ...) of the cooperative sweep: every block
 // adds one arrival to a counter that is never reset during the launch and waits
-// until it reaches (nb + 1) blocks -- the last block to arrive has nothing more
-// to do, so the barrier costs one atomic and the polls.  Bounded: a wait that
-// exceeds kSpinLimit polls sets status bit 1 and returns false, and every later
-// barrier returns false at once, so all blocks leave within one time-out.
-// `idle()` runs in every thread once the block has arrived, while thread 0 waits.
+// until it reaches (nb + 1) blocks (+ `extra`, 0 but under fault injection) --
+// the last block to arrive has nothing more to do, so the barrier costs one
+// atomic and the polls.  Bounded: a wait that expires sets status bit 1 and
+// returns false, and every later barrier returns false at once, so all blocks
+// leave within one time-out.  `idle()` runs in every thread once the block has
+// arrived, while thread 0 waits.
 template <class Idle>
-__device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, int* s_flag, Idle&& idle) {
+__device__ bool lsm_grid_sync(const LsmSweep& Y, unsigned nb, unsigned extra, int* s_flag, Idle&& idle) {
   __threadfence();
   __syncthreads();
   idle();
   if (threadIdx.x == 0) {
     int ok = (*(volatile int*)Y.status & 2) == 0;
     if (ok) {
-      const unsigned target = (nb + 1u) * gridDim.x;
+      const unsigned target = (nb + 1u) * gridDim.x + extra;
       atomicAdd(Y.count, 1u);
+      const unsigned long long t0 = global_ns();
       unsigned it = 0;
       while (*(volatile unsigned*)Y.count < target) {
-        if (++it > kSpinLimit) {
+        if (wait_expired(++it, t0)) {
           atomicOr(Y.status, 2);
           ok = 0;
           break;
@@ -865,7 +883,8 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     float2* rows = Y.rows + (size_t)(d & 1) * gridDim.x * kNReg;
     sweep_block_row(s_w, nv, s_quad, rows);
     // once every thread is past date d's rule, its buffer takes date d - 2
-    if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), &s_flag, [&] {
+    const unsigned extra = d == L.n_ex - 1 ? (unsigned)L.barrier_extra : 0u;
+    if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), extra, &s_flag, [&] {
           if (BULK && d >= 2) issue(d - 2);
         })) {
       drain();

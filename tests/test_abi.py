@@ -100,7 +100,9 @@ def test_fault_injection_hook_arguments(libpath):
     assert lib.simr_inject_fault(0, 0) == 0
     assert lib.simr_inject_fault(2, 1) == 0
     assert lib.simr_inject_fault(0, 0) == 0
-    assert lib.simr_inject_fault(3, 1) != 0
+    assert lib.simr_inject_fault(3, 1) == 0
+    assert lib.simr_inject_fault(0, 0) == 0
+    assert lib.simr_inject_fault(4, 1) != 0
     assert lib.simr_inject_fault(1, 0) != 0
 
 

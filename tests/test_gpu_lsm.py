@@ -233,3 +233,24 @@ def test_lsm_rejects_bad_arguments(simr):
         simr.lsm_price(BASE, -1.0, True, 64, 4, 1000, 1)
     with pytest.raises(simr.SimrError):
         simr.lsm_price(BASE, 100.0, True, 64, 4, 1, 1)      # one path
+
+
+def test_barrier_wait_runs_out_and_the_context_survives(simr):
+    # fault injection: the next sweep's first grid barrier waits for one block more
+    # than the grid holds, so its bounded wait runs out (0.25 s); the blocks leave,
+    # the status reports SIMR_ETIMEOUT, and the next valuation on the same context
+    # is the normal one
+    import time
+
+    args = (BASE, 100.0, True, 32, 2, 1 << 14, 3)
+    ref = simr.lsm_price(*args)[0].item()
+    simr.sync()
+    simr.inject_fault("barrier")
+    t0 = time.perf_counter()
+    simr.lsm_price(*args)
+    with pytest.raises(simr.SimrError) as e:
+        simr.sync()
+    assert e.value.code == -4, e.value
+    assert time.perf_counter() - t0 < 10.0
+    assert simr.lsm_price(*args)[0].item() == ref
+    simr.sync()  # the status word was cleared
