@@ -359,6 +359,11 @@ SIMR_API int simr_set_scheme(simr_ctx* ctx, int scheme);
  *   stop[paths] (nullable)       out  int32 exercise date per path, -1 = never
  * Outputs may be host or device pointers (host: the call synchronises).  The
  * context owns the per-path states (8 n_ex bytes per path) between calls.
+ * The backward induction runs as one cooperative launch where the GPU keeps
+ * enough blocks resident (otherwise one launch per date); its grid barriers and
+ * state copies are bounded waits (0.25 s): one that runs out invalidates the
+ * results and is reported as SIMR_ETIMEOUT by this call (host outputs) or the
+ * next simr_sync.
  */
 SIMR_API int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put, uint32_t steps,
                             uint32_t exercise_every, uint64_t paths, uint64_t seed, uint32_t option_index,
