@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-unit-rates", action="store_true",
+                    help="skip the measurement of the FP32 / MUFU / multiply / FP64 unit rates")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint vs bump-and-revalue leg")
     ap.add_argument("--no-book", action="store_true", help="skip the 1,024-option heterogeneous book leg")
     ap.add_argument("--no-lsm", action="store_true", help="skip the Longstaff-Schwartz Bermudan put leg")
@@ -732,6 +734,9 @@ def run_native(args):
     flops_step = flops_per_path_step(greeks)
     achieved_tflops = flops_step * path_steps / (ms * 1e-3) / 1e12  # per GPU, one launch per step
     sha = kernel_source_sha()
+    # the units' measured throughput on this GPU (after the timed legs): the derived
+    # FP32 peak above is the denominator, the measured packed-FMA rate its check
+    rates = None if args.no_unit_rates else simr.unit_rates(dev if isinstance(dev, int) else dev.index or 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -748,7 +753,9 @@ def run_native(args):
                      "flops_per_path_step": flops_step,
                      # the same kernel's FP32 (FMA) and MUFU pipe activity as ncu counts it, from the
                      # committed summary of this source (None if the sources changed since)
-                     "ncu_pipes": profiled_pipes(sha)},
+                     "ncu_pipes": profiled_pipes(sha),
+                     "measured_fp32_fma2_tflops": rates["fp32_fma2_tflops"] if rates else None,
+                     "frac_of_measured_fma2": achieved_tflops / rates["fp32_fma2_tflops"] if rates else None},
         "fp32_peak_frac": achieved_tflops / fp32_peak_tflops,
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -759,6 +766,7 @@ def run_native(args):
         "basket": basket,
         "headline": head,
         "lsm": lsm_leg,
+        "unit_rates": rates,
         "kernel_source_sha": sha,
         "wall_s_timed_region": t_wall,
     }

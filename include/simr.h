@@ -401,6 +401,22 @@ SIMR_API int simr_normals(simr_ctx* ctx, const uint32_t* words, uint64_t n, floa
                           void* stream);
 
 /*
+ * Measured throughput of the execution units the path kernels use -- the
+ * roofline's denominators on the GPU in use (no counterpart in the paper).
+ * Kernels that run one operation in long dependent chains (eight independent
+ * chains per thread, 2,048 threads per SM), timed with CUDA events on `stream`
+ * (which the call synchronises; about 0.1 s in all):
+ *   rates[0]  FP32 FMA, scalar fma.rn.f32            TFLOP/s (2 flops per FMA)
+ *   rates[1]  FP32 FMA, packed fma.rn.f32x2          TFLOP/s (4 flops per instruction)
+ *   rates[2]  special-function unit, rsqrt.approx    T operations/s
+ *   rates[3]  32 x 32 -> 64-bit multiply (mul.wide)  T operations/s (Philox's products)
+ *   rates[4]  FP64 FMA                               TFLOP/s
+ *   rates[5]  elapsed time of the whole measurement  ms
+ * rates: HOST array of 6 doubles.  SIMR_EINVAL for NULL or device pointers.
+ */
+SIMR_API int simr_unit_rates(simr_ctx* ctx, double* rates, void* stream);
+
+/*
  * Terminal state of paths [path_begin, path_begin + n_paths): x_T = ln(S_T/S0)
  * and v_T per path, FP32, the state the paper's writeLongstaffSchwartzPath stage
  * writes out (Sec. 5).  x_T[n_paths], v_T[n_paths] out; v_T may be NULL.

@@ -27,7 +27,7 @@ tensors or sequences give a synchronous call with host buffers.
 """
 from .api import (ADJOINT_COLUMNS, HestonAdjoint, adjoint_interval, basket_price, batch, finalize_sums,  # noqa: F401
                   greeks_adjoint, greeks_fd, heston_price, inject_fault, lsm_price, normals, path_sums,
-                  paths_adjoint, paths_terminal, philox_words, price, scheme, set_scheme, sync)
+                  paths_adjoint, paths_terminal, philox_words, price, scheme, set_scheme, sync, unit_rates)
 from ._simr import (G_ALL, G_CORR, G_DELTA, G_GAMMA, G_KAPPA, G_LRVAR, G_RHO, G_THETA, G_VEGA,  # noqa: F401
                     G_VOLVOL, GREEK_BITS, Heston, SimrError, greek_mask, load)
 

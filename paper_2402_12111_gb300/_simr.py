@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
         L.simr_price_noalloc.argtypes = [H, dp, c_int, c_int, u32, u64, u64, u32, dp, dp, vp]
         L.simr_philox_words.argtypes = [vp, u64, u32, u64, u64, u32, u32, dp, vp]
         L.simr_normals.argtypes = [vp, dp, u64, dp, dp, vp]
+        L.simr_unit_rates.argtypes = [vp, dp, vp]
         _lib = L
         return L
 

@@ -317,3 +317,15 @@ def normals(words: torch.Tensor, paired: bool = True, stream=None):
     ctx = S.context(_device_index(w, None))
     S.check(L.simr_normals(ctx, _ptr(w), w.numel(), _ptr(z), _ptr(zp), _stream(w, stream)))
     return z, zp
+
+
+UNIT_RATES = ("fp32_fma_tflops", "fp32_fma2_tflops", "mufu_rsqrt_tops", "mul_wide_tops", "fp64_fma_tflops", "ms")
+
+
+def unit_rates(device: int = 0, stream=None) -> dict:
+    """simr_unit_rates: the measured throughput of the units the path kernels use, keyed as UNIT_RATES."""
+    out = (ctypes.c_double * 6)()
+    L = S.load()
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    S.check(L.simr_unit_rates(S.context(device), out, ctypes.c_void_p(st.cuda_stream)))
+    return dict(zip(UNIT_RATES, list(out)))

@@ -1492,6 +1492,22 @@ int simr_normals(simr_ctx* ctx, const uint32_t* words, uint64_t n, float* z, flo
   return SIMR_OK;
 }
 
+int simr_unit_rates(simr_ctx* ctx, double* rates, void* stream) {
+  const NvtxRange nvtx("simr_unit_rates");
+  if (!ctx) return fail(SIMR_EINVAL, "context is NULL");
+  if (!rates) return fail(SIMR_EINVAL, "rates is NULL");
+  if (is_device_ptr(rates)) return fail(SIMR_EINVAL, "rates must be a host array");
+  int rc = with_device(ctx);
+  if (rc) return rc;
+  if ((rc = ensure(&ctx->dev_f32, &ctx->f32_cap, unit_rates_scratch_floats(ctx->num_sms), "unit-rate scratch")))
+    return rc;
+  cudaError_t e = take_fault(SIMR_FAULT_LAUNCH)
+                      ? cudaErrorLaunchOutOfResources
+                      : measure_unit_rates(ctx->num_sms, ctx->dev_f32, (cudaStream_t)stream, rates);
+  if (e != cudaSuccess) return cuda_fail(e, "measuring the unit rates");
+  return SIMR_OK;
+}
+
 int simr_basket_price(simr_ctx* ctx, const simr_heston* assets, int n_assets, const double* corr,
                       const double* weights, const double* strikes, int n_strikes, int is_put, uint32_t steps,
                       uint64_t paths, uint64_t seed, double* price, double* stderr_out, void* stream) {

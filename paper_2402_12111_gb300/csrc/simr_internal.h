@@ -240,6 +240,11 @@ struct LsmBuffers {
 cudaError_t launch_lsm(const LsmLaunch& L, const LsmBuffers& B, int num_sms, cudaStream_t stream);
 size_t lsm_partial_doubles(int num_sms);
 
+// simr_rates.cu: throughput of the FP32 FMA (scalar, packed), MUFU rsqrt,
+// 32 x 32 -> 64 multiply and FP64 FMA units, then the elapsed ms (rates[6]).
+cudaError_t measure_unit_rates(int num_sms, float* scratch, cudaStream_t st, double* rates);
+size_t unit_rates_scratch_floats(int num_sms);
+
 // Basket options on correlated assets (simr_basket.cu).
 constexpr int kMaxAssets = 16;
 
