@@ -1633,7 +1633,8 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
   if (!price) return fail(SIMR_EINVAL, "price is NULL");
   if ((rc = with_device(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t nS = (size_t)n_ex * paths;
+  const uint64_t pitch = (paths + 3) & ~3ull;  // 16-byte rows, so that the sweep's bulk copies start aligned
+  const size_t nS = (size_t)n_ex * pitch;
   if ((rc = ensure(&ctx->lsm_S, &ctx->lsm_S_cap, nS, "exercise-date spots"))) return rc;
   if ((rc = ensure(&ctx->lsm_V, &ctx->lsm_V_cap, nS, "exercise-date variances"))) return rc;
   if ((rc = ensure(&ctx->lsm_cash, &ctx->lsm_cash_cap, (size_t)paths, "cash flows"))) return rc;
@@ -1692,6 +1693,7 @@ int simr_lsm_price(simr_ctx* ctx, const simr_heston* model, double K, int is_put
   L.steps = steps;
   L.option_index = option_index;
   L.paths = paths;
+  L.pitch = pitch;
   L.disc0 = std::exp(-model->r * dt_ex);
   L.Kd = K;
   L.wd = w > 0.0 ? w : 1.0;

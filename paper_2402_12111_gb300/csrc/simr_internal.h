@@ -211,6 +211,7 @@ struct LsmLaunch {
   int32_t is_put, n_ex, every, min_itm;
   uint32_t steps, option_index;
   uint64_t paths;
+  uint64_t pitch;      // floats per date row of the states: paths rounded up to a multiple of 4 (16 bytes)
   double disc0;        // e^{-r t_0}
   double Kd, wd;       // strike and basis scale w in FP64 (coefficient conversion)
   int32_t scheme;      // 0: QE; 1: QE-M
@@ -219,8 +220,8 @@ struct LsmLaunch {
 };
 
 struct LsmBuffers {
-  float* S;            // [n_ex][paths]
-  float* V;            // [n_ex][paths]
+  float* S;            // [n_ex][pitch], the first `paths` of each row used
+  float* V;            // [n_ex][pitch]
   float* cash;         // [paths] payoff at the exercise date (0: never exercised)
   int32_t* stop;       // [paths] exercise date, -1 = never
   double* beta;        // [n_ex][6] in the basis (1, x, x^2, y, xy, y^2); NaN row = no regression

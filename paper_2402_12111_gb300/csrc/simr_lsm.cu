@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_paths_kernel(const __grid_constan
           V_out[row + idx[j]] = v[j];
         }
       }
-      row += L.paths;
+      row += L.pitch;
     };
     for (uint32_t p = 0; 2 * p < L.steps; ++p) {
       uint4 w[kLsmPpt];
@@ -321,10 +321,10 @@ __global__ void __launch_bounds__(kLsmTpb) lsm_date_kernel(const __grid_constant
   const int jr = j - 1;
   const float4 tj = B.xform[j];                   // update date
   const float4 tr = B.xform[REGRESS ? jr : j];    // regression date
-  const float* Sj = B.S + (size_t)j * P;
-  const float* Vj = B.V + (size_t)j * P;
-  const float* Sr = B.S + (size_t)(REGRESS ? jr : 0) * P;
-  const float* Vr = B.V + (size_t)(REGRESS ? jr : 0) * P;
+  const float* Sj = B.S + (size_t)j * L.pitch;
+  const float* Vj = B.V + (size_t)j * L.pitch;
+  const float* Sr = B.S + (size_t)(REGRESS ? jr : 0) * L.pitch;
+  const float* Vr = B.V + (size_t)(REGRESS ? jr : 0) * L.pitch;
   // two paths per iteration, all their loads issued before either is used
   const uint64_t gt = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P; i0 += 2 * gt) {
@@ -692,24 +692,22 @@ __device__ __forceinline__ void sweep_total(const float2* rows, int nv, DF* s_to
   __syncthreads();
 }
 
-// BULK (paths a multiple of 4, so that every block's range of a date starts on
-// 16 bytes): each date's states come into shared memory by bulk copies issued a
-// date ahead, into two buffers used in turn; otherwise by loads from L2 after a
-// prefetch a date ahead.
-template <int M, bool BULK>
+// Each date's states come into shared memory by bulk copies issued a date ahead,
+// into two buffers used in turn (every block's range of a date starts on 16
+// bytes: the rows' pitch is a multiple of 4 floats).
+template <int M>
 __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_constant__ LsmLaunch L,
                                                                  const LsmBuffers B, const LsmSweep Y) {
-  // dynamic shared memory, [M][thread] each: the states of a date (S, then v;
-  // BULK: two such buffers, date j in buffer j & 1) -- the regression of date j
-  // reads them, the rule of date j reads them again -- then the thread's paths'
-  // cash flows and exercise dates for the whole sweep (each thread its own
-  // slots), then the discount table (n_ex floats)
+  // dynamic shared memory, [M][thread] each: the states of a date (S, then v; two
+  // such buffers, date j in buffer j & 1) -- the regression of date j reads them,
+  // the rule of date j reads them again -- then the thread's paths' cash flows
+  // and exercise dates for the whole sweep (each thread its own slots), then the
+  // discount table (n_ex floats)
   extern __shared__ __align__(16) float s_keep[];
-  constexpr int kBufs = BULK ? 2 : 1;
-  float* s_c = s_keep + kBufs * 2 * M * kSweepTpb;
+  float* s_c = s_keep + 4 * M * kSweepTpb;
   int* s_st = reinterpret_cast<int*>(s_c + M * kSweepTpb);
   float* s_dpow = s_c + 2 * M * kSweepTpb;
-  auto states = [&](int j) { return s_keep + (BULK ? (j & 1) * 2 * M * kSweepTpb : 0); };
+  auto states = [&](int j) { return s_keep + (j & 1) * 2 * M * kSweepTpb; };
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ float s_w[kSweepWarps][kNReg];
   __shared__ DF s_quad[4 * kNReg];
@@ -731,30 +729,32 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     s_c[m * kSweepTpb + threadIdx.x] = i < P ? B.cash[i] : 0.0f;
     s_st[m * kSweepTpb + threadIdx.x] = i < P ? B.stop[i] : -1;
   }
-  // BULK: block's share of date j: for each m the paths m gt + blockIdx.x 1024 +
-  // [0, 1024), cut at P (a multiple of 4 floats since P is); the block's last
-  // thread issues the copies (thread 0 runs the grid barrier meanwhile)
+  // the block's share of date j: for each m the paths m gt + blockIdx.x 1024 +
+  // [0, 1024), cut at P rounded up to 4 floats (within the row's pitch; slots of
+  // paths >= P are never used); the block's last thread issues the copies
+  // (thread 0 runs the grid barrier meanwhile)
   // per buffer b (bit b, the same in every thread): the parity of its next phase,
   // and whether a copy into it is in flight
   uint32_t parity = 0u, pending = 0u;
   auto issue = [&](int j) {
     if (threadIdx.x == kSweepTpb - 1) {
       float* dst = states(j);
-      const float* Sg = B.S + (size_t)j * P;
-      const float* Vg = B.V + (size_t)j * P;
+      const float* Sg = B.S + (size_t)j * L.pitch;
+      const float* Vg = B.V + (size_t)j * L.pitch;
+      auto floats = [&](uint64_t a) -> uint32_t {  // the copy's length at path a (a multiple of 4)
+        const uint64_t n = a < P ? (P - a < kSweepTpb ? P - a : kSweepTpb) : 0;
+        return (uint32_t)((n + 3) & ~3ull);
+      };
       uint32_t total = 0;
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const uint64_t a = (uint64_t)m * gt + (uint64_t)blockIdx.x * kSweepTpb;
-        total += a < P ? 8u * (uint32_t)(P - a < kSweepTpb ? P - a : kSweepTpb) : 0u;
-      }
+      for (int m = 0; m < M; ++m) total += 8u * floats((uint64_t)m * gt + (uint64_t)blockIdx.x * kSweepTpb);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer before the copies
       mbar_arrive_expect(&s_bar[j & 1], total);
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const uint64_t a = (uint64_t)m * gt + (uint64_t)blockIdx.x * kSweepTpb;
         if (a < P) {
-          const uint32_t bytes = 4u * (uint32_t)(P - a < kSweepTpb ? P - a : kSweepTpb);
+          const uint32_t bytes = 4u * floats(a);
           bulk_copy_g2s(dst + m * kSweepTpb, Sg + a, bytes, &s_bar[j & 1]);
           bulk_copy_g2s(dst + (M + m) * kSweepTpb, Vg + a, bytes, &s_bar[j & 1]);
         }
@@ -764,20 +764,17 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
   };
   // before an early return: the copies still in flight land first (bounded)
   auto drain = [&]() {
-    if (BULK)
-      for (int b = 0; b < 2; ++b)
-        if ((pending >> b) & 1u) (void)mbar_wait(&s_bar[b], (parity >> b) & 1u);
+    for (int b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) (void)mbar_wait(&s_bar[b], (parity >> b) & 1u);
   };
   if (threadIdx.x == 0) {
     s_has = 0;
-    if (BULK) {
-      mbar_init(&s_bar[0]);
-      mbar_init(&s_bar[1]);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();  // (the barriers' initialisation before the last thread's first copies)
-  if (BULK && L.n_ex >= 2) issue(L.n_ex - 2);
+  if (L.n_ex >= 2) issue(L.n_ex - 2);
   float4 tj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // date d's basis scaling (loaded a date ahead)
   for (int d = L.n_ex - 1; d >= 0; --d) {
     const bool regress = d >= 1;
@@ -810,7 +807,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     for (int k = 0; k < kNReg; ++k) acc[k] = 0.0f;
     if (regress) {
       float Sn[M], Vn[M];
-      if constexpr (BULK) {  // date d - 1's copies, issued a date ago
+      {  // date d - 1's copies, issued a date ago
         const int b = (d - 1) & 1;
         const bool late = !mbar_wait(&s_bar[b], (parity >> b) & 1u);
         if (__syncthreads_or(late)) {  // the whole block leaves
@@ -825,32 +822,6 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
         for (int m = 0; m < M; ++m) {
           Sn[m] = sr[m * kSweepTpb + threadIdx.x];
           Vn[m] = sr[(M + m) * kSweepTpb + threadIdx.x];
-        }
-      } else {
-        const float* Sr = B.S + (size_t)(d - 1) * P;
-        const float* Vr = B.V + (size_t)(d - 1) * P;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {  // all loads first
-          const uint64_t i = g0 + (uint64_t)m * gt;
-          Sn[m] = i < P ? __ldcg(Sr + i) : 0.0f;
-          Vn[m] = i < P ? __ldcg(Vr + i) : 0.0f;
-        }
-#pragma unroll
-        for (int m = 0; m < M; ++m) {  // this thread's own slots: no barrier needed before the next date reads them
-          s_keep[m * kSweepTpb + threadIdx.x] = Sn[m];
-          s_keep[(M + m) * kSweepTpb + threadIdx.x] = Vn[m];
-        }
-      }
-      if (!BULK && d >= 2) {  // the date after next into L2 while this one is reduced and solved
-        const float* Sp = B.S + (size_t)(d - 2) * P;
-        const float* Vp = B.V + (size_t)(d - 2) * P;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const uint64_t i = g0 + (uint64_t)m * gt;
-          if (i < P) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(Sp + i));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(Vp + i));
-          }
         }
       }
 #pragma unroll
@@ -885,7 +856,7 @@ __global__ void __launch_bounds__(kSweepTpb, 1) lsm_sweep_kernel(const __grid_co
     // once every thread is past date d's rule, its buffer takes date d - 2
     const unsigned extra = d == L.n_ex - 1 ? (unsigned)L.barrier_extra : 0u;
     if (!lsm_grid_sync(Y, (unsigned)(L.n_ex - 1 - d), extra, &s_flag, [&] {
-          if (BULK && d >= 2) issue(d - 2);
+          if (d >= 2) issue(d - 2);
         })) {
       drain();
       return;
@@ -960,12 +931,12 @@ size_t lsm_partial_doubles(int num_sms) { return (size_t)num_sms * kLsmMaxBlocks
 
 namespace {
 
-template <int M, bool BULK>
-cudaError_t try_sweep_mb(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
-                         bool* used) {
-  // S and v (two buffers with BULK), cash flow, exercise date; the discount table
-  const size_t smem = ((size_t)(BULK ? 6 : 4) * M * kSweepTpb + (size_t)L.n_ex) * sizeof(float);
-  auto kern = lsm_sweep_kernel<M, BULK>;
+template <int M>
+cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
+                        bool* used) {
+  // S and v (two buffers), cash flow, exercise date; the discount table
+  const size_t smem = ((size_t)6 * M * kSweepTpb + (size_t)L.n_ex) * sizeof(float);
+  auto kern = lsm_sweep_kernel<M>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -985,14 +956,6 @@ cudaError_t try_sweep_mb(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kSweepTpb), args, smem, st);
   if (e == cudaSuccess) *used = true;
   return e;
-}
-
-template <int M>
-cudaError_t try_sweep_m(const LsmLaunch& L, const LsmBuffers& B, const LsmSweep& Y, int num_sms, cudaStream_t st,
-                        bool* used) {
-  // bulk copies need every block's range of a date on 16 bytes: P a multiple of 4
-  if (L.paths % 4 == 0) return try_sweep_mb<M, true>(L, B, Y, num_sms, st, used);
-  return try_sweep_mb<M, false>(L, B, Y, num_sms, st, used);
 }
 
 // The backward induction as one cooperative launch when the device supports it
