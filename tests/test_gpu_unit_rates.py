@@ -25,6 +25,7 @@ def test_unit_rates_are_plausible():
     assert 0.3 * fp32_cap < r["fp32_fma_tflops"] < 1.05 * fp32_cap, r
     assert 0.3 * fp32_cap < r["fp32_fma2_tflops"] < 1.05 * fp32_cap, r
     assert 0.3 * mufu_cap < r["mufu_rsqrt_tops"] < 1.05 * mufu_cap, r
-    assert r["mul_wide_tops"] < r["fp32_fma_tflops"], r  # a 64-bit product costs more than an FMA
-    assert r["fp64_fma_tflops"] < r["fp32_fma_tflops"], r
+    # a 64-bit product takes the FMA-heavy pipe longer than an FMA: fewer per second than FMAs (flops / 2)
+    assert r["mul_wide_tops"] < 0.5 * r["fp32_fma_tflops"], r
+    assert r["fp64_fma_tflops"] < 0.1 * r["fp32_fma_tflops"], r
     assert r["ms"] < 2000.0, r
