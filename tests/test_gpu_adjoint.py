@@ -162,6 +162,8 @@ CASES = [
     ("ckpt_beyond_steps", CFG, [100.0], True, 10, 4097, 4, 64, 1e-3, 0.0, 2e-3),
     ("hard_exp_branch", HARD, [90.0, 100.0, 110.0], False, 64, 16384, 5, 8, 5e-3, 0.08, 2.5, 1e-3),
     ("one_step", CFG, [100.0], False, 1, 2048, 6, 2, 1e-3, 0.0, 2e-3),
+    # the largest strike count the adjoint takes: 8 tiles of 32 strikes
+    ("strikes_256_max", CFG, np.linspace(60.0, 140.0, 256), False, 16, 65536, 14, 4, 1e-3, 0.0, 2e-3),
 ]
 
 # Parameter edges: vol-of-vol near the Black-Scholes limit (the constants divide

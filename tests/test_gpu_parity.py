@@ -109,6 +109,8 @@ PRICE_CASES = [
     ("one_step", CFG, [90.0, 100.0, 110.0], True, 1, 4097, 2),
     ("strikes_40", CFG, np.linspace(60, 140, 40), False, 16, 8192, 4),
     ("seed_hi_word", CFG, [100.0], False, 16, 8192, (0xABCDEF << 32) | 12345),
+    # the largest strike count simr_price takes: 32 tiles of 32 strikes
+    ("strikes_1024_max", CFG, np.linspace(50.0, 150.0, 1024), True, 16, 8192, 12),
 ]
 
 
@@ -186,6 +188,8 @@ GREEK_CASES = [
      ("delta", "gamma", "vega", "theta", "rho", "corr")),
     ("small_kappa", dict(CFG, kappa=1e-3), [90.0, 100.0, 110.0], True, 32, 1 << 15, 8,
      ("delta", "gamma", "vega", "theta", "rho", "lrvar")),
+    # the largest strike count the bump-and-revalue kernels take: 8 tiles of 32
+    ("strikes_256_max", CFG, np.linspace(60.0, 140.0, 256), False, 16, 1 << 14, 13, ("delta", "gamma", "vega", "rho")),
 ]
 
 ORACLE_BITS = {"delta": oracle.G_DELTA, "gamma": oracle.G_GAMMA, "vega": oracle.G_VEGA, "theta": oracle.G_THETA,
@@ -252,6 +256,13 @@ def test_invalid_sizes_rejected(simr):
         simr.price(CFG, [100.0, -5.0], False, 8, 100, 1)        # host strike checked on the host
     with pytest.raises(simr.SimrError):
         simr.greeks_fd(CFG, [100.0], False, 8, 100, 1, greeks=0)
+    # one strike past each entry point's maximum
+    for call, n in ((lambda K: simr.price(CFG, K, False, 8, 100, 1), 1025),
+                    (lambda K: simr.greeks_fd(CFG, K, False, 8, 100, 1), 257),
+                    (lambda K: simr.greeks_adjoint(CFG, K, False, 8, 100, 1), 257)):
+        with pytest.raises(simr.SimrError) as e:
+            call(_dev(np.full(n, 100.0)))
+        assert e.value.code == -1
 
 
 def test_device_strike_error_reported_by_sync(simr):
