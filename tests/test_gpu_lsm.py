@@ -169,10 +169,11 @@ def test_lsm_full_size_properties(simr):
     assert agree > 0.995, agree
 
 
-def _perturbed_oracle_spread(model, K, is_put, steps, every, paths, seed, n=3):
+def _perturbed_oracle_spread(model, K, is_put, steps, every, paths, seed, n=3, eps=1e-7):
     """The oracle's own sensitivity: its price and exercise dates with S and v
-    perturbed by 1e-7 relative (the size of the FP32 path error), n draws.
-    Returns (max |price change|, max fraction of paths whose date changed)."""
+    perturbed by eps relative (the size of the FP32 path error), n draws.
+    Returns (the unperturbed result, max |price change|, max fraction of paths
+    whose date changed)."""
     base = olsm.lsm(model, K, is_put, steps, every, paths, seed)
     orig = olsm.states
     dp, ds = 0.0, 0.0
@@ -181,7 +182,7 @@ def _perturbed_oracle_spread(model, K, is_put, steps, every, paths, seed, n=3):
 
         def noisy(*a, **kw):
             S, v = orig(*a, **kw)
-            return S * (1 + 1e-7 * rng.standard_normal(S.shape)), v * (1 + 1e-7 * rng.standard_normal(v.shape))
+            return S * (1 + eps * rng.standard_normal(S.shape)), v * (1 + eps * rng.standard_normal(v.shape))
 
         olsm.states = noisy
         try:
@@ -224,6 +225,28 @@ def test_cooperative_sweep_and_per_date_launches_agree(simr, paths, monkeypatch)
         assert np.mean(sa != sb) <= 2e-2
     ba, bb = a[2].cpu().numpy(), b[2].cpu().numpy()
     np.testing.assert_array_equal(np.isnan(ba), np.isnan(bb))
+
+
+def test_lsm_at_the_maximum_date_count(simr, monkeypatch):
+    # 8,192 exercise dates (the limit): the sweep's discount table fills 32 KB of
+    # shared memory and its grid barrier runs 8,192 times.  With dates this close
+    # most paths stay near the exercise boundary for many dates, and the estimator
+    # is chaotic at the FP32 path error (3e-8 sqrt(N) relative after N steps): the
+    # oracle itself, its states perturbed that much, moves the exercise date of
+    # about a third of the paths (measured 0.33-0.36) and the price by up to 0.07.
+    # The GPU must stay within that spread, and the sweep agree with the per-date
+    # launches.
+    args = (dict(BASE, T=2.0), 100.0, True, 8192, 1, 2048, 15)
+    ref, dp, ds = _perturbed_oracle_spread(*args, eps=3e-8 * math.sqrt(8192))
+    p, se, _, stop = simr.lsm_price(*args, with_stop=True)
+    assert abs(p.item() - ref.price) <= 2 * dp + 1e-5 * ref.price, (p.item(), ref.price, dp)
+    assert abs(p.item() - ref.price) <= 0.5 * se.item()
+    assert np.mean(stop.cpu().numpy() != ref.stop) <= 1.5 * ds + 0.02, ds
+    monkeypatch.setenv("SIMR_LSM_SWEEP", "0")
+    q = simr.lsm_price(*args)[0].item()
+    assert q == pytest.approx(p.item(), rel=1e-6)
+    with pytest.raises(simr.SimrError):
+        simr.lsm_price(BASE, 100.0, True, 8193, 1, 2048, 15)  # one date past it
 
 
 def test_lsm_rejects_bad_arguments(simr):
