@@ -139,6 +139,9 @@ C_MISTAKES = [
      lambda: pins.test_flipped_decision_gradient_matches_finite_differences("qem")),
     ("adjoint_drops_rate_discount", "grad[j * 7 + 6] -= m->T * price[j];", "",
      pins.test_adjoint_matches_fd_and_closed_form_delta),
+    # QE-M at a zero mean (v = theta = 0): M = 1 exists; taking the plain step instead
+    ("qem_zero_mean_takes_plain_step", "  if (m <= 0.0) return 0.0;", "  if (m <= 0.0) { *ok = 0; return 0.0; }",
+     lambda: pins.test_adjoint_at_zero_variance_in_closed_form("qem")),
     # QE-M martingale correction
     ("qem_quadratic_log_sign", "- 0.5 * log(1.0 - 2.0 * A * a);", "+ 0.5 * log(1.0 - 2.0 * A * a);",
      lambda: qem_pins.test_one_step_expectation_is_a_martingale(qem_pins.BASE)),
