@@ -115,3 +115,13 @@ def test_profile_provenance_is_parsed_by_source_hash():
     assert bench.profiled_adjoint_k32_traffic("0" * 16) is None
     t = bench.profiled_traffic(bench.kernel_source_sha())
     assert t is None or t > 0
+
+
+def test_committed_profiles_were_taken_on_the_current_kernel_sources():
+    # the bench-step and adjoint summaries under profiles/ name the hashes of the
+    # sources they were captured on; a change to those sources (comments aside)
+    # needs a new capture, else the bench line's roofline.traffic goes null
+    import bench
+
+    assert bench.profiled_traffic(bench.kernel_source_sha()) is not None, "re-capture the bench-step profile"
+    assert bench.profiled_adjoint_k32_traffic(bench.adjoint_source_sha()) is not None, "re-capture the adjoint profile"
